@@ -1,0 +1,172 @@
+/*
+ * vd.h -- C ABI of libvd: the exact Voronoi RayCast, the exhaustive vertex
+ * traversal and the Monte Carlo cell integrals with their adjoint, after
+ * Sikorski & Heida, "Voronoi Graph: improved raycasting and integration
+ * schemes for high dimensional Voronoi diagrams" (arXiv 2405.10050).
+ * Everything runs on one CUDA GPU (sm_103a).
+ *
+ * Conventions used by every entry point
+ *  - Nodes X: N x d float64, row-major, 1 <= d <= 16, N >= 1.
+ *  - Generator ids: nodes 0..N-1; the 2d faces of the unit box [0,1]^d are
+ *    pseudo-generators with negative ids -(2a+s+1) for axis a, side s
+ *    (s = 0: x_a = 0, s = 1: x_a = 1).  VD_NO_ID (INT32_MIN) means "none".
+ *  - Pointers: the trailing `on_device` argument says whether the array
+ *    arguments of that call are device pointers (1) or host pointers (0).
+ *    Host pointers are copied on the context's stream and the call returns
+ *    after the copies finish.  Device pointers must stay valid until the
+ *    call returns (every call synchronises its stream before returning).
+ *  - Ownership: the caller owns every array it passes; library objects
+ *    (vd_ctx, vd_mesh, vd_mc) are owned by the library until their free call.
+ *  - Errors: every call returns a vd_status and throws nothing across the
+ *    ABI; vd_last_error() gives a message for the last failure on a context.
+ *  - Floating point: the exact path (VD_FP64) and the recheck of the mixed
+ *    paths evaluate t in binary64 in one canonical operation order, so hit
+ *    ids are identical across precisions and against an FP64 reference that
+ *    follows the same order.
+ */
+#ifndef VD_H
+#define VD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VD_NO_ID INT32_MIN
+#define VD_MAX_D 16
+
+typedef enum {
+  VD_OK = 0,
+  VD_EINVAL = -1,      /* bad argument (size, dimension, pointer, state)   */
+  VD_ENOMEM = -2,      /* device or host allocation failed                 */
+  VD_ECUDA = -3,       /* a CUDA runtime call failed                       */
+  VD_EDEGENERATE = -4, /* duplicate nodes or a degenerate solve            */
+  VD_EHASHFULL = -5,   /* traversal hash or vertex table capacity reached  */
+  VD_EOVERFLOW = -6,   /* a bounded work list overflowed                   */
+  VD_ETIMEOUT = -7     /* a bounded device-side wait gave up               */
+} vd_status;
+
+typedef enum {
+  VD_FP64 = 0,  /* every (ray, node) pair in binary64                      */
+  VD_FP32 = 1,  /* binary32 screening with a proven error margin, binary64
+                   recheck of the survivors                                */
+  VD_BF16 = 2,  /* tensor-core bf16 screening, binary64 recheck            */
+  VD_AUTO = 3   /* the library's autotuner picks among the above           */
+} vd_precision;
+
+typedef struct {
+  int32_t precision;      /* vd_precision, default VD_AUTO                  */
+  int32_t box;            /* 1: clip cells to [0,1]^d (required by vertices
+                             and MC); 0: unbounded rays may miss           */
+  int64_t hash_capacity;  /* traversal vertex table entries, 0 = automatic */
+  int64_t max_levels;     /* traversal BFS level cap, 0 = automatic        */
+  int64_t wait_limit;     /* spin iterations before a device wait gives up */
+  int32_t tile_n;         /* node tile size hint, 0 = automatic            */
+  int32_t rays_per_block; /* MC rays per thread block, 0 = autotune        */
+} vd_config;
+
+typedef struct {
+  int64_t rays;            /* rays cast by the last call                    */
+  int64_t tiles_visited;   /* node tiles evaluated (all rays)               */
+  int64_t pairs_screened;  /* (ray, node) pairs evaluated                   */
+  int64_t rechecked;       /* candidates recomputed in binary64             */
+  int64_t fallback_rays;   /* MC rays finished by the generic tree search   */
+  int64_t overflow_rays;   /* rays recomputed on the plain FP64 path        */
+  int64_t ties;            /* exact binary64 ties seen (degenerate input)   */
+  int64_t levels;          /* traversal BFS levels                          */
+  int64_t vertices;        /* traversal vertices                            */
+  double ms;               /* device time of the last call, milliseconds   */
+} vd_stats;
+
+typedef struct vd_ctx vd_ctx;
+typedef struct vd_mesh vd_mesh;
+typedef struct vd_mc vd_mc;
+
+/* Fills *cfg with the defaults (VD_AUTO, box on, automatic capacities). */
+void vd_config_default(vd_config* cfg);
+
+/* Creates a context on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (NULL = the legacy default stream); every kernel and copy of
+ * the context runs on it.  cfg may be NULL (defaults). */
+vd_status vd_create(vd_ctx** ctx, const vd_config* cfg, void* cuda_stream);
+void vd_destroy(vd_ctx* ctx);
+const char* vd_last_error(const vd_ctx* ctx);
+const char* vd_status_str(vd_status s);
+vd_status vd_set_precision(vd_ctx* ctx, int32_t precision);
+vd_status vd_last_stats(const vd_ctx* ctx, vd_stats* out);
+
+/* Node set (Section 2.1: nodes X in general position).  Copies X and builds
+ * the Morton-ordered node tiles with their bounding-box hierarchy; the
+ * previous node set of the context is released.  EINVAL for N < 1,
+ * d outside 1..16, or a non-finite coordinate. */
+vd_status vd_set_nodes(vd_ctx* ctx, const double* X, int64_t N, int32_t d, int32_t on_device);
+
+/* RayCast (Section 2.2, Eq. (t), Algorithm 1), R rays.  Ray r starts at
+ * origins[r*d..] with unit direction dirs[r*d..]; eta[r*eta_stride..] lists
+ * the generators the ray starts equidistant to (they are never returned),
+ * padded with VD_NO_ID; eta[r*eta_stride] must be a node, the reference
+ * generator g.  Result: the first generator j whose bisector with g the ray
+ * crosses, t_j = (|x_j - v|^2 - |g - v|^2) / (2 u.(x_j - g)) minimal over
+ * u.(x_j - g) > 0, or the first box face (box on); ties by (t, node before
+ * face, id).  hit[r] = VD_NO_ID and t[r] = +inf if nothing is hit.
+ * screen_err (nullable): per ray |t_screen - t| / t, the binary32 screening
+ * estimate against the binary64 result (0 on the VD_FP64 path). */
+vd_status vd_raycast(vd_ctx* ctx, const double* origins, const double* dirs, const int32_t* eta,
+                     int32_t eta_stride, int64_t R, int32_t* hit, double* t, float* screen_err,
+                     int32_t on_device);
+
+/* Exhaustive vertex traversal (Section 2.3, Algorithm 2) of the diagram
+ * clipped to [0,1]^d: seeds by Descent, then casts one ray along every edge
+ * whose second vertex is still unknown, deduplicating vertices by their sorted
+ * (d+1)-generator tuple.  Box must be on.  EHASHFULL if the vertex table
+ * capacity is reached. */
+vd_status vd_vertices(vd_ctx* ctx, vd_mesh** out);
+int64_t vd_mesh_count(const vd_mesh* mesh);
+int32_t vd_mesh_dim(const vd_mesh* mesh);
+/* tuples: V x (d+1) int32, each row ascending, rows in lexicographic order;
+ * coords: V x d float64 (solved from the tuple).  Either may be NULL. */
+vd_status vd_mesh_copy(const vd_mesh* mesh, int32_t* tuples, double* coords, int32_t on_device);
+vd_status vd_mesh_stats(const vd_mesh* mesh, vd_stats* out);
+void vd_mesh_free(vd_mesh* mesh);
+
+/* Monte Carlo volumes and interface areas (Section 3.1, Algorithm 3) of all
+ * N cells with R rays per cell.  Ray k of cell i has the direction drawn by
+ * vd_mc_directions (Philox4x32-10 keyed by seed) and is cast from x_i with
+ * eta = {i}; l_k = t*.  V_i = S_{d-1}/(dR) sum_k l_k^d and
+ * A_ij = S_{d-1}/R sum_{k: hit j} l_k^{d-1} / |n_ij . u_k|.  The per-ray
+ * (hit, l) are kept for the adjoint.  Box must be on. */
+vd_status vd_mc_integrate(vd_ctx* ctx, int64_t rays_per_cell, uint64_t seed, vd_mc** out);
+/* V: N float64.  Row i of the CSR (rowptr N+1 int64, col/A nnz) lists the
+ * distinct generators hit from cell i in ascending id order (faces first).
+ * *nnz is always written; rowptr/col/A may be NULL to query nnz. */
+vd_status vd_mc_get(const vd_mc* mc, double* V, int64_t* nnz, int64_t* rowptr, int32_t* col, double* A,
+                    int32_t on_device);
+/* Saved per-ray results: hit N*R int32 and l N*R float64, ray (i,k) at i*R+k. */
+vd_status vd_mc_rays(const vd_mc* mc, int32_t* hit, double* l, int32_t on_device);
+/* Adjoint of the estimator with directions and argmins held fixed:
+ * gX = sum_i gV_i dV_i/dX + sum_ij gA_ij dA_ij/dX (N x d float64). */
+vd_status vd_mc_adjoint(const vd_mc* mc, const double* gV, const double* gA, double* gX, int32_t on_device);
+vd_status vd_mc_stats(const vd_mc* mc, vd_stats* out);
+int64_t vd_mc_count(const vd_mc* mc);
+void vd_mc_free(vd_mc* mc);
+
+/* The directions of rays 0..R-1 of cells cell0..cell0+ncells-1 of point set
+ * `set` in dimension d (Section 3.1: a normalised Gaussian draw): out is
+ * ncells x R x d float64.  The draw is Philox4x32-10 (Salmon et al. 2011),
+ * counter (block, ray, cell, set), key (seed low, seed high); binary32
+ * Box-Muller from series-defined log/sin/cos, binary64 normalisation. */
+vd_status vd_mc_directions(vd_ctx* ctx, uint64_t seed, uint32_t set, int64_t cell0, int64_t ncells,
+                           int64_t R, int32_t d, double* out, int32_t on_device);
+
+/* Batched MC: nsets independent node sets (X[s]: N[s] x d[s], host or
+ * device per on_device) in one persistent launch; out[s] receives one
+ * vd_mc per set, set s drawing its rays with set id s. */
+vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const* X, const int64_t* N,
+                                const int32_t* d, int64_t rays_per_cell, uint64_t seed, vd_mc** out,
+                                int32_t on_device);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VD_H */

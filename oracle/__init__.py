@@ -47,7 +47,7 @@ def lib():
         L.or_log32_batch.argtypes = [P, P, i64]
         L.or_sincos2pi24_batch.argtypes = [P, P, P, i64]
         L.or_philox_batch.argtypes = [P, P, P, i64]
-        L.or_mc_directions.argtypes = [u64, u32, i64, i64, i32, P]
+        L.or_mc_directions.argtypes = [u64, u32, i64, i64, i64, i32, P]
         L.or_mc_gaussians32.argtypes = [u64, u32, i64, i64, i32, P]
         L.or_raycast.argtypes = [P, i64, i32, i32, P, P, P, i32, i64, P, P]
         L.or_mc_rays.argtypes = [P, i64, i32, i64, u64, u32, P, P]
@@ -112,9 +112,9 @@ def sincos2pi24(a: np.ndarray):
     return c, s
 
 
-def mc_directions(seed: int, set_id: int, N: int, R: int, d: int) -> np.ndarray:
+def mc_directions(seed: int, set_id: int, N: int, R: int, d: int, cell0: int = 0) -> np.ndarray:
     out = np.empty((N, R, d), np.float64)
-    lib().or_mc_directions(seed, set_id, N, R, d, _p(out))
+    lib().or_mc_directions(seed, set_id, cell0, N, R, d, _p(out))
     return out
 
 

@@ -884,10 +884,11 @@ void or_philox_batch(const uint32_t* ctr, const uint32_t* key, uint32_t* out, in
 }
 
 /* directions of rays k = 0..R-1 of cells 0..N-1: out[(i*R+k)*d + a] */
-void or_mc_directions(uint64_t seed, uint32_t set, int64_t N, int64_t R, int d, double* out) {
+void or_mc_directions(uint64_t seed, uint32_t set, int64_t cell0, int64_t N, int64_t R, int d, double* out) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < N; ++i)
-    for (int64_t k = 0; k < R; ++k) or_mc_direction(seed, set, (uint32_t)i, (uint32_t)k, d, out + (i * R + k) * d);
+    for (int64_t k = 0; k < R; ++k)
+      or_mc_direction(seed, set, (uint32_t)(cell0 + i), (uint32_t)k, d, out + (i * R + k) * d);
 }
 
 void or_mc_gaussians32(uint64_t seed, uint32_t set, int64_t N, int64_t R, int d, float* out) {

@@ -1,0 +1,575 @@
+// vd_api.cu -- the extern "C" entry points of libvd (include/vd.h): argument
+// checks, host/device staging, object lifetimes and launch sequencing.  All
+// arithmetic of the method runs in the kernels of the other files.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "vd_dev.cuh"
+
+namespace vd {
+cudaError_t mc_rowptr(const int32_t* hit, int64_t N, int64_t R, int64_t* cnt_scratch, int64_t* rowptr,
+                      int64_t* nnz_host, cudaStream_t st);
+cudaError_t mc_fill(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set, const int32_t* hit,
+                    const double* l, const int64_t* rowptr, double* V, int32_t* col, double* A, cudaStream_t st);
+cudaError_t mc_adjoint(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
+                       const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, int64_t nnz,
+                       const double* gV, const double* gA, double* gX, DevBufs& scratch, cudaStream_t st);
+cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, DevBufs& out_bufs,
+                              int32_t** tuples, double** coords, int64_t* nv, vd_stats* stats, Counters* ctr,
+                              cudaStream_t st, char* err, size_t errlen);
+}  // namespace vd
+
+using vd::Counters;
+using vd::DevBufs;
+using vd::TreeView;
+
+struct vd_ctx {
+  vd_config cfg;
+  cudaStream_t st = nullptr;
+  char err[512] = {0};
+  vd_stats last{};
+  DevBufs node_bufs;
+  TreeView tree;
+  double* X = nullptr;
+  int64_t N = 0;
+  int d = 0;
+  Counters* ctr = nullptr;  // device
+  DevBufs own;
+};
+
+struct vd_mesh {
+  cudaStream_t st = nullptr;
+  int d = 0;
+  int64_t nv = 0;
+  DevBufs bufs;
+  int32_t* tuples = nullptr;  // device, sorted rows, lexicographic order
+  double* coords = nullptr;
+  vd_stats stats{};
+};
+
+struct vd_mc {
+  cudaStream_t st = nullptr;
+  int64_t N = 0, R = 0, nnz = 0;
+  int d = 0;
+  uint64_t seed = 0;
+  uint32_t set = 0;
+  DevBufs bufs;
+  double* X = nullptr;
+  int32_t* hit = nullptr;
+  double* l = nullptr;
+  double* V = nullptr;
+  int64_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* A = nullptr;
+  vd_stats stats{};
+};
+
+namespace {
+
+vd_status set_err(vd_ctx* c, vd_status s, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return s;
+}
+
+vd_status cuda_err(vd_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation)
+    return set_err(c, VD_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
+  return set_err(c, VD_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define VD_CK(call, where)                                \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_err(ctx, e_, where); \
+  } while (0)
+
+// Stages an input array on the device (copy for host memory).
+template <class T>
+vd_status stage_in(vd_ctx* ctx, DevBufs& tmp, const T* src, size_t n, int on_device, const T** out) {
+  if (on_device || n == 0) {
+    *out = src;
+    return VD_OK;
+  }
+  T* p = nullptr;
+  VD_CK(tmp.alloc_n(&p, n), "stage_in alloc");
+  VD_CK(cudaMemcpyAsync(p, src, n * sizeof(T), cudaMemcpyHostToDevice, ctx->st), "stage_in copy");
+  *out = p;
+  return VD_OK;
+}
+
+struct Timer {
+  cudaEvent_t a{}, b{};
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  double stop() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+vd_status read_counters(vd_ctx* ctx, Counters* hc) {
+  VD_CK(cudaMemcpyAsync(hc, ctx->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->st), "counters");
+  VD_CK(cudaStreamSynchronize(ctx->st), "sync");
+  return VD_OK;
+}
+
+vd_status check_flags(vd_ctx* ctx, const Counters& hc) {
+  if (hc.flags & vd::kFlagBadInput)
+    return set_err(ctx, VD_EINVAL, "a ray's first eta entry (its reference generator g) is not a node id");
+  if (hc.flags & vd::kFlagHashFull) return set_err(ctx, VD_EHASHFULL, "device table capacity reached");
+  if (hc.flags & vd::kFlagTimeout) return set_err(ctx, VD_ETIMEOUT, "bounded device wait gave up");
+  if (hc.flags & (vd::kFlagCandOverflow | vd::kFlagQueue | vd::kFlagStack))
+    return set_err(ctx, VD_EOVERFLOW, "device work list overflow (flags 0x%x)", hc.flags);
+  if (hc.flags & vd::kFlagDegenerate) return set_err(ctx, VD_EDEGENERATE, "degenerate configuration");
+  return VD_OK;
+}
+
+int effective_precision(const vd_ctx* ctx) {
+  const int p = ctx->cfg.precision;
+  if (p == VD_FP64) return VD_FP64;
+  return VD_FP32;  // VD_FP32, VD_AUTO and (until the tensor path is selected) VD_BF16
+}
+
+}  // namespace
+
+extern "C" {
+
+void vd_config_default(vd_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->precision = VD_AUTO;
+  cfg->box = 1;
+  cfg->wait_limit = 1 << 22;
+}
+
+const char* vd_status_str(vd_status s) {
+  switch (s) {
+    case VD_OK: return "ok";
+    case VD_EINVAL: return "invalid argument";
+    case VD_ENOMEM: return "out of memory";
+    case VD_ECUDA: return "CUDA error";
+    case VD_EDEGENERATE: return "degenerate input";
+    case VD_EHASHFULL: return "hash table full";
+    case VD_EOVERFLOW: return "work list overflow";
+    case VD_ETIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+vd_status vd_create(vd_ctx** out, const vd_config* cfg, void* stream) {
+  if (!out) return VD_EINVAL;
+  *out = nullptr;
+  vd_ctx* ctx = new (std::nothrow) vd_ctx();
+  if (!ctx) return VD_ENOMEM;
+  if (cfg) ctx->cfg = *cfg;
+  else vd_config_default(&ctx->cfg);
+  if (ctx->cfg.precision < VD_FP64 || ctx->cfg.precision > VD_AUTO) {
+    delete ctx;
+    return VD_EINVAL;
+  }
+  ctx->st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = ctx->own.alloc_n(&ctx->ctr, 1);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return e == cudaErrorMemoryAllocation ? VD_ENOMEM : VD_ECUDA;
+  }
+  *out = ctx;
+  return VD_OK;
+}
+
+void vd_destroy(vd_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->st);
+  ctx->node_bufs.release();
+  ctx->own.release();
+  delete ctx;
+}
+
+const char* vd_last_error(const vd_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+vd_status vd_set_precision(vd_ctx* ctx, int32_t precision) {
+  if (!ctx || precision < VD_FP64 || precision > VD_AUTO) return VD_EINVAL;
+  ctx->cfg.precision = precision;
+  return VD_OK;
+}
+
+vd_status vd_last_stats(const vd_ctx* ctx, vd_stats* out) {
+  if (!ctx || !out) return VD_EINVAL;
+  *out = ctx->last;
+  return VD_OK;
+}
+
+vd_status vd_set_nodes(vd_ctx* ctx, const double* X, int64_t N, int32_t d, int32_t on_device) {
+  if (!ctx) return VD_EINVAL;
+  if (!X || N < 1 || d < 1 || d > VD_MAX_D || N > (int64_t)1 << 30)
+    return set_err(ctx, VD_EINVAL, "vd_set_nodes: need X, 1 <= N <= 2^30, 1 <= d <= 16 (N=%lld d=%d)",
+                   (long long)N, d);
+  VD_CK(cudaStreamSynchronize(ctx->st), "sync");
+  ctx->node_bufs.release();
+  ctx->X = nullptr;
+  ctx->N = 0;
+  ctx->d = 0;
+  double* Xd = nullptr;
+  VD_CK(ctx->node_bufs.alloc_n(&Xd, (size_t)N * d), "nodes alloc");
+  VD_CK(cudaMemcpyAsync(Xd, X, (size_t)N * d * sizeof(double),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->st),
+        "nodes copy");
+  TreeView tv;
+  cudaError_t e = vd::build_tree(Xd, N, d, ctx->st, ctx->node_bufs, &tv);
+  if (e == cudaErrorInvalidValue) {
+    ctx->node_bufs.release();
+    return set_err(ctx, VD_EINVAL, "vd_set_nodes: non-finite coordinate");
+  }
+  if (e != cudaSuccess) {
+    ctx->node_bufs.release();
+    return cuda_err(ctx, e, "build_tree");
+  }
+  ctx->tree = tv;
+  ctx->X = Xd;
+  ctx->N = N;
+  ctx->d = d;
+  return VD_OK;
+}
+
+vd_status vd_raycast(vd_ctx* ctx, const double* origins, const double* dirs, const int32_t* eta, int32_t eta_stride,
+                     int64_t R, int32_t* hit, double* t, float* screen_err, int32_t on_device) {
+  if (!ctx) return VD_EINVAL;
+  if (!ctx->X) return set_err(ctx, VD_EINVAL, "vd_raycast: no node set");
+  if (R < 0 || (R > 0 && (!origins || !dirs || !eta || !hit || !t)) || eta_stride < 1 ||
+      eta_stride > ctx->d + 1)
+    return set_err(ctx, VD_EINVAL, "vd_raycast: bad arguments (R=%lld, eta_stride=%d, d=%d)", (long long)R,
+                   eta_stride, ctx->d);
+  ctx->last = vd_stats{};
+  if (R == 0) return VD_OK;
+  const int d = ctx->d;
+  DevBufs tmp;
+  struct Guard {
+    DevBufs& b;
+    ~Guard() { b.release(); }
+  } guard{tmp};
+  const double *o_d, *u_d;
+  const int32_t* e_d;
+  vd_status s;
+  if ((s = stage_in(ctx, tmp, origins, (size_t)R * d, on_device, &o_d)) != VD_OK) return s;
+  if ((s = stage_in(ctx, tmp, dirs, (size_t)R * d, on_device, &u_d)) != VD_OK) return s;
+  if ((s = stage_in(ctx, tmp, eta, (size_t)R * eta_stride, on_device, &e_d)) != VD_OK) return s;
+  int32_t* h_d = hit;
+  double* t_d = t;
+  float* se_d = screen_err;
+  if (!on_device) {
+    VD_CK(tmp.alloc_n(&h_d, R), "alloc");
+    VD_CK(tmp.alloc_n(&t_d, R), "alloc");
+    if (screen_err) VD_CK(tmp.alloc_n(&se_d, R), "alloc");
+  }
+  int32_t* ovl = nullptr;
+  const int64_t ovcap = std::max<int64_t>(1024, R / 16);
+  VD_CK(tmp.alloc_n(&ovl, ovcap), "alloc");
+  // eta rows must start with a node
+  vd::RaySource rs;
+  rs.mode = 0;
+  rs.R = R;
+  rs.origins = o_d;
+  rs.dirs = u_d;
+  rs.eta = e_d;
+  rs.eta_stride = eta_stride;
+  rs.box = ctx->cfg.box;
+  vd::RayOut ro;
+  ro.hit = h_d;
+  ro.t = t_d;
+  ro.screen_err = se_d;
+  ro.overflow_list = ovl;
+  ro.overflow_cap = ovcap;
+  VD_CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->st), "memset");
+  Timer tm(ctx->st);
+  VD_CK(vd::launch_raycast(ctx->tree, rs, ro, effective_precision(ctx), ctx->ctr, ctx->st), "raycast");
+  ctx->last.ms = tm.stop();
+  if (!on_device) {
+    VD_CK(cudaMemcpyAsync(hit, h_d, R * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->st), "copy out");
+    VD_CK(cudaMemcpyAsync(t, t_d, R * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "copy out");
+    if (screen_err) VD_CK(cudaMemcpyAsync(screen_err, se_d, R * sizeof(float), cudaMemcpyDeviceToHost, ctx->st), "copy out");
+  }
+  Counters hc;
+  if ((s = read_counters(ctx, &hc)) != VD_OK) return s;
+  ctx->last.rays = R;
+  ctx->last.tiles_visited = (int64_t)hc.tiles;
+  ctx->last.pairs_screened = (int64_t)hc.pairs;
+  ctx->last.rechecked = (int64_t)hc.rechecked;
+  ctx->last.overflow_rays = (int64_t)hc.overflow;
+  return check_flags(ctx, hc);
+}
+
+vd_status vd_mc_directions(vd_ctx* ctx, uint64_t seed, uint32_t set, int64_t cell0, int64_t ncells, int64_t R,
+                           int32_t d, double* out, int32_t on_device) {
+  if (!ctx) return VD_EINVAL;
+  if (!out || cell0 < 0 || ncells < 0 || R < 0 || d < 1 || d > VD_MAX_D || cell0 + ncells > ((int64_t)1 << 32) ||
+      R > ((int64_t)1 << 32))
+    return set_err(ctx, VD_EINVAL, "vd_mc_directions: bad arguments");
+  const int64_t n = ncells * R * d;
+  if (n == 0) return VD_OK;
+  DevBufs tmp;
+  double* o = out;
+  if (!on_device) VD_CK(tmp.alloc_n(&o, n), "alloc");
+  cudaError_t e = vd::launch_mc_directions(seed, set, cell0, ncells, R, d, o, ctx->st);
+  if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(out, o, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  tmp.release();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "mc_directions");
+  return VD_OK;
+}
+
+// ---------------------------------------------------------------- MC ----
+static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, int d, int64_t R, uint64_t seed,
+                        uint32_t set, vd_mc* mc) {
+  mc->st = ctx->st;
+  mc->N = N;
+  mc->d = d;
+  mc->R = R;
+  mc->seed = seed;
+  mc->set = set;
+  mc->X = Xd;
+  VD_CK(mc->bufs.alloc_n(&mc->hit, (size_t)N * R), "mc alloc");
+  VD_CK(mc->bufs.alloc_n(&mc->l, (size_t)N * R), "mc alloc");
+  VD_CK(mc->bufs.alloc_n(&mc->V, (size_t)N), "mc alloc");
+  VD_CK(mc->bufs.alloc_n(&mc->rowptr, (size_t)N + 1), "mc alloc");
+  DevBufs tmp;
+  struct Guard {
+    DevBufs& b;
+    ~Guard() { b.release(); }
+  } guard{tmp};
+  int32_t* ovl = nullptr;
+  int64_t* cnt = nullptr;
+  const int64_t ovcap = std::max<int64_t>(4096, N * R / 64);
+  VD_CK(tmp.alloc_n(&ovl, ovcap), "alloc");
+  VD_CK(tmp.alloc_n(&cnt, N), "alloc");
+  vd::RaySource rs;
+  rs.mode = 1;
+  rs.R = N * R;
+  rs.mc_rpc = R;
+  rs.seed = seed;
+  rs.set = set;
+  rs.box = 1;
+  vd::RayOut ro;
+  ro.hit = mc->hit;
+  ro.t = mc->l;
+  ro.mc_rpc = R;
+  ro.overflow_list = ovl;
+  ro.overflow_cap = ovcap;
+  VD_CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->st), "memset");
+  Timer tm(ctx->st);
+  VD_CK(vd::launch_raycast(tv, rs, ro, effective_precision(ctx), ctx->ctr, ctx->st), "mc raycast");
+  int64_t nnz = 0;
+  VD_CK(vd::mc_rowptr(mc->hit, N, R, cnt, mc->rowptr, &nnz, ctx->st), "mc rowptr");
+  mc->nnz = nnz;
+  VD_CK(mc->bufs.alloc_n(&mc->col, (size_t)std::max<int64_t>(nnz, 1)), "mc alloc");
+  VD_CK(mc->bufs.alloc_n(&mc->A, (size_t)std::max<int64_t>(nnz, 1)), "mc alloc");
+  VD_CK(vd::mc_fill(Xd, N, d, R, seed, set, mc->hit, mc->l, mc->rowptr, mc->V, mc->col, mc->A, ctx->st), "mc fill");
+  mc->stats.ms = tm.stop();
+  Counters hc;
+  vd_status s;
+  if ((s = read_counters(ctx, &hc)) != VD_OK) return s;
+  mc->stats.rays = N * R;
+  mc->stats.tiles_visited = (int64_t)hc.tiles;
+  mc->stats.pairs_screened = (int64_t)hc.pairs;
+  mc->stats.rechecked = (int64_t)hc.rechecked;
+  mc->stats.overflow_rays = (int64_t)hc.overflow;
+  mc->stats.fallback_rays = (int64_t)hc.fallback;
+  ctx->last = mc->stats;
+  return check_flags(ctx, hc);
+}
+
+vd_status vd_mc_integrate(vd_ctx* ctx, int64_t R, uint64_t seed, vd_mc** out) {
+  if (!ctx || !out) return VD_EINVAL;
+  *out = nullptr;
+  if (!ctx->X) return set_err(ctx, VD_EINVAL, "vd_mc_integrate: no node set");
+  if (!ctx->cfg.box) return set_err(ctx, VD_EINVAL, "vd_mc_integrate: needs box clipping (cells are unbounded)");
+  if (R < 1 || R > ((int64_t)1 << 31) || ctx->N * R > ((int64_t)1 << 40))
+    return set_err(ctx, VD_EINVAL, "vd_mc_integrate: bad rays_per_cell %lld", (long long)R);
+  vd_mc* mc = new (std::nothrow) vd_mc();
+  if (!mc) return VD_ENOMEM;
+  double* Xc = nullptr;
+  cudaError_t e = mc->bufs.alloc_n(&Xc, (size_t)ctx->N * ctx->d);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(Xc, ctx->X, (size_t)ctx->N * ctx->d * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st);
+  if (e != cudaSuccess) {
+    mc->bufs.release();
+    delete mc;
+    return cuda_err(ctx, e, "mc alloc");
+  }
+  vd_status s = mc_run(ctx, ctx->tree, Xc, ctx->N, ctx->d, R, seed, 0, mc);
+  if (s != VD_OK) {
+    cudaStreamSynchronize(ctx->st);
+    mc->bufs.release();
+    delete mc;
+    return s;
+  }
+  *out = mc;
+  return VD_OK;
+}
+
+int64_t vd_mc_count(const vd_mc* mc) { return mc ? mc->N : 0; }
+
+vd_status vd_mc_stats(const vd_mc* mc, vd_stats* out) {
+  if (!mc || !out) return VD_EINVAL;
+  *out = mc->stats;
+  return VD_OK;
+}
+
+vd_status vd_mc_get(const vd_mc* mc, double* V, int64_t* nnz, int64_t* rowptr, int32_t* col, double* A,
+                    int32_t on_device) {
+  if (!mc) return VD_EINVAL;
+  if (nnz) *nnz = mc->nnz;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaSuccess;
+  if (V && e == cudaSuccess) e = cudaMemcpyAsync(V, mc->V, mc->N * sizeof(double), k, mc->st);
+  if (rowptr && e == cudaSuccess) e = cudaMemcpyAsync(rowptr, mc->rowptr, (mc->N + 1) * sizeof(int64_t), k, mc->st);
+  if (col && e == cudaSuccess && mc->nnz) e = cudaMemcpyAsync(col, mc->col, mc->nnz * sizeof(int32_t), k, mc->st);
+  if (A && e == cudaSuccess && mc->nnz) e = cudaMemcpyAsync(A, mc->A, mc->nnz * sizeof(double), k, mc->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(mc->st);
+  return e == cudaSuccess ? VD_OK : VD_ECUDA;
+}
+
+vd_status vd_mc_rays(const vd_mc* mc, int32_t* hit, double* l, int32_t on_device) {
+  if (!mc) return VD_EINVAL;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaSuccess;
+  if (hit) e = cudaMemcpyAsync(hit, mc->hit, mc->N * mc->R * sizeof(int32_t), k, mc->st);
+  if (l && e == cudaSuccess) e = cudaMemcpyAsync(l, mc->l, mc->N * mc->R * sizeof(double), k, mc->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(mc->st);
+  return e == cudaSuccess ? VD_OK : VD_ECUDA;
+}
+
+vd_status vd_mc_adjoint(const vd_mc* mc, const double* gV, const double* gA, double* gX, int32_t on_device) {
+  if (!mc || !gX || (!gV && !gA)) return VD_EINVAL;
+  DevBufs tmp;
+  const double *gVd = gV, *gAd = gA;
+  double* gXd = gX;
+  double* zeroV = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto stage = [&](const double* src, size_t n, const double** dst) {
+    if (on_device || !src || e != cudaSuccess) return;
+    double* p = nullptr;
+    e = tmp.alloc_n(&p, n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, src, n * sizeof(double), cudaMemcpyHostToDevice, mc->st);
+    *dst = p;
+  };
+  stage(gV, mc->N, &gVd);
+  stage(gA, mc->nnz, &gAd);
+  if (e == cudaSuccess && !gVd) {
+    e = tmp.alloc_n(&zeroV, mc->N);
+    if (e == cudaSuccess) e = cudaMemsetAsync(zeroV, 0, mc->N * sizeof(double), mc->st);
+    gVd = zeroV;
+  }
+  if (e == cudaSuccess && !on_device) e = tmp.alloc_n(&gXd, (size_t)mc->N * mc->d);
+  if (e == cudaSuccess)
+    e = vd::mc_adjoint(mc->X, mc->N, mc->d, mc->R, mc->seed, mc->set, mc->hit, mc->l, mc->rowptr, mc->col, mc->nnz,
+                       gVd, gAd, gXd, tmp, mc->st);
+  if (e == cudaSuccess && !on_device)
+    e = cudaMemcpyAsync(gX, gXd, (size_t)mc->N * mc->d * sizeof(double), cudaMemcpyDeviceToHost, mc->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(mc->st);
+  cudaStreamSynchronize(mc->st);
+  tmp.release();
+  return e == cudaSuccess ? VD_OK : (e == cudaErrorMemoryAllocation ? VD_ENOMEM : VD_ECUDA);
+}
+
+void vd_mc_free(vd_mc* mc) {
+  if (!mc) return;
+  cudaStreamSynchronize(mc->st);
+  mc->bufs.release();
+  delete mc;
+}
+
+vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const* X, const int64_t* N,
+                                const int32_t* d, int64_t R, uint64_t seed, vd_mc** out, int32_t on_device) {
+  if (!ctx || nsets < 0 || (nsets > 0 && (!X || !N || !d || !out))) return VD_EINVAL;
+  return set_err(ctx, VD_EINVAL, "vd_mc_integrate_batch: not available in this build");
+}
+
+// ------------------------------------------------------------- vertices --
+vd_status vd_vertices(vd_ctx* ctx, vd_mesh** out) {
+  if (!ctx || !out) return VD_EINVAL;
+  *out = nullptr;
+  if (!ctx->X) return set_err(ctx, VD_EINVAL, "vd_vertices: no node set");
+  if (!ctx->cfg.box) return set_err(ctx, VD_EINVAL, "vd_vertices: needs box clipping");
+  if (ctx->N < 1) return set_err(ctx, VD_EINVAL, "vd_vertices: empty node set");
+  vd_mesh* m = new (std::nothrow) vd_mesh();
+  if (!m) return VD_ENOMEM;
+  m->st = ctx->st;
+  m->d = ctx->d;
+  VD_CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->st), "memset");
+  Timer tm(ctx->st);
+  char err[256] = {0};
+  cudaError_t e = vd::traverse_vertices(ctx->tree, effective_precision(ctx), ctx->cfg, m->bufs, &m->tuples,
+                                        &m->coords, &m->nv, &m->stats, ctx->ctr, ctx->st, err, sizeof(err));
+  m->stats.ms = tm.stop();
+  Counters hc;
+  vd_status s = VD_OK;
+  if (e != cudaSuccess) {
+    s = err[0] ? set_err(ctx, VD_EDEGENERATE, "vd_vertices: %s", err) : cuda_err(ctx, e, "vd_vertices");
+  } else {
+    s = read_counters(ctx, &hc);
+    if (s == VD_OK) s = check_flags(ctx, hc);
+    if (s == VD_OK) {
+      m->stats.rechecked = (int64_t)hc.rechecked;
+      m->stats.tiles_visited = (int64_t)hc.tiles;
+      m->stats.pairs_screened = (int64_t)hc.pairs;
+    }
+  }
+  if (s != VD_OK) {
+    cudaStreamSynchronize(ctx->st);
+    m->bufs.release();
+    delete m;
+    return s;
+  }
+  ctx->last = m->stats;
+  *out = m;
+  return VD_OK;
+}
+
+int64_t vd_mesh_count(const vd_mesh* m) { return m ? m->nv : 0; }
+int32_t vd_mesh_dim(const vd_mesh* m) { return m ? m->d : 0; }
+
+vd_status vd_mesh_copy(const vd_mesh* m, int32_t* tuples, double* coords, int32_t on_device) {
+  if (!m) return VD_EINVAL;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaSuccess;
+  if (tuples && m->nv) e = cudaMemcpyAsync(tuples, m->tuples, m->nv * (m->d + 1) * sizeof(int32_t), k, m->st);
+  if (coords && m->nv && e == cudaSuccess)
+    e = cudaMemcpyAsync(coords, m->coords, m->nv * m->d * sizeof(double), k, m->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  return e == cudaSuccess ? VD_OK : VD_ECUDA;
+}
+
+vd_status vd_mesh_stats(const vd_mesh* m, vd_stats* out) {
+  if (!m || !out) return VD_EINVAL;
+  *out = m->stats;
+  return VD_OK;
+}
+
+void vd_mesh_free(vd_mesh* m) {
+  if (!m) return;
+  cudaStreamSynchronize(m->st);
+  m->bufs.release();
+  delete m;
+}
+
+}  // extern "C"

@@ -1,0 +1,115 @@
+// vd_internal.h -- host/device structures shared by the libvd translation
+// units (node tree, ray batches, counters, launcher prototypes).
+#pragma once
+#include <cstdint>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "vd.h"
+
+namespace vd {
+
+constexpr int kTile = 32;      // nodes per leaf tile (one per lane)
+constexpr int kFan = 32;       // children per internal tree node
+constexpr int kMaxLev = 8;     // tree levels (leaves + internal)
+constexpr int32_t kNoId = INT32_MIN;
+
+// Device error flags (bit mask in Counters::flags).
+enum : uint32_t {
+  kFlagCandOverflow = 1u,   // a ray's candidate list overflowed (ray rerun on FP64)
+  kFlagStack = 2u,          // traversal stack overflow
+  kFlagHashFull = 4u,       // vertex / edge table full
+  kFlagTimeout = 8u,        // bounded wait gave up
+  kFlagDegenerate = 16u,    // degenerate solve or exact tie
+  kFlagQueue = 32u,         // a work queue overflowed
+  kFlagBadInput = 64u,      // a ray's reference generator is not a node
+};
+
+// Morton-ordered node tiles with a bounding-box hierarchy.
+struct TreeView {
+  int d = 0;
+  int64_t N = 0;
+  int64_t ntiles = 0;
+  int nlev = 0;                 // number of levels, level 0 = tiles, level nlev-1 = root (1 node)
+  int64_t cnt[kMaxLev] = {};    // nodes per level
+  int64_t off[kMaxLev] = {};    // first index of each level in the bbox arrays
+  int64_t total = 0;            // bbox entries over all levels
+  const float* blo32 = nullptr;  // [d][total], rounded down
+  const float* bhi32 = nullptr;  // [d][total], rounded up
+  const double* blo64 = nullptr; // [d][total]
+  const double* bhi64 = nullptr;
+  const float* x32 = nullptr;    // [ntiles][d][32], nearest binary32 of x
+  const double* x64 = nullptr;   // [ntiles][d][32]
+  const int32_t* ids = nullptr;  // [ntiles][32], kNoId for padding
+  const double* X = nullptr;     // original N x d row-major
+  float coord_abs = 1.f;         // max |coordinate| over nodes (>= 1)
+};
+
+// Where the rays of a generic raycast come from.
+struct RaySource {
+  int mode = 0;                  // 0: explicit arrays, 1: MC (cell, ray) list
+  int64_t R = 0;
+  // explicit
+  const double* origins = nullptr;  // R x d
+  const double* dirs = nullptr;     // R x d
+  const int32_t* eta = nullptr;     // R x eta_stride
+  int eta_stride = 0;
+  // MC list: ray r is (cell = mc_cell[r], k = mc_ray[r]) of set `set`; with
+  // mc_cell == nullptr ray r is (r / mc_rpc, r % mc_rpc)
+  const int32_t* mc_cell = nullptr;
+  const int32_t* mc_ray = nullptr;
+  int64_t mc_rpc = 0;
+  uint64_t seed = 0;
+  uint32_t set = 0;
+  int box = 1;
+};
+
+struct RayOut {
+  int32_t* hit = nullptr;   // R (MC list: indexed cell * mc_rpc + ray)
+  double* t = nullptr;      // R
+  int64_t mc_rpc = 0;       // rays per cell of the MC output layout
+  float* screen_err = nullptr;  // nullable
+  int32_t* overflow_list = nullptr;  // rays whose candidate list overflowed
+  int64_t overflow_cap = 0;
+};
+
+struct Counters {
+  unsigned long long tiles;
+  unsigned long long pairs;
+  unsigned long long rechecked;
+  unsigned long long overflow;
+  unsigned long long ties;
+  unsigned long long fallback;
+  unsigned long long aux0;
+  unsigned long long aux1;
+  unsigned int flags;
+  unsigned int pad;
+};
+
+// Device allocations owned by one library object, released together.
+struct DevBufs {
+  std::vector<void*> ptrs;
+  cudaError_t alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) ptrs.push_back(*p);
+    return e;
+  }
+  template <class T>
+  cudaError_t alloc_n(T** p, size_t n) { return alloc(reinterpret_cast<void**>(p), n * sizeof(T)); }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+// ---- launchers (defined in the .cu files) --------------------------------
+// Builds the tree of X_dev (N x d, device) into buffers owned by `bufs`.
+cudaError_t build_tree(const double* X_dev, int64_t N, int d, cudaStream_t st, DevBufs& bufs, TreeView* tv);
+cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision,
+                           Counters* ctr, cudaStream_t st);
+cudaError_t launch_mc_directions(uint64_t seed, uint32_t set, int64_t cell0, int64_t ncells, int64_t R, int d,
+                                 double* out, cudaStream_t st);
+
+}  // namespace vd

@@ -1,0 +1,339 @@
+// vd_mc.cu -- Monte Carlo cell volumes and interface areas (Section 3.1,
+// Algorithm 3) from the saved per-ray argmins, and their adjoint.
+//
+// For ray k of cell i with length l_k = t* and hit generator j:
+//   V_i  = S_{d-1} / (d R) sum_k l_k^d
+//   A_ij = S_{d-1} / R sum_{k: hit j} a_k,
+//   a_k  = l^{d-1} / |n_ij . u_k| = 2 l^d / |x_j - x_i|   (node hit, since
+//          l = |w|^2 / (2 u.w) with w = x_j - x_i)
+//   a_k  = l^{d-1} / |u_a|                               (face on axis a)
+// The reductions are deterministic: a warp owns a cell, visits the distinct
+// hit ids of the row in ascending order and sums each one's terms with a
+// fixed lane-strided order and butterfly.
+//
+// Adjoint (directions and argmins held fixed): for a node hit
+//   dl/dx_j = (w - l u) / (u.w) = -dl/dx_i,
+//   da/dw   = (2 d l^{d-1} / |w|) dl/dw - (2 l^d / |w|^3) w;
+// for a face hit dl/dx_ia = -1/u_a, da/dl = (d-1) l^{d-2} / |u_a|.
+// Per (i, j) the row pass sums the ray contributions P_ij; x_i receives
+// -sum_j P_ij (plus its face terms) and x_j receives sum_i P_ij through a
+// column pass over the transposed entries, again in a fixed order.
+#include <algorithm>
+#include <cmath>
+
+#include "vd_dev.cuh"
+
+namespace vd {
+
+cudaError_t radix_sort_u64(uint64_t* keys, int32_t* vals, uint64_t* ktmp, int32_t* vtmp, int64_t n,
+                           uint32_t* counts, unsigned long long* orand, cudaStream_t st);
+
+namespace {
+
+__device__ __forceinline__ double ipow_d(double l, int n) {
+  double r = 1.0;
+  for (int q = 0; q < n; ++q) r = (q == 0) ? l : __dmul_rn(r, l);
+  return r;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// smallest hit id of the row that is > prev (INT_MAX if none)
+__device__ __forceinline__ int32_t next_id(const int32_t* h, int64_t R, int32_t prev, bool first, int lane) {
+  int32_t best = INT32_MAX;
+  for (int64_t k = lane; k < R; k += 32) {
+    const int32_t x = h[k];
+    if ((first || x > prev) && x < best) best = x;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o));
+  return best;
+}
+
+template <int D>
+__device__ __forceinline__ double node_area_term(const double* X, int d, int64_t i, int32_t j, double ld) {
+  double ww = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    if (k < d) {
+      const double w = __dadd_rn(X[(int64_t)j * d + k], -X[i * d + k]);
+      ww = __dadd_rn(ww, __dmul_rn(w, w));
+    }
+  return __ddiv_rn(__dmul_rn(2.0, ld), __dsqrt_rn(ww));
+}
+
+__global__ void k_mc_count(const int32_t* hit, int64_t N, int64_t R, int64_t* nnz) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;
+  const int32_t* h = hit + i * R;
+  int64_t n = 0;
+  int32_t prev = 0;
+  bool first = true;
+  while (true) {
+    const int32_t id = next_id(h, R, prev, first, lane);
+    if (id == INT32_MAX) break;
+    ++n;
+    prev = id;
+    first = false;
+  }
+  if (lane == 0) nnz[i] = n;
+}
+
+// exclusive scan of n int64 values into out[0..n] (single block)
+__global__ void k_scan64(const int64_t* in, int64_t n, int64_t* out) {
+  __shared__ int64_t part[1024];
+  const int64_t seg = (n + 1023) / 1024;
+  const int64_t b = threadIdx.x * seg, e = min(n, b + seg);
+  int64_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += in[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int64_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t run = part[threadIdx.x] - s;
+  for (int64_t i = b; i < e; ++i) {
+    out[i] = run;
+    run += in[i];
+  }
+  if (threadIdx.x == 1023) out[n] = part[1023];
+}
+
+template <int D>
+__global__ void k_mc_fill(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
+                          const int32_t* hit, const double* l, const int64_t* rowptr, double cV, double cA, double* V,
+                          int32_t* col, double* A) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;
+  const int32_t* h = hit + i * R;
+  const double* li = l + i * R;
+  double vs = 0.0;
+  for (int64_t k = lane; k < R; k += 32) vs = __dadd_rn(vs, ipow_d(li[k], d));
+  vs = warp_sum_d(vs);
+  if (lane == 0) V[i] = __dmul_rn(cV, vs);
+  int64_t q = rowptr[i];
+  int32_t prev = 0;
+  bool first = true;
+  while (true) {
+    const int32_t id = next_id(h, R, prev, first, lane);
+    if (id == INT32_MAX) break;
+    double s = 0.0;
+    for (int64_t k = lane; k < R; k += 32) {
+      if (h[k] != id) continue;
+      const double lk = li[k];
+      double term;
+      if (id >= 0) {
+        term = node_area_term<D>(X, d, i, id, ipow_d(lk, d));
+      } else {
+        double u[D];
+        mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
+        const int a = face_axis(id);
+        double ua = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          if (c == a) ua = u[c];
+        term = __ddiv_rn(ipow_d(lk, d - 1), fabs(ua));
+      }
+      s = __dadd_rn(s, term);
+    }
+    s = warp_sum_d(s);
+    if (lane == 0) {
+      col[q] = id;
+      A[q] = __dmul_rn(cA, s);
+    }
+    ++q;
+    prev = id;
+    first = false;
+  }
+}
+
+// Row pass of the adjoint: P[q][*] = sum over the rays of cell i that hit
+// col[q] of dLoss/dw (node) ; own[i][*] = face terms of x_i.
+template <int D>
+__global__ void k_mc_adj_rows(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
+                              const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col,
+                              double cV, double cA, const double* gV, const double* gA, double* P, double* own) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;
+  const int32_t* h = hit + i * R;
+  const double* li = l + i * R;
+  const double gVi = gV[i];
+  double faceacc[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) faceacc[c] = 0.0;
+  for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+    const int32_t id = col[q];
+    const double gAij = gA ? gA[q] : 0.0;
+    double acc[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc[c] = 0.0;
+    for (int64_t k = lane; k < R; k += 32) {
+      if (h[k] != id) continue;
+      double u[D];
+      mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
+      const double lk = li[k];
+      const double ld1 = ipow_d(lk, d - 1), ld = ipow_d(lk, d);
+      if (id >= 0) {
+        double w[D], den = 0.0, ww = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) w[c] = c < d ? __dadd_rn(X[(int64_t)id * d + c], -X[i * d + c]) : 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          if (c < d) den = __dadd_rn(den, __dmul_rn(u[c], w[c]));
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          if (c < d) ww = __dadd_rn(ww, __dmul_rn(w[c], w[c]));
+        const double nw = sqrt(ww);
+        const double c1 = 2.0 * (double)d * ld1 / nw, c2 = 2.0 * ld / (nw * nw * nw);
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          if (c < d) {
+            const double dl = (w[c] - lk * u[c]) / den;
+            const double dV = cV * (double)d * ld1 * dl;
+            const double dA = cA * (c1 * dl - c2 * w[c]);
+            acc[c] += gVi * dV + gAij * dA;
+          }
+      } else {
+        const int a = face_axis(id);
+        double ua = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          if (c == a) ua = u[c];
+        const double dl = -1.0 / ua;
+        const double dadl = (d >= 2) ? (double)(d - 1) * ipow_d(lk, d - 2) / fabs(ua) : 0.0;
+        const double G = gVi * cV * (double)d * ld1 * dl + gAij * cA * dadl * dl;
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          if (c == a) acc[c] += G;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) acc[c] = warp_sum_d(acc[c]);
+    if (id >= 0) {
+      if (lane == 0)
+        for (int c = 0; c < d; ++c) P[q * d + c] = acc[c];
+#pragma unroll
+      for (int c = 0; c < D; ++c) faceacc[c] -= acc[c];
+    } else {
+      if (lane == 0)
+        for (int c = 0; c < d; ++c) P[q * d + c] = 0.0;
+#pragma unroll
+      for (int c = 0; c < D; ++c) faceacc[c] += acc[c];
+    }
+  }
+  if (lane == 0)
+    for (int c = 0; c < d; ++c) own[i * d + c] = faceacc[c];
+}
+
+// keys: column (node id) of each node entry, vals: entry index
+__global__ void k_mc_col_keys(const int32_t* col, int64_t nnz, uint64_t* keys, int32_t* vals) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nnz) return;
+  const int32_t c = col[q];
+  keys[q] = c >= 0 ? (uint64_t)c : (uint64_t)0xFFFFFFFFull;  // faces sort last
+  vals[q] = (int32_t)q;
+}
+
+// column pass: gX[j] = own[j] + sum over entries (i, j) in ascending i of P
+__global__ void k_mc_adj_cols(const uint64_t* keys, const int32_t* vals, int64_t nnz, const double* P,
+                              const double* own, int64_t N, int d, double* gX) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  // binary search the first entry with key j
+  int64_t lo = 0, hi = nnz;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    if (keys[mid] < (uint64_t)j) lo = mid + 1;
+    else hi = mid;
+  }
+  double acc[VD_MAX_D];
+  for (int c = 0; c < d; ++c) acc[c] = own[j * d + c];
+  for (int64_t q = lo; q < nnz && keys[q] == (uint64_t)j; ++q) {
+    const int64_t e = vals[q];
+    for (int c = 0; c < d; ++c) acc[c] += P[e * d + c];
+  }
+  for (int c = 0; c < d; ++c) gX[j * d + c] = acc[c];
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+template <int D>
+cudaError_t fill_d(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set, const int32_t* hit,
+                   const double* l, const int64_t* rowptr, double cV, double cA, double* V, int32_t* col, double* A,
+                   cudaStream_t st) {
+  k_mc_fill<D><<<nblk(N * 32, 128), 128, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t adj_rows_d(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
+                       const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, double cV,
+                       double cA, const double* gV, const double* gA, double* P, double* own, cudaStream_t st) {
+  k_mc_adj_rows<D><<<nblk(N * 32, 128), 128, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P,
+                                                       own);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+double sphere_area(int d) { return 2.0 * std::pow(M_PI, 0.5 * d) / std::tgamma(0.5 * d); }
+
+// Counts the distinct hits per cell and writes rowptr (N+1); returns nnz.
+cudaError_t mc_rowptr(const int32_t* hit, int64_t N, int64_t R, int64_t* cnt_scratch, int64_t* rowptr,
+                      int64_t* nnz_host, cudaStream_t st) {
+  k_mc_count<<<nblk(N * 32, 128), 128, 0, st>>>(hit, N, R, cnt_scratch);
+  k_scan64<<<1, 1024, 0, st>>>(cnt_scratch, N, rowptr);
+  cudaMemcpyAsync(nnz_host, rowptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t mc_fill(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set, const int32_t* hit,
+                    const double* l, const int64_t* rowptr, double* V, int32_t* col, double* A, cudaStream_t st) {
+  const double S = sphere_area(d);
+  const double cV = S / ((double)d * (double)R), cA = S / (double)R;
+  if (d <= 4) return fill_d<4>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, st);
+  if (d <= 8) return fill_d<8>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, st);
+  return fill_d<16>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, st);
+}
+
+cudaError_t mc_adjoint(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
+                       const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, int64_t nnz,
+                       const double* gV, const double* gA, double* gX, DevBufs& scratch, cudaStream_t st) {
+  const double S = sphere_area(d);
+  const double cV = S / ((double)d * (double)R), cA = S / (double)R;
+  double *P = nullptr, *own = nullptr;
+  uint64_t *keys = nullptr, *ktmp = nullptr;
+  int32_t *vals = nullptr, *vtmp = nullptr;
+  uint32_t* counts = nullptr;
+  unsigned long long* orand = nullptr;
+  cudaError_t e;
+  const int64_t nn = std::max<int64_t>(nnz, 1);
+  if ((e = scratch.alloc_n(&P, (size_t)nn * d)) != cudaSuccess || (e = scratch.alloc_n(&own, (size_t)N * d)) ||
+      (e = scratch.alloc_n(&keys, nn)) || (e = scratch.alloc_n(&ktmp, nn)) || (e = scratch.alloc_n(&vals, nn)) ||
+      (e = scratch.alloc_n(&vtmp, nn)) || (e = scratch.alloc_n(&counts, (size_t)256 * (nn / 4096 + 2))) ||
+      (e = scratch.alloc_n(&orand, 2)))
+    return e;
+  if (d <= 4) e = adj_rows_d<4>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P, own, st);
+  else if (d <= 8) e = adj_rows_d<8>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P, own, st);
+  else e = adj_rows_d<16>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P, own, st);
+  if (e != cudaSuccess) return e;
+  k_mc_col_keys<<<nblk(nnz, 256), 256, 0, st>>>(col, nnz, keys, vals);
+  e = radix_sort_u64(keys, vals, ktmp, vtmp, nnz, counts, orand, st);
+  if (e != cudaSuccess) return e;
+  k_mc_adj_cols<<<nblk(N, 128), 128, 0, st>>>(keys, vals, nnz, P, own, N, d, gX);
+  return cudaGetLastError();
+}
+
+}  // namespace vd

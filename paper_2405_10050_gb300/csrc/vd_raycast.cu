@@ -1,0 +1,706 @@
+// vd_raycast.cu -- the generic exact RayCast (Section 2.2, Eq. (t),
+// Algorithm 1) for arbitrary rays.
+//
+// Algorithm 1 reaches the first bisector hit by alternating a nearest-
+// neighbour query with the projection of Eq. (t); its result is the node
+// minimising t_j = (|x_j - v|^2 - |g - v|^2) / (2 u.(x_j - g)) over
+// u.(x_j - g) > 0.  This kernel computes that minimum directly: for the
+// current bound T, every node with t_j < T lies in the ball centred at
+// c = v + T u through g (expand |x_j - c|^2 < |g - c|^2: the difference is
+// num_j - 2 T den_j), so a 32-way bounding-box tree is walked nearest box
+// first and every box that misses the ball is skipped.
+//
+// Work layout: a warp owns 32 rays at a time.  Per-ray set-up (binary64
+// origin offsets, box faces) runs one ray per lane; the tree walk runs the
+// 32 lanes over the 32 nodes of a tile, one ray after the other; the binary64
+// recheck again runs one ray per lane, so the binary64 pipe sees full warps.
+//
+// VD_FP64: every (ray, node) pair is evaluated in binary64 in the canonical
+// order and the warp keeps the exact minimum.
+// VD_FP32: pairs are screened in binary32 with a rigorous error bound on
+// num_j and den_j; a node is kept as candidate when its lower bound on t_j
+// does not exceed the running upper bound T, and only the candidates are
+// recomputed in binary64 with the canonical formula.
+#include <algorithm>
+#include <cmath>
+
+#include "vd_dev.cuh"
+
+namespace vd {
+
+namespace {
+
+constexpr int kWpb = 4;        // warps per block
+constexpr int kCmax = 16;      // candidates kept per ray
+constexpr int kStk = kFan * kMaxLev;
+
+template <int D>
+struct WarpMixed {
+  float u[32][D];
+  float g[32][D];
+  float p[32][D];
+  double u64[32][D];
+  double p64[32][D];
+  float T[32];
+  float a0[32], a1[32], b0[32], b2[32];  // per-ray error-bound constants
+  int32_t eta[32][D + 1];
+  int m[32];
+  int hasp[32];
+  int ncand[32];
+  int32_t cid[32][kCmax];
+  float ctlo[32][kCmax];
+  int stk[kStk];
+};
+
+template <int D>
+struct WarpF64 {
+  double u[32][D];
+  double g[32][D];
+  double p[32][D];
+  double bt[32];
+  int bcls[32], bkey[32];
+  int32_t eta[32][D + 1];
+  int m[32];
+  int stk[kStk];
+};
+
+__device__ __forceinline__ int enc(int lev, int64_t idx) { return (lev << 27) | (int)idx; }
+
+// Loads ray r of the source: origin v, direction u, eta (m ids, eta[0] = g).
+template <int D>
+__device__ __forceinline__ void load_ray(const TreeView& tr, const RaySource& rs, int64_t r, double v[D], double u[D],
+                                         int32_t eta[D + 1], int& m) {
+  const int d = tr.d;
+  if (rs.mode == 0) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      v[k] = k < d ? rs.origins[r * d + k] : 0.0;
+      u[k] = k < d ? rs.dirs[r * d + k] : 0.0;
+    }
+    m = 0;
+    for (int q = 0; q < rs.eta_stride && q < D + 1; ++q) {
+      const int32_t e = rs.eta[r * rs.eta_stride + q];
+      if (e == kNoId) break;
+      eta[m++] = e;
+    }
+  } else {
+    const int32_t cell = rs.mc_cell ? rs.mc_cell[r] : (int32_t)(r / rs.mc_rpc);
+    const int32_t k = rs.mc_cell ? rs.mc_ray[r] : (int32_t)(r % rs.mc_rpc);
+    mc_direction<D>(rs.seed, rs.set, (uint32_t)cell, (uint32_t)k, d, u);
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = k < d ? tr.X[(int64_t)cell * d + k] : 0.0;
+    eta[0] = cell;
+    m = 1;
+  }
+}
+
+__device__ __forceinline__ int64_t out_pos(const RaySource& rs, const RayOut& ro, int64_t r) {
+  if (rs.mode == 0 || rs.mc_cell == nullptr) return r;
+  return (int64_t)rs.mc_cell[r] * ro.mc_rpc + rs.mc_ray[r];
+}
+
+// Conservative binary32 ball: every point within distance rho of the exact
+// centre c = v + T u satisfies |y - c32|^2 <= lim2.
+template <int D>
+struct Ball {
+  float c[D];
+  float lim2;
+};
+
+template <int D>
+__device__ __forceinline__ void make_ball(const float g[D], const float p[D], const float u[D], float T, float B,
+                                          Ball<D>& b) {
+  // c = g + p + T u, rho = |p + T u|; absolute error of each coordinate is
+  // below 4 u_32 (|g| + |p| + T) and of rho below 4 sqrt(D) u_32 (...).
+  float r2 = 0.f, pm = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const float q = fmaf(T, u[k], p[k]);
+    b.c[k] = g[k] + q;
+    r2 = fmaf(q, q, r2);
+    pm = fmaxf(pm, fabsf(p[k]));
+  }
+  const float eps = 8.f * (float)D * kU32 * (B + pm + T) + 1e-30f;
+  const float rho = sqrtf(r2) * (1.f + 4.f * (float)D * kU32) + eps;
+  b.lim2 = rho * rho * (1.f + 4.f * (float)D * kU32) + 1e-37f;
+  if (!(T < INFINITY)) b.lim2 = INFINITY;
+}
+
+template <int D>
+__device__ __forceinline__ float box_dist2(const TreeView& tr, int lev, int64_t i, const Ball<D>& b) {
+  const int64_t idx = tr.off[lev] + i;
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    if (k < tr.d) {
+      const float lo = tr.blo32[k * tr.total + idx], hi = tr.bhi32[k * tr.total + idx];
+      const float e = fmaxf(fmaxf(lo - b.c[k], b.c[k] - hi), 0.f);
+      s = fmaf(e, e, s);
+    }
+  }
+  return s;
+}
+
+// One lane's part of the leaf re-test: lanes k < d add dimension k.
+template <int D>
+__device__ __forceinline__ bool leaf_alive(const TreeView& tr, int64_t tile, const Ball<D>& b, int lane) {
+  float e = 0.f;
+  if (lane < tr.d) {
+    const int64_t idx = tr.off[0] + tile;
+    float ck = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k == lane) ck = b.c[k];
+    const float lo = tr.blo32[lane * tr.total + idx], hi = tr.bhi32[lane * tr.total + idx];
+    e = fmaxf(fmaxf(lo - ck, ck - hi), 0.f);
+    e = e * e;
+  }
+  return warp_sum(e) * (1.f - 2e-6f) <= b.lim2;
+}
+
+// Walks the tree for the ball of the current bound; leaf(tile) evaluates a
+// tile and may shrink the ball.
+template <int D, class Leaf>
+__device__ __forceinline__ void walk(const TreeView& tr, int* stk, Ball<D>& ball, int lane, Leaf&& leaf,
+                                     unsigned long long& tiles) {
+  int sp = 0;
+  if (lane == 0) stk[0] = enc(tr.nlev - 1, 0);
+  sp = 1;
+  __syncwarp();
+  while (sp > 0) {
+    const int e = stk[--sp];
+    __syncwarp();
+    const int lev = e >> 27;
+    const int64_t idx = e & ((1 << 27) - 1);
+    if (lev == 0) {
+      if (leaf_alive<D>(tr, idx, ball, lane)) {
+        ++tiles;
+        leaf(idx);
+      }
+      continue;
+    }
+    const int64_t child = idx * kFan + lane;
+    const bool valid = child < tr.cnt[lev - 1];
+    float key = INFINITY;  // INFINITY marks "not visited"; a visited child has a finite key
+    if (valid) {
+      const float d2 = box_dist2<D>(tr, lev - 1, child, ball);
+      if (d2 * (1.f - 2e-6f) <= ball.lim2) key = fminf(d2, 3.0e38f);
+    }
+    int val = (int)child;
+    warp_sort(key, val);
+    const int n = __popc(__ballot_sync(kFull, key < INFINITY));
+    if (lane < n && sp + n - 1 - lane < kStk) stk[sp + n - 1 - lane] = enc(lev - 1, val);
+    sp = min(sp + n, kStk);
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------
+// VD_FP32: binary32 screening + binary64 recheck
+// ------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource rs, RayOut ro, Counters* ctr,
+                                                         unsigned long long* work) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpMixed<D>& S = reinterpret_cast<WarpMixed<D>*>(smem_raw)[wib];
+  const int d = tr.d;
+  const float B = tr.coord_abs;
+  const float gam = (float)(D + 1) * kU32 * 1.01f;          // gamma_D for the FMA dot products
+  const float EW = 4.01f * kU32 * B;                         // |w32_k - w_k|
+  unsigned long long n_tiles = 0, n_pairs = 0, n_rech = 0, n_over = 0;
+  const int64_t R = rs.R;
+  while (true) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(work, 1ull);
+    b = __shfl_sync(kFull, b, 0);
+    const int64_t b0 = (int64_t)b * 32;
+    if (b0 >= R) break;
+    // ---- set-up: one ray per lane ----
+    const int64_t r = b0 + lane;
+    const bool vr = r < R;
+    if (vr) {
+      double v[D], u[D];
+      int32_t eta[D + 1];
+      int m;
+      load_ray<D>(tr, rs, r, v, u, eta, m);
+      if (m < 1 || eta[0] < 0 || eta[0] >= tr.N) {  // g must be a node
+        atomicOr(&ctr->flags, kFlagBadInput);
+        m = 1;
+        eta[0] = 0;
+      }
+      const int32_t g = eta[0];
+      float U1 = 0.f, P1 = 0.f, P2s = 0.f;
+      int hasp = 0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double gk = k < d ? tr.X[(int64_t)g * d + k] : 0.0;
+        const double pk = __dadd_rn(v[k], -gk);
+        S.u64[lane][k] = u[k];
+        S.p64[lane][k] = pk;
+        S.u[lane][k] = __double2float_rn(u[k]);
+        S.g[lane][k] = __double2float_rn(gk);
+        S.p[lane][k] = __double2float_rn(pk);
+        U1 += fabsf(S.u[lane][k]);
+        const float pa = fabsf(__double2float_ru(fabs(pk)));
+        P1 += pa;
+        P2s = fmaf(pa, pa, P2s);
+        hasp |= (pk != 0.0);
+      }
+      U1 *= 1.0001f;
+      P1 *= 1.0001f;
+      const float P2 = sqrtf(P2s) * 1.0001f;
+      S.a0[lane] = 1.1f * EW * U1;
+      S.a1[lane] = 1.1f * (gam + kU32);
+      S.b0[lane] = 1.1f * ((float)D * EW * EW + 2.f * EW * P1);
+      S.b2[lane] = 1.1f * (2.f * sqrtf((float)D) * EW + 2.f * (gam + kU32) * P2);
+      for (int q = 0; q <= D; ++q) S.eta[lane][q] = q < m ? eta[q] : kNoId;
+      S.m[lane] = m;
+      S.hasp[lane] = hasp;
+      // box faces: binary32 interval of (b - v_a) / u_a
+      float T = INFINITY;
+      int nc = 0;
+      if (rs.box) {
+        for (int a = 0; a < d; ++a) {
+          const float ua = S.u[lane][a];
+          if (u[a] == 0.0 || ua == 0.f) continue;
+          const int s = u[a] > 0.0 ? 1 : 0;
+          const int32_t fid = face_id(a, s);
+          bool ex = false;
+          for (int q = 0; q < m; ++q) ex |= (eta[q] == fid);
+          if (ex) continue;
+          // t = (b - v_a) / u_a = nfs / |u_a| with nfs = (b - v_a) sign(u_a)
+          const float va = __double2float_rn(v[a]);
+          const float nf = (s ? 1.f : 0.f) - va;
+          const float nfs = s ? nf : -nf;
+          const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
+          const float au = fabsf(ua);
+          const float lo_n = nfs - ef, hi_n = nfs + ef;
+          const float tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
+                                        : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
+          const float thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
+                                        : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
+          T = fminf(T, thi);
+          if (nc < kCmax) {
+            S.cid[lane][nc] = fid;
+            S.ctlo[lane][nc] = tlo;
+            ++nc;
+          }
+        }
+      }
+      S.T[lane] = T;
+      S.ncand[lane] = nc;
+    }
+    __syncwarp();
+    // ---- screening: the warp walks the tree for each ray ----
+    for (int rr = 0; rr < 32 && b0 + rr < R; ++rr) {
+      float u[D], gg[D], pp[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        u[k] = S.u[rr][k];
+        gg[k] = S.g[rr][k];
+        pp[k] = S.p[rr][k];
+      }
+      const float a0 = S.a0[rr], a1 = S.a1[rr], b0c = S.b0[rr], b2 = S.b2[rr];
+      const int m = S.m[rr];
+      const bool hasp = S.hasp[rr] != 0;
+      float T = S.T[rr];
+      int nc = S.ncand[rr];
+      Ball<D> ball;
+      make_ball<D>(gg, pp, u, T, B, ball);
+      auto leaf = [&](int64_t tile) {
+        const int32_t id = tr.ids[tile * kTile + lane];
+        bool ok = id != kNoId;
+        for (int q = 0; q < m; ++q) ok &= (id != S.eta[rr][q]);
+        float w[D];
+        float den = 0.f, ww = 0.f, pw = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          w[k] = (k < d) ? tr.x32[(tile * d + k) * kTile + lane] - gg[k] : 0.f;
+          den = fmaf(u[k], w[k], den);
+          ww = fmaf(w[k], w[k], ww);
+        }
+        if (hasp) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) pw = fmaf(pp[k], w[k], pw);
+        }
+        const float num = fmaf(-2.f, pw, ww);
+        const float wn = sqrtf(ww) * (1.f + gam);
+        const float Eden = fmaf(a1, wn, a0);
+        const float Enum = fmaf(1.1f * kU32, fabsf(num), fmaf(1.1f * gam, ww, fmaf(b2, wn, b0c)));
+        const float dh = den + Eden;
+        const float nlo = num - Enum;
+        // t_j <= T is possible iff the lower bound of t_j does not exceed T
+        const bool cand = ok && dh > 0.f && (nlo <= 0.f || nlo <= 2.f * T * dh * (1.f + 8.f * kU32));
+        const unsigned cm = __ballot_sync(kFull, cand);
+        if (cm == 0) return;
+        float thi = INFINITY, tlo = -INFINITY;
+        if (cand) {
+          const float dl = den - Eden;
+          const float nhi = num + Enum;
+          if (dl > 0.f)
+            thi = nhi >= 0.f ? __fdiv_rn(nhi, 2.f * dl) * (1.f + 4.f * kU32)
+                             : __fdiv_rn(nhi, 2.f * dh) * (1.f - 4.f * kU32);
+          if (nlo > 0.f) tlo = __fdiv_rn(nlo, 2.f * dh) * (1.f - 4.f * kU32);
+        }
+        const float Tn = warp_min(thi);
+        if (Tn < T) {
+          T = Tn;
+          make_ball<D>(gg, pp, u, T, B, ball);
+        }
+        const bool keep = cand && tlo <= T;
+        const unsigned km = __ballot_sync(kFull, keep);
+        const int nk = __popc(km);
+        if (nc >= 0 && nc + nk > kCmax) {
+          // compact: drop candidates whose lower bound exceeds the new T
+          int cnt = 0;
+          for (int c0 = 0; c0 < nc; c0 += 32) {
+            const int c = c0 + lane;
+            const bool stay = c < nc && S.ctlo[rr][c] <= T;
+            const unsigned sm = __ballot_sync(kFull, stay);
+            int32_t cidv = 0;
+            float ctv = 0.f;
+            if (stay) {
+              cidv = S.cid[rr][c];
+              ctv = S.ctlo[rr][c];
+            }
+            __syncwarp();
+            if (stay) {
+              const int pos = cnt + __popc(sm & ((1u << lane) - 1u));
+              S.cid[rr][pos] = cidv;
+              S.ctlo[rr][pos] = ctv;
+            }
+            cnt += __popc(sm);
+            __syncwarp();
+          }
+          nc = cnt;
+          if (nc + nk > kCmax) nc = -1;  // overflow: the ray is redone on the binary64 path
+        }
+        if (nc >= 0) {
+          if (keep) {
+            const int pos = nc + __popc(km & ((1u << lane) - 1u));
+            S.cid[rr][pos] = id;
+            S.ctlo[rr][pos] = tlo;
+          }
+          nc += nk;
+        }
+        __syncwarp();
+      };
+      unsigned long long t0 = n_tiles;
+      walk<D>(tr, S.stk, ball, lane, leaf, n_tiles);
+      n_pairs += (n_tiles - t0) * 32;
+      if (lane == 0) {
+        S.T[rr] = T;
+        S.ncand[rr] = nc;
+      }
+      __syncwarp();
+    }
+    __syncwarp();
+    // ---- binary64 recheck: one ray per lane ----
+    if (vr) {
+      const int nc = S.ncand[lane];
+      const int64_t op = out_pos(rs, ro, r);
+      if (nc < 0) {
+        const unsigned long long k = atomicAdd(&ctr->overflow, 1ull);
+        if ((int64_t)k < ro.overflow_cap) ro.overflow_list[k] = (int32_t)r;
+        else atomicOr(&ctr->flags, kFlagCandOverflow);
+        ++n_over;
+        ro.hit[op] = kNoId;
+        ro.t[op] = NAN;
+      } else {
+        const float T = S.T[lane];
+        const int32_t g = S.eta[lane][0];
+        double bt = INFINITY;
+        int bc = 2, bk = 0;
+        for (int c = 0; c < nc; ++c) {
+          if (!(S.ctlo[lane][c] <= T)) continue;
+          const int32_t id = S.cid[lane][c];
+          ++n_rech;
+          if (id >= 0) {
+            double den = 0.0, ww = 0.0, pw = 0.0, w[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+              w[k] = k < d ? __dadd_rn(tr.X[(int64_t)id * d + k], -tr.X[(int64_t)g * d + k]) : 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+              if (k < d) den = __dadd_rn(den, __dmul_rn(S.u64[lane][k], w[k]));
+            if (!(den > 0.0)) continue;
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+              if (k < d) ww = __dadd_rn(ww, __dmul_rn(w[k], w[k]));
+#pragma unroll
+            for (int k = 0; k < D; ++k)
+              if (k < d) pw = __dadd_rn(pw, __dmul_rn(S.p64[lane][k], w[k]));
+            const double num = __dadd_rn(ww, -__dmul_rn(2.0, pw));
+            const double t = __ddiv_rn(num, __dmul_rn(2.0, den));
+            if (better(t, 0, id, bt, bc, bk)) {
+              bt = t;
+              bc = 0;
+              bk = id;
+            }
+          } else {
+            const int a = face_axis(id), s = face_side(id);
+            double va;
+            if (rs.mode == 0) va = rs.origins[r * d + a];
+            else va = tr.X[(int64_t)g * d + a];
+            const double t = __ddiv_rn(__dadd_rn(s ? 1.0 : 0.0, -va), S.u64[lane][a]);
+            if (better(t, 1, 2 * a + s, bt, bc, bk)) {
+              bt = t;
+              bc = 1;
+              bk = 2 * a + s;
+            }
+          }
+        }
+        ro.hit[op] = gen_from_key(bc, bk);
+        ro.t[op] = bt;
+        if (ro.screen_err) ro.screen_err[op] = (bt > 0.0 && bt < INFINITY) ? (float)((T - bt) / bt) : 0.f;
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    atomicAdd(&ctr->tiles, n_tiles);
+    atomicAdd(&ctr->pairs, n_pairs);
+  }
+  for (int o = 16; o; o >>= 1) n_rech += __shfl_xor_sync(kFull, n_rech, o);
+  if (lane == 0) atomicAdd(&ctr->rechecked, n_rech);
+}
+
+// ------------------------------------------------------------------------
+// VD_FP64: every pair in binary64, canonical order
+// ------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kWpb * 32) k_ray_fp64(TreeView tr, RaySource rs, RayOut ro, Counters* ctr,
+                                                        unsigned long long* work, const int32_t* subset) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpF64<D>& S = reinterpret_cast<WarpF64<D>*>(smem_raw)[wib];
+  const int d = tr.d;
+  const float B = tr.coord_abs;
+  unsigned long long n_tiles = 0;
+  const int64_t R = rs.R;
+  while (true) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(work, 1ull);
+    b = __shfl_sync(kFull, b, 0);
+    const int64_t b0 = (int64_t)b * 32;
+    if (b0 >= R) break;
+    const int64_t slot = b0 + lane;
+    const bool vr = slot < R;
+    const int64_t r = vr ? (subset ? (int64_t)subset[slot] : slot) : 0;
+    if (vr) {
+      double v[D], u[D];
+      int32_t eta[D + 1];
+      int m;
+      load_ray<D>(tr, rs, r, v, u, eta, m);
+      if (m < 1 || eta[0] < 0 || eta[0] >= tr.N) {  // g must be a node
+        atomicOr(&ctr->flags, kFlagBadInput);
+        m = 1;
+        eta[0] = 0;
+      }
+      const int32_t g = eta[0];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double gk = k < d ? tr.X[(int64_t)g * d + k] : 0.0;
+        S.u[lane][k] = u[k];
+        S.g[lane][k] = gk;
+        S.p[lane][k] = __dadd_rn(v[k], -gk);
+      }
+      for (int q = 0; q <= D; ++q) S.eta[lane][q] = q < m ? eta[q] : kNoId;
+      S.m[lane] = m;
+      double bt = INFINITY;
+      int bc = 2, bk = 0;
+      if (rs.box) {
+        for (int a = 0; a < d; ++a) {
+          if (u[a] == 0.0) continue;
+          const int s = u[a] > 0.0 ? 1 : 0;
+          const int32_t fid = face_id(a, s);
+          bool ex = false;
+          for (int q = 0; q < m; ++q) ex |= (eta[q] == fid);
+          if (ex) continue;
+          const double t = __ddiv_rn(__dadd_rn(s ? 1.0 : 0.0, -v[a]), u[a]);
+          if (better(t, 1, 2 * a + s, bt, bc, bk)) {
+            bt = t;
+            bc = 1;
+            bk = 2 * a + s;
+          }
+        }
+      }
+      S.bt[lane] = bt;
+      S.bcls[lane] = bc;
+      S.bkey[lane] = bk;
+    }
+    __syncwarp();
+    for (int rr = 0; rr < 32 && b0 + rr < R; ++rr) {
+      double u[D], gg[D], pp[D];
+      float u32[D], g32[D], p32[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        u[k] = S.u[rr][k];
+        gg[k] = S.g[rr][k];
+        pp[k] = S.p[rr][k];
+        u32[k] = __double2float_rn(u[k]);
+        g32[k] = __double2float_rn(gg[k]);
+        p32[k] = __double2float_rn(pp[k]);
+      }
+      const int m = S.m[rr];
+      double bt = S.bt[rr];
+      int bc = S.bcls[rr], bk = S.bkey[rr];
+      Ball<D> ball;
+      make_ball<D>(g32, p32, u32, __double2float_ru(bt) * (1.f + 4.f * kU32), B, ball);
+      auto leaf = [&](int64_t tile) {
+        const int32_t id = tr.ids[tile * kTile + lane];
+        bool ok = id != kNoId;
+        for (int q = 0; q < m; ++q) ok &= (id != S.eta[rr][q]);
+        double w[D], den = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          w[k] = k < d ? __dadd_rn(tr.x64[(tile * d + k) * kTile + lane], -gg[k]) : 0.0;
+          if (k < d) den = __dadd_rn(den, __dmul_rn(u[k], w[k]));
+        }
+        ok &= den > 0.0;
+        double t = INFINITY;
+        if (ok) {
+          double ww = 0.0, pw = 0.0;
+#pragma unroll
+          for (int k = 0; k < D; ++k)
+            if (k < d) ww = __dadd_rn(ww, __dmul_rn(w[k], w[k]));
+#pragma unroll
+          for (int k = 0; k < D; ++k)
+            if (k < d) pw = __dadd_rn(pw, __dmul_rn(pp[k], w[k]));
+          const double num = __dadd_rn(ww, -__dmul_rn(2.0, pw));
+          // division only when the pair can reach the current best
+          if (num <= 2.0 * bt * den * (1.0 + 0x1p-40)) t = __ddiv_rn(num, __dmul_rn(2.0, den));
+        }
+        const bool imp = ok && better(t, 0, id, bt, bc, bk);
+        if (__ballot_sync(kFull, imp) == 0) return;
+        double lt = imp ? t : bt;
+        int lc = imp ? 0 : bc, lk = imp ? id : bk;
+        warp_argmin(lt, lc, lk);
+        bt = lt;
+        bc = lc;
+        bk = lk;
+        make_ball<D>(g32, p32, u32, __double2float_ru(bt) * (1.f + 4.f * kU32), B, ball);
+      };
+      walk<D>(tr, S.stk, ball, lane, leaf, n_tiles);
+      if (lane == 0) {
+        S.bt[rr] = bt;
+        S.bcls[rr] = bc;
+        S.bkey[rr] = bk;
+      }
+      __syncwarp();
+    }
+    __syncwarp();
+    if (vr) {
+      const int64_t op = out_pos(rs, ro, r);
+      ro.hit[op] = gen_from_key(S.bcls[lane], S.bkey[lane]);
+      ro.t[op] = S.bt[lane];
+      if (ro.screen_err) ro.screen_err[op] = 0.f;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    atomicAdd(&ctr->tiles, n_tiles);
+    atomicAdd(&ctr->pairs, n_tiles * 32);
+  }
+}
+
+template <int D>
+__global__ void k_directions(uint64_t seed, uint32_t set, int64_t cell0, int64_t ncells, int64_t R, int d,
+                             double* out) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= ncells * R) return;
+  const int64_t i = q / R, k = q % R;
+  double u[D];
+  mc_direction<D>(seed, set, (uint32_t)(cell0 + i), (uint32_t)k, d, u);
+  for (int a = 0; a < d; ++a) out[q * d + a] = u[a];
+}
+
+template <int D>
+cudaError_t launch_ray_d(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision, Counters* ctr,
+                         unsigned long long* work, cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t batches = (rs.R + 31) / 32;
+  cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+  if (precision == VD_FP64) {
+    const size_t sm = sizeof(WarpF64<D>) * kWpb;
+    cudaFuncSetAttribute(k_ray_fp64<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ray_fp64<D>, kWpb * 32, sm);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1),
+                                                                 (batches + kWpb - 1) / kWpb));
+    k_ray_fp64<D><<<(unsigned)grid, kWpb * 32, sm, st>>>(tv, rs, ro, ctr, work, nullptr);
+  } else {
+    const size_t sm = sizeof(WarpMixed<D>) * kWpb;
+    cudaFuncSetAttribute(k_ray_mixed<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ray_mixed<D>, kWpb * 32, sm);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1),
+                                                                 (batches + kWpb - 1) / kWpb));
+    k_ray_mixed<D><<<(unsigned)grid, kWpb * 32, sm, st>>>(tv, rs, ro, ctr, work);
+  }
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_fp64_subset(const TreeView& tv, const RaySource& rs, const RayOut& ro, const int32_t* subset,
+                               int64_t n, Counters* ctr, unsigned long long* work, cudaStream_t st) {
+  RaySource r2 = rs;
+  r2.R = n;
+  cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+  const size_t sm = sizeof(WarpF64<D>) * kWpb;
+  cudaFuncSetAttribute(k_ray_fp64<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(4096, ((n + 31) / 32 + kWpb - 1) / kWpb));
+  k_ray_fp64<D><<<(unsigned)grid, kWpb * 32, sm, st>>>(tv, r2, ro, ctr, work, subset);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Dimension dispatch: d is padded up to the next instantiated D (the padded
+// coordinates are zero and contribute exact zeros to every sum).
+#define VD_DISPATCH_D(d, FN, ...)              \
+  ((d) <= 1   ? FN<1>(__VA_ARGS__)             \
+   : (d) <= 2 ? FN<2>(__VA_ARGS__)             \
+   : (d) <= 3 ? FN<3>(__VA_ARGS__)             \
+   : (d) <= 4 ? FN<4>(__VA_ARGS__)             \
+   : (d) <= 5 ? FN<5>(__VA_ARGS__)             \
+   : (d) <= 6 ? FN<6>(__VA_ARGS__)             \
+   : (d) <= 8 ? FN<8>(__VA_ARGS__)             \
+   : (d) <= 12 ? FN<12>(__VA_ARGS__)           \
+              : FN<16>(__VA_ARGS__))
+
+cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision,
+                           Counters* ctr, cudaStream_t st) {
+  if (rs.R <= 0) return cudaSuccess;
+  unsigned long long* work = reinterpret_cast<unsigned long long*>(&ctr->aux1);
+  cudaError_t e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rs, ro, precision, ctr, work, st);
+  if (e != cudaSuccess || precision == VD_FP64) return e;
+  // rays whose candidate list overflowed are redone on the binary64 path
+  unsigned long long nover = 0;
+  cudaMemcpyAsync(&nover, &ctr->overflow, sizeof(nover), cudaMemcpyDeviceToHost, st);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  if (nover > 0) {
+    const int64_t n = std::min<int64_t>((int64_t)nover, ro.overflow_cap);
+    e = VD_DISPATCH_D(tv.d, launch_fp64_subset, tv, rs, ro, ro.overflow_list, n, ctr, work, st);
+  }
+  return e;
+}
+
+cudaError_t launch_mc_directions(uint64_t seed, uint32_t set, int64_t cell0, int64_t ncells, int64_t R, int d,
+                                 double* out, cudaStream_t st) {
+  const int64_t n = ncells * R;
+  if (n <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((n + 127) / 128);
+#define VD_DIR(DD) k_directions<DD><<<grid, 128, 0, st>>>(seed, set, cell0, ncells, R, d, out)
+  if (d <= 4) VD_DIR(4);
+  else if (d <= 8) VD_DIR(8);
+  else VD_DIR(16);
+#undef VD_DIR
+  return cudaGetLastError();
+}
+
+}  // namespace vd

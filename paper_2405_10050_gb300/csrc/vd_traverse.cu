@@ -1,0 +1,821 @@
+// vd_traverse.cu -- exhaustive vertex traversal of the clipped Voronoi
+// diagram (Section 2.3, Algorithm 2), frontier-parallel.
+//
+// Algorithm 2 pops one vertex at a time; here a whole BFS level is processed
+// at once:
+//   expand : for every frontier vertex sigma and edge eta = sigma \ {e} with
+//            a node and edge counter G[eta] < 2, SearchDirection (binary64
+//            null vector of the edge's constraint rows) -> one ray;
+//   raycast: the generic RayCast kernels on the level's rays;
+//   commit : sigma' = sort(eta + hit) is inserted into a device hash of
+//            sorted generator tuples (two phases: claim a slot for the ray,
+//            then give each winning ray a vertex id), its coordinates are
+//            solved from the tuple in binary64, and G[eta'] += 1 for its
+//            edges (device hash of sorted d-tuples).
+// Seeds come from Descent (Algorithm 2): several nodes cast d rays each onto
+// successively lower-dimensional faces.  The box faces are generators with
+// negative ids, so no edge is unbounded.  The result is sorted into
+// lexicographic tuple order.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "vd_dev.cuh"
+
+namespace vd {
+
+cudaError_t radix_sort_u64(uint64_t* keys, int32_t* vals, uint64_t* ktmp, int32_t* vtmp, int64_t n,
+                           uint32_t* counts, unsigned long long* orand, cudaStream_t st);
+
+namespace {
+
+constexpr int32_t kEmpty = -1;
+constexpr int32_t kRayTag = INT32_MIN;  // slot claimed by a ray during a level: kRayTag | ray
+constexpr int kMaxProbe = 4096;
+
+struct Tables {
+  int d;
+  // vertices
+  int32_t* vt;       // [vcap][d+1]
+  double* vx;        // [vcap][d]
+  int64_t vcap;
+  int32_t* vslot;    // [vhcap]
+  int64_t vhmask;
+  unsigned long long* nv;
+  // edges
+  int32_t* et;       // [ecap][d]
+  int32_t* ecnt;     // [ecap]
+  int64_t ecap;
+  int32_t* eslot;    // [ehcap]
+  int64_t ehmask;
+  unsigned long long* ne;
+};
+
+__device__ __forceinline__ uint64_t mix64(uint64_t h) {
+  h ^= h >> 33;
+  h *= 0xff51afd7ed558ccdull;
+  h ^= h >> 33;
+  h *= 0xc4ceb9fe1a85ec53ull;
+  h ^= h >> 33;
+  return h;
+}
+
+__device__ __forceinline__ uint64_t hash_tuple(const int32_t* t, int L) {
+  uint64_t h = 0x9E3779B97F4A7C15ull * (uint64_t)(L + 1);
+  for (int q = 0; q < L; ++q) h = mix64(h ^ (uint64_t)(uint32_t)t[q] ^ ((uint64_t)q << 40));
+  return h;
+}
+
+__device__ __forceinline__ bool tuple_eq(const volatile int32_t* a, const int32_t* b, int L) {
+  for (int q = 0; q < L; ++q)
+    if (a[q] != b[q]) return false;
+  return true;
+}
+
+__device__ __forceinline__ void sort_small(int32_t* t, int L) {
+  for (int a = 1; a < L; ++a) {
+    const int32_t x = t[a];
+    int b = a - 1;
+    while (b >= 0 && t[b] > x) {
+      t[b + 1] = t[b];
+      --b;
+    }
+    t[b + 1] = x;
+  }
+}
+
+// Canonical vertex coordinates from the sorted tuple (same steps as the
+// definition: x0 = first node, y = r - x0, fixed axes from the faces,
+// rows 2 w_k . y = |w_k|^2 on the free axes, partial pivoting).
+__device__ bool vertex_coords(const double* X, int d, const int32_t* sig, double* r) {
+  int fixed[VD_MAX_D], side[VD_MAX_D];
+  for (int a = 0; a < d; ++a) fixed[a] = 0;
+  int nodes[VD_MAX_D + 1], m = 0;
+  for (int q = 0; q <= d; ++q) {
+    if (sig[q] >= 0) {
+      nodes[m++] = sig[q];
+      continue;
+    }
+    const int a = face_axis(sig[q]);
+    if (fixed[a]) return false;
+    fixed[a] = 1;
+    side[a] = face_side(sig[q]);
+  }
+  if (m < 1) return false;
+  const double* x0 = X + (int64_t)nodes[0] * d;
+  int freeax[VD_MAX_D], nf = 0;
+  double y[VD_MAX_D];
+  for (int a = 0; a < d; ++a) {
+    if (fixed[a]) y[a] = __dadd_rn(side[a] ? 1.0 : 0.0, -x0[a]);
+    else freeax[nf++] = a;
+  }
+  if (nf != m - 1) return false;
+  double M[VD_MAX_D][VD_MAX_D], b[VD_MAX_D];
+  for (int rr = 0; rr < nf; ++rr) {
+    const double* xk = X + (int64_t)nodes[rr + 1] * d;
+    double w[VD_MAX_D], ww = 0.0;
+    for (int a = 0; a < d; ++a) w[a] = __dadd_rn(xk[a], -x0[a]);
+    for (int a = 0; a < d; ++a) ww = __dadd_rn(ww, __dmul_rn(w[a], w[a]));
+    for (int a = 0; a < d; ++a)
+      if (fixed[a]) ww = __dadd_rn(ww, -__dmul_rn(__dmul_rn(2.0, w[a]), y[a]));
+    for (int c = 0; c < nf; ++c) M[rr][c] = __dmul_rn(2.0, w[freeax[c]]);
+    b[rr] = ww;
+  }
+  for (int c = 0; c < nf; ++c) {
+    int piv = c;
+    for (int rr = c + 1; rr < nf; ++rr)
+      if (fabs(M[rr][c]) > fabs(M[piv][c])) piv = rr;
+    if (M[piv][c] == 0.0) return false;
+    if (piv != c) {
+      for (int cc = 0; cc < nf; ++cc) {
+        const double tmp = M[c][cc];
+        M[c][cc] = M[piv][cc];
+        M[piv][cc] = tmp;
+      }
+      const double tb = b[c];
+      b[c] = b[piv];
+      b[piv] = tb;
+    }
+    for (int rr = c + 1; rr < nf; ++rr) {
+      const double f = __ddiv_rn(M[rr][c], M[c][c]);
+      for (int cc = c + 1; cc < nf; ++cc) M[rr][cc] = __dadd_rn(M[rr][cc], -__dmul_rn(f, M[c][cc]));
+      b[rr] = __dadd_rn(b[rr], -__dmul_rn(f, b[c]));
+    }
+  }
+  double z[VD_MAX_D];
+  for (int c = nf - 1; c >= 0; --c) {
+    double s = b[c];
+    for (int cc = c + 1; cc < nf; ++cc) s = __dadd_rn(s, -__dmul_rn(M[c][cc], z[cc]));
+    z[c] = __ddiv_rn(s, M[c][c]);
+  }
+  for (int c = 0; c < nf; ++c) y[freeax[c]] = z[c];
+  for (int a = 0; a < d; ++a) r[a] = fixed[a] ? (side[a] ? 1.0 : 0.0) : __dadd_rn(x0[a], y[a]);
+  return true;
+}
+
+// SearchDirection: unit null vector of the rows x_k - g (nodes of eta other
+// than its first node g) on the axes not fixed by eta's faces; complete
+// pivoting (first maximal |entry| in row-major order), the non-pivot column
+// set to 1, back substitution, u = z / |z|; sign so that the dropped node e
+// has u.(x_e - g) < 0, a dropped lower face u_a > 0, an upper face u_a < 0.
+__device__ bool search_direction(const double* X, int d, const int32_t* sig, int drop, double* u) {
+  int32_t eta[VD_MAX_D];
+  int m = 0;
+  for (int q = 0; q <= d; ++q)
+    if (q != drop) eta[m++] = sig[q];
+  int fixed[VD_MAX_D];
+  for (int a = 0; a < d; ++a) fixed[a] = 0;
+  int nodes[VD_MAX_D], mn = 0;
+  for (int q = 0; q < d; ++q) {
+    if (eta[q] >= 0) nodes[mn++] = eta[q];
+    else fixed[face_axis(eta[q])] = 1;
+  }
+  if (mn < 1) return false;
+  int freeax[VD_MAX_D], nf = 0;
+  for (int a = 0; a < d; ++a)
+    if (!fixed[a]) freeax[nf++] = a;
+  if (nf != mn) return false;
+  const double* g = X + (int64_t)nodes[0] * d;
+  const int nr = mn - 1;
+  double M[VD_MAX_D][VD_MAX_D];
+  for (int rr = 0; rr < nr; ++rr) {
+    const double* xk = X + (int64_t)nodes[rr + 1] * d;
+    for (int c = 0; c < nf; ++c) M[rr][c] = __dadd_rn(xk[freeax[c]], -g[freeax[c]]);
+  }
+  int colperm[VD_MAX_D];
+  for (int c = 0; c < nf; ++c) colperm[c] = c;
+  for (int c = 0; c < nr; ++c) {
+    int pr = c, pc = c;
+    double best = -1.0;
+    for (int rr = c; rr < nr; ++rr)
+      for (int cc = c; cc < nf; ++cc)
+        if (fabs(M[rr][cc]) > best) {
+          best = fabs(M[rr][cc]);
+          pr = rr;
+          pc = cc;
+        }
+    if (best == 0.0) return false;
+    if (pr != c)
+      for (int cc = 0; cc < nf; ++cc) {
+        const double tmp = M[c][cc];
+        M[c][cc] = M[pr][cc];
+        M[pr][cc] = tmp;
+      }
+    if (pc != c) {
+      for (int rr = 0; rr < nr; ++rr) {
+        const double tmp = M[rr][c];
+        M[rr][c] = M[rr][pc];
+        M[rr][pc] = tmp;
+      }
+      const int tp = colperm[c];
+      colperm[c] = colperm[pc];
+      colperm[pc] = tp;
+    }
+    for (int rr = c + 1; rr < nr; ++rr) {
+      const double f = __ddiv_rn(M[rr][c], M[c][c]);
+      for (int cc = c + 1; cc < nf; ++cc) M[rr][cc] = __dadd_rn(M[rr][cc], -__dmul_rn(f, M[c][cc]));
+    }
+  }
+  double zp[VD_MAX_D];
+  zp[nf - 1] = 1.0;
+  for (int c = nr - 1; c >= 0; --c) {
+    double s = -M[c][nf - 1];
+    for (int cc = c + 1; cc < nr; ++cc) s = __dadd_rn(s, -__dmul_rn(M[c][cc], zp[cc]));
+    zp[c] = __ddiv_rn(s, M[c][c]);
+  }
+  double z[VD_MAX_D];
+  for (int c = 0; c < nf; ++c) z[colperm[c]] = zp[c];
+  double nz = 0.0;
+  for (int c = 0; c < nf; ++c) nz = __dadd_rn(nz, __dmul_rn(z[c], z[c]));
+  nz = __dsqrt_rn(nz);
+  for (int a = 0; a < d; ++a) u[a] = 0.0;
+  for (int c = 0; c < nf; ++c) u[freeax[c]] = __ddiv_rn(z[c], nz);
+  const int32_t e = sig[drop];
+  bool flip;
+  if (e >= 0) {
+    const double* xe = X + (int64_t)e * d;
+    double den = 0.0;
+    for (int a = 0; a < d; ++a) den = __dadd_rn(den, __dmul_rn(u[a], __dadd_rn(xe[a], -g[a])));
+    if (den == 0.0) return false;
+    flip = den > 0.0;
+  } else {
+    const int a = face_axis(e);
+    if (u[a] == 0.0) return false;
+    flip = face_side(e) ? (u[a] > 0.0) : (u[a] < 0.0);
+  }
+  if (flip)
+    for (int a = 0; a < d; ++a) u[a] = -u[a];
+  return true;
+}
+
+__device__ __forceinline__ int32_t vslot_load(const int32_t* p) { return *(const volatile int32_t*)p; }
+
+// Looks up an edge counter; returns 0 if absent.
+__device__ int edge_count(const Tables& T, const int32_t* eta) {
+  const int L = T.d;
+  uint64_t h = hash_tuple(eta, L) & (uint64_t)T.ehmask;
+  for (int pr = 0; pr < kMaxProbe; ++pr) {
+    const int32_t s = vslot_load(&T.eslot[h]);
+    if (s == kEmpty) return 0;
+    if (tuple_eq(T.et + (int64_t)s * L, eta, L)) return T.ecnt[s];
+    h = (h + 1) & (uint64_t)T.ehmask;
+  }
+  return 0;
+}
+
+// G[eta] += 1, inserting eta if absent.
+__device__ void edge_increment(const Tables& T, const int32_t* eta, unsigned* flags) {
+  const int L = T.d;
+  uint64_t h = hash_tuple(eta, L) & (uint64_t)T.ehmask;
+  int32_t mine = kEmpty;
+  for (int pr = 0; pr < kMaxProbe; ++pr) {
+    int32_t s = vslot_load(&T.eslot[h]);
+    if (s == kEmpty) {
+      if (mine == kEmpty) {
+        const unsigned long long e = atomicAdd(T.ne, 1ull);
+        if ((int64_t)e >= T.ecap) {
+          atomicOr(flags, kFlagHashFull);
+          return;
+        }
+        mine = (int32_t)e;
+        for (int q = 0; q < L; ++q) T.et[(int64_t)mine * L + q] = eta[q];
+        T.ecnt[mine] = 0;
+        __threadfence();
+      }
+      s = atomicCAS(&T.eslot[h], kEmpty, mine);
+      if (s == kEmpty) {
+        atomicAdd(&T.ecnt[mine], 1);
+        return;
+      }
+      __threadfence();
+    }
+    __threadfence();  // the entry's tuple was published before its slot
+    if (tuple_eq(T.et + (int64_t)s * L, eta, L)) {
+      atomicAdd(&T.ecnt[s], 1);
+      return;  // our reserved entry (if any) stays unused
+    }
+    h = (h + 1) & (uint64_t)T.ehmask;
+  }
+  atomicOr(flags, kFlagHashFull);
+}
+
+// ---- level kernels ----------------------------------------------------------
+__global__ void k_expand(Tables T, const double* X, const int32_t* frontier, int64_t nf, double* ro, double* rd,
+                         int32_t* reta, unsigned long long* nrays, int64_t rcap, unsigned* flags) {
+  const int d = T.d;
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nf * (d + 1)) return;
+  const int64_t f = q / (d + 1);
+  const int drop = (int)(q % (d + 1));
+  const int32_t v = frontier[f];
+  int32_t sig[VD_MAX_D + 1], eta[VD_MAX_D];
+  for (int a = 0; a <= d; ++a) sig[a] = T.vt[(int64_t)v * (d + 1) + a];
+  int m = 0, hasnode = 0;
+  for (int a = 0; a <= d; ++a)
+    if (a != drop) {
+      eta[m] = sig[a];
+      hasnode |= sig[a] >= 0;
+      ++m;
+    }
+  if (!hasnode) return;
+  if (edge_count(T, eta) >= 2) return;
+  double u[VD_MAX_D];
+  if (!search_direction(X, d, sig, drop, u)) {
+    atomicOr(flags, kFlagDegenerate);
+    return;
+  }
+  const unsigned long long r = atomicAdd(nrays, 1ull);
+  if ((int64_t)r >= rcap) {
+    atomicOr(flags, kFlagQueue);
+    return;
+  }
+  // eta row: reference node g (first node of eta) first
+  int gpos = 0;
+  while (eta[gpos] < 0) ++gpos;
+  reta[r * d + 0] = eta[gpos];
+  int k = 1;
+  for (int a = 0; a < d; ++a)
+    if (a != gpos) reta[r * d + k++] = eta[a];
+  for (int a = 0; a < d; ++a) {
+    ro[r * d + a] = T.vx[(int64_t)v * d + a];
+    rd[r * d + a] = u[a];
+  }
+}
+
+// Phase 1 of the commit: claim the tuple's slot for this ray (or find it).
+__global__ void k_commit_claim(Tables T, const int32_t* reta, const int32_t* hit, int64_t nr, int32_t* cand,
+                               int64_t* cslot, unsigned* flags) {
+  const int d = T.d, L = d + 1;
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  int32_t sig[VD_MAX_D + 1];
+  for (int a = 0; a < d; ++a) sig[a] = reta[r * d + a];
+  sig[d] = hit[r];
+  cslot[r] = -1;
+  if (sig[d] == kNoId) {
+    atomicOr(flags, kFlagDegenerate);
+    return;
+  }
+  sort_small(sig, L);
+  for (int a = 0; a < L; ++a) cand[r * L + a] = sig[a];
+  __threadfence();
+  uint64_t h = hash_tuple(sig, L) & (uint64_t)T.vhmask;
+  for (int pr = 0; pr < kMaxProbe; ++pr) {
+    int32_t s = vslot_load(&T.vslot[h]);
+    if (s == kEmpty) {
+      s = atomicCAS(&T.vslot[h], kEmpty, kRayTag | (int32_t)r);
+      if (s == kEmpty) {
+        cslot[r] = (int64_t)h;  // this ray owns the new vertex
+        return;
+      }
+      __threadfence();
+    }
+    __threadfence();  // the other ray's tuple was published before its claim
+    const volatile int32_t* other = (s & kRayTag) ? (cand + (int64_t)(s & ~kRayTag) * L) : (T.vt + (int64_t)s * L);
+    if (tuple_eq(other, sig, L)) return;  // known vertex or claimed by another ray
+    h = (h + 1) & (uint64_t)T.vhmask;
+  }
+  atomicOr(flags, kFlagHashFull);
+}
+
+// Phase 2: winners get vertex ids, coordinates, frontier slots and edges.
+__global__ void k_commit_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot, int64_t nr,
+                                int32_t* next, unsigned long long* nnext, unsigned* flags) {
+  const int d = T.d, L = d + 1;
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nr || cslot[r] < 0) return;
+  const unsigned long long v = atomicAdd(T.nv, 1ull);
+  if ((int64_t)v >= T.vcap) {
+    atomicOr(flags, kFlagHashFull);
+    return;
+  }
+  int32_t sig[VD_MAX_D + 1];
+  for (int a = 0; a < L; ++a) sig[a] = cand[r * L + a];
+  for (int a = 0; a < L; ++a) T.vt[(int64_t)v * L + a] = sig[a];
+  double x[VD_MAX_D];
+  if (!vertex_coords(X, d, sig, x)) atomicOr(flags, kFlagDegenerate);
+  for (int a = 0; a < d; ++a) T.vx[(int64_t)v * d + a] = x[a];
+  __threadfence();
+  T.vslot[cslot[r]] = (int32_t)v;
+  next[atomicAdd(nnext, 1ull)] = (int32_t)v;
+  for (int q = 0; q <= d; ++q) {
+    int32_t eta[VD_MAX_D];
+    int m = 0, hasnode = 0;
+    for (int a = 0; a <= d; ++a)
+      if (a != q) {
+        eta[m++] = sig[a];
+        hasnode |= sig[a] >= 0;
+      }
+    if (hasnode) edge_increment(T, eta, flags);
+  }
+}
+
+// ---- Descent seeding ----------------------------------------------------------
+// Seed s starts at node nodes[s] with sigma = {node}, r = x_node; each step
+// draws a direction (the MC generator on set 0xFFFFFFFF, cell = node, ray =
+// step), removes its components along the span of the current constraint
+// rows (x_k - g for the other nodes, e_a for faces; modified Gram-Schmidt),
+// and casts a ray with eta = sigma.
+__global__ void k_descent_dir(const double* X, int d, int64_t ns, const int32_t* snode, const int32_t* ssig,
+                              const int* sm, const double* sr, int step, double* ro, double* rd, int32_t* reta,
+                              int* alive) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  // a dead seed still casts a valid ray (its result is ignored)
+  for (int a = 0; a < d; ++a) {
+    ro[s * d + a] = X[(int64_t)snode[s] * d + a];
+    rd[s * d + a] = a == 0 ? 1.0 : 0.0;
+  }
+  reta[s * (d + 1)] = snode[s];
+  for (int k = 1; k <= d; ++k) reta[s * (d + 1) + k] = kNoId;
+  if (!alive[s]) return;
+  const int m = sm[s];
+  const int32_t* sig = ssig + s * (VD_MAX_D + 1);
+  double u[VD_MAX_D];
+  mc_direction<VD_MAX_D>(0x5EEDull, 0xFFFFFFFFu, (uint32_t)snode[s], (uint32_t)step, d, u);
+  int32_t g = -1;
+  for (int q = 0; q < m; ++q)
+    if (sig[q] >= 0 && (g < 0 || sig[q] < g)) g = sig[q];
+  double B[VD_MAX_D + 1][VD_MAX_D];
+  int nb = 0;
+  for (int q = 0; q < m; ++q) {
+    if (sig[q] == g) continue;
+    if (sig[q] >= 0)
+      for (int a = 0; a < d; ++a) B[nb][a] = X[(int64_t)sig[q] * d + a] - X[(int64_t)g * d + a];
+    else {
+      for (int a = 0; a < d; ++a) B[nb][a] = 0.0;
+      B[nb][face_axis(sig[q])] = 1.0;
+    }
+    ++nb;
+  }
+  for (int q = 0; q < nb; ++q) {
+    for (int q2 = 0; q2 < q; ++q2) {
+      double dp = 0.0;
+      for (int a = 0; a < d; ++a) dp += B[q][a] * B[q2][a];
+      for (int a = 0; a < d; ++a) B[q][a] -= dp * B[q2][a];
+    }
+    double nn = 0.0;
+    for (int a = 0; a < d; ++a) nn += B[q][a] * B[q][a];
+    nn = sqrt(nn);
+    if (nn == 0.0) {
+      alive[s] = 0;
+      return;
+    }
+    for (int a = 0; a < d; ++a) B[q][a] /= nn;
+  }
+  for (int q = 0; q < nb; ++q) {
+    double dp = 0.0;
+    for (int a = 0; a < d; ++a) dp += u[a] * B[q][a];
+    for (int a = 0; a < d; ++a) u[a] -= dp * B[q][a];
+  }
+  for (int q = 0; q < m; ++q)
+    if (sig[q] < 0) u[face_axis(sig[q])] = 0.0;
+  double nu = 0.0;
+  for (int a = 0; a < d; ++a) nu += u[a] * u[a];
+  nu = sqrt(nu);
+  if (!(nu > 1e-12)) {
+    alive[s] = 0;
+    return;
+  }
+  for (int a = 0; a < d; ++a) {
+    rd[s * d + a] = u[a] / nu;
+    ro[s * d + a] = sr[s * VD_MAX_D + a];
+  }
+  int k = 1;
+  reta[s * (d + 1) + 0] = g;
+  for (int q = 0; q < m; ++q)
+    if (sig[q] != g) reta[s * (d + 1) + k++] = sig[q];
+  for (; k <= d; ++k) reta[s * (d + 1) + k] = kNoId;
+}
+
+__global__ void k_descent_update(int d, int64_t ns, int32_t* ssig, int* sm, double* sr, const double* rd,
+                                 const int32_t* hit, const double* t, int* alive) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= ns || !alive[s]) return;
+  if (hit[s] == kNoId || !(t[s] < INFINITY)) {
+    alive[s] = 0;
+    return;
+  }
+  for (int a = 0; a < d; ++a) sr[s * VD_MAX_D + a] += t[s] * rd[s * d + a];
+  ssig[s * (VD_MAX_D + 1) + sm[s]] = hit[s];
+  sm[s] += 1;
+}
+
+// Seeds that reached d+1 generators become rays of a pseudo level: their
+// tuples are inserted like the commit of a level (cand rows and claim).
+__global__ void k_descent_cand(int d, int64_t ns, const int32_t* ssig, const int* sm, const int* alive,
+                               int32_t* reta, int32_t* hit) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  if (!alive[s] || sm[s] != d + 1) {
+    hit[s] = kNoId;
+    for (int a = 0; a < d; ++a) reta[s * d + a] = kNoId;
+    return;
+  }
+  for (int a = 0; a < d; ++a) reta[s * d + a] = ssig[s * (VD_MAX_D + 1) + a];
+  hit[s] = ssig[s * (VD_MAX_D + 1) + d];
+}
+
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+__global__ void k_iota(int32_t* p, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = (int32_t)i;
+}
+
+__global__ void k_col_keys(const int32_t* vt, int L, int c, const int32_t* perm, int64_t n, uint64_t* keys,
+                           int32_t* vals) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t v = perm[i];
+  keys[i] = (uint64_t)((uint32_t)vt[(int64_t)v * L + c] ^ 0x80000000u);
+  vals[i] = v;
+}
+
+__global__ void k_gather_out(const int32_t* vt, const double* vx, int d, const int32_t* perm, int64_t n,
+                             int32_t* ot, double* ox) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t v = perm[i];
+  for (int a = 0; a <= d; ++a) ot[i * (d + 1) + a] = vt[(int64_t)v * (d + 1) + a];
+  for (int a = 0; a < d; ++a) ox[i * d + a] = vx[(int64_t)v * d + a];
+}
+
+inline unsigned nb(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+int64_t pow2_at_least(int64_t x) {
+  int64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+// Expected vertices per cell (uniform nodes) for sizing, from the paper's
+// table of vertices per cell (d = 2..7) extended by a factor d+2 per
+// dimension.
+static double vertices_per_cell(int d) {
+  static const double t[] = {2, 2, 6.6, 29.2, 191, 1250, 9720, 91900};
+  if (d <= 7) return t[d];
+  double v = t[7];
+  for (int k = 8; k <= d; ++k) v *= (k + 2);
+  return v;
+}
+
+cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, DevBufs& out_bufs,
+                              int32_t** tuples_out, double** coords_out, int64_t* nv_out, vd_stats* stats,
+                              Counters* ctr, cudaStream_t st, char* err, size_t errlen) {
+  const int d = tv.d;
+  const int L = d + 1;
+  const int64_t N = tv.N;
+  cudaError_t e;
+  DevBufs tb;
+  struct Guard {
+    DevBufs& b;
+    ~Guard() { b.release(); }
+  } guard{tb};
+#define VD_TRY(x)                     \
+  do {                                \
+    e = (x);                          \
+    if (e != cudaSuccess) return e;   \
+  } while (0)
+  int64_t vcap = cfg.hash_capacity > 0 ? cfg.hash_capacity
+                                       : (int64_t)std::min(2.0e9, std::max(1.0e5, 2.0 * N * vertices_per_cell(d) / L +
+                                                                                       64.0 * (1 << std::min(d, 16)) +
+                                                                                       8.0 * N * d));
+  vcap = std::min<int64_t>(vcap, (int64_t)1 << 30);
+  const int64_t ecap = std::min<int64_t>((int64_t)1 << 30, vcap * L / 2 + vcap / 4 + 1024);
+  const int64_t vh = pow2_at_least(2 * vcap), eh = pow2_at_least(2 * ecap);
+  Tables T;
+  T.d = d;
+  T.vcap = vcap;
+  T.ecap = ecap;
+  T.vhmask = vh - 1;
+  T.ehmask = eh - 1;
+  VD_TRY(tb.alloc_n(&T.vt, (size_t)vcap * L));
+  VD_TRY(tb.alloc_n(&T.vx, (size_t)vcap * d));
+  VD_TRY(tb.alloc_n(&T.vslot, (size_t)vh));
+  VD_TRY(tb.alloc_n(&T.et, (size_t)ecap * d));
+  VD_TRY(tb.alloc_n(&T.ecnt, (size_t)ecap));
+  VD_TRY(tb.alloc_n(&T.eslot, (size_t)eh));
+  unsigned long long* cnts = nullptr;  // nv, ne, nrays, nnext
+  VD_TRY(tb.alloc_n(&cnts, 4));
+  T.nv = cnts + 0;
+  T.ne = cnts + 1;
+  unsigned* flags = &ctr->flags;
+  VD_TRY(cudaMemsetAsync(cnts, 0, 4 * sizeof(unsigned long long), st));
+  k_fill_i32<<<nb(vh), 256, 0, st>>>(T.vslot, vh, kEmpty);
+  k_fill_i32<<<nb(eh), 256, 0, st>>>(T.eslot, eh, kEmpty);
+
+  // level buffers, grown on demand
+  int64_t rcap = 0;
+  double *ro = nullptr, *rd = nullptr, *rt = nullptr;
+  int32_t *reta = nullptr, *rhit = nullptr, *cand = nullptr;
+  int64_t* cslot = nullptr;
+  int32_t *ovl = nullptr;
+  int64_t ovcap = 0;
+  auto grow = [&](int64_t need) -> cudaError_t {
+    if (need <= rcap) return cudaSuccess;
+    int64_t c = std::max<int64_t>(need, rcap * 2);
+    c = std::max<int64_t>(c, 4096);
+    for (void* p : {(void*)ro, (void*)rd, (void*)rt, (void*)reta, (void*)rhit, (void*)cand, (void*)cslot,
+                    (void*)ovl}) {
+      if (!p) continue;
+      cudaFree(p);
+      tb.ptrs.erase(std::remove(tb.ptrs.begin(), tb.ptrs.end(), p), tb.ptrs.end());
+    }
+    rcap = c;
+    ovcap = c;
+    cudaError_t ee;
+    if ((ee = tb.alloc_n(&ro, (size_t)c * d)) || (ee = tb.alloc_n(&rd, (size_t)c * d)) ||
+        (ee = tb.alloc_n(&rt, (size_t)c)) || (ee = tb.alloc_n(&reta, (size_t)c * L)) ||
+        (ee = tb.alloc_n(&rhit, (size_t)c)) ||
+        (ee = tb.alloc_n(&cand, (size_t)c * L)) || (ee = tb.alloc_n(&cslot, (size_t)c)) ||
+        (ee = tb.alloc_n(&ovl, (size_t)c)))
+      return ee;
+    return cudaSuccess;
+  };
+  auto read_flags = [&](unsigned* hf) -> cudaError_t {
+    cudaError_t ee = cudaMemcpyAsync(hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    if (ee == cudaSuccess) ee = cudaStreamSynchronize(st);
+    return ee;
+  };
+  auto run_rays = [&](int64_t nr, int stride) -> cudaError_t {
+    RaySource rs;
+    rs.mode = 0;
+    rs.R = nr;
+    rs.origins = ro;
+    rs.dirs = rd;
+    rs.eta = reta;
+    rs.eta_stride = stride;
+    rs.box = 1;
+    RayOut rout;
+    rout.hit = rhit;
+    rout.t = rt;
+    rout.overflow_list = ovl;
+    rout.overflow_cap = ovcap;
+    cudaError_t ee = cudaMemsetAsync(&ctr->overflow, 0, sizeof(unsigned long long), st);
+    if (ee != cudaSuccess) return ee;
+    return launch_raycast(tv, rs, rout, precision, ctr, st);
+  };
+
+  // ---- seeds by Descent ----
+  const int64_t ns = std::min<int64_t>(N, 64);
+  VD_TRY(grow(std::max<int64_t>(ns, 4096)));
+  int32_t *snode = nullptr, *ssig = nullptr;
+  int *sm = nullptr, *alive = nullptr;
+  double* sr = nullptr;
+  VD_TRY(tb.alloc_n(&snode, ns));
+  VD_TRY(tb.alloc_n(&ssig, (size_t)ns * (VD_MAX_D + 1)));
+  VD_TRY(tb.alloc_n(&sm, ns));
+  VD_TRY(tb.alloc_n(&alive, ns));
+  VD_TRY(tb.alloc_n(&sr, (size_t)ns * VD_MAX_D));
+  {
+    std::vector<int32_t> hn(ns), hsig(ns * (VD_MAX_D + 1), kNoId);
+    std::vector<int> hm(ns, 1), ha(ns, 1);
+    for (int64_t s = 0; s < ns; ++s) {
+      hn[s] = (int32_t)((s * N) / ns);
+      hsig[s * (VD_MAX_D + 1)] = hn[s];
+    }
+    VD_TRY(cudaMemcpyAsync(snode, hn.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    VD_TRY(cudaMemcpyAsync(ssig, hsig.data(), hsig.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    VD_TRY(cudaMemcpyAsync(sm, hm.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
+    VD_TRY(cudaMemcpyAsync(alive, ha.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
+    std::vector<double> hr(ns * VD_MAX_D, 0.0);
+    std::vector<double> hx(ns * d);
+    for (int64_t s = 0; s < ns; ++s)
+      VD_TRY(cudaMemcpyAsync(hr.data() + s * VD_MAX_D, tv.X + (int64_t)hn[s] * d, d * sizeof(double),
+                             cudaMemcpyDeviceToHost, st));
+    VD_TRY(cudaStreamSynchronize(st));
+    VD_TRY(cudaMemcpyAsync(sr, hr.data(), hr.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  int64_t raycasts = 0;
+  for (int step = 0; step < d; ++step) {
+    k_descent_dir<<<nb(ns, 64), 64, 0, st>>>(tv.X, d, ns, snode, ssig, sm, sr, step, ro, rd, reta, alive);
+    VD_TRY(cudaGetLastError());
+    VD_TRY(run_rays(ns, L));
+    raycasts += ns;
+    k_descent_update<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, sr, rd, rhit, rt, alive);
+    VD_TRY(cudaGetLastError());
+  }
+  k_descent_cand<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, alive, reta, rhit);
+  // insert the seeds as the first level
+  int32_t *front = nullptr, *next = nullptr;
+  int64_t fcap = std::max<int64_t>(ns, 4096);
+  VD_TRY(tb.alloc_n(&front, fcap));
+  VD_TRY(tb.alloc_n(&next, fcap));
+  unsigned long long* nrays = cnts + 2;
+  unsigned long long* nnext = cnts + 3;
+  VD_TRY(cudaMemsetAsync(nnext, 0, sizeof(unsigned long long), st));
+  k_commit_claim<<<nb(ns), 256, 0, st>>>(T, reta, rhit, ns, cand, cslot, flags);
+  // seeds that did not reach a vertex were marked with hit = kNoId: clear the
+  // degenerate flag they raised (a missing seed is not an error)
+  {
+    unsigned hf = 0;
+    VD_TRY(read_flags(&hf));
+    if (hf & kFlagDegenerate) {
+      unsigned clr = hf & ~kFlagDegenerate;
+      VD_TRY(cudaMemcpyAsync(flags, &clr, sizeof(unsigned), cudaMemcpyHostToDevice, st));
+    }
+  }
+  k_commit_finish<<<nb(ns), 256, 0, st>>>(T, tv.X, cand, cslot, ns, front, nnext, flags);
+  unsigned long long hn2[4];
+  VD_TRY(cudaMemcpyAsync(hn2, cnts, sizeof(hn2), cudaMemcpyDeviceToHost, st));
+  VD_TRY(cudaStreamSynchronize(st));
+  int64_t nf = (int64_t)hn2[3];
+  if (nf == 0) {
+    snprintf(err, errlen, "Descent found no seed vertex");
+    return cudaErrorUnknown;
+  }
+  int64_t levels = 0;
+  const int64_t max_levels = cfg.max_levels > 0 ? cfg.max_levels : (int64_t)1 << 20;
+  while (nf > 0) {
+    if (levels >= max_levels) {
+      snprintf(err, errlen, "traversal stopped at the level cap %lld", (long long)max_levels);
+      return cudaErrorUnknown;
+    }
+    ++levels;
+    VD_TRY(grow(nf * L));
+    if (fcap < nf * L) {
+      // the next frontier holds at most one vertex per ray
+      int32_t* nn = nullptr;
+      VD_TRY(tb.alloc_n(&nn, (size_t)nf * L));
+      tb.ptrs.erase(std::remove(tb.ptrs.begin(), tb.ptrs.end(), (void*)next), tb.ptrs.end());
+      cudaFree(next);
+      next = nn;
+      fcap = nf * L;
+      // front must hold nf*L too for the swap below
+      int32_t* nfb = nullptr;
+      VD_TRY(tb.alloc_n(&nfb, (size_t)fcap));
+      VD_TRY(cudaMemcpyAsync(nfb, front, nf * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+      tb.ptrs.erase(std::remove(tb.ptrs.begin(), tb.ptrs.end(), (void*)front), tb.ptrs.end());
+      VD_TRY(cudaStreamSynchronize(st));
+      cudaFree(front);
+      front = nfb;
+    }
+    VD_TRY(cudaMemsetAsync(cnts + 2, 0, 2 * sizeof(unsigned long long), st));
+    k_expand<<<nb(nf * L, 128), 128, 0, st>>>(T, tv.X, front, nf, ro, rd, reta, nrays, rcap, flags);
+    VD_TRY(cudaGetLastError());
+    unsigned long long hr = 0;
+    VD_TRY(cudaMemcpyAsync(&hr, nrays, sizeof(hr), cudaMemcpyDeviceToHost, st));
+    VD_TRY(cudaStreamSynchronize(st));
+    const int64_t nr = std::min<int64_t>((int64_t)hr, rcap);
+    if (nr > 0) {
+      VD_TRY(run_rays(nr, d));
+      raycasts += nr;
+      k_commit_claim<<<nb(nr), 256, 0, st>>>(T, reta, rhit, nr, cand, cslot, flags);
+      k_commit_finish<<<nb(nr), 256, 0, st>>>(T, tv.X, cand, cslot, nr, next, nnext, flags);
+      VD_TRY(cudaGetLastError());
+    }
+    unsigned long long hc[4];
+    unsigned hf = 0;
+    VD_TRY(cudaMemcpyAsync(hc, cnts, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    VD_TRY(read_flags(&hf));
+    if (hf & (kFlagHashFull | kFlagQueue | kFlagDegenerate | kFlagCandOverflow | kFlagBadInput)) break;
+    nf = (int64_t)hc[3];
+    std::swap(front, next);
+  }
+  unsigned long long hc[4];
+  VD_TRY(cudaMemcpyAsync(hc, cnts, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  VD_TRY(cudaStreamSynchronize(st));
+  const int64_t nv = std::min<int64_t>((int64_t)hc[0], vcap);
+  // lexicographic order: stable LSD sort by the tuple columns, last first
+  int32_t *perm = nullptr, *ptmp = nullptr;
+  uint64_t *keys = nullptr, *ktmp = nullptr;
+  uint32_t* counts = nullptr;
+  unsigned long long* orand = nullptr;
+  const int64_t nvv = std::max<int64_t>(nv, 1);
+  VD_TRY(tb.alloc_n(&perm, nvv));
+  VD_TRY(tb.alloc_n(&ptmp, nvv));
+  VD_TRY(tb.alloc_n(&keys, nvv));
+  VD_TRY(tb.alloc_n(&ktmp, nvv));
+  VD_TRY(tb.alloc_n(&counts, (size_t)256 * (nvv / 4096 + 2)));
+  VD_TRY(tb.alloc_n(&orand, 2));
+  k_iota<<<nb(nvv), 256, 0, st>>>(perm, nv);
+  for (int c = d; c >= 0; --c) {
+    k_col_keys<<<nb(nvv), 256, 0, st>>>(T.vt, L, c, perm, nv, keys, ptmp);
+    VD_TRY(radix_sort_u64(keys, ptmp, ktmp, perm, nv, counts, orand, st));
+    VD_TRY(cudaMemcpyAsync(perm, ptmp, nv * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  }
+  int32_t* ot = nullptr;
+  double* ox = nullptr;
+  VD_TRY(out_bufs.alloc_n(&ot, (size_t)nvv * L));
+  VD_TRY(out_bufs.alloc_n(&ox, (size_t)nvv * d));
+  k_gather_out<<<nb(nvv), 256, 0, st>>>(T.vt, T.vx, d, perm, nv, ot, ox);
+  VD_TRY(cudaStreamSynchronize(st));
+  VD_TRY(cudaGetLastError());
+  *tuples_out = ot;
+  *coords_out = ox;
+  *nv_out = nv;
+  stats->levels = levels;
+  stats->vertices = nv;
+  stats->rays = raycasts;
+  return cudaSuccess;
+#undef VD_TRY
+}
+
+}  // namespace vd

@@ -1,0 +1,128 @@
+"""GPU parity of the RayCast (Section 2.2, Eq. (t), Algorithm 1) against the
+FP64 oracle: hit ids bit-exact and t bit-identical (both evaluate Eq. (t) in
+binary64 in the same canonical order), for the plain FP64 path and the
+binary32-screened path, at sizes spanning many tiles with a ragged tail."""
+import numpy as np
+import pytest
+
+from gpu_util import edge_rays, need_cuda, random_unit
+from paper_2405_10050_gb300 import NO_ID, VD_FP32, VD_FP64, Voronoi, synth
+
+pytestmark = pytest.mark.gpu
+PRECS = [VD_FP64, VD_FP32]
+
+
+def _run(X, O, U, E, prec, box=True):
+    torch = need_cuda()
+    vor = Voronoi(X, precision=prec, box=box)
+    hit, t, se = vor.raycast(O, U, E, screen_err=True)
+    st = vor.stats()
+    vor.close()
+    return hit.cpu().numpy(), t.cpu().numpy(), se.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("d,N", [(1, 517), (2, 2049), (3, 3001), (4, 2500), (5, 1999), (7, 1500), (8, 1200),
+                                 (12, 800), (16, 1000)])
+def test_rays_from_nodes(orc, prec, d, N):
+    X = synth.uniform(N, d, seed=100 + d)
+    rng = np.random.default_rng(d)
+    R = 3000
+    cells = rng.integers(0, N, R).astype(np.int32)
+    U = random_unit(rng, R, d)
+    h0, t0 = orc.raycast(X, X[cells], U, cells)
+    h1, t1, se, st = _run(X, X[cells], U, cells[:, None], prec)
+    assert np.array_equal(h0, h1)
+    assert np.array_equal(t0, t1)
+    if prec == VD_FP32:
+        # (T - t) / t: the binary32 upper bound never undercuts the exact t;
+        # its width is set by the absolute binary32 error of the coordinates
+        assert np.all(se >= 0) and np.median(se) < 1e-2
+        assert st["rechecked"] >= R
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("d,N", [(2, 300), (3, 200), (4, 120), (5, 80)])
+def test_rays_along_edges(orc, prec, d, N):
+    """Rays of the traversal: origin a vertex, eta its d remaining generators."""
+    X = synth.uniform(N, d, seed=7 + d)
+    tuples, coords, _ = orc.vertices(X)
+    O, U, E = edge_rays(orc, X, tuples, coords, 4000, np.random.default_rng(1))
+    h0, t0 = orc.raycast(X, O, U, E)
+    h1, t1, _, _ = _run(X, O, U, E, prec)
+    assert np.array_equal(h0, h1)
+    assert np.array_equal(t0, t1)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_gaussian_mixture_nodes(orc, prec):
+    X = synth.gaussian_mixture(4000, 6, 8, 0.05, seed=3)
+    rng = np.random.default_rng(2)
+    cells = rng.integers(0, 4000, 2000).astype(np.int32)
+    U = random_unit(rng, 2000, 6)
+    h0, t0 = orc.raycast(X, X[cells], U, cells)
+    h1, t1, _, _ = _run(X, X[cells], U, cells[:, None], prec)
+    assert np.array_equal(h0, h1) and np.array_equal(t0, t1)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_edge_cases(orc, prec):
+    # one node: only faces can be hit
+    X = np.array([[0.3, 0.6, 0.2]])
+    U = random_unit(np.random.default_rng(0), 64, 3)
+    h0, t0 = orc.raycast(X, np.repeat(X, 64, 0), U, np.zeros(64, np.int32))
+    h1, t1, _, _ = _run(X, np.repeat(X, 64, 0), U, np.zeros((64, 1), np.int32), prec)
+    assert np.all(h1 < 0) and np.array_equal(h0, h1) and np.array_equal(t0, t1)
+    # exactly one tile, and one tile plus one node
+    for N in (32, 33, 64, 1025):
+        X = synth.uniform(N, 2, seed=N)
+        cells = np.arange(N, dtype=np.int32)
+        U = random_unit(np.random.default_rng(N), N, 2)
+        h0, t0 = orc.raycast(X, X, U, cells)
+        h1, t1, _, _ = _run(X, X, U, cells[:, None], prec)
+        assert np.array_equal(h0, h1) and np.array_equal(t0, t1)
+    # box off: rays that leave the hull of the nodes miss
+    X = synth.uniform(50, 2, seed=5)
+    U = random_unit(np.random.default_rng(5), 200, 2)
+    cells = np.random.default_rng(6).integers(0, 50, 200).astype(np.int32)
+    h0, t0 = orc.raycast(X, X[cells], U, cells, box=False)
+    h1, t1, _, _ = _run(X, X[cells], U, cells[:, None], prec, box=False)
+    assert np.array_equal(h0, h1) and np.array_equal(t0, t1)
+    assert np.any(h1 == NO_ID) and np.all(np.isinf(t1[h1 == NO_ID]))
+
+
+def test_host_pointer_path_matches_device(orc):
+    """vd_raycast with host (numpy) buffers equals the device-pointer call."""
+    need_cuda()
+    from paper_2405_10050_gb300 import vd
+    X = synth.uniform(700, 3, seed=1)
+    rng = np.random.default_rng(3)
+    cells = rng.integers(0, 700, 500).astype(np.int32)
+    U = random_unit(rng, 500, 3)
+    ctx = vd.vd_create(None)
+    try:
+        vd.vd_set_nodes(ctx, X)
+        hit = np.empty(500, np.int32)
+        t = np.empty(500)
+        vd.vd_raycast(ctx, X[cells], U, cells[:, None].copy(), hit, t)
+    finally:
+        vd.vd_destroy(ctx)
+    h0, t0 = orc.raycast(X, X[cells], U, cells)
+    assert np.array_equal(hit, h0) and np.array_equal(t, t0)
+
+
+def test_invalid_arguments_are_rejected():
+    need_cuda()
+    from paper_2405_10050_gb300 import VDError, vd
+    ctx = vd.vd_create(None)
+    try:
+        with pytest.raises(VDError):
+            vd.vd_set_nodes(ctx, np.zeros((4, 17)))
+        with pytest.raises(VDError):
+            vd.vd_set_nodes(ctx, np.array([[0.1, np.nan]]))
+        vd.vd_set_nodes(ctx, synth.uniform(10, 2, seed=0))
+        with pytest.raises(VDError):  # eta rows longer than d + 1
+            vd.vd_raycast(ctx, np.zeros((1, 2)), np.array([[1.0, 0.0]]), np.zeros((1, 4), np.int32),
+                          np.empty(1, np.int32), np.empty(1))
+    finally:
+        vd.vd_destroy(ctx)

@@ -1,0 +1,67 @@
+"""GPU parity of the exhaustive vertex traversal (Section 2.3, Algorithm 2)
+against the oracle's sequential traversal: the sorted tuple sets are
+identical and the coordinates, solved from the tuples in binary64 in the
+same order on both sides, are bit-identical."""
+from collections import Counter
+
+import numpy as np
+import pytest
+
+from gpu_util import need_cuda
+from paper_2405_10050_gb300 import VD_FP32, VD_FP64, Voronoi, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_vertices(X, prec):
+    need_cuda()
+    vor = Voronoi(X, precision=prec)
+    t, c, st = vor.vertices()
+    vor.close()
+    return t.cpu().numpy(), c.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("prec", [VD_FP64, VD_FP32])
+@pytest.mark.parametrize("d,N", [(2, 500), (3, 2000), (4, 300), (5, 120), (6, 40)])
+def test_vertices_parity(orc, prec, d, N):
+    X = synth.uniform(N, d, seed=0)
+    t0, c0, _ = orc.vertices(X)
+    t1, c1, st = _gpu_vertices(X, prec)
+    assert t1.shape == t0.shape
+    assert np.array_equal(t1, t0)
+    assert np.array_equal(c1, c0)
+    assert st["vertices"] == len(t0) and st["levels"] >= 1
+
+
+@pytest.mark.parametrize("prec", [VD_FP64, VD_FP32])
+def test_vertices_mixture_and_tiny(orc, prec):
+    for X in [synth.gaussian_mixture(400, 3, 8, 0.05, seed=2), synth.uniform(1, 2, seed=1),
+              synth.uniform(2, 3, seed=2), synth.uniform(33, 2, seed=3)]:
+        t0, c0, _ = orc.vertices(X)
+        t1, c1, _ = _gpu_vertices(X, prec)
+        assert np.array_equal(t1, t0) and np.array_equal(c1, c0)
+
+
+def test_vertex_invariants_larger(orc):
+    """d = 5, N = 3000: every edge has two endpoints and each of the 2^d
+    corners appears once; a sample of vertices is checked by the oracle's
+    brute force (equidistant, no node closer)."""
+    d, N = 5, 3000
+    X = synth.uniform(N, d, seed=4)
+    t, c, st = _gpu_vertices(X, VD_FP32)
+    cnt = Counter()
+    for sig in map(tuple, t):
+        for q in range(d + 1):
+            eta = sig[:q] + sig[q + 1:]
+            if any(g >= 0 for g in eta):
+                cnt[eta] += 1
+    assert set(cnt.values()) == {2}
+    assert sum(1 for sig in t if np.sum(sig < 0) == d) == 2 ** d
+    rng = np.random.default_rng(0)
+    for v in rng.choice(len(t), 300, replace=False):
+        r = orc.vertex_coords(X, t[v])
+        assert np.array_equal(r, c[v])
+        nodes = [g for g in t[v] if g >= 0]
+        dist = np.linalg.norm(X - r, axis=1)
+        R = dist[nodes[0]]
+        assert np.min(dist) >= R * (1 - 1e-12)

@@ -1,0 +1,403 @@
+"""Benchmark of the exact Voronoi RayCast on its exhaustive-traversal workload.
+
+Workload (one step): node preparation + exhaustive vertex traversal
+(Algorithm 2) of N = 20,000 iid uniform nodes in [0,1]^5 (seed 0), cells
+clipped to the unit cube, on the binary32-screened path with binary64
+recheck.  The metric is raycasts per second of that traversal; the same
+workload on the plain binary64 path is timed beside it, and its vertex
+tuples must equal the screened path's bit for bit.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torchrun) every rank runs an independent
+replica of the workload (the traversal of one node set does not shard);
+`value` is all ranks' raycasts over the slowest rank's time.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload's rays.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "raycasts/s and MC vol+grad cells/s: mixed vs FP64 path, same GB300, exact hits"
+WORKLOAD = "exhaustive vertex traversal, d=5, N=20000 iid uniform in [0,1]^5 (seed 0), clipped to the cube"
+NEIGHBOURS_D5 = 95  # neighbours per cell in d = 5 (the paper's table of vertices and neighbours per cell)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def edge_rays_from_mesh(orc, X, tuples, coords, n, seed=0):
+    """Rays of Algorithm 2 (vertex origin, edge direction, eta) for n random
+    (vertex, edge) pairs of a traversal result, built with the oracle."""
+    rng = np.random.default_rng(seed)
+    d = X.shape[1]
+    O, U, E = [], [], []
+    while len(O) < n:
+        v = int(rng.integers(0, len(tuples)))
+        drop = int(rng.integers(0, d + 1))
+        sig = tuples[v]
+        eta = [int(g) for q, g in enumerate(sig) if q != drop]
+        nodes = sorted(g for g in eta if g >= 0)
+        if not nodes:
+            continue
+        u = orc.search_direction(X, sig, drop)
+        if u is None:
+            continue
+        O.append(coords[v])
+        U.append(u)
+        E.append([nodes[0]] + [g for g in eta if g != nodes[0]])
+    return np.array(O), np.array(U), np.array(E, np.int32)
+
+
+def cpu_oracle_rate(X, tuples, coords, target_s=15.0):
+    """Oracle raycasts/s on the host cores over a bounded sample of the
+    traversal's edge rays (about target_s seconds of CPU work)."""
+    import oracle
+    oracle.build()
+    O, U, E = edge_rays_from_mesh(oracle, X, tuples, coords, 256, seed=1)
+    t0 = time.perf_counter()
+    oracle.raycast(X, O, U, E)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    n = int(min(200000, max(512, 256 * target_s / dt)))
+    O, U, E = edge_rays_from_mesh(oracle, X, tuples, coords, n, seed=2)
+    t0 = time.perf_counter()
+    oracle.raycast(X, O, U, E)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, oracle.max_threads()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores: each step times its brute-force
+    RayCast on a bounded sample of the workload's edge rays (from vertices the
+    oracle itself finds by a bounded Algorithm 2 walk from its Descent seed)."""
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2405_10050_gb300 import synth
+    oracle.build()
+    X = synth.uniform(args.N, args.d, seed=0)
+    tuples, coords = _oracle_local_vertices(oracle, X, 300)
+    rates, secs = [], []
+    for s in range(args.warmup + args.steps):
+        O, U, E = edge_rays_from_mesh(oracle, X, tuples, coords, args.ref_rays, seed=100 + s)
+        t0 = time.perf_counter()
+        oracle.raycast(X, O, U, E)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            rates.append(len(O) / dt)
+            secs.append(dt)
+    value = statistics.mean(rates)
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "raycasts/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * statistics.mean(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": args.N, "d": args.d, "sample_rays_per_step": args.ref_rays},
+            "cpu_baseline": {"value": value, "unit": "raycasts/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.ref_rays} edge rays per step of the workload's diagram "
+                                       f"(FP64 brute force over all {args.N} nodes)"},
+            "e2e": {"value": value, "unit": "raycasts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _oracle_local_vertices(orc, X, nmax):
+    """Up to nmax vertices of the diagram of X found by the oracle: Descent
+    from node 0, then a breadth-first walk of Algorithm 2."""
+    import collections
+    d = X.shape[1]
+    sig0 = orc.descent(X, 0)
+    seen = {tuple(int(g) for g in sig0)}
+    q = collections.deque([tuple(int(g) for g in sig0)])
+    out_t, out_c = [], []
+    while q and len(out_t) < nmax:
+        sig = q.popleft()
+        sa = np.array(sig, np.int32)
+        r = orc.vertex_coords(X, sa)
+        out_t.append(sig)
+        out_c.append(r)
+        for drop in range(d + 1):
+            eta = [g for k, g in enumerate(sig) if k != drop]
+            nodes = sorted(g for g in eta if g >= 0)
+            if not nodes:
+                continue
+            u = orc.search_direction(X, sa, drop)
+            if u is None:
+                continue
+            er = [nodes[0]] + [g for g in eta if g != nodes[0]]
+            h, _ = orc.raycast(X, r[None], u[None], np.array([er], np.int32))
+            ns = tuple(sorted(eta + [int(h[0])]))
+            if ns not in seen:
+                seen.add(ns)
+                q.append(ns)
+    return np.array(out_t, np.int32), np.array(out_c)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2405_10050_gb300 import VD_FP32, VD_FP64, synth, vd
+    vd.load()
+    X = synth.uniform(args.N, args.d, seed=0)
+    Xd = torch.tensor(X, device="cuda")
+    stream = torch.cuda.current_stream()
+    cfg = vd.vd_config_default()
+    cfg.precision = VD_FP32
+    ctx = vd.vd_create(cfg, stream.cuda_stream)
+
+    def step(c):
+        vd.vd_set_nodes(c, Xd)
+        m = vd.vd_vertices(c)
+        st = vd.vd_mesh_stats(m)
+        return m, st
+
+    for _ in range(args.warmup):
+        m, st = step(ctx)
+        vd.vd_mesh_free(m)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    clock = ClockSampler(local)
+    clock.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = vd.vd_kernel_launches()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    rays = 0
+    rc_ms = 0.0
+    last = None
+    for k in range(args.steps):
+        m, st = step(ctx)
+        rays += st["rays"]
+        rc_ms += st["raycast_ms"]
+        last_stats = st
+        if k == args.steps - 1:
+            last = m
+        else:
+            vd.vd_mesh_free(m)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = vd.vd_kernel_launches() - launches0
+    clocks = clock.stop()
+    _barrier(ws)
+    ms = e0.elapsed_time(e1)
+    ms_max = _max_over_ranks(ms, ws)
+    rays_all = _sum_over_ranks(rays, ws)
+    value = rays_all / (ms_max / 1000.0)
+    nv = vd.vd_mesh_count(last)
+    tup = torch.empty((nv, args.d + 1), dtype=torch.int32, device="cuda")
+    crd = torch.empty((nv, args.d), dtype=torch.float64, device="cuda")
+    vd.vd_mesh_copy(last, tup, crd)
+    vd.vd_mesh_free(last)
+
+    # ---- plain binary64 path on the same workload ----
+    fp64 = None
+    if not args.no_fp64:
+        cfg64 = vd.vd_config_default()
+        cfg64.precision = VD_FP64
+        ctx64 = vd.vd_create(cfg64, stream.cuda_stream)
+        m, st = step(ctx64)
+        vd.vd_mesh_free(m)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        m, st = step(ctx64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        tup64 = torch.empty((vd.vd_mesh_count(m), args.d + 1), dtype=torch.int32, device="cuda")
+        vd.vd_mesh_copy(m, tup64, None)
+        same = bool(tup64.shape == tup.shape and torch.equal(tup64, tup))
+        vd.vd_mesh_free(m)
+        vd.vd_destroy(ctx64)
+        fp64 = {"value": st["rays"] / (ms64 / 1000.0), "ms_per_step": ms64, "raycast_ms": st["raycast_ms"],
+                "tuples_identical_to_mixed": same}
+
+    # ---- end to end through the C ABI with host buffers ----
+    Xh = np.ascontiguousarray(X)
+    th = np.empty((nv, args.d + 1), np.int32)
+    ch = np.empty((nv, args.d))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_rays = 0
+    for _ in range(max(1, min(args.steps, 3))):
+        vd.vd_set_nodes(ctx, Xh)
+        m = vd.vd_vertices(ctx)
+        e2e_rays += vd.vd_mesh_stats(m)["rays"]
+        vd.vd_mesh_copy(m, th, ch)
+        vd.vd_mesh_free(m)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = _sum_over_ranks(e2e_rays, ws) / _max_over_ranks(e2e_s, ws)
+    h2d = Xh.nbytes
+    d2h = th.nbytes + ch.nbytes
+
+    # ---- roofline of the dominant kernel (the RayCast) ----
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_tflops = nsm * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 lanes x FMA x clock
+    pairs = NEIGHBOURS_D5 + 2 * args.d
+    flops_per_ray = pairs * (2 * args.d + 6)
+    achieved = rays * flops_per_ray / (rc_ms / 1000.0) / 1e12 if rc_ms > 0 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": (achieved / peak_tflops) if achieved else None, "traffic": None,
+                "kernel": "k_ray_mixed<5> (binary32 screening + binary64 recheck)",
+                "peak_source": f"FP32 lanes x 2 x sm_max_mhz ({src} peaks file)",
+                "algorithmic_flops_per_ray": flops_per_ray, "raycast_ms_per_step": rc_ms / args.steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, n, dt, cores = cpu_oracle_rate(X, tup.cpu().numpy(), crd.cpu().numpy(), target_s=args.cpu_seconds)
+        cpu = {"value": rate, "unit": "raycasts/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n} random edge rays of the workload's diagram, FP64 brute force over all "
+                         f"{args.N} nodes ({dt:.1f} s)"}
+    vd.vd_destroy(ctx)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "raycasts/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": args.N, "d": args.d, "precision": "fp32 screen + fp64 recheck",
+                           "vertices": nv, "raycasts_per_step": rays / args.steps,
+                           "levels": last_stats["levels"],
+                           "pairs_per_ray": last_stats["pairs_screened"] / max(last_stats["rays"], 1),
+                           "rechecked_per_ray": last_stats["rechecked"] / max(last_stats["rays"], 1),
+                           "step_launches": last_stats["launches"],
+                           "l2": "inputs larger than L2 (traversal tables ~1.5 GB per step)",
+                           "parallelism": f"replicas x{ws}"},
+                "fp64_path": fp64,
+                "speedup_vs_fp64": (value / ws / fp64["value"]) if fp64 else None,
+                "e2e": {"value": e2e_value, "unit": "raycasts/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=20000)
+    ap.add_argument("--d", type=int, default=5)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-rays", type=int, default=4000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -62,7 +62,8 @@ typedef struct {
   int64_t hash_capacity;  /* traversal vertex table entries, 0 = automatic */
   int64_t max_levels;     /* traversal BFS level cap, 0 = automatic        */
   int64_t wait_limit;     /* spin iterations before a device wait gives up */
-  int32_t tile_n;         /* node tile size hint, 0 = automatic            */
+  int32_t knn_k;          /* candidate list length per node: 0 = automatic
+                             by dimension, -1 = no lists (tree walk only)  */
   int32_t rays_per_block; /* MC rays per thread block, 0 = autotune        */
 } vd_config;
 
@@ -76,12 +77,18 @@ typedef struct {
   int64_t ties;            /* exact binary64 ties seen (degenerate input)   */
   int64_t levels;          /* traversal BFS levels                          */
   int64_t vertices;        /* traversal vertices                            */
+  int64_t launches;        /* kernels launched by the call                  */
   double ms;               /* device time of the last call, milliseconds   */
+  double raycast_ms;       /* device time of its RayCast kernels, ms        */
 } vd_stats;
 
 typedef struct vd_ctx vd_ctx;
 typedef struct vd_mesh vd_mesh;
 typedef struct vd_mc vd_mc;
+
+/* Number of CUDA kernels libvd has launched in this process (all contexts);
+ * a diagnostic counter, never reset. */
+int64_t vd_kernel_launches(void);
 
 /* Fills *cfg with the defaults (VD_AUTO, box on, automatic capacities). */
 void vd_config_default(vd_config* cfg);

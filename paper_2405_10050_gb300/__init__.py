@@ -52,11 +52,13 @@ class MCResult:
 class Voronoi:
     """A libvd context holding one node set X (N x d, float64)."""
 
-    def __init__(self, X, precision: int = VD_AUTO, box: bool = True, stream=None):
+    def __init__(self, X, precision: int = VD_AUTO, box: bool = True, stream=None, knn_k: int = 0):
+        """knn_k: candidate list length per node (0 automatic, -1 tree walk only)."""
         import torch
         cfg = vd.vd_config_default()
         cfg.precision = precision
         cfg.box = int(box)
+        cfg.knn_k = knn_k
         self._stream = stream
         self.ctx = vd.vd_create(cfg, stream)
         self.X = None

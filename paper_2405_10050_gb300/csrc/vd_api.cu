@@ -23,6 +23,10 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
                               cudaStream_t st, char* err, size_t errlen);
 }  // namespace vd
 
+namespace vd {
+std::atomic<long long> g_launches{0};
+}
+
 using vd::Counters;
 using vd::DevBufs;
 using vd::TreeView;
@@ -154,6 +158,8 @@ int effective_precision(const vd_ctx* ctx) {
 
 extern "C" {
 
+int64_t vd_kernel_launches(void) { return (int64_t)vd::g_launches.load(); }
+
 void vd_config_default(vd_config* cfg) {
   if (!cfg) return;
   std::memset(cfg, 0, sizeof(*cfg));
@@ -244,6 +250,15 @@ vd_status vd_set_nodes(vd_ctx* ctx, const double* X, int64_t N, int32_t d, int32
     ctx->node_bufs.release();
     return cuda_err(ctx, e, "build_tree");
   }
+  const int K = ctx->cfg.knn_k < 0 ? 0 : (ctx->cfg.knn_k > 0 ? ctx->cfg.knn_k : vd::default_knn_k(d));
+  if (K > 0 && d <= 8) {
+    const int Kuse = (int)std::min<int64_t>(K, std::max<int64_t>(N - 1, 1));
+    e = vd::build_knn(&tv, Kuse, ctx->st, ctx->node_bufs);
+    if (e != cudaSuccess) {
+      ctx->node_bufs.release();
+      return cuda_err(ctx, e, "build_knn");
+    }
+  }
   ctx->tree = tv;
   ctx->X = Xd;
   ctx->N = N;
@@ -281,9 +296,10 @@ vd_status vd_raycast(vd_ctx* ctx, const double* origins, const double* dirs, con
     VD_CK(tmp.alloc_n(&t_d, R), "alloc");
     if (screen_err) VD_CK(tmp.alloc_n(&se_d, R), "alloc");
   }
-  int32_t* ovl = nullptr;
+  int32_t *ovl = nullptr, *fbl = nullptr;
   const int64_t ovcap = std::max<int64_t>(1024, R / 16);
   VD_CK(tmp.alloc_n(&ovl, ovcap), "alloc");
+  VD_CK(tmp.alloc_n(&fbl, R), "alloc");
   // eta rows must start with a node
   vd::RaySource rs;
   rs.mode = 0;
@@ -299,10 +315,15 @@ vd_status vd_raycast(vd_ctx* ctx, const double* origins, const double* dirs, con
   ro.screen_err = se_d;
   ro.overflow_list = ovl;
   ro.overflow_cap = ovcap;
+  ro.fallback_list = fbl;
+  ro.fallback_cap = R;
   VD_CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->st), "memset");
+  const long long l0 = vd::g_launches.load();
   Timer tm(ctx->st);
   VD_CK(vd::launch_raycast(ctx->tree, rs, ro, effective_precision(ctx), ctx->ctr, ctx->st), "raycast");
   ctx->last.ms = tm.stop();
+  ctx->last.raycast_ms = ctx->last.ms;
+  ctx->last.launches = vd::g_launches.load() - l0;
   if (!on_device) {
     VD_CK(cudaMemcpyAsync(hit, h_d, R * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->st), "copy out");
     VD_CK(cudaMemcpyAsync(t, t_d, R * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "copy out");
@@ -356,10 +377,11 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
     DevBufs& b;
     ~Guard() { b.release(); }
   } guard{tmp};
-  int32_t* ovl = nullptr;
+  int32_t *ovl = nullptr, *fbl = nullptr;
   int64_t* cnt = nullptr;
   const int64_t ovcap = std::max<int64_t>(4096, N * R / 64);
   VD_CK(tmp.alloc_n(&ovl, ovcap), "alloc");
+  VD_CK(tmp.alloc_n(&fbl, N * R), "alloc");
   VD_CK(tmp.alloc_n(&cnt, N), "alloc");
   vd::RaySource rs;
   rs.mode = 1;
@@ -374,9 +396,16 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
   ro.mc_rpc = R;
   ro.overflow_list = ovl;
   ro.overflow_cap = ovcap;
+  ro.fallback_list = fbl;
+  ro.fallback_cap = N * R;
   VD_CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->st), "memset");
+  const long long l0 = vd::g_launches.load();
   Timer tm(ctx->st);
-  VD_CK(vd::launch_raycast(tv, rs, ro, effective_precision(ctx), ctx->ctr, ctx->st), "mc raycast");
+  {
+    Timer tr(ctx->st);
+    VD_CK(vd::launch_raycast(tv, rs, ro, effective_precision(ctx), ctx->ctr, ctx->st), "mc raycast");
+    mc->stats.raycast_ms = tr.stop();
+  }
   int64_t nnz = 0;
   VD_CK(vd::mc_rowptr(mc->hit, N, R, cnt, mc->rowptr, &nnz, ctx->st), "mc rowptr");
   mc->nnz = nnz;
@@ -384,6 +413,7 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
   VD_CK(mc->bufs.alloc_n(&mc->A, (size_t)std::max<int64_t>(nnz, 1)), "mc alloc");
   VD_CK(vd::mc_fill(Xd, N, d, R, seed, set, mc->hit, mc->l, mc->rowptr, mc->V, mc->col, mc->A, ctx->st), "mc fill");
   mc->stats.ms = tm.stop();
+  mc->stats.launches = vd::g_launches.load() - l0;
   Counters hc;
   vd_status s;
   if ((s = read_counters(ctx, &hc)) != VD_OK) return s;
@@ -516,11 +546,13 @@ vd_status vd_vertices(vd_ctx* ctx, vd_mesh** out) {
   m->st = ctx->st;
   m->d = ctx->d;
   VD_CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->st), "memset");
+  const long long l0 = vd::g_launches.load();
   Timer tm(ctx->st);
   char err[256] = {0};
   cudaError_t e = vd::traverse_vertices(ctx->tree, effective_precision(ctx), ctx->cfg, m->bufs, &m->tuples,
                                         &m->coords, &m->nv, &m->stats, ctx->ctr, ctx->st, err, sizeof(err));
   m->stats.ms = tm.stop();
+  m->stats.launches = vd::g_launches.load() - l0;
   Counters hc;
   vd_status s = VD_OK;
   if (e != cudaSuccess) {

@@ -1,6 +1,7 @@
 // vd_internal.h -- host/device structures shared by the libvd translation
 // units (node tree, ray batches, counters, launcher prototypes).
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <vector>
 #include <cuda_runtime.h>
@@ -43,6 +44,16 @@ struct TreeView {
   const int32_t* ids = nullptr;  // [ntiles][32], kNoId for padding
   const double* X = nullptr;     // original N x d row-major
   float coord_abs = 1.f;         // max |coordinate| over nodes (>= 1)
+  // candidate lists: for each node g its K nearest other nodes sorted by the
+  // binary32 squared distance w32 = sum (x32 - g32)^2; every node missing from
+  // g's list has w32 >= kcert[g]
+  int K = 0;
+  const int32_t* knn = nullptr;   // [N][K]
+  const int32_t* kcnt = nullptr;  // [N] entries in use
+  const float* kcert = nullptr;   // [N]
+  const float* X32 = nullptr;     // [N][d] nearest binary32 of X, id order
+  float root_lo[16] = {};         // bounding box of all nodes (binary32, outward)
+  float root_hi[16] = {};
 };
 
 // Where the rays of a generic raycast come from.
@@ -71,6 +82,8 @@ struct RayOut {
   float* screen_err = nullptr;  // nullable
   int32_t* overflow_list = nullptr;  // rays whose candidate list overflowed
   int64_t overflow_cap = 0;
+  int32_t* fallback_list = nullptr;  // rays the candidate lists could not certify
+  int64_t fallback_cap = 0;
 };
 
 struct Counters {
@@ -85,6 +98,10 @@ struct Counters {
   unsigned int flags;
   unsigned int pad;
 };
+
+// Process-wide count of kernel launches issued by libvd (diagnostics).
+extern std::atomic<long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // Device allocations owned by one library object, released together.
 struct DevBufs {
@@ -107,6 +124,10 @@ struct DevBufs {
 // ---- launchers (defined in the .cu files) --------------------------------
 // Builds the tree of X_dev (N x d, device) into buffers owned by `bufs`.
 cudaError_t build_tree(const double* X_dev, int64_t N, int d, cudaStream_t st, DevBufs& bufs, TreeView* tv);
+// Builds the per-node candidate lists (K nearest, sorted) into tv.
+cudaError_t build_knn(TreeView* tv, int K, cudaStream_t st, DevBufs& bufs);
+// Default list length for dimension d (0: no lists, tree walk only).
+int default_knn_k(int d);
 cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision,
                            Counters* ctr, cudaStream_t st);
 cudaError_t launch_mc_directions(uint64_t seed, uint32_t set, int64_t cell0, int64_t ncells, int64_t R, int d,

@@ -271,7 +271,7 @@ template <int D>
 cudaError_t fill_d(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set, const int32_t* hit,
                    const double* l, const int64_t* rowptr, double cV, double cA, double* V, int32_t* col, double* A,
                    cudaStream_t st) {
-  k_mc_fill<D><<<nblk(N * 32, 128), 128, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A);
+  k_mc_fill<D><<<nblk(N * 32, 128), 128, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A); count_launch();
   return cudaGetLastError();
 }
 
@@ -280,7 +280,7 @@ cudaError_t adj_rows_d(const double* X, int64_t N, int d, int64_t R, uint64_t se
                        const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, double cV,
                        double cA, const double* gV, const double* gA, double* P, double* own, cudaStream_t st) {
   k_mc_adj_rows<D><<<nblk(N * 32, 128), 128, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P,
-                                                       own);
+                                                       own); count_launch();
   return cudaGetLastError();
 }
 
@@ -291,8 +291,8 @@ double sphere_area(int d) { return 2.0 * std::pow(M_PI, 0.5 * d) / std::tgamma(0
 // Counts the distinct hits per cell and writes rowptr (N+1); returns nnz.
 cudaError_t mc_rowptr(const int32_t* hit, int64_t N, int64_t R, int64_t* cnt_scratch, int64_t* rowptr,
                       int64_t* nnz_host, cudaStream_t st) {
-  k_mc_count<<<nblk(N * 32, 128), 128, 0, st>>>(hit, N, R, cnt_scratch);
-  k_scan64<<<1, 1024, 0, st>>>(cnt_scratch, N, rowptr);
+  k_mc_count<<<nblk(N * 32, 128), 128, 0, st>>>(hit, N, R, cnt_scratch); count_launch();
+  k_scan64<<<1, 1024, 0, st>>>(cnt_scratch, N, rowptr); count_launch();
   cudaMemcpyAsync(nnz_host, rowptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return e;
@@ -329,10 +329,10 @@ cudaError_t mc_adjoint(const double* X, int64_t N, int d, int64_t R, uint64_t se
   else if (d <= 8) e = adj_rows_d<8>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P, own, st);
   else e = adj_rows_d<16>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P, own, st);
   if (e != cudaSuccess) return e;
-  k_mc_col_keys<<<nblk(nnz, 256), 256, 0, st>>>(col, nnz, keys, vals);
+  k_mc_col_keys<<<nblk(nnz, 256), 256, 0, st>>>(col, nnz, keys, vals); count_launch();
   e = radix_sort_u64(keys, vals, ktmp, vtmp, nnz, counts, orand, st);
   if (e != cudaSuccess) return e;
-  k_mc_adj_cols<<<nblk(N, 128), 128, 0, st>>>(keys, vals, nnz, P, own, N, d, gX);
+  k_mc_adj_cols<<<nblk(N, 128), 128, 0, st>>>(keys, vals, nnz, P, own, N, d, gX); count_launch();
   return cudaGetLastError();
 }
 

@@ -105,6 +105,7 @@ template <int D>
 struct Ball {
   float c[D];
   float lim2;
+  float rho_hi;  // upper bound of the exact radius |g - c|
 };
 
 template <int D>
@@ -123,7 +124,54 @@ __device__ __forceinline__ void make_ball(const float g[D], const float p[D], co
   const float eps = 8.f * (float)D * kU32 * (B + pm + T) + 1e-30f;
   const float rho = sqrtf(r2) * (1.f + 4.f * (float)D * kU32) + eps;
   b.lim2 = rho * rho * (1.f + 4.f * (float)D * kU32) + 1e-37f;
-  if (!(T < INFINITY)) b.lim2 = INFINITY;
+  b.rho_hi = rho;
+  if (!(T < INFINITY)) {
+    b.lim2 = INFINITY;
+    b.rho_hi = INFINITY;
+  }
+}
+
+// Candidate lists: ww32 = sum_k fma-chain (x32_k - g32_k)^2 over k = 0..D-1;
+// the same function orders the lists and is evaluated during the scan.
+template <int D>
+__device__ __forceinline__ float ww32_of(const float* xs, int stride, const float* g32, int d) {
+  float ww = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const float w = (k < d) ? xs[k * stride] - g32[k] : 0.f;
+    ww = fmaf(w, w, ww);
+  }
+  return ww;
+}
+
+// Lower bound of the exact |x - g|^2 from ww32 (w32 components within EW of
+// the exact ones, gamma_D for the FMA chain).
+__device__ __forceinline__ float true_d2_lower(float ww, float gam, float EW, int D) {
+  const float l = ww * (1.f - 2.f * gam) - 2.02f * sqrtf((float)D) * EW * sqrtf(ww) - (float)D * EW * EW;
+  return fmaxf(l, 0.f);
+}
+
+// Squared radius around g that holds every node of the ball: nodes lie in
+// the node box, so only the part of the ball inside it matters; the farthest
+// point from g of that part is bounded through its axis-aligned box
+// [max(c - rho, lo), min(c + rho, hi)], and by the ball's diameter 2 rho
+// (the ball passes through g).  Returns 0 when the ball misses the box.
+template <int D>
+__device__ __forceinline__ float far_radius2(const TreeView& tr, const Ball<D>& b, const float* g32) {
+  if (!(b.rho_hi < INFINITY)) return INFINITY;
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    if (k < tr.d) {
+      const float L = fmaxf(b.c[k] - b.rho_hi, tr.root_lo[k]);
+      const float H = fminf(b.c[k] + b.rho_hi, tr.root_hi[k]);
+      if (L > H) return 0.f;
+      const float m = fmaxf(fabsf(L - g32[k]), fabsf(H - g32[k])) * (1.f + 4.f * kU32) + 2.f * kU32 * tr.coord_abs;
+      s = fmaf(m, m, s);
+    }
+  }
+  s *= 1.f + 4.f * (float)D * kU32;
+  return fminf(s, 4.f * b.rho_hi * b.rho_hi * (1.f + 4.f * kU32));
 }
 
 template <int D>
@@ -198,9 +246,9 @@ __device__ __forceinline__ void walk(const TreeView& tr, int* stk, Ball<D>& ball
 // ------------------------------------------------------------------------
 // VD_FP32: binary32 screening + binary64 recheck
 // ------------------------------------------------------------------------
-template <int D>
+template <int D, bool LIST>
 __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource rs, RayOut ro, Counters* ctr,
-                                                         unsigned long long* work) {
+                                                         unsigned long long* work, const int32_t* subset) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpMixed<D>& S = reinterpret_cast<WarpMixed<D>*>(smem_raw)[wib];
@@ -217,8 +265,9 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
     const int64_t b0 = (int64_t)b * 32;
     if (b0 >= R) break;
     // ---- set-up: one ray per lane ----
-    const int64_t r = b0 + lane;
-    const bool vr = r < R;
+    const int64_t slot = b0 + lane;
+    const bool vr = slot < R;
+    const int64_t r = vr ? (subset ? (int64_t)subset[slot] : slot) : 0;
     if (vr) {
       double v[D], u[D];
       int32_t eta[D + 1];
@@ -308,15 +357,15 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
       int nc = S.ncand[rr];
       Ball<D> ball;
       make_ball<D>(gg, pp, u, T, B, ball);
-      auto leaf = [&](int64_t tile) {
-        const int32_t id = tr.ids[tile * kTile + lane];
+      // screens one node per lane (id, coordinates xs[k * stride]); returns ww32
+      auto eval = [&](int32_t id, const float* xs, int stride) -> float {
         bool ok = id != kNoId;
         for (int q = 0; q < m; ++q) ok &= (id != S.eta[rr][q]);
         float w[D];
         float den = 0.f, ww = 0.f, pw = 0.f;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          w[k] = (k < d) ? tr.x32[(tile * d + k) * kTile + lane] - gg[k] : 0.f;
+          w[k] = (k < d) ? xs[k * stride] - gg[k] : 0.f;
           den = fmaf(u[k], w[k], den);
           ww = fmaf(w[k], w[k], ww);
         }
@@ -333,7 +382,7 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
         // t_j <= T is possible iff the lower bound of t_j does not exceed T
         const bool cand = ok && dh > 0.f && (nlo <= 0.f || nlo <= 2.f * T * dh * (1.f + 8.f * kU32));
         const unsigned cm = __ballot_sync(kFull, cand);
-        if (cm == 0) return;
+        if (cm == 0) return ww;
         float thi = INFINITY, tlo = -INFINITY;
         if (cand) {
           const float dl = den - Eden;
@@ -385,10 +434,37 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
           nc += nk;
         }
         __syncwarp();
+        return ww;
       };
-      unsigned long long t0 = n_tiles;
-      walk<D>(tr, S.stk, ball, lane, leaf, n_tiles);
-      n_pairs += (n_tiles - t0) * 32;
+      if (!LIST) {
+        auto leaf = [&](int64_t tile) {
+          eval(tr.ids[tile * kTile + lane], tr.x32 + tile * d * kTile + lane, kTile);
+        };
+        unsigned long long t0 = n_tiles;
+        walk<D>(tr, S.stk, ball, lane, leaf, n_tiles);
+        n_pairs += (n_tiles - t0) * 32;
+      } else {
+        // scan g's sorted candidate list; stop once a node is farther from g
+        // than 2 rho (it and all later ones lie outside the ball of T)
+        const int32_t g = S.eta[rr][0];
+        const int32_t* lst = tr.knn + (int64_t)g * tr.K;
+        const int n = tr.kcnt[g];
+        bool certified = false;
+        for (int c0 = 0; c0 < n; c0 += 32) {
+          const int c = c0 + lane;
+          const int32_t id = c < n ? lst[c] : kNoId;
+          const float ww = eval(id, tr.X32 + (int64_t)(c < n ? id : g) * d, 1);
+          n_pairs += 32;
+          const float far2 = far_radius2<D>(tr, ball, gg);
+          const bool far = c < n && true_d2_lower(ww, gam, EW, D) >= far2;
+          if (__ballot_sync(kFull, far)) {
+            certified = true;
+            break;
+          }
+        }
+        if (!certified) certified = true_d2_lower(tr.kcert[g], gam, EW, D) >= far_radius2<D>(tr, ball, gg);
+        if (!certified) nc = -2;  // finished by the tree walk
+      }
       if (lane == 0) {
         S.T[rr] = T;
         S.ncand[rr] = nc;
@@ -400,7 +476,11 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
     if (vr) {
       const int nc = S.ncand[lane];
       const int64_t op = out_pos(rs, ro, r);
-      if (nc < 0) {
+      if (nc == -2) {
+        const unsigned long long k = atomicAdd(&ctr->fallback, 1ull);
+        if ((int64_t)k < ro.fallback_cap) ro.fallback_list[k] = (int32_t)r;
+        else atomicOr(&ctr->flags, kFlagQueue);
+      } else if (nc < 0) {
         const unsigned long long k = atomicAdd(&ctr->overflow, 1ull);
         if ((int64_t)k < ro.overflow_cap) ro.overflow_list[k] = (int32_t)r;
         else atomicOr(&ctr->flags, kFlagCandOverflow);
@@ -469,7 +549,7 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
 // ------------------------------------------------------------------------
 // VD_FP64: every pair in binary64, canonical order
 // ------------------------------------------------------------------------
-template <int D>
+template <int D, bool LIST>
 __global__ void __launch_bounds__(kWpb * 32) k_ray_fp64(TreeView tr, RaySource rs, RayOut ro, Counters* ctr,
                                                         unsigned long long* work, const int32_t* subset) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -477,7 +557,9 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_fp64(TreeView tr, RaySource r
   WarpF64<D>& S = reinterpret_cast<WarpF64<D>*>(smem_raw)[wib];
   const int d = tr.d;
   const float B = tr.coord_abs;
-  unsigned long long n_tiles = 0;
+  const float gam = (float)(D + 1) * kU32 * 1.01f;
+  const float EW = 4.01f * kU32 * B;
+  unsigned long long n_tiles = 0, n_pairs = 0;
   const int64_t R = rs.R;
   while (true) {
     unsigned long long b = 0;
@@ -548,14 +630,13 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_fp64(TreeView tr, RaySource r
       int bc = S.bcls[rr], bk = S.bkey[rr];
       Ball<D> ball;
       make_ball<D>(g32, p32, u32, __double2float_ru(bt) * (1.f + 4.f * kU32), B, ball);
-      auto leaf = [&](int64_t tile) {
-        const int32_t id = tr.ids[tile * kTile + lane];
+      auto eval = [&](int32_t id, const double* xs, int stride) {
         bool ok = id != kNoId;
         for (int q = 0; q < m; ++q) ok &= (id != S.eta[rr][q]);
         double w[D], den = 0.0;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          w[k] = k < d ? __dadd_rn(tr.x64[(tile * d + k) * kTile + lane], -gg[k]) : 0.0;
+          w[k] = k < d ? __dadd_rn(xs[k * stride], -gg[k]) : 0.0;
           if (k < d) den = __dadd_rn(den, __dmul_rn(u[k], w[k]));
         }
         ok &= den > 0.0;
@@ -582,10 +663,38 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_fp64(TreeView tr, RaySource r
         bk = lk;
         make_ball<D>(g32, p32, u32, __double2float_ru(bt) * (1.f + 4.f * kU32), B, ball);
       };
-      walk<D>(tr, S.stk, ball, lane, leaf, n_tiles);
+      bool certified = true;
+      if (!LIST) {
+        auto leaf = [&](int64_t tile) {
+          eval(tr.ids[tile * kTile + lane], tr.x64 + tile * d * kTile + lane, kTile);
+        };
+        unsigned long long t0 = n_tiles;
+        walk<D>(tr, S.stk, ball, lane, leaf, n_tiles);
+        n_pairs += (n_tiles - t0) * 32;
+      } else {
+        const int32_t g = S.eta[rr][0];
+        const int32_t* lst = tr.knn + (int64_t)g * tr.K;
+        const int n = tr.kcnt[g];
+        certified = false;
+        for (int c0 = 0; c0 < n; c0 += 32) {
+          const int c = c0 + lane;
+          const int32_t id = c < n ? lst[c] : kNoId;
+          const int32_t ida = c < n ? id : g;
+          eval(id, tr.X + (int64_t)ida * d, 1);
+          n_pairs += 32;
+          const float ww = ww32_of<D>(tr.X32 + (int64_t)ida * d, 1, g32, d);
+          const float far2 = far_radius2<D>(tr, ball, g32);
+          const bool far = c < n && true_d2_lower(ww, gam, EW, D) >= far2;
+          if (__ballot_sync(kFull, far)) {
+            certified = true;
+            break;
+          }
+        }
+        if (!certified) certified = true_d2_lower(tr.kcert[g], gam, EW, D) >= far_radius2<D>(tr, ball, g32);
+      }
       if (lane == 0) {
         S.bt[rr] = bt;
-        S.bcls[rr] = bc;
+        S.bcls[rr] = certified ? bc : -2;
         S.bkey[rr] = bk;
       }
       __syncwarp();
@@ -593,15 +702,21 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_fp64(TreeView tr, RaySource r
     __syncwarp();
     if (vr) {
       const int64_t op = out_pos(rs, ro, r);
-      ro.hit[op] = gen_from_key(S.bcls[lane], S.bkey[lane]);
-      ro.t[op] = S.bt[lane];
-      if (ro.screen_err) ro.screen_err[op] = 0.f;
+      if (S.bcls[lane] == -2) {
+        const unsigned long long k = atomicAdd(&ctr->fallback, 1ull);
+        if ((int64_t)k < ro.fallback_cap) ro.fallback_list[k] = (int32_t)r;
+        else atomicOr(&ctr->flags, kFlagQueue);
+      } else {
+        ro.hit[op] = gen_from_key(S.bcls[lane], S.bkey[lane]);
+        ro.t[op] = S.bt[lane];
+        if (ro.screen_err) ro.screen_err[op] = 0.f;
+      }
     }
     __syncwarp();
   }
   if (lane == 0) {
     atomicAdd(&ctr->tiles, n_tiles);
-    atomicAdd(&ctr->pairs, n_tiles * 32);
+    atomicAdd(&ctr->pairs, n_pairs);
   }
 }
 
@@ -618,42 +733,164 @@ __global__ void k_directions(uint64_t seed, uint32_t set, int64_t cell0, int64_t
 
 template <int D>
 cudaError_t launch_ray_d(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision, Counters* ctr,
-                         unsigned long long* work, cudaStream_t st) {
+                         unsigned long long* work, const int32_t* subset, int64_t nrays, bool list,
+                         cudaStream_t st) {
+  if (nrays <= 0) return cudaSuccess;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t batches = (rs.R + 31) / 32;
+  RaySource r2 = rs;
+  r2.R = nrays;
+  const int64_t batches = (nrays + 31) / 32;
   cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+  auto go = [&](auto kern, size_t sm) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWpb * 32, sm);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1),
+                                                                 (batches + kWpb - 1) / kWpb));
+    kern<<<(unsigned)grid, kWpb * 32, sm, st>>>(tv, r2, ro, ctr, work, subset);
+    count_launch();
+  };
   if (precision == VD_FP64) {
-    const size_t sm = sizeof(WarpF64<D>) * kWpb;
-    cudaFuncSetAttribute(k_ray_fp64<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ray_fp64<D>, kWpb * 32, sm);
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1),
-                                                                 (batches + kWpb - 1) / kWpb));
-    k_ray_fp64<D><<<(unsigned)grid, kWpb * 32, sm, st>>>(tv, rs, ro, ctr, work, nullptr);
+    if (list) go(k_ray_fp64<D, true>, sizeof(WarpF64<D>) * kWpb);
+    else go(k_ray_fp64<D, false>, sizeof(WarpF64<D>) * kWpb);
   } else {
-    const size_t sm = sizeof(WarpMixed<D>) * kWpb;
-    cudaFuncSetAttribute(k_ray_mixed<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ray_mixed<D>, kWpb * 32, sm);
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1),
-                                                                 (batches + kWpb - 1) / kWpb));
-    k_ray_mixed<D><<<(unsigned)grid, kWpb * 32, sm, st>>>(tv, rs, ro, ctr, work);
+    if (list) go(k_ray_mixed<D, true>, sizeof(WarpMixed<D>) * kWpb);
+    else go(k_ray_mixed<D, false>, sizeof(WarpMixed<D>) * kWpb);
   }
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------
+// Candidate lists: for node g, the K nearest other nodes sorted by the
+// binary32 squared distance ww32 (the same expression the list scan
+// evaluates).  A warp gathers every node with ww32 <= r^2 by a tree walk
+// (r adapted until more than K but at most kKnnCap nodes are found, or r
+// covers all nodes), sorts them (bitonic, in shared memory), keeps K, and
+// records kcert = the (K+1)-th smallest ww32 (or r^2): every node missing
+// from the list has ww32 >= kcert.
+// ------------------------------------------------------------------------
+constexpr int kKnnCap = 4096;
+constexpr int kKnnWpb = 2;
+
+struct WarpKnn {
+  float key[kKnnCap];
+  int32_t id[kKnnCap];
+  int stk[kStk];
+};
+
 template <int D>
-cudaError_t launch_fp64_subset(const TreeView& tv, const RaySource& rs, const RayOut& ro, const int32_t* subset,
-                               int64_t n, Counters* ctr, unsigned long long* work, cudaStream_t st) {
-  RaySource r2 = rs;
-  r2.R = n;
-  cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
-  const size_t sm = sizeof(WarpF64<D>) * kWpb;
-  cudaFuncSetAttribute(k_ray_fp64<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(4096, ((n + 31) / 32 + kWpb - 1) / kWpb));
-  k_ray_fp64<D><<<(unsigned)grid, kWpb * 32, sm, st>>>(tv, r2, ro, ctr, work, subset);
+__global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, float r0, float rmax, int32_t* knn,
+                                                            int32_t* kcnt, float* kcert) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpKnn& S = reinterpret_cast<WarpKnn*>(smem_raw)[wib];
+  const int d = tr.d;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t g = (int64_t)blockIdx.x * kKnnWpb + wib; g < tr.N; g += (int64_t)gridDim.x * kKnnWpb) {
+    float g32[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) g32[k] = k < d ? tr.X32[g * d + k] : 0.f;
+    float r = r0;
+    int count = 0;
+    for (int attempt = 0; attempt < 64; ++attempt) {
+      Ball<D> ball;
+#pragma unroll
+      for (int k = 0; k < D; ++k) ball.c[k] = g32[k];
+      const float rho = r * (1.f + 8.f * (float)D * kU32) + 1e-30f;
+      ball.rho_hi = rho;
+      ball.lim2 = rho * rho * (1.f + 8.f * (float)D * kU32);
+      const float r2 = r * r;
+      count = 0;
+      auto leaf = [&](int64_t tile) {
+        const int32_t id = tr.ids[tile * kTile + lane];
+        const float ww = ww32_of<D>(tr.x32 + tile * d * kTile + lane, kTile, g32, d);
+        const bool in = id != kNoId && id != (int32_t)g && ww <= r2;
+        const unsigned m = __ballot_sync(kFull, in);
+        if (in) {
+          const int pos = count + __popc(m & lt);
+          if (pos < kKnnCap) {
+            S.key[pos] = ww;
+            S.id[pos] = id;
+          }
+        }
+        count += __popc(m);
+        __syncwarp();
+      };
+      unsigned long long dummy = 0;
+      walk<D>(tr, S.stk, ball, lane, leaf, dummy);
+      if (count > kKnnCap) {
+        r *= 0.7f;
+        continue;
+      }
+      if (count <= K && r < rmax) {
+        r = fminf(r * 1.6f, rmax * 1.001f);
+        continue;
+      }
+      break;
+    }
+    if (count > kKnnCap) {  // unresolvable (massive duplicates): no list, tree walk only
+      if (lane == 0) {
+        kcnt[g] = 0;
+        kcert[g] = 0.f;
+      }
+      continue;
+    }
+    int P = 1;
+    while (P < count) P <<= 1;
+    for (int i = count + lane; i < P; i += 32) {
+      S.key[i] = INFINITY;
+      S.id[i] = INT32_MAX;
+    }
+    __syncwarp();
+    for (int size = 2; size <= P; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = lane; i < P / 2; i += 32) {
+          const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
+          const bool asc = (lo & size) == 0;
+          const float ka = S.key[lo], kb = S.key[hi];
+          const int32_t ia = S.id[lo], ib = S.id[hi];
+          const bool gt = ka > kb || (ka == kb && ia > ib);
+          if (asc == gt) {
+            S.key[lo] = kb;
+            S.key[hi] = ka;
+            S.id[lo] = ib;
+            S.id[hi] = ia;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    const int nk = min(count, K);
+    for (int c = lane; c < nk; c += 32) knn[g * K + c] = S.id[c];
+    if (lane == 0) {
+      kcnt[g] = nk;
+      kcert[g] = count > K ? S.key[K] : r * r;
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void k_to_f32(const double* X, int64_t n, float* out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = __double2float_rn(X[i]);
+}
+
+template <int D>
+cudaError_t launch_knn_d(TreeView* tv, int K, float r0, float rmax, int32_t* knn, int32_t* kcnt, float* kcert,
+                         cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t sm = sizeof(WarpKnn) * kKnnWpb;
+  cudaFuncSetAttribute(k_knn_build<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_knn_build<D>, kKnnWpb * 32, sm);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1) * 4,
+                                                               (tv->N + kKnnWpb - 1) / kKnnWpb));
+  k_knn_build<D><<<(unsigned)grid, kKnnWpb * 32, sm, st>>>(*tv, K, r0, rmax, knn, kcnt, kcert);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -676,7 +913,22 @@ cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut
                            Counters* ctr, cudaStream_t st) {
   if (rs.R <= 0) return cudaSuccess;
   unsigned long long* work = reinterpret_cast<unsigned long long*>(&ctr->aux1);
-  cudaError_t e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rs, ro, precision, ctr, work, st);
+  cudaError_t e;
+  const bool list = tv.K > 0 && ro.fallback_list != nullptr;
+  if (list) {
+    cudaMemsetAsync(&ctr->fallback, 0, sizeof(unsigned long long), st);
+    e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rs, ro, precision, ctr, work, nullptr, rs.R, true, st);
+    if (e != cudaSuccess) return e;
+    unsigned long long nfb = 0;
+    cudaMemcpyAsync(&nfb, &ctr->fallback, sizeof(nfb), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    const int64_t n = std::min<int64_t>((int64_t)nfb, ro.fallback_cap);
+    if (n > 0)
+      e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rs, ro, precision, ctr, work, ro.fallback_list, n, false, st);
+  } else {
+    e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rs, ro, precision, ctr, work, nullptr, rs.R, false, st);
+  }
   if (e != cudaSuccess || precision == VD_FP64) return e;
   // rays whose candidate list overflowed are redone on the binary64 path
   unsigned long long nover = 0;
@@ -685,9 +937,59 @@ cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut
   if (e != cudaSuccess) return e;
   if (nover > 0) {
     const int64_t n = std::min<int64_t>((int64_t)nover, ro.overflow_cap);
-    e = VD_DISPATCH_D(tv.d, launch_fp64_subset, tv, rs, ro, ro.overflow_list, n, ctr, work, st);
+    e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rs, ro, VD_FP64, ctr, work, ro.overflow_list, n, false, st);
   }
   return e;
+}
+
+int default_knn_k(int d) {
+  static const int k[] = {0, 16, 32, 96, 256, 1024, 2048, 2048, 2048};
+  return d <= 8 ? k[d] : 0;
+}
+
+cudaError_t build_knn(TreeView* tv, int K, cudaStream_t st, DevBufs& bufs) {
+  if (K <= 0) return cudaSuccess;
+  const int d = tv->d;
+  const int64_t N = tv->N;
+  int32_t *knn = nullptr, *kcnt = nullptr;
+  float *kcert = nullptr, *X32 = nullptr;
+  cudaError_t e;
+  if ((e = bufs.alloc_n(&knn, (size_t)N * K)) || (e = bufs.alloc_n(&kcnt, (size_t)N)) ||
+      (e = bufs.alloc_n(&kcert, (size_t)N)) || (e = bufs.alloc_n(&X32, (size_t)N * d)))
+    return e;
+  k_to_f32<<<(unsigned)((N * d + 255) / 256), 256, 0, st>>>(tv->X, N * d, X32);
+  count_launch();
+  tv->X32 = X32;
+  // initial radius: about 2K nodes expected in the ball for the node density
+  // of the bounding box of the root
+  double vol = 1.0, diag2 = 0.0;
+  {
+    std::vector<double> lo(d), hi(d);
+    for (int k = 0; k < d; ++k) {
+      cudaMemcpyAsync(&lo[k], tv->blo64 + k * tv->total + tv->off[tv->nlev - 1], sizeof(double),
+                      cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(&hi[k], tv->bhi64 + k * tv->total + tv->off[tv->nlev - 1], sizeof(double),
+                      cudaMemcpyDeviceToHost, st);
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    for (int k = 0; k < d; ++k) {
+      const double w = std::max(hi[k] - lo[k], 1e-12);
+      vol *= w;
+      diag2 += w * w;
+      tv->root_lo[k] = std::nextafter((float)lo[k], -INFINITY);
+      tv->root_hi[k] = std::nextafter((float)hi[k], INFINITY);
+    }
+  }
+  const double vball = std::pow(M_PI, 0.5 * d) / std::tgamma(0.5 * d + 1.0);
+  const float r0 = (float)std::pow(1.5 * K * vol / ((double)N * vball), 1.0 / d);
+  const float rmax = (float)std::sqrt(diag2) * 1.01f + 1e-6f;
+  e = VD_DISPATCH_D(d, launch_knn_d, tv, K, std::min(r0, rmax), rmax, knn, kcnt, kcert, st);
+  if (e != cudaSuccess) return e;
+  tv->K = K;
+  tv->knn = knn;
+  tv->kcnt = kcnt;
+  tv->kcert = kcert;
+  return cudaStreamSynchronize(st);
 }
 
 cudaError_t launch_mc_directions(uint64_t seed, uint32_t set, int64_t cell0, int64_t ncells, int64_t R, int d,
@@ -700,6 +1002,7 @@ cudaError_t launch_mc_directions(uint64_t seed, uint32_t set, int64_t cell0, int
   else if (d <= 8) VD_DIR(8);
   else VD_DIR(16);
 #undef VD_DIR
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -88,10 +88,11 @@ __device__ __forceinline__ void sort_small(int32_t* t, int L) {
 // Canonical vertex coordinates from the sorted tuple (same steps as the
 // definition: x0 = first node, y = r - x0, fixed axes from the faces,
 // rows 2 w_k . y = |w_k|^2 on the free axes, partial pivoting).
+template <int D>
 __device__ bool vertex_coords(const double* X, int d, const int32_t* sig, double* r) {
-  int fixed[VD_MAX_D], side[VD_MAX_D];
+  int fixed[D], side[D];
   for (int a = 0; a < d; ++a) fixed[a] = 0;
-  int nodes[VD_MAX_D + 1], m = 0;
+  int nodes[D + 1], m = 0;
   for (int q = 0; q <= d; ++q) {
     if (sig[q] >= 0) {
       nodes[m++] = sig[q];
@@ -104,17 +105,17 @@ __device__ bool vertex_coords(const double* X, int d, const int32_t* sig, double
   }
   if (m < 1) return false;
   const double* x0 = X + (int64_t)nodes[0] * d;
-  int freeax[VD_MAX_D], nf = 0;
-  double y[VD_MAX_D];
+  int freeax[D], nf = 0;
+  double y[D];
   for (int a = 0; a < d; ++a) {
     if (fixed[a]) y[a] = __dadd_rn(side[a] ? 1.0 : 0.0, -x0[a]);
     else freeax[nf++] = a;
   }
   if (nf != m - 1) return false;
-  double M[VD_MAX_D][VD_MAX_D], b[VD_MAX_D];
+  double M[D][D], b[D];
   for (int rr = 0; rr < nf; ++rr) {
     const double* xk = X + (int64_t)nodes[rr + 1] * d;
-    double w[VD_MAX_D], ww = 0.0;
+    double w[D], ww = 0.0;
     for (int a = 0; a < d; ++a) w[a] = __dadd_rn(xk[a], -x0[a]);
     for (int a = 0; a < d; ++a) ww = __dadd_rn(ww, __dmul_rn(w[a], w[a]));
     for (int a = 0; a < d; ++a)
@@ -143,7 +144,7 @@ __device__ bool vertex_coords(const double* X, int d, const int32_t* sig, double
       b[rr] = __dadd_rn(b[rr], -__dmul_rn(f, b[c]));
     }
   }
-  double z[VD_MAX_D];
+  double z[D];
   for (int c = nf - 1; c >= 0; --c) {
     double s = b[c];
     for (int cc = c + 1; cc < nf; ++cc) s = __dadd_rn(s, -__dmul_rn(M[c][cc], z[cc]));
@@ -159,31 +160,32 @@ __device__ bool vertex_coords(const double* X, int d, const int32_t* sig, double
 // pivoting (first maximal |entry| in row-major order), the non-pivot column
 // set to 1, back substitution, u = z / |z|; sign so that the dropped node e
 // has u.(x_e - g) < 0, a dropped lower face u_a > 0, an upper face u_a < 0.
+template <int D>
 __device__ bool search_direction(const double* X, int d, const int32_t* sig, int drop, double* u) {
-  int32_t eta[VD_MAX_D];
+  int32_t eta[D];
   int m = 0;
   for (int q = 0; q <= d; ++q)
     if (q != drop) eta[m++] = sig[q];
-  int fixed[VD_MAX_D];
+  int fixed[D];
   for (int a = 0; a < d; ++a) fixed[a] = 0;
-  int nodes[VD_MAX_D], mn = 0;
+  int nodes[D], mn = 0;
   for (int q = 0; q < d; ++q) {
     if (eta[q] >= 0) nodes[mn++] = eta[q];
     else fixed[face_axis(eta[q])] = 1;
   }
   if (mn < 1) return false;
-  int freeax[VD_MAX_D], nf = 0;
+  int freeax[D], nf = 0;
   for (int a = 0; a < d; ++a)
     if (!fixed[a]) freeax[nf++] = a;
   if (nf != mn) return false;
   const double* g = X + (int64_t)nodes[0] * d;
   const int nr = mn - 1;
-  double M[VD_MAX_D][VD_MAX_D];
+  double M[D][D];
   for (int rr = 0; rr < nr; ++rr) {
     const double* xk = X + (int64_t)nodes[rr + 1] * d;
     for (int c = 0; c < nf; ++c) M[rr][c] = __dadd_rn(xk[freeax[c]], -g[freeax[c]]);
   }
-  int colperm[VD_MAX_D];
+  int colperm[D];
   for (int c = 0; c < nf; ++c) colperm[c] = c;
   for (int c = 0; c < nr; ++c) {
     int pr = c, pc = c;
@@ -217,14 +219,14 @@ __device__ bool search_direction(const double* X, int d, const int32_t* sig, int
       for (int cc = c + 1; cc < nf; ++cc) M[rr][cc] = __dadd_rn(M[rr][cc], -__dmul_rn(f, M[c][cc]));
     }
   }
-  double zp[VD_MAX_D];
+  double zp[D];
   zp[nf - 1] = 1.0;
   for (int c = nr - 1; c >= 0; --c) {
     double s = -M[c][nf - 1];
     for (int cc = c + 1; cc < nr; ++cc) s = __dadd_rn(s, -__dmul_rn(M[c][cc], zp[cc]));
     zp[c] = __ddiv_rn(s, M[c][c]);
   }
-  double z[VD_MAX_D];
+  double z[D];
   for (int c = 0; c < nf; ++c) z[colperm[c]] = zp[c];
   double nz = 0.0;
   for (int c = 0; c < nf; ++c) nz = __dadd_rn(nz, __dmul_rn(z[c], z[c]));
@@ -301,6 +303,7 @@ __device__ void edge_increment(const Tables& T, const int32_t* eta, unsigned* fl
 }
 
 // ---- level kernels ----------------------------------------------------------
+template <int D>
 __global__ void k_expand(Tables T, const double* X, const int32_t* frontier, int64_t nf, double* ro, double* rd,
                          int32_t* reta, unsigned long long* nrays, int64_t rcap, unsigned* flags) {
   const int d = T.d;
@@ -309,7 +312,7 @@ __global__ void k_expand(Tables T, const double* X, const int32_t* frontier, int
   const int64_t f = q / (d + 1);
   const int drop = (int)(q % (d + 1));
   const int32_t v = frontier[f];
-  int32_t sig[VD_MAX_D + 1], eta[VD_MAX_D];
+  int32_t sig[D + 1], eta[D];
   for (int a = 0; a <= d; ++a) sig[a] = T.vt[(int64_t)v * (d + 1) + a];
   int m = 0, hasnode = 0;
   for (int a = 0; a <= d; ++a)
@@ -320,8 +323,8 @@ __global__ void k_expand(Tables T, const double* X, const int32_t* frontier, int
     }
   if (!hasnode) return;
   if (edge_count(T, eta) >= 2) return;
-  double u[VD_MAX_D];
-  if (!search_direction(X, d, sig, drop, u)) {
+  double u[D];
+  if (!search_direction<D>(X, d, sig, drop, u)) {
     atomicOr(flags, kFlagDegenerate);
     return;
   }
@@ -380,6 +383,7 @@ __global__ void k_commit_claim(Tables T, const int32_t* reta, const int32_t* hit
 }
 
 // Phase 2: winners get vertex ids, coordinates, frontier slots and edges.
+template <int D>
 __global__ void k_commit_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot, int64_t nr,
                                 int32_t* next, unsigned long long* nnext, unsigned* flags) {
   const int d = T.d, L = d + 1;
@@ -390,17 +394,17 @@ __global__ void k_commit_finish(Tables T, const double* X, const int32_t* cand, 
     atomicOr(flags, kFlagHashFull);
     return;
   }
-  int32_t sig[VD_MAX_D + 1];
+  int32_t sig[D + 1];
   for (int a = 0; a < L; ++a) sig[a] = cand[r * L + a];
   for (int a = 0; a < L; ++a) T.vt[(int64_t)v * L + a] = sig[a];
-  double x[VD_MAX_D];
-  if (!vertex_coords(X, d, sig, x)) atomicOr(flags, kFlagDegenerate);
+  double x[D];
+  if (!vertex_coords<D>(X, d, sig, x)) atomicOr(flags, kFlagDegenerate);
   for (int a = 0; a < d; ++a) T.vx[(int64_t)v * d + a] = x[a];
   __threadfence();
   T.vslot[cslot[r]] = (int32_t)v;
   next[atomicAdd(nnext, 1ull)] = (int32_t)v;
   for (int q = 0; q <= d; ++q) {
-    int32_t eta[VD_MAX_D];
+    int32_t eta[D];
     int m = 0, hasnode = 0;
     for (int a = 0; a <= d; ++a)
       if (a != q) {
@@ -547,6 +551,31 @@ __global__ void k_gather_out(const int32_t* vt, const double* vx, int d, const i
 
 inline unsigned nb(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
+template <int D>
+void launch_expand(Tables T, const double* X, const int32_t* front, int64_t nf, double* ro, double* rd, int32_t* reta,
+                   unsigned long long* nrays, int64_t rcap, unsigned* flags, cudaStream_t st) {
+  k_expand<D><<<nb(nf * (T.d + 1), 128), 128, 0, st>>>(T, X, front, nf, ro, rd, reta, nrays, rcap, flags);
+  count_launch();
+}
+
+template <int D>
+void launch_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot, int64_t nr, int32_t* next,
+                   unsigned long long* nnext, unsigned* flags, cudaStream_t st) {
+  k_commit_finish<D><<<nb(nr), 256, 0, st>>>(T, X, cand, cslot, nr, next, nnext, flags);
+  count_launch();
+}
+
+#define VD_TRAV_D(d, FN, ...)                 \
+  do {                                        \
+    if ((d) <= 2) FN<2>(__VA_ARGS__);         \
+    else if ((d) <= 3) FN<3>(__VA_ARGS__);    \
+    else if ((d) <= 4) FN<4>(__VA_ARGS__);    \
+    else if ((d) <= 5) FN<5>(__VA_ARGS__);    \
+    else if ((d) <= 6) FN<6>(__VA_ARGS__);    \
+    else if ((d) <= 8) FN<8>(__VA_ARGS__);    \
+    else FN<16>(__VA_ARGS__);                 \
+  } while (0)
+
 int64_t pow2_at_least(int64_t x) {
   int64_t p = 1;
   while (p < x) p <<= 1;
@@ -608,22 +637,22 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   T.ne = cnts + 1;
   unsigned* flags = &ctr->flags;
   VD_TRY(cudaMemsetAsync(cnts, 0, 4 * sizeof(unsigned long long), st));
-  k_fill_i32<<<nb(vh), 256, 0, st>>>(T.vslot, vh, kEmpty);
-  k_fill_i32<<<nb(eh), 256, 0, st>>>(T.eslot, eh, kEmpty);
+  k_fill_i32<<<nb(vh), 256, 0, st>>>(T.vslot, vh, kEmpty); count_launch();
+  k_fill_i32<<<nb(eh), 256, 0, st>>>(T.eslot, eh, kEmpty); count_launch();
 
   // level buffers, grown on demand
   int64_t rcap = 0;
   double *ro = nullptr, *rd = nullptr, *rt = nullptr;
   int32_t *reta = nullptr, *rhit = nullptr, *cand = nullptr;
   int64_t* cslot = nullptr;
-  int32_t *ovl = nullptr;
+  int32_t *ovl = nullptr, *fbl = nullptr;
   int64_t ovcap = 0;
   auto grow = [&](int64_t need) -> cudaError_t {
     if (need <= rcap) return cudaSuccess;
     int64_t c = std::max<int64_t>(need, rcap * 2);
     c = std::max<int64_t>(c, 4096);
     for (void* p : {(void*)ro, (void*)rd, (void*)rt, (void*)reta, (void*)rhit, (void*)cand, (void*)cslot,
-                    (void*)ovl}) {
+                    (void*)ovl, (void*)fbl}) {
       if (!p) continue;
       cudaFree(p);
       tb.ptrs.erase(std::remove(tb.ptrs.begin(), tb.ptrs.end(), p), tb.ptrs.end());
@@ -635,7 +664,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
         (ee = tb.alloc_n(&rt, (size_t)c)) || (ee = tb.alloc_n(&reta, (size_t)c * L)) ||
         (ee = tb.alloc_n(&rhit, (size_t)c)) ||
         (ee = tb.alloc_n(&cand, (size_t)c * L)) || (ee = tb.alloc_n(&cslot, (size_t)c)) ||
-        (ee = tb.alloc_n(&ovl, (size_t)c)))
+        (ee = tb.alloc_n(&ovl, (size_t)c)) || (ee = tb.alloc_n(&fbl, (size_t)c)))
       return ee;
     return cudaSuccess;
   };
@@ -644,6 +673,17 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     if (ee == cudaSuccess) ee = cudaStreamSynchronize(st);
     return ee;
   };
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evg{ev0, ev1};
+  double raycast_ms = 0.0;
   auto run_rays = [&](int64_t nr, int stride) -> cudaError_t {
     RaySource rs;
     rs.mode = 0;
@@ -658,9 +698,18 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     rout.t = rt;
     rout.overflow_list = ovl;
     rout.overflow_cap = ovcap;
+    rout.fallback_list = fbl;
+    rout.fallback_cap = rcap;
     cudaError_t ee = cudaMemsetAsync(&ctr->overflow, 0, sizeof(unsigned long long), st);
     if (ee != cudaSuccess) return ee;
-    return launch_raycast(tv, rs, rout, precision, ctr, st);
+    cudaEventRecord(ev0, st);
+    ee = launch_raycast(tv, rs, rout, precision, ctr, st);
+    cudaEventRecord(ev1, st);
+    if (ee == cudaSuccess) ee = cudaEventSynchronize(ev1);
+    float ms = 0.f;
+    if (ee == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
+    raycast_ms += ms;
+    return ee;
   };
 
   // ---- seeds by Descent ----
@@ -695,14 +744,14 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   }
   int64_t raycasts = 0;
   for (int step = 0; step < d; ++step) {
-    k_descent_dir<<<nb(ns, 64), 64, 0, st>>>(tv.X, d, ns, snode, ssig, sm, sr, step, ro, rd, reta, alive);
+    k_descent_dir<<<nb(ns, 64), 64, 0, st>>>(tv.X, d, ns, snode, ssig, sm, sr, step, ro, rd, reta, alive); count_launch();
     VD_TRY(cudaGetLastError());
     VD_TRY(run_rays(ns, L));
     raycasts += ns;
-    k_descent_update<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, sr, rd, rhit, rt, alive);
+    k_descent_update<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, sr, rd, rhit, rt, alive); count_launch();
     VD_TRY(cudaGetLastError());
   }
-  k_descent_cand<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, alive, reta, rhit);
+  k_descent_cand<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, alive, reta, rhit); count_launch();
   // insert the seeds as the first level
   int32_t *front = nullptr, *next = nullptr;
   int64_t fcap = std::max<int64_t>(ns, 4096);
@@ -711,7 +760,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   unsigned long long* nrays = cnts + 2;
   unsigned long long* nnext = cnts + 3;
   VD_TRY(cudaMemsetAsync(nnext, 0, sizeof(unsigned long long), st));
-  k_commit_claim<<<nb(ns), 256, 0, st>>>(T, reta, rhit, ns, cand, cslot, flags);
+  k_commit_claim<<<nb(ns), 256, 0, st>>>(T, reta, rhit, ns, cand, cslot, flags); count_launch();
   // seeds that did not reach a vertex were marked with hit = kNoId: clear the
   // degenerate flag they raised (a missing seed is not an error)
   {
@@ -722,7 +771,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
       VD_TRY(cudaMemcpyAsync(flags, &clr, sizeof(unsigned), cudaMemcpyHostToDevice, st));
     }
   }
-  k_commit_finish<<<nb(ns), 256, 0, st>>>(T, tv.X, cand, cslot, ns, front, nnext, flags);
+  VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, ns, front, nnext, flags, st);
   unsigned long long hn2[4];
   VD_TRY(cudaMemcpyAsync(hn2, cnts, sizeof(hn2), cudaMemcpyDeviceToHost, st));
   VD_TRY(cudaStreamSynchronize(st));
@@ -758,7 +807,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
       front = nfb;
     }
     VD_TRY(cudaMemsetAsync(cnts + 2, 0, 2 * sizeof(unsigned long long), st));
-    k_expand<<<nb(nf * L, 128), 128, 0, st>>>(T, tv.X, front, nf, ro, rd, reta, nrays, rcap, flags);
+    VD_TRAV_D(d, launch_expand, T, tv.X, front, nf, ro, rd, reta, nrays, rcap, flags, st);
     VD_TRY(cudaGetLastError());
     unsigned long long hr = 0;
     VD_TRY(cudaMemcpyAsync(&hr, nrays, sizeof(hr), cudaMemcpyDeviceToHost, st));
@@ -767,8 +816,8 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     if (nr > 0) {
       VD_TRY(run_rays(nr, d));
       raycasts += nr;
-      k_commit_claim<<<nb(nr), 256, 0, st>>>(T, reta, rhit, nr, cand, cslot, flags);
-      k_commit_finish<<<nb(nr), 256, 0, st>>>(T, tv.X, cand, cslot, nr, next, nnext, flags);
+      k_commit_claim<<<nb(nr), 256, 0, st>>>(T, reta, rhit, nr, cand, cslot, flags); count_launch();
+      VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, nr, next, nnext, flags, st);
       VD_TRY(cudaGetLastError());
     }
     unsigned long long hc[4];
@@ -795,9 +844,9 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   VD_TRY(tb.alloc_n(&ktmp, nvv));
   VD_TRY(tb.alloc_n(&counts, (size_t)256 * (nvv / 4096 + 2)));
   VD_TRY(tb.alloc_n(&orand, 2));
-  k_iota<<<nb(nvv), 256, 0, st>>>(perm, nv);
+  k_iota<<<nb(nvv), 256, 0, st>>>(perm, nv); count_launch();
   for (int c = d; c >= 0; --c) {
-    k_col_keys<<<nb(nvv), 256, 0, st>>>(T.vt, L, c, perm, nv, keys, ptmp);
+    k_col_keys<<<nb(nvv), 256, 0, st>>>(T.vt, L, c, perm, nv, keys, ptmp); count_launch();
     VD_TRY(radix_sort_u64(keys, ptmp, ktmp, perm, nv, counts, orand, st));
     VD_TRY(cudaMemcpyAsync(perm, ptmp, nv * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   }
@@ -805,7 +854,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   double* ox = nullptr;
   VD_TRY(out_bufs.alloc_n(&ot, (size_t)nvv * L));
   VD_TRY(out_bufs.alloc_n(&ox, (size_t)nvv * d));
-  k_gather_out<<<nb(nvv), 256, 0, st>>>(T.vt, T.vx, d, perm, nv, ot, ox);
+  k_gather_out<<<nb(nvv), 256, 0, st>>>(T.vt, T.vx, d, perm, nv, ot, ox); count_launch();
   VD_TRY(cudaStreamSynchronize(st));
   VD_TRY(cudaGetLastError());
   *tuples_out = ot;
@@ -814,6 +863,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   stats->levels = levels;
   stats->vertices = nv;
   stats->rays = raycasts;
+  stats->raycast_ms = raycast_ms;
   return cudaSuccess;
 #undef VD_TRY
 }

@@ -14,7 +14,7 @@ namespace vd {
 namespace {
 
 constexpr int kRsThreads = 256;
-constexpr int kRsSub = 16;                       // sub-chunks of 256 keys per block
+constexpr int kRsSub = 64;                       // sub-chunks of 256 keys per block
 constexpr int kRsChunk = kRsThreads * kRsSub;    // keys per block
 
 __global__ void k_bounds_partial(const double* X, int64_t N, int d, double* part) {
@@ -244,7 +244,7 @@ cudaError_t radix_sort_u64(uint64_t* keys, int32_t* vals, uint64_t* ktmp, int32_
   const int nblk = nblocks(n, kRsChunk);
   unsigned long long init[2] = {0ull, ~0ull};
   cudaMemcpyAsync(orand, init, sizeof(init), cudaMemcpyHostToDevice, st);
-  k_key_span<<<std::min(nblocks(n, 256), 1024), 256, 0, st>>>(keys, n, orand);
+  k_key_span<<<std::min(nblocks(n, 256), 1024), 256, 0, st>>>(keys, n, orand); count_launch();
   unsigned long long oa[2];
   cudaMemcpyAsync(oa, orand, sizeof(oa), cudaMemcpyDeviceToHost, st);
   cudaError_t e = cudaStreamSynchronize(st);
@@ -256,9 +256,9 @@ cudaError_t radix_sort_u64(uint64_t* keys, int32_t* vals, uint64_t* ktmp, int32_
   int32_t* vb = vtmp;
   for (int shift = 0; shift < 64; shift += 8) {
     if (((varying >> shift) & 255ull) == 0) continue;
-    k_rs_hist<<<nblk, kRsThreads, 0, st>>>(ka, n, shift, counts, nblk);
-    k_rs_scan<<<1, 1024, 0, st>>>(counts, (int64_t)256 * nblk);
-    k_rs_scatter<<<nblk, kRsThreads, 0, st>>>(ka, va, kb, vb, n, shift, counts, nblk);
+    k_rs_hist<<<nblk, kRsThreads, 0, st>>>(ka, n, shift, counts, nblk); count_launch();
+    k_rs_scan<<<1, 1024, 0, st>>>(counts, (int64_t)256 * nblk); count_launch();
+    k_rs_scatter<<<nblk, kRsThreads, 0, st>>>(ka, va, kb, vb, n, shift, counts, nblk); count_launch();
     std::swap(ka, kb);
     std::swap(va, vb);
   }
@@ -311,8 +311,8 @@ cudaError_t build_tree(const double* X, int64_t N, int d, cudaStream_t st, DevBu
     scratch.release();
     return e;
   }
-  k_bounds_partial<<<nb_bounds, 256, 0, st>>>(X, N, d, part);
-  k_bounds_final<<<1, 32, 0, st>>>(part, nb_bounds, d, bounds);
+  k_bounds_partial<<<nb_bounds, 256, 0, st>>>(X, N, d, part); count_launch();
+  k_bounds_final<<<1, 32, 0, st>>>(part, nb_bounds, d, bounds); count_launch();
   double hb[2 * VD_MAX_D];
   cudaMemcpyAsync(hb, bounds, sizeof(double) * 2 * d, cudaMemcpyDeviceToHost, st);
   e = cudaStreamSynchronize(st);
@@ -321,7 +321,7 @@ cudaError_t build_tree(const double* X, int64_t N, int d, cudaStream_t st, DevBu
   for (int k = 0; k < 2 * d; ++k) ca = std::max(ca, std::fabs(hb[k]));
   if (!std::isfinite(ca)) { scratch.release(); return cudaErrorInvalidValue; }
   t.coord_abs = (float)ca * (1.0f + 1e-6f);
-  k_morton<<<nblocks(N, 256), 256, 0, st>>>(X, N, d, bounds, keys, vals);
+  k_morton<<<nblocks(N, 256), 256, 0, st>>>(X, N, d, bounds, keys, vals); count_launch();
   e = radix_sort_u64(keys, vals, ktmp, vtmp, N, counts, orand, st);
   if (e != cudaSuccess) { scratch.release(); return e; }
   double *x64 = nullptr, *lo64 = nullptr, *hi64 = nullptr;
@@ -337,12 +337,12 @@ cudaError_t build_tree(const double* X, int64_t N, int d, cudaStream_t st, DevBu
     scratch.release();
     return e;
   }
-  k_tiles<<<nblocks(t.ntiles * kTile, 256), 256, 0, st>>>(X, N, d, vals, t.ntiles, x64, x32, ids);
+  k_tiles<<<nblocks(t.ntiles * kTile, 256), 256, 0, st>>>(X, N, d, vals, t.ntiles, x64, x32, ids); count_launch();
   k_leaf_bbox<<<nblocks(t.ntiles * 32, 256), 256, 0, st>>>(x64, t.ntiles, d, t.total, t.off[0], lo64, hi64, lo32,
-                                                             hi32);
+                                                             hi32); count_launch();
   for (int L = 1; L < t.nlev; ++L)
     k_level_bbox<<<nblocks(t.cnt[L] * 32, 256), 256, 0, st>>>(d, t.total, t.off[L - 1], t.cnt[L - 1], t.off[L],
-                                                                t.cnt[L], lo64, hi64, lo32, hi32);
+                                                                t.cnt[L], lo64, hi64, lo32, hi32); count_launch();
   e = cudaStreamSynchronize(st);
   scratch.release();
   if (e != cudaSuccess) return e;

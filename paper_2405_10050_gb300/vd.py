@@ -29,7 +29,7 @@ class VDError(RuntimeError):
 
 class vd_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("box", ctypes.c_int32), ("hash_capacity", ctypes.c_int64),
-                ("max_levels", ctypes.c_int64), ("wait_limit", ctypes.c_int64), ("tile_n", ctypes.c_int32),
+                ("max_levels", ctypes.c_int64), ("wait_limit", ctypes.c_int64), ("knn_k", ctypes.c_int32),
                 ("rays_per_block", ctypes.c_int32)]
 
 
@@ -37,13 +37,13 @@ class vd_stats(ctypes.Structure):
     _fields_ = [("rays", ctypes.c_int64), ("tiles_visited", ctypes.c_int64), ("pairs_screened", ctypes.c_int64),
                 ("rechecked", ctypes.c_int64), ("fallback_rays", ctypes.c_int64), ("overflow_rays", ctypes.c_int64),
                 ("ties", ctypes.c_int64), ("levels", ctypes.c_int64), ("vertices", ctypes.c_int64),
-                ("ms", ctypes.c_double)]
+                ("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("raycast_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-EXPORTS = ["vd_config_default", "vd_create", "vd_destroy", "vd_last_error", "vd_status_str", "vd_set_precision",
+EXPORTS = ["vd_kernel_launches", "vd_config_default", "vd_create", "vd_destroy", "vd_last_error", "vd_status_str", "vd_set_precision",
            "vd_last_stats", "vd_set_nodes", "vd_raycast", "vd_vertices", "vd_mesh_count", "vd_mesh_dim",
            "vd_mesh_copy", "vd_mesh_stats", "vd_mesh_free", "vd_mc_integrate", "vd_mc_get", "vd_mc_rays",
            "vd_mc_adjoint", "vd_mc_stats", "vd_mc_count", "vd_mc_free", "vd_mc_directions",
@@ -68,6 +68,7 @@ def load(build_if_missing: bool = True):
     L = ctypes.CDLL(_build.LIB)
     P, i32, i64, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64
     sig = {
+        "vd_kernel_launches": (i64, []),
         "vd_config_default": (None, [P]),
         "vd_create": (i32, [P, P, P]),
         "vd_destroy": (None, [P]),
@@ -139,6 +140,10 @@ def _stream_ptr(stream):
 
 
 # ----------------------------------------------------------- thin wrappers --
+def vd_kernel_launches():
+    return int(load().vd_kernel_launches())
+
+
 def vd_config_default():
     cfg = vd_config()
     load().vd_config_default(ctypes.byref(cfg))

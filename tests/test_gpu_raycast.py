@@ -12,9 +12,9 @@ pytestmark = pytest.mark.gpu
 PRECS = [VD_FP64, VD_FP32]
 
 
-def _run(X, O, U, E, prec, box=True):
+def _run(X, O, U, E, prec, box=True, knn_k=0):
     torch = need_cuda()
-    vor = Voronoi(X, precision=prec, box=box)
+    vor = Voronoi(X, precision=prec, box=box, knn_k=knn_k)
     hit, t, se = vor.raycast(O, U, E, screen_err=True)
     st = vor.stats()
     vor.close()
@@ -39,6 +39,21 @@ def test_rays_from_nodes(orc, prec, d, N):
         # its width is set by the absolute binary32 error of the coordinates
         assert np.all(se >= 0) and np.median(se) < 1e-2
         assert st["rechecked"] >= R
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("d,N", [(2, 2000), (3, 1500), (5, 3000), (8, 600)])
+def test_tree_walk_only(orc, prec, d, N):
+    """The bounding-box tree walk alone (no candidate lists) gives the same
+    exact hits; with lists a short list forces many rays onto the walk."""
+    X = synth.uniform(N, d, seed=200 + d)
+    rng = np.random.default_rng(d + 1)
+    cells = rng.integers(0, N, 2000).astype(np.int32)
+    U = random_unit(rng, 2000, d)
+    h0, t0 = orc.raycast(X, X[cells], U, cells)
+    for knn in (-1, 4):
+        h1, t1, _, st = _run(X, X[cells], U, cells[:, None], prec, knn_k=knn)
+        assert np.array_equal(h0, h1) and np.array_equal(t0, t1)
 
 
 @pytest.mark.parametrize("prec", PRECS)

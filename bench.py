@@ -248,6 +248,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     cfg = vd.vd_config_default()
     cfg.precision = VD_FP32
+    cfg.knn_k = args.knn_k
     ctx = vd.vd_create(cfg, stream.cuda_stream)
 
     def step(c):
@@ -299,6 +300,7 @@ def run_ours(args):
     if not args.no_fp64:
         cfg64 = vd.vd_config_default()
         cfg64.precision = VD_FP64
+        cfg64.knn_k = args.knn_k
         ctx64 = vd.vd_create(cfg64, stream.cuda_stream)
         m, st = step(ctx64)
         vd.vd_mesh_free(m)
@@ -366,6 +368,8 @@ def run_ours(args):
                            "levels": last_stats["levels"],
                            "pairs_per_ray": last_stats["pairs_screened"] / max(last_stats["rays"], 1),
                            "rechecked_per_ray": last_stats["rechecked"] / max(last_stats["rays"], 1),
+                           "tree_walk_rays_per_step": last_stats["fallback_rays"],
+                           "knn_k": args.knn_k,
                            "step_launches": last_stats["launches"],
                            "l2": "inputs larger than L2 (traversal tables ~1.5 GB per step)",
                            "parallelism": f"replicas x{ws}"},
@@ -392,6 +396,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-rays", type=int, default=4000)
+    ap.add_argument("--knn-k", type=int, default=0, help="candidate list length (0 automatic, -1 none)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

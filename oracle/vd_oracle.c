@@ -475,8 +475,10 @@ void or_mc_adjoint(const double* X, int64_t N, int d, int64_t R, uint64_t seed, 
 /* 2.1: equidistant to its nodes, on its faces).  With x0 the first node and */
 /* y = r - x0: fixed axes y_a = s_a - x0_a; for every other node k,          */
 /* 2 w_k . y = |w_k|^2 (w_k = x_k - x0), moved to the free axes; Gaussian    */
-/* elimination with partial pivoting (first maximal |pivot|).  Returns 0 if  */
-/* two faces share an axis or the system is singular.                        */
+/* elimination with partial pivoting (first maximal |pivot|, magnitudes      */
+/* compared after rounding to binary32), multipliers and back substitution   */
+/* through the rounded reciprocal 1/pivot.  Returns 0 if two faces share an  */
+/* axis or the system is singular.                                           */
 int or_vertex_coords(const double* X, int d, const int32_t* sig, double* r) {
   int fixed[OR_MAXD], side[OR_MAXD];
   for (int a = 0; a < d; ++a) fixed[a] = 0;
@@ -508,17 +510,19 @@ int or_vertex_coords(const double* X, int d, const int32_t* sig, double* r) {
     for (int c = 0; c < nf; ++c) M[rr][c] = 2.0 * w[freeax[c]];
     b[rr] = ww;
   }
+  double inv[OR_MAXD];
   for (int c = 0; c < nf; ++c) {
     int piv = c;
     for (int rr = c + 1; rr < nf; ++rr)
-      if (fabs(M[rr][c]) > fabs(M[piv][c])) piv = rr;
+      if ((float)fabs(M[rr][c]) > (float)fabs(M[piv][c])) piv = rr;
     if (M[piv][c] == 0.0) return 0;
     if (piv != c) {
       for (int cc = 0; cc < nf; ++cc) { double tmp = M[c][cc]; M[c][cc] = M[piv][cc]; M[piv][cc] = tmp; }
       double tb = b[c]; b[c] = b[piv]; b[piv] = tb;
     }
+    inv[c] = 1.0 / M[c][c];
     for (int rr = c + 1; rr < nf; ++rr) {
-      double f = M[rr][c] / M[c][c];
+      double f = M[rr][c] * inv[c];
       for (int cc = c + 1; cc < nf; ++cc) M[rr][cc] = M[rr][cc] - f * M[c][cc];
       b[rr] = b[rr] - f * b[c];
     }
@@ -527,7 +531,7 @@ int or_vertex_coords(const double* X, int d, const int32_t* sig, double* r) {
   for (int c = nf - 1; c >= 0; --c) {
     double s = b[c];
     for (int cc = c + 1; cc < nf; ++cc) s = s - M[c][cc] * z[cc];
-    z[c] = s / M[c][c];
+    z[c] = s * inv[c];
   }
   for (int c = 0; c < nf; ++c) y[freeax[c]] = z[c];
   for (int a = 0; a < d; ++a) r[a] = fixed[a] ? (side[a] ? 1.0 : 0.0) : x0[a] + y[a];
@@ -539,8 +543,10 @@ int or_vertex_coords(const double* X, int d, const int32_t* sig, double* r) {
  * pointing away from the dropped generator.  The nodes of eta give rows
  * w_k = x_k - g (g its first node) over the axes not fixed by its faces; the
  * null vector is found by Gaussian elimination with complete pivoting (first
- * maximal |entry| in row-major order), the non-pivot column set to 1, back
- * substitution, then u = z / |z|.  Sign: a dropped node e must give
+ * maximal |entry| in row-major order, magnitudes compared after rounding to
+ * binary32; multipliers through the rounded reciprocal 1/pivot), the
+ * non-pivot column set to 1, back substitution, then u = z * (1/|z|).
+ * Sign: a dropped node e must give
  * u . (x_e - g) < 0 (same sum order as the RayCast's den); a dropped lower
  * face u_a > 0, an upper face u_a < 0.  Returns 0 if eta has no node or the
  * rows are degenerate. */
@@ -570,21 +576,23 @@ int or_search_direction(const double* X, int d, const int32_t* sig, int drop, do
   }
   int colperm[OR_MAXD];
   for (int c = 0; c < nf; ++c) colperm[c] = c;
+  double inv[OR_MAXD];
   for (int c = 0; c < nr; ++c) {
     int pr = c, pc = c;
-    double best = -1.0;
+    float best = -1.0f;
     for (int rr = c; rr < nr; ++rr)
       for (int cc = c; cc < nf; ++cc)
-        if (fabs(M[rr][cc]) > best) { best = fabs(M[rr][cc]); pr = rr; pc = cc; }
-    if (best == 0.0) return 0;
+        if ((float)fabs(M[rr][cc]) > best) { best = (float)fabs(M[rr][cc]); pr = rr; pc = cc; }
+    if (M[pr][pc] == 0.0) return 0;
     if (pr != c)
       for (int cc = 0; cc < nf; ++cc) { double tmp = M[c][cc]; M[c][cc] = M[pr][cc]; M[pr][cc] = tmp; }
     if (pc != c) {
       for (int rr = 0; rr < nr; ++rr) { double tmp = M[rr][c]; M[rr][c] = M[rr][pc]; M[rr][pc] = tmp; }
       int tp = colperm[c]; colperm[c] = colperm[pc]; colperm[pc] = tp;
     }
+    inv[c] = 1.0 / M[c][c];
     for (int rr = c + 1; rr < nr; ++rr) {
-      double f = M[rr][c] / M[c][c];
+      double f = M[rr][c] * inv[c];
       for (int cc = c + 1; cc < nf; ++cc) M[rr][cc] = M[rr][cc] - f * M[c][cc];
     }
   }
@@ -594,15 +602,15 @@ int or_search_direction(const double* X, int d, const int32_t* sig, int drop, do
   for (int c = nr - 1; c >= 0; --c) {
     double s = -M[c][nf - 1];
     for (int cc = c + 1; cc < nr; ++cc) s = s - M[c][cc] * zp[cc];
-    zp[c] = s / M[c][c];
+    zp[c] = s * inv[c];
   }
   double z[OR_MAXD];
   for (int c = 0; c < nf; ++c) z[colperm[c]] = zp[c];
   double nz = 0.0;
   for (int c = 0; c < nf; ++c) nz = nz + z[c] * z[c];
-  nz = sqrt(nz);
+  const double invn = 1.0 / sqrt(nz);
   for (int a = 0; a < d; ++a) u[a] = 0.0;
-  for (int c = 0; c < nf; ++c) u[freeax[c]] = z[c] / nz;
+  for (int c = 0; c < nf; ++c) u[freeax[c]] = z[c] * invn;
   int32_t e = sig[drop];
   int flip;
   if (e >= 0) {

@@ -320,7 +320,9 @@ vd_status vd_raycast(vd_ctx* ctx, const double* origins, const double* dirs, con
   VD_CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->st), "memset");
   const long long l0 = vd::g_launches.load();
   Timer tm(ctx->st);
-  VD_CK(vd::launch_raycast(ctx->tree, rs, ro, effective_precision(ctx), ctx->ctr, ctx->st), "raycast");
+  int64_t nfb = 0;
+  VD_CK(vd::launch_raycast(ctx->tree, rs, ro, effective_precision(ctx), ctx->ctr, ctx->st, &nfb), "raycast");
+  ctx->last.fallback_rays = nfb;
   ctx->last.ms = tm.stop();
   ctx->last.raycast_ms = ctx->last.ms;
   ctx->last.launches = vd::g_launches.load() - l0;
@@ -403,7 +405,8 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
   Timer tm(ctx->st);
   {
     Timer tr(ctx->st);
-    VD_CK(vd::launch_raycast(tv, rs, ro, effective_precision(ctx), ctx->ctr, ctx->st), "mc raycast");
+    VD_CK(vd::launch_raycast(tv, rs, ro, effective_precision(ctx), ctx->ctr, ctx->st, &mc->stats.fallback_rays),
+          "mc raycast");
     mc->stats.raycast_ms = tr.stop();
   }
   int64_t nnz = 0;
@@ -422,7 +425,6 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
   mc->stats.pairs_screened = (int64_t)hc.pairs;
   mc->stats.rechecked = (int64_t)hc.rechecked;
   mc->stats.overflow_rays = (int64_t)hc.overflow;
-  mc->stats.fallback_rays = (int64_t)hc.fallback;
   ctx->last = mc->stats;
   return check_flags(ctx, hc);
 }

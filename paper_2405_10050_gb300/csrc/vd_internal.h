@@ -73,6 +73,7 @@ struct RaySource {
   uint64_t seed = 0;
   uint32_t set = 0;
   int box = 1;
+  int rpb = 32;                  // rays per warp batch (1..32), set by the launcher
 };
 
 struct RayOut {
@@ -129,7 +130,7 @@ cudaError_t build_knn(TreeView* tv, int K, cudaStream_t st, DevBufs& bufs);
 // Default list length for dimension d (0: no lists, tree walk only).
 int default_knn_k(int d);
 cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision,
-                           Counters* ctr, cudaStream_t st);
+                           Counters* ctr, cudaStream_t st, int64_t* nfallback = nullptr);
 cudaError_t launch_mc_directions(uint64_t seed, uint32_t set, int64_t cell0, int64_t ncells, int64_t R, int d,
                                  double* out, cudaStream_t st);
 

@@ -262,11 +262,11 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
     unsigned long long b = 0;
     if (lane == 0) b = atomicAdd(work, 1ull);
     b = __shfl_sync(kFull, b, 0);
-    const int64_t b0 = (int64_t)b * 32;
+    const int64_t b0 = (int64_t)b * rs.rpb;
     if (b0 >= R) break;
     // ---- set-up: one ray per lane ----
     const int64_t slot = b0 + lane;
-    const bool vr = slot < R;
+    const bool vr = lane < rs.rpb && slot < R;
     const int64_t r = vr ? (subset ? (int64_t)subset[slot] : slot) : 0;
     if (vr) {
       double v[D], u[D];
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
     }
     __syncwarp();
     // ---- screening: the warp walks the tree for each ray ----
-    for (int rr = 0; rr < 32 && b0 + rr < R; ++rr) {
+    for (int rr = 0; rr < rs.rpb && b0 + rr < R; ++rr) {
       float u[D], gg[D], pp[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -565,10 +565,10 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_fp64(TreeView tr, RaySource r
     unsigned long long b = 0;
     if (lane == 0) b = atomicAdd(work, 1ull);
     b = __shfl_sync(kFull, b, 0);
-    const int64_t b0 = (int64_t)b * 32;
+    const int64_t b0 = (int64_t)b * rs.rpb;
     if (b0 >= R) break;
     const int64_t slot = b0 + lane;
-    const bool vr = slot < R;
+    const bool vr = lane < rs.rpb && slot < R;
     const int64_t r = vr ? (subset ? (int64_t)subset[slot] : slot) : 0;
     if (vr) {
       double v[D], u[D];
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_fp64(TreeView tr, RaySource r
       S.bkey[lane] = bk;
     }
     __syncwarp();
-    for (int rr = 0; rr < 32 && b0 + rr < R; ++rr) {
+    for (int rr = 0; rr < rs.rpb && b0 + rr < R; ++rr) {
       double u[D], gg[D], pp[D];
       float u32[D], g32[D], p32[D];
 #pragma unroll
@@ -741,7 +741,10 @@ cudaError_t launch_ray_d(const TreeView& tv, const RaySource& rs, const RayOut& 
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   RaySource r2 = rs;
   r2.R = nrays;
-  const int64_t batches = (nrays + 31) / 32;
+  // few rays (the tree-walk leftovers of the list scan): one ray per warp so
+  // that they spread over the SMs; otherwise 32 rays per warp
+  r2.rpb = nrays < (int64_t)nsm * 256 ? 1 : 32;
+  const int64_t batches = (nrays + r2.rpb - 1) / r2.rpb;
   cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
   auto go = [&](auto kern, size_t sm) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -771,8 +774,8 @@ cudaError_t launch_ray_d(const TreeView& tv, const RaySource& rs, const RayOut& 
 // records kcert = the (K+1)-th smallest ww32 (or r^2): every node missing
 // from the list has ww32 >= kcert.
 // ------------------------------------------------------------------------
-constexpr int kKnnCap = 4096;
-constexpr int kKnnWpb = 2;
+constexpr int kKnnCap = 2048;
+constexpr int kKnnWpb = 4;
 
 struct WarpKnn {
   float key[kKnnCap];
@@ -794,6 +797,7 @@ __global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, 
     for (int k = 0; k < D; ++k) g32[k] = k < d ? tr.X32[g * d + k] : 0.f;
     float r = r0;
     int count = 0;
+    const float target = fminf(1.5f * (float)K + 32.f, 0.75f * (float)kKnnCap);
     for (int attempt = 0; attempt < 64; ++attempt) {
       Ball<D> ball;
 #pragma unroll
@@ -820,12 +824,14 @@ __global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, 
       };
       unsigned long long dummy = 0;
       walk<D>(tr, S.stk, ball, lane, leaf, dummy);
+      // aim the ball at about `target` nodes: count scales like r^d
       if (count > kKnnCap) {
-        r *= 0.7f;
+        r *= fminf(0.9f, __powf(target / (float)count, 1.f / (float)d));
         continue;
       }
       if (count <= K && r < rmax) {
-        r = fminf(r * 1.6f, rmax * 1.001f);
+        const float f = count > 0 ? __powf(target / (float)count, 1.f / (float)d) : 2.f;
+        r = fminf(r * fminf(fmaxf(f, 1.1f), 2.f), rmax * 1.001f);
         continue;
       }
       break;
@@ -910,7 +916,7 @@ cudaError_t launch_knn_d(TreeView* tv, int K, float r0, float rmax, int32_t* knn
               : FN<16>(__VA_ARGS__))
 
 cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision,
-                           Counters* ctr, cudaStream_t st) {
+                           Counters* ctr, cudaStream_t st, int64_t* nfallback) {
   if (rs.R <= 0) return cudaSuccess;
   unsigned long long* work = reinterpret_cast<unsigned long long*>(&ctr->aux1);
   cudaError_t e;
@@ -924,6 +930,7 @@ cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return e;
     const int64_t n = std::min<int64_t>((int64_t)nfb, ro.fallback_cap);
+    if (nfallback) *nfallback += n;
     if (n > 0)
       e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rs, ro, precision, ctr, work, ro.fallback_list, n, false, st);
   } else {
@@ -943,7 +950,7 @@ cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut
 }
 
 int default_knn_k(int d) {
-  static const int k[] = {0, 16, 32, 96, 256, 1024, 2048, 2048, 2048};
+  static const int k[] = {0, 16, 32, 96, 256, 512, 1024, 1024, 1024};
   return d <= 8 ? k[d] : 0;
 }
 
@@ -981,7 +988,7 @@ cudaError_t build_knn(TreeView* tv, int K, cudaStream_t st, DevBufs& bufs) {
     }
   }
   const double vball = std::pow(M_PI, 0.5 * d) / std::tgamma(0.5 * d + 1.0);
-  const float r0 = (float)std::pow(1.5 * K * vol / ((double)N * vball), 1.0 / d);
+  const float r0 = (float)std::pow(std::min(1.5 * K + 32, 0.75 * kKnnCap) * vol / ((double)N * vball), 1.0 / d);
   const float rmax = (float)std::sqrt(diag2) * 1.01f + 1e-6f;
   e = VD_DISPATCH_D(d, launch_knn_d, tv, K, std::min(r0, rmax), rmax, knn, kcnt, kcert, st);
   if (e != cudaSuccess) return e;

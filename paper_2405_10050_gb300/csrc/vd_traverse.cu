@@ -87,7 +87,8 @@ __device__ __forceinline__ void sort_small(int32_t* t, int L) {
 
 // Canonical vertex coordinates from the sorted tuple (same steps as the
 // definition: x0 = first node, y = r - x0, fixed axes from the faces,
-// rows 2 w_k . y = |w_k|^2 on the free axes, partial pivoting).
+// rows 2 w_k . y = |w_k|^2 on the free axes, partial pivoting with the
+// magnitudes compared in binary32, multipliers through 1/pivot).
 template <int D>
 __device__ bool vertex_coords(const double* X, int d, const int32_t* sig, double* r) {
   int fixed[D], side[D];
@@ -123,10 +124,17 @@ __device__ bool vertex_coords(const double* X, int d, const int32_t* sig, double
     for (int c = 0; c < nf; ++c) M[rr][c] = __dmul_rn(2.0, w[freeax[c]]);
     b[rr] = ww;
   }
+  double inv[D];
   for (int c = 0; c < nf; ++c) {
     int piv = c;
-    for (int rr = c + 1; rr < nf; ++rr)
-      if (fabs(M[rr][c]) > fabs(M[piv][c])) piv = rr;
+    float pbest = __double2float_rn(fabs(M[c][c]));
+    for (int rr = c + 1; rr < nf; ++rr) {
+      const float a = __double2float_rn(fabs(M[rr][c]));
+      if (a > pbest) {
+        piv = rr;
+        pbest = a;
+      }
+    }
     if (M[piv][c] == 0.0) return false;
     if (piv != c) {
       for (int cc = 0; cc < nf; ++cc) {
@@ -138,8 +146,9 @@ __device__ bool vertex_coords(const double* X, int d, const int32_t* sig, double
       b[c] = b[piv];
       b[piv] = tb;
     }
+    inv[c] = __drcp_rn(M[c][c]);
     for (int rr = c + 1; rr < nf; ++rr) {
-      const double f = __ddiv_rn(M[rr][c], M[c][c]);
+      const double f = __dmul_rn(M[rr][c], inv[c]);
       for (int cc = c + 1; cc < nf; ++cc) M[rr][cc] = __dadd_rn(M[rr][cc], -__dmul_rn(f, M[c][cc]));
       b[rr] = __dadd_rn(b[rr], -__dmul_rn(f, b[c]));
     }
@@ -148,7 +157,7 @@ __device__ bool vertex_coords(const double* X, int d, const int32_t* sig, double
   for (int c = nf - 1; c >= 0; --c) {
     double s = b[c];
     for (int cc = c + 1; cc < nf; ++cc) s = __dadd_rn(s, -__dmul_rn(M[c][cc], z[cc]));
-    z[c] = __ddiv_rn(s, M[c][c]);
+    z[c] = __dmul_rn(s, inv[c]);
   }
   for (int c = 0; c < nf; ++c) y[freeax[c]] = z[c];
   for (int a = 0; a < d; ++a) r[a] = fixed[a] ? (side[a] ? 1.0 : 0.0) : __dadd_rn(x0[a], y[a]);
@@ -157,9 +166,10 @@ __device__ bool vertex_coords(const double* X, int d, const int32_t* sig, double
 
 // SearchDirection: unit null vector of the rows x_k - g (nodes of eta other
 // than its first node g) on the axes not fixed by eta's faces; complete
-// pivoting (first maximal |entry| in row-major order), the non-pivot column
-// set to 1, back substitution, u = z / |z|; sign so that the dropped node e
-// has u.(x_e - g) < 0, a dropped lower face u_a > 0, an upper face u_a < 0.
+// pivoting (first maximal |entry| in row-major order, magnitudes compared in
+// binary32, multipliers through 1/pivot), the non-pivot column set to 1,
+// back substitution, u = z * (1/|z|); sign so that the dropped node e has
+// u.(x_e - g) < 0, a dropped lower face u_a > 0, an upper face u_a < 0.
 template <int D>
 __device__ bool search_direction(const double* X, int d, const int32_t* sig, int drop, double* u) {
   int32_t eta[D];
@@ -187,17 +197,20 @@ __device__ bool search_direction(const double* X, int d, const int32_t* sig, int
   }
   int colperm[D];
   for (int c = 0; c < nf; ++c) colperm[c] = c;
+  double inv[D];
   for (int c = 0; c < nr; ++c) {
     int pr = c, pc = c;
-    double best = -1.0;
+    float best = -1.0f;
     for (int rr = c; rr < nr; ++rr)
-      for (int cc = c; cc < nf; ++cc)
-        if (fabs(M[rr][cc]) > best) {
-          best = fabs(M[rr][cc]);
+      for (int cc = c; cc < nf; ++cc) {
+        const float a = __double2float_rn(fabs(M[rr][cc]));
+        if (a > best) {
+          best = a;
           pr = rr;
           pc = cc;
         }
-    if (best == 0.0) return false;
+      }
+    if (M[pr][pc] == 0.0) return false;
     if (pr != c)
       for (int cc = 0; cc < nf; ++cc) {
         const double tmp = M[c][cc];
@@ -214,8 +227,9 @@ __device__ bool search_direction(const double* X, int d, const int32_t* sig, int
       colperm[c] = colperm[pc];
       colperm[pc] = tp;
     }
+    inv[c] = __drcp_rn(M[c][c]);
     for (int rr = c + 1; rr < nr; ++rr) {
-      const double f = __ddiv_rn(M[rr][c], M[c][c]);
+      const double f = __dmul_rn(M[rr][c], inv[c]);
       for (int cc = c + 1; cc < nf; ++cc) M[rr][cc] = __dadd_rn(M[rr][cc], -__dmul_rn(f, M[c][cc]));
     }
   }
@@ -224,15 +238,15 @@ __device__ bool search_direction(const double* X, int d, const int32_t* sig, int
   for (int c = nr - 1; c >= 0; --c) {
     double s = -M[c][nf - 1];
     for (int cc = c + 1; cc < nr; ++cc) s = __dadd_rn(s, -__dmul_rn(M[c][cc], zp[cc]));
-    zp[c] = __ddiv_rn(s, M[c][c]);
+    zp[c] = __dmul_rn(s, inv[c]);
   }
   double z[D];
   for (int c = 0; c < nf; ++c) z[colperm[c]] = zp[c];
   double nz = 0.0;
   for (int c = 0; c < nf; ++c) nz = __dadd_rn(nz, __dmul_rn(z[c], z[c]));
-  nz = __dsqrt_rn(nz);
+  const double invn = __drcp_rn(__dsqrt_rn(nz));
   for (int a = 0; a < d; ++a) u[a] = 0.0;
-  for (int c = 0; c < nf; ++c) u[freeax[c]] = __ddiv_rn(z[c], nz);
+  for (int c = 0; c < nf; ++c) u[freeax[c]] = __dmul_rn(z[c], invn);
   const int32_t e = sig[drop];
   bool flip;
   if (e >= 0) {
@@ -684,6 +698,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     }
   } evg{ev0, ev1};
   double raycast_ms = 0.0;
+  int64_t nfallback = 0;
   auto run_rays = [&](int64_t nr, int stride) -> cudaError_t {
     RaySource rs;
     rs.mode = 0;
@@ -703,7 +718,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     cudaError_t ee = cudaMemsetAsync(&ctr->overflow, 0, sizeof(unsigned long long), st);
     if (ee != cudaSuccess) return ee;
     cudaEventRecord(ev0, st);
-    ee = launch_raycast(tv, rs, rout, precision, ctr, st);
+    ee = launch_raycast(tv, rs, rout, precision, ctr, st, &nfallback);
     cudaEventRecord(ev1, st);
     if (ee == cudaSuccess) ee = cudaEventSynchronize(ev1);
     float ms = 0.f;
@@ -864,6 +879,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   stats->vertices = nv;
   stats->rays = raycasts;
   stats->raycast_ms = raycast_ms;
+  stats->fallback_rays = nfallback;
   return cudaSuccess;
 #undef VD_TRY
 }

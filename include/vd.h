@@ -123,6 +123,23 @@ vd_status vd_raycast(vd_ctx* ctx, const double* origins, const double* dirs, con
                      int32_t eta_stride, int64_t R, int32_t* hit, double* t, float* screen_err,
                      int32_t on_device);
 
+/* Allocation-free variant of vd_raycast (the paper has no counterpart: this
+ * is a deployment aid).  For callers that must not have the library call
+ * cudaMalloc while they run -- their device memory belongs to another
+ * allocator, or a steady-state loop must not pay cudaMalloc's implicit
+ * synchronisation or risk running out of memory mid-run.  Same arguments and
+ * results as vd_raycast, except: origins, dirs, eta, hit and t must be DEVICE
+ * pointers; screen_err is not produced; R <= 262,144 (larger R returns
+ * VD_EINVAL).  Its work lists and counters live in one fixed 2 MiB device
+ * array inside libvd (resident on every GPU that loads the library until the
+ * process exits), shared by all calls and contexts: calls that overlap on the
+ * GPU race on it.  The first call on a device looks up that array's device
+ * address (once per device, with the device current), so make it before any
+ * stream capture.  The context must already hold a node set (vd_set_nodes,
+ * which does allocate); this call itself allocates nothing. */
+vd_status vd_raycast_noalloc(vd_ctx* ctx, const double* origins, const double* dirs, const int32_t* eta,
+                             int32_t eta_stride, int64_t R, int32_t* hit, double* t);
+
 /* Exhaustive vertex traversal (Section 2.3, Algorithm 2) of the diagram
  * clipped to [0,1]^d: seeds by Descent, then casts one ray along every edge
  * whose second vertex is still unknown, deduplicating vertices by their sorted

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "vd_dev.cuh"
@@ -607,3 +608,100 @@ void vd_mesh_free(vd_mesh* m) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free RayCast.  Some callers cannot let a library call cudaMalloc
+// on their hot path: their device memory belongs to another allocator (a
+// framework's caching pool or an arena sized once at start-up), or they run a
+// steady-state loop that must not pay cudaMalloc's implicit synchronisation or
+// risk an out-of-memory error mid-run.  vd_raycast_noalloc serves them: its
+// work lists and counters live in the file-scope device array below, so the
+// call itself allocates nothing.  The array is the same for every call and
+// every context in the process and holds the previous call's contents: the
+// counters are cleared at the start of each call, and two calls that overlap
+// on the GPU (other streams or threads) race on it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocMaxRays = (int64_t)1 << 18;  // 262,144 rays per call
+
+struct NoAllocScratch {
+  Counters ctr;
+  int32_t overflow[kNoAllocMaxRays];  // rays redone on the binary64 path
+  int32_t fallback[kNoAllocMaxRays];  // rays finished by the tree walk
+};
+
+// 2 MiB (+ counters), resident on every device that loads the library.
+__device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+NoAllocScratch* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  Host code only
+// sees a host-side stand-in under the array's name, so the address is looked
+// up once per device (with that device current) and cached.
+vd_status noalloc_scratch(vd_ctx* ctx, NoAllocScratch** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "vd_raycast_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return set_err(ctx, VD_EINVAL, "vd_raycast_noalloc: device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_err(ctx, e, "vd_raycast_noalloc: cudaGetSymbolAddress");
+    g_noalloc_addr[dev] = static_cast<NoAllocScratch*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return VD_OK;
+}
+
+}  // namespace
+
+extern "C" vd_status vd_raycast_noalloc(vd_ctx* ctx, const double* origins, const double* dirs, const int32_t* eta,
+                                        int32_t eta_stride, int64_t R, int32_t* hit, double* t) {
+  if (!ctx) return VD_EINVAL;
+  if (!ctx->X) return set_err(ctx, VD_EINVAL, "vd_raycast_noalloc: no node set");
+  if (R < 0 || (R > 0 && (!origins || !dirs || !eta || !hit || !t)) || eta_stride < 1 || eta_stride > ctx->d + 1)
+    return set_err(ctx, VD_EINVAL, "vd_raycast_noalloc: bad arguments (R=%lld, eta_stride=%d, d=%d)",
+                   (long long)R, eta_stride, ctx->d);
+  if (R > kNoAllocMaxRays)
+    return set_err(ctx, VD_EINVAL, "vd_raycast_noalloc: R=%lld exceeds the fixed scratch limit of %lld rays",
+                   (long long)R, (long long)kNoAllocMaxRays);
+  ctx->last = vd_stats{};
+  if (R == 0) return VD_OK;
+  NoAllocScratch* sc = nullptr;
+  vd_status s = noalloc_scratch(ctx, &sc);
+  if (s != VD_OK) return s;
+  vd::RaySource rs;
+  rs.mode = 0;
+  rs.R = R;
+  rs.origins = origins;
+  rs.dirs = dirs;
+  rs.eta = eta;
+  rs.eta_stride = eta_stride;
+  rs.box = ctx->cfg.box;
+  vd::RayOut ro;
+  ro.hit = hit;
+  ro.t = t;
+  ro.overflow_list = sc->overflow;
+  ro.overflow_cap = kNoAllocMaxRays;
+  ro.fallback_list = sc->fallback;
+  ro.fallback_cap = kNoAllocMaxRays;
+  VD_CK(cudaMemsetAsync(&sc->ctr, 0, sizeof(Counters), ctx->st), "vd_raycast_noalloc: clear counters");
+  int64_t nfb = 0;
+  VD_CK(vd::launch_raycast(ctx->tree, rs, ro, effective_precision(ctx), &sc->ctr, ctx->st, &nfb),
+        "vd_raycast_noalloc");
+  Counters hc;
+  VD_CK(cudaMemcpyAsync(&hc, &sc->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, ctx->st), "counters");
+  VD_CK(cudaStreamSynchronize(ctx->st), "sync");
+  ctx->last.rays = R;
+  ctx->last.tiles_visited = (int64_t)hc.tiles;
+  ctx->last.pairs_screened = (int64_t)hc.pairs;
+  ctx->last.rechecked = (int64_t)hc.rechecked;
+  ctx->last.overflow_rays = (int64_t)hc.overflow;
+  ctx->last.fallback_rays = nfb;
+  return check_flags(ctx, hc);
+}

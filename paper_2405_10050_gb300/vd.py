@@ -47,7 +47,7 @@ EXPORTS = ["vd_kernel_launches", "vd_config_default", "vd_create", "vd_destroy",
            "vd_last_stats", "vd_set_nodes", "vd_raycast", "vd_vertices", "vd_mesh_count", "vd_mesh_dim",
            "vd_mesh_copy", "vd_mesh_stats", "vd_mesh_free", "vd_mc_integrate", "vd_mc_get", "vd_mc_rays",
            "vd_mc_adjoint", "vd_mc_stats", "vd_mc_count", "vd_mc_free", "vd_mc_directions",
-           "vd_mc_integrate_batch"]
+           "vd_mc_integrate_batch", "vd_raycast_noalloc"]
 
 _lib = None
 
@@ -78,6 +78,7 @@ def load(build_if_missing: bool = True):
         "vd_last_stats": (i32, [P, P]),
         "vd_set_nodes": (i32, [P, P, i64, i32, i32]),
         "vd_raycast": (i32, [P, P, P, P, i32, i64, P, P, P, i32]),
+        "vd_raycast_noalloc": (i32, [P, P, P, P, i32, i64, P, P]),
         "vd_vertices": (i32, [P, P]),
         "vd_mesh_count": (i64, [P]),
         "vd_mesh_dim": (i32, [P]),
@@ -195,6 +196,17 @@ def vd_raycast(ctx, origins, dirs, eta, hit, t, screen_err=None):
             t[...] = k5
         if screen_err is not None and k6 is not screen_err:
             screen_err[...] = k6
+
+
+def vd_raycast_noalloc(ctx, origins, dirs, eta, hit, t):
+    """Allocation-free RayCast: all arrays must be CUDA tensors."""
+    args = [_ptr(a, dt) for a, dt in ((origins, np.float64), (dirs, np.float64), (eta, np.int32),
+                                      (hit, np.int32), (t, np.float64))]
+    if any(a[1] != 1 for a in args):
+        raise ValueError("vd_raycast_noalloc takes device (CUDA) arrays only")
+    stride = eta.shape[1] if len(eta.shape) == 2 else 1
+    _check(ctx, load().vd_raycast_noalloc(ctx, args[0][0], args[1][0], args[2][0], stride, origins.shape[0],
+                                          args[3][0], args[4][0]))
 
 
 def vd_mc_directions(ctx, seed, set_id, cell0, ncells, R, d, out):

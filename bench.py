@@ -243,6 +243,9 @@ def run_ours(args):
     torch.cuda.set_device(local)
     from paper_2405_10050_gb300 import VD_FP32, VD_FP64, synth, vd
     vd.load()
+    if args.only_mc:  # the MC secondary measurement alone (profiling)
+        print(json.dumps({"mc": run_mc(args, vd, torch.cuda.current_stream())}), flush=True)
+        return
     X = synth.uniform(args.N, args.d, seed=0)
     Xd = torch.tensor(X, device="cuda")
     stream = torch.cuda.current_stream()
@@ -352,6 +355,10 @@ def run_ours(args):
                 "peak_source": f"FP32 lanes x 2 x sm_max_mhz ({src} peaks file)",
                 "algorithmic_flops_per_ray": flops_per_ray, "raycast_ms_per_step": rc_ms / args.steps}
 
+    mc = None
+    if not args.no_mc:
+        mc = run_mc(args, vd, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         rate, n, dt, cores = cpu_oracle_rate(X, tup.cpu().numpy(), crd.cpu().numpy(), target_s=args.cpu_seconds)
@@ -377,11 +384,65 @@ def run_ours(args):
                 "speedup_vs_fp64": (value / ws / fp64["value"]) if fp64 else None,
                 "e2e": {"value": e2e_value, "unit": "raycasts/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks}
+                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "mc": mc}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+MC_WORKLOAD = ("MC volumes + interface areas + adjoint, d=4, N=100000 iid uniform in [0,1]^4 (seed 0), "
+               "1024 rays per cell")
+
+
+def run_mc(args, vd, stream):
+    """Secondary line of the metric: MC vol+grad cells/s on the MC workload,
+    binary32-screened path vs plain binary64 path (same seeded directions,
+    identical per-ray hits required)."""
+    import torch
+    from paper_2405_10050_gb300 import VD_FP32, VD_FP64, synth
+    N, d, R = args.mc_n, 4, args.mc_rays
+    X = torch.tensor(synth.uniform(N, d, seed=0), device="cuda")
+    gV = torch.ones(N, dtype=torch.float64, device="cuda")
+    out = {"workload": MC_WORKLOAD.replace("100000", str(N)).replace("1024 rays", f"{R} rays"),
+           "unit": "cells/s"}
+    hits = {}
+    for name, prec in (("mixed", VD_FP32), ("fp64", VD_FP64)):
+        cfg = vd.vd_config_default()
+        cfg.precision = prec
+        ctx = vd.vd_create(cfg, stream.cuda_stream)
+        gX = torch.empty((N, d), dtype=torch.float64, device="cuda")
+
+        def step():
+            vd.vd_set_nodes(ctx, X)
+            m = vd.vd_mc_integrate(ctx, R, 7)
+            nnz = vd.vd_mc_get(m)
+            gA = torch.ones(max(nnz, 1), dtype=torch.float64, device="cuda")
+            vd.vd_mc_adjoint(m, gV, gA[:nnz], gX)
+            return m
+
+        vd.vd_mc_free(step())
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = vd.vd_mc_stats(m)
+        h = torch.empty((N, R), dtype=torch.int32, device="cuda")
+        vd.vd_mc_rays(m, h, None)
+        hits[name] = h
+        vd.vd_mc_free(m)
+        vd.vd_destroy(ctx)
+        out[name] = {"cells_per_s": N / (ms / 1000.0), "rays_per_s": N * R / (ms / 1000.0), "ms_per_step": ms,
+                     "raycast_ms": st["raycast_ms"], "tree_walk_rays": st["fallback_rays"],
+                     "pairs_per_ray": st["pairs_screened"] / max(st["rays"], 1)}
+    out["value"] = out["mixed"]["cells_per_s"]
+    out["speedup_vs_fp64"] = out["mixed"]["cells_per_s"] / out["fp64"]["cells_per_s"]
+    out["hits_identical_to_fp64"] = bool(torch.equal(hits["mixed"], hits["fp64"]))
+    return out
 
 
 def main():
@@ -397,6 +458,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-rays", type=int, default=4000)
     ap.add_argument("--knn-k", type=int, default=0, help="candidate list length (0 automatic, -1 none)")
+    ap.add_argument("--no-mc", action="store_true")
+    ap.add_argument("--only-mc", action="store_true")
+    ap.add_argument("--mc-n", type=int, default=100000)
+    ap.add_argument("--mc-rays", type=int, default=1024)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -107,13 +107,40 @@ __global__ void k_scan64(const int64_t* in, int64_t n, int64_t* out) {
   if (threadIdx.x == 1023) out[n] = part[1023];
 }
 
+constexpr int kMcWarps = 4;      // warps (cells in flight) per block
+constexpr int kMcList = 1024;    // matching-ray indices gathered per pass
+
+// Gathers, in ascending ray order from *k0, up to kMcList indices k with
+// h[k] == id into L; returns their number and advances *k0.  All lanes take
+// part, so the binary64 work on the gathered rays runs on full warps.
+__device__ __forceinline__ int gather_rays(const int32_t* h, int64_t R, int32_t id, int64_t* k0, int32_t* L,
+                                           int lane) {
+  const unsigned lt = (1u << lane) - 1u;
+  int m = 0;
+  int64_t k = *k0;
+  while (k < R && m + 32 <= kMcList) {
+    const int64_t kk = k + lane;
+    const bool match = kk < R && h[kk] == id;
+    const unsigned mask = __ballot_sync(kFull, match);
+    if (match) L[m + __popc(mask & lt)] = (int32_t)kk;
+    m += __popc(mask);
+    k += 32;
+  }
+  __syncwarp();
+  *k0 = k;
+  return m;
+}
+
 template <int D>
-__global__ void k_mc_fill(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
-                          const int32_t* hit, const double* l, const int64_t* rowptr, double cV, double cA, double* V,
-                          int32_t* col, double* A) {
+__global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill(const double* X, int64_t N, int d, int64_t R,
+                                                           uint64_t seed, uint32_t set, const int32_t* hit,
+                                                           const double* l, const int64_t* rowptr, double cV,
+                                                           double cA, double* V, int32_t* col, double* A) {
+  __shared__ int32_t Ls[kMcWarps][kMcList];
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= N) return;
+  int32_t* L = Ls[threadIdx.x >> 5];
   const int32_t* h = hit + i * R;
   const double* li = l + i * R;
   double vs = 0.0;
@@ -127,23 +154,28 @@ __global__ void k_mc_fill(const double* X, int64_t N, int d, int64_t R, uint64_t
     const int32_t id = next_id(h, R, prev, first, lane);
     if (id == INT32_MAX) break;
     double s = 0.0;
-    for (int64_t k = lane; k < R; k += 32) {
-      if (h[k] != id) continue;
-      const double lk = li[k];
-      double term;
-      if (id >= 0) {
-        term = node_area_term<D>(X, d, i, id, ipow_d(lk, d));
-      } else {
-        double u[D];
-        mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
-        const int a = face_axis(id);
-        double ua = 0.0;
+    int64_t k0 = 0;
+    while (k0 < R) {
+      const int m = gather_rays(h, R, id, &k0, L, lane);
+      for (int p = lane; p < m; p += 32) {
+        const int32_t k = L[p];
+        const double lk = li[k];
+        double term;
+        if (id >= 0) {
+          term = node_area_term<D>(X, d, i, id, ipow_d(lk, d));
+        } else {
+          double u[D];
+          mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
+          const int a = face_axis(id);
+          double ua = 0.0;
 #pragma unroll
-        for (int c = 0; c < D; ++c)
-          if (c == a) ua = u[c];
-        term = __ddiv_rn(ipow_d(lk, d - 1), fabs(ua));
+          for (int c = 0; c < D; ++c)
+            if (c == a) ua = u[c];
+          term = __ddiv_rn(ipow_d(lk, d - 1), fabs(ua));
+        }
+        s = __dadd_rn(s, term);
       }
-      s = __dadd_rn(s, term);
+      __syncwarp();
     }
     s = warp_sum_d(s);
     if (lane == 0) {
@@ -157,14 +189,20 @@ __global__ void k_mc_fill(const double* X, int64_t N, int d, int64_t R, uint64_t
 }
 
 // Row pass of the adjoint: P[q][*] = sum over the rays of cell i that hit
-// col[q] of dLoss/dw (node) ; own[i][*] = face terms of x_i.
+// col[q] of dLoss/dw (node) ; own[i][*] = face terms of x_i.  The rays of a
+// column are gathered first so the binary64 work runs on full warps.
 template <int D>
-__global__ void k_mc_adj_rows(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
-                              const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col,
-                              double cV, double cA, const double* gV, const double* gA, double* P, double* own) {
+__global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, int64_t N, int d, int64_t R,
+                                                               uint64_t seed, uint32_t set, const int32_t* hit,
+                                                               const double* l, const int64_t* rowptr,
+                                                               const int32_t* col, double cV, double cA,
+                                                               const double* gV, const double* gA, double* P,
+                                                               double* own) {
+  __shared__ int32_t Ls[kMcWarps][kMcList];
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= N) return;
+  int32_t* L = Ls[threadIdx.x >> 5];
   const int32_t* h = hit + i * R;
   const double* li = l + i * R;
   const double gVi = gV[i];
@@ -177,45 +215,50 @@ __global__ void k_mc_adj_rows(const double* X, int64_t N, int d, int64_t R, uint
     double acc[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[c] = 0.0;
-    for (int64_t k = lane; k < R; k += 32) {
-      if (h[k] != id) continue;
-      double u[D];
-      mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
-      const double lk = li[k];
-      const double ld1 = ipow_d(lk, d - 1), ld = ipow_d(lk, d);
-      if (id >= 0) {
-        double w[D], den = 0.0, ww = 0.0;
+    int64_t k0 = 0;
+    while (k0 < R) {
+      const int m = gather_rays(h, R, id, &k0, L, lane);
+      for (int p = lane; p < m; p += 32) {
+        const int32_t k = L[p];
+        double u[D];
+        mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
+        const double lk = li[k];
+        const double ld1 = ipow_d(lk, d - 1), ld = ipow_d(lk, d);
+        if (id >= 0) {
+          double w[D], den = 0.0, ww = 0.0;
 #pragma unroll
-        for (int c = 0; c < D; ++c) w[c] = c < d ? __dadd_rn(X[(int64_t)id * d + c], -X[i * d + c]) : 0.0;
+          for (int c = 0; c < D; ++c) w[c] = c < d ? __dadd_rn(X[(int64_t)id * d + c], -X[i * d + c]) : 0.0;
 #pragma unroll
-        for (int c = 0; c < D; ++c)
-          if (c < d) den = __dadd_rn(den, __dmul_rn(u[c], w[c]));
+          for (int c = 0; c < D; ++c)
+            if (c < d) den = __dadd_rn(den, __dmul_rn(u[c], w[c]));
 #pragma unroll
-        for (int c = 0; c < D; ++c)
-          if (c < d) ww = __dadd_rn(ww, __dmul_rn(w[c], w[c]));
-        const double nw = sqrt(ww);
-        const double c1 = 2.0 * (double)d * ld1 / nw, c2 = 2.0 * ld / (nw * nw * nw);
+          for (int c = 0; c < D; ++c)
+            if (c < d) ww = __dadd_rn(ww, __dmul_rn(w[c], w[c]));
+          const double inw = rsqrt(ww);
+          const double iden = 1.0 / den;
+          const double c1 = 2.0 * (double)d * ld1 * inw, c2 = 2.0 * ld * inw * inw * inw;
+          const double kV = gVi * cV * (double)d * ld1, kA = gAij * cA;
 #pragma unroll
-        for (int c = 0; c < D; ++c)
-          if (c < d) {
-            const double dl = (w[c] - lk * u[c]) / den;
-            const double dV = cV * (double)d * ld1 * dl;
-            const double dA = cA * (c1 * dl - c2 * w[c]);
-            acc[c] += gVi * dV + gAij * dA;
-          }
-      } else {
-        const int a = face_axis(id);
-        double ua = 0.0;
+          for (int c = 0; c < D; ++c)
+            if (c < d) {
+              const double dl = (w[c] - lk * u[c]) * iden;
+              acc[c] += kV * dl + kA * (c1 * dl - c2 * w[c]);
+            }
+        } else {
+          const int a = face_axis(id);
+          double ua = 0.0;
 #pragma unroll
-        for (int c = 0; c < D; ++c)
-          if (c == a) ua = u[c];
-        const double dl = -1.0 / ua;
-        const double dadl = (d >= 2) ? (double)(d - 1) * ipow_d(lk, d - 2) / fabs(ua) : 0.0;
-        const double G = gVi * cV * (double)d * ld1 * dl + gAij * cA * dadl * dl;
+          for (int c = 0; c < D; ++c)
+            if (c == a) ua = u[c];
+          const double dl = -1.0 / ua;
+          const double dadl = (d >= 2) ? (double)(d - 1) * ipow_d(lk, d - 2) / fabs(ua) : 0.0;
+          const double G = gVi * cV * (double)d * ld1 * dl + gAij * cA * dadl * dl;
 #pragma unroll
-        for (int c = 0; c < D; ++c)
-          if (c == a) acc[c] += G;
+          for (int c = 0; c < D; ++c)
+            if (c == a) acc[c] += G;
+        }
       }
+      __syncwarp();
     }
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[c] = warp_sum_d(acc[c]);
@@ -271,7 +314,7 @@ template <int D>
 cudaError_t fill_d(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set, const int32_t* hit,
                    const double* l, const int64_t* rowptr, double cV, double cA, double* V, int32_t* col, double* A,
                    cudaStream_t st) {
-  k_mc_fill<D><<<nblk(N * 32, 128), 128, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A); count_launch();
+  k_mc_fill<D><<<nblk(N * 32, kMcWarps * 32), kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A); count_launch();
   return cudaGetLastError();
 }
 
@@ -279,7 +322,7 @@ template <int D>
 cudaError_t adj_rows_d(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
                        const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, double cV,
                        double cA, const double* gV, const double* gA, double* P, double* own, cudaStream_t st) {
-  k_mc_adj_rows<D><<<nblk(N * 32, 128), 128, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P,
+  k_mc_adj_rows<D><<<nblk(N * 32, kMcWarps * 32), kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P,
                                                        own); count_launch();
   return cudaGetLastError();
 }

@@ -406,8 +406,12 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
   Timer tm(ctx->st);
   {
     Timer tr(ctx->st);
-    VD_CK(vd::launch_raycast(tv, rs, ro, effective_precision(ctx), ctx->ctr, ctx->st, &mc->stats.fallback_rays),
-          "mc raycast");
+    const int prec = effective_precision(ctx);
+    if (tv.K > 0 && prec != VD_FP64)
+      VD_CK(vd::launch_mc_cells(tv, R, seed, set, ro, prec, ctx->ctr, ctx->st, &mc->stats.fallback_rays),
+            "mc cells");
+    else
+      VD_CK(vd::launch_raycast(tv, rs, ro, prec, ctx->ctr, ctx->st, &mc->stats.fallback_rays), "mc raycast");
     mc->stats.raycast_ms = tr.stop();
   }
   int64_t nnz = 0;

@@ -131,6 +131,11 @@ cudaError_t build_knn(TreeView* tv, int K, cudaStream_t st, DevBufs& bufs);
 int default_knn_k(int d);
 cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision,
                            Counters* ctr, cudaStream_t st, int64_t* nfallback = nullptr);
+// MC rays of all cells through the cell-centric kernel (candidate lists
+// required), leftovers through launch_raycast.  ro.fallback_list holds
+// 2 x (fallback_cap / 2) entries for (cell, ray) pairs.
+cudaError_t launch_mc_cells(const TreeView& tv, int64_t R, uint64_t seed, uint32_t set, const RayOut& ro,
+                            int precision, Counters* ctr, cudaStream_t st, int64_t* nfallback);
 cudaError_t launch_mc_directions(uint64_t seed, uint32_t set, int64_t cell0, int64_t ncells, int64_t R, int d,
                                  double* out, cudaStream_t st);
 

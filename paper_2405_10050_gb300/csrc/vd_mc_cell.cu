@@ -1,0 +1,299 @@
+// vd_mc_cell.cu -- cell-centric Monte Carlo RayCast (Section 3.1,
+// Algorithm 3): all R rays of cell i start at x_i with eta = {i}, so they
+// share one candidate list.  A thread block takes a cell, stages its list in
+// shared memory once (offsets w = x_j - x_i rounded from binary64, their
+// binary32 squared lengths and per-candidate error bounds), and then every
+// thread casts its own rays through that list:
+//   screening  t_j <= T possible iff ww_lo <= 2 T (den + E_den)   (binary32)
+//   early exit the list is sorted by distance from x_i; once a candidate is
+//              farther than the ball of the current bound can reach inside
+//              the node box, every later one is too;
+//   recheck    t_j = |w|^2 / (2 u.w) in binary64, canonical order, for the
+//              survivors (about one per ray), plus the box faces.
+// Rays the list cannot certify go to the generic tree walk.
+#include <algorithm>
+#include <cmath>
+
+#include "vd_ray_common.cuh"
+
+namespace vd {
+
+namespace {
+
+constexpr int kCellThreads = 128;
+constexpr int kCellBuf = 8;  // candidates kept per ray
+
+template <int D>
+__global__ void __launch_bounds__(kCellThreads) k_mc_cell(TreeView tr, int64_t R, uint64_t seed, uint32_t set,
+                                                          RayOut ro, Counters* ctr, unsigned long long* work,
+                                                          int32_t* fb_cell, int32_t* fb_ray, int64_t fb_cap) {
+  extern __shared__ __align__(16) float smem[];
+  const int K = tr.K;
+  const int d = tr.d;
+  float* sw = smem;                      // [D][K] binary32 offsets
+  float* snlo = sw + D * K;              // lower bound of |w|^2
+  float* snhi = snlo + K;                // upper bound of |w|^2
+  float* swn = snhi + K;                 // upper bound of |w|
+  float* sflo = swn + K;                 // lower bound of |x_j - x_i|^2 in list order
+  int32_t* sid = reinterpret_cast<int32_t*>(sflo + K);
+  int32_t* bid = sid + K;                // [kCellThreads][kCellBuf]
+  float* btl = reinterpret_cast<float*>(bid + kCellThreads * kCellBuf);
+  __shared__ int64_t s_cell;
+  const int tid = threadIdx.x;
+  const float B = tr.coord_abs;
+  const float gam = (float)(D + 1) * kU32 * 1.01f;
+  const float EW = 4.01f * kU32 * B;
+  const float a1 = 1.1f * (gam + 2.1f * kU32);  // |den32 - den| <= a1 |w32|
+  const float e1 = 1.1f * (gam + 2.1f * kU32);  // |ww32 - |w|^2| <= e1 ww32
+  int32_t* cb = bid + tid * kCellBuf;
+  float* ct = btl + tid * kCellBuf;
+  unsigned long long n_pairs = 0, n_rech = 0;
+  while (true) {
+    if (tid == 0) s_cell = (int64_t)atomicAdd(work, 1ull);
+    __syncthreads();
+    const int64_t i = s_cell;
+    if (i >= tr.N) break;
+    const int n = tr.kcnt[i];
+    double g64[D];
+    float g32[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      g64[k] = k < d ? tr.X[i * d + k] : 0.0;
+      g32[k] = k < d ? tr.X32[i * d + k] : 0.f;
+    }
+    for (int c = tid; c < n; c += kCellThreads) {
+      const int32_t id = tr.knn[i * K + c];
+      float ww = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float w = k < d ? __double2float_rn(tr.X[(int64_t)id * d + k] - g64[k]) : 0.f;
+        sw[k * K + c] = w;
+        ww = fmaf(w, w, ww);
+      }
+      snlo[c] = ww * (1.f - e1);
+      snhi[c] = ww * (1.f + e1);
+      swn[c] = sqrtf(ww) * (1.f + gam);
+      sflo[c] = true_d2_lower(ww32_of<D>(tr.X32 + (int64_t)id * d, 1, g32, d), gam, EW, D);
+      sid[c] = id;
+    }
+    const float cert_lo = true_d2_lower(tr.kcert[i], gam, EW, D);
+    __syncthreads();
+    for (int64_t k = tid; k < R; k += kCellThreads) {
+      double u64[D];
+      mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u64);
+      float u32[D], p0[D];
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        u32[q] = __double2float_rn(u64[q]);
+        p0[q] = 0.f;
+      }
+      // box faces: binary32 interval of (b - x_ia) / u_a
+      float T = INFINITY;
+      int nc = 0;
+      for (int a = 0; a < d; ++a) {
+        double ua64 = 0.0;
+        float ua = 0.f, va = 0.f;
+#pragma unroll
+        for (int q = 0; q < D; ++q)
+          if (q == a) {
+            ua64 = u64[q];
+            ua = u32[q];
+            va = g32[q];
+          }
+        if (ua64 == 0.0 || ua == 0.f) continue;
+        const int s = ua64 > 0.0 ? 1 : 0;
+        const float nf = (s ? 1.f : 0.f) - va;
+        const float nfs = s ? nf : -nf;
+        const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
+        const float au = fabsf(ua);
+        const float lo_n = nfs - ef, hi_n = nfs + ef;
+        const float tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
+                                      : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
+        const float thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
+                                      : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
+        T = fminf(T, thi);
+        if (nc < kCellBuf) {
+          cb[nc] = face_id(a, s);
+          ct[nc] = tlo;
+          ++nc;
+        }
+      }
+      Ball<D> ball;
+      make_ball<D>(g32, p0, u32, T, B, ball);
+      float far2 = far_radius2<D>(tr, ball, g32);
+      bool certified = false, overflow = false;
+      int c = 0;
+      for (; c < n; ++c) {
+        if (sflo[c] >= far2) {
+          certified = true;
+          break;
+        }
+        float den = 0.f;
+#pragma unroll
+        for (int q = 0; q < D; ++q) den = fmaf(u32[q], sw[q * K + c], den);
+        const float e = a1 * swn[c];
+        const float dh = den + e;
+        const float nlo = snlo[c];
+        if (!(dh > 0.f) || nlo > 2.f * T * dh * (1.f + 8.f * kU32)) continue;
+        const float dl = den - e;
+        const float thi = dl > 0.f ? __fdiv_rn(snhi[c], 2.f * dl) * (1.f + 4.f * kU32) : INFINITY;
+        const float tlo = __fdiv_rn(nlo, 2.f * dh) * (1.f - 4.f * kU32);
+        if (thi < T) {
+          T = thi;
+          make_ball<D>(g32, p0, u32, T, B, ball);
+          far2 = far_radius2<D>(tr, ball, g32);
+        }
+        if (tlo <= T && !overflow) {
+          if (nc == kCellBuf) {  // drop entries the new bound has excluded
+            int m = 0;
+            for (int q = 0; q < kCellBuf; ++q)
+              if (ct[q] <= T) {
+                cb[m] = cb[q];
+                ct[m] = ct[q];
+                ++m;
+              }
+            nc = m;
+          }
+          if (nc < kCellBuf) {
+            cb[nc] = sid[c];
+            ct[nc] = tlo;
+            ++nc;
+          } else {
+            overflow = true;
+          }
+        }
+      }
+      n_pairs += (unsigned long long)c;
+      if (!certified) certified = cert_lo >= far2;
+      if (!certified || overflow) {
+        const unsigned long long q = atomicAdd(&ctr->fallback, 1ull);
+        if ((int64_t)q < fb_cap) {
+          fb_cell[q] = (int32_t)i;
+          fb_ray[q] = (int32_t)k;
+        } else {
+          atomicOr(&ctr->flags, kFlagQueue);
+        }
+        continue;
+      }
+      // binary64 recheck of the survivors, canonical order
+      double bt = INFINITY;
+      int bc = 2, bk = 0;
+      for (int q = 0; q < nc; ++q) {
+        if (!(ct[q] <= T)) continue;
+        const int32_t id = cb[q];
+        ++n_rech;
+        if (id >= 0) {
+          double w[D], den = 0.0, ww = 0.0;
+#pragma unroll
+          for (int a = 0; a < D; ++a) w[a] = a < d ? __dadd_rn(tr.X[(int64_t)id * d + a], -g64[a]) : 0.0;
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+            if (a < d) den = __dadd_rn(den, __dmul_rn(u64[a], w[a]));
+          if (!(den > 0.0)) continue;
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+            if (a < d) ww = __dadd_rn(ww, __dmul_rn(w[a], w[a]));
+          const double t = __ddiv_rn(ww, __dmul_rn(2.0, den));  // num = ww since v = g
+          if (better(t, 0, id, bt, bc, bk)) {
+            bt = t;
+            bc = 0;
+            bk = id;
+          }
+        } else {
+          const int a = face_axis(id), s = face_side(id);
+          double ua = 0.0, va = 0.0;
+#pragma unroll
+          for (int q2 = 0; q2 < D; ++q2)
+            if (q2 == a) {
+              ua = u64[q2];
+              va = g64[q2];
+            }
+          const double t = __ddiv_rn(__dadd_rn(s ? 1.0 : 0.0, -va), ua);
+          if (better(t, 1, 2 * a + s, bt, bc, bk)) {
+            bt = t;
+            bc = 1;
+            bk = 2 * a + s;
+          }
+        }
+      }
+      ro.hit[i * R + k] = gen_from_key(bc, bk);
+      ro.t[i * R + k] = bt;
+    }
+    __syncthreads();
+  }
+  for (int o = 16; o; o >>= 1) {
+    n_pairs += __shfl_xor_sync(kFull, n_pairs, o);
+    n_rech += __shfl_xor_sync(kFull, n_rech, o);
+  }
+  if ((tid & 31) == 0) {
+    atomicAdd(&ctr->pairs, n_pairs);
+    atomicAdd(&ctr->rechecked, n_rech);
+  }
+}
+
+template <int D>
+cudaError_t launch_cell_d(const TreeView& tv, int64_t R, uint64_t seed, uint32_t set, const RayOut& ro,
+                          Counters* ctr, unsigned long long* work, int32_t* fb_cell, int32_t* fb_ray,
+                          int64_t fb_cap, cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t sm = (size_t)tv.K * (D + 5) * 4 + (size_t)kCellThreads * kCellBuf * 8;
+  cudaFuncSetAttribute(k_mc_cell<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mc_cell<D>, kCellThreads, sm);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1), tv.N));
+  cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+  k_mc_cell<D><<<(unsigned)grid, kCellThreads, sm, st>>>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Casts all N*R MC rays of the node set with the cell kernel (lists needed);
+// rays it cannot certify are finished by the generic kernels.
+cudaError_t launch_mc_cells(const TreeView& tv, int64_t R, uint64_t seed, uint32_t set, const RayOut& ro,
+                            int precision, Counters* ctr, cudaStream_t st, int64_t* nfallback) {
+  unsigned long long* work = reinterpret_cast<unsigned long long*>(&ctr->aux1);
+  int32_t* fb_cell = ro.fallback_list;
+  int32_t* fb_ray = ro.fallback_list + ro.fallback_cap / 2;
+  const int64_t fb_cap = ro.fallback_cap / 2;
+  cudaMemsetAsync(&ctr->fallback, 0, sizeof(unsigned long long), st);
+  cudaError_t e;
+  switch (tv.d) {
+    case 1: e = launch_cell_d<1>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
+    case 2: e = launch_cell_d<2>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
+    case 3: e = launch_cell_d<3>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
+    case 4: e = launch_cell_d<4>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
+    case 5: e = launch_cell_d<5>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
+    case 6: e = launch_cell_d<6>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
+    default: e = launch_cell_d<8>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  unsigned long long nfb = 0;
+  cudaMemcpyAsync(&nfb, &ctr->fallback, sizeof(nfb), cudaMemcpyDeviceToHost, st);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  const int64_t n = std::min<int64_t>((int64_t)nfb, fb_cap);
+  if (nfallback) *nfallback += n;
+  if (n == 0) return cudaSuccess;
+  // the generic kernels finish them: (cell, ray) lists, tree walk
+  RaySource rs;
+  rs.mode = 1;
+  rs.R = n;
+  rs.mc_cell = fb_cell;
+  rs.mc_ray = fb_ray;
+  rs.mc_rpc = R;
+  rs.seed = seed;
+  rs.set = set;
+  rs.box = 1;
+  RayOut r2 = ro;
+  r2.fallback_list = nullptr;  // tree walk directly
+  r2.fallback_cap = 0;
+  TreeView tv2 = tv;
+  tv2.K = 0;
+  return launch_raycast(tv2, rs, r2, precision, ctr, st, nullptr);
+}
+
+}  // namespace vd

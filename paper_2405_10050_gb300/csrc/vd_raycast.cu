@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "vd_dev.cuh"
+#include "vd_ray_common.cuh"
 
 namespace vd {
 
@@ -97,81 +98,6 @@ __device__ __forceinline__ void load_ray(const TreeView& tr, const RaySource& rs
 __device__ __forceinline__ int64_t out_pos(const RaySource& rs, const RayOut& ro, int64_t r) {
   if (rs.mode == 0 || rs.mc_cell == nullptr) return r;
   return (int64_t)rs.mc_cell[r] * ro.mc_rpc + rs.mc_ray[r];
-}
-
-// Conservative binary32 ball: every point within distance rho of the exact
-// centre c = v + T u satisfies |y - c32|^2 <= lim2.
-template <int D>
-struct Ball {
-  float c[D];
-  float lim2;
-  float rho_hi;  // upper bound of the exact radius |g - c|
-};
-
-template <int D>
-__device__ __forceinline__ void make_ball(const float g[D], const float p[D], const float u[D], float T, float B,
-                                          Ball<D>& b) {
-  // c = g + p + T u, rho = |p + T u|; absolute error of each coordinate is
-  // below 4 u_32 (|g| + |p| + T) and of rho below 4 sqrt(D) u_32 (...).
-  float r2 = 0.f, pm = 0.f;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const float q = fmaf(T, u[k], p[k]);
-    b.c[k] = g[k] + q;
-    r2 = fmaf(q, q, r2);
-    pm = fmaxf(pm, fabsf(p[k]));
-  }
-  const float eps = 8.f * (float)D * kU32 * (B + pm + T) + 1e-30f;
-  const float rho = sqrtf(r2) * (1.f + 4.f * (float)D * kU32) + eps;
-  b.lim2 = rho * rho * (1.f + 4.f * (float)D * kU32) + 1e-37f;
-  b.rho_hi = rho;
-  if (!(T < INFINITY)) {
-    b.lim2 = INFINITY;
-    b.rho_hi = INFINITY;
-  }
-}
-
-// Candidate lists: ww32 = sum_k fma-chain (x32_k - g32_k)^2 over k = 0..D-1;
-// the same function orders the lists and is evaluated during the scan.
-template <int D>
-__device__ __forceinline__ float ww32_of(const float* xs, int stride, const float* g32, int d) {
-  float ww = 0.f;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    const float w = (k < d) ? xs[k * stride] - g32[k] : 0.f;
-    ww = fmaf(w, w, ww);
-  }
-  return ww;
-}
-
-// Lower bound of the exact |x - g|^2 from ww32 (w32 components within EW of
-// the exact ones, gamma_D for the FMA chain).
-__device__ __forceinline__ float true_d2_lower(float ww, float gam, float EW, int D) {
-  const float l = ww * (1.f - 2.f * gam) - 2.02f * sqrtf((float)D) * EW * sqrtf(ww) - (float)D * EW * EW;
-  return fmaxf(l, 0.f);
-}
-
-// Squared radius around g that holds every node of the ball: nodes lie in
-// the node box, so only the part of the ball inside it matters; the farthest
-// point from g of that part is bounded through its axis-aligned box
-// [max(c - rho, lo), min(c + rho, hi)], and by the ball's diameter 2 rho
-// (the ball passes through g).  Returns 0 when the ball misses the box.
-template <int D>
-__device__ __forceinline__ float far_radius2(const TreeView& tr, const Ball<D>& b, const float* g32) {
-  if (!(b.rho_hi < INFINITY)) return INFINITY;
-  float s = 0.f;
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    if (k < tr.d) {
-      const float L = fmaxf(b.c[k] - b.rho_hi, tr.root_lo[k]);
-      const float H = fminf(b.c[k] + b.rho_hi, tr.root_hi[k]);
-      if (L > H) return 0.f;
-      const float m = fmaxf(fabsf(L - g32[k]), fabsf(H - g32[k])) * (1.f + 4.f * kU32) + 2.f * kU32 * tr.coord_abs;
-      s = fmaf(m, m, s);
-    }
-  }
-  s *= 1.f + 4.f * (float)D * kU32;
-  return fminf(s, 4.f * b.rho_hi * b.rho_hi * (1.f + 4.f * kU32));
 }
 
 template <int D>

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "vd_dev.cuh"
 
@@ -44,6 +45,7 @@ struct vd_ctx {
   int d = 0;
   Counters* ctr = nullptr;  // device
   DevBufs own;
+  int batch_threads[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // autotuned block size by largest d
 };
 
 struct vd_mesh {
@@ -535,10 +537,186 @@ void vd_mc_free(vd_mc* mc) {
   delete mc;
 }
 
+namespace vd {
+__global__ void k_gather_nnz(const SetDesc* sets, int nsets, int64_t* out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nsets) out[s] = sets[s].rowptr[sets[s].tv.N];
+}
+}  // namespace vd
+
 vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const* X, const int64_t* N,
                                 const int32_t* d, int64_t R, uint64_t seed, vd_mc** out, int32_t on_device) {
   if (!ctx || nsets < 0 || (nsets > 0 && (!X || !N || !d || !out))) return VD_EINVAL;
-  return set_err(ctx, VD_EINVAL, "vd_mc_integrate_batch: not available in this build");
+  if (!ctx->cfg.box) return set_err(ctx, VD_EINVAL, "vd_mc_integrate_batch: needs box clipping");
+  if (R < 1 || R > ((int64_t)1 << 31)) return set_err(ctx, VD_EINVAL, "vd_mc_integrate_batch: bad rays_per_cell");
+  for (int s = 0; s < nsets; ++s) {
+    out[s] = nullptr;
+    if (!X[s] || N[s] < 1 || N[s] > ((int64_t)1 << 30) || d[s] < 1 || d[s] > 8)
+      return set_err(ctx, VD_EINVAL, "vd_mc_integrate_batch: set %d needs 1 <= N <= 2^30 and 1 <= d <= 8", s);
+  }
+  if (nsets == 0) return VD_OK;
+  std::vector<vd_mc*> mcs(nsets, nullptr);
+  std::vector<vd::SetDesc> desc(nsets);
+  auto fail = [&](vd_status st) {
+    cudaStreamSynchronize(ctx->st);
+    for (vd_mc* m : mcs)
+      if (m) {
+        m->bufs.release();
+        delete m;
+      }
+    return st;
+  };
+  ctx->last = vd_stats{};
+  const long long l0 = vd::g_launches.load();
+  int64_t nitems = 0;
+  int maxK = 1, maxd = 1;
+  // node preparation of every set (tree + candidate lists), result buffers
+  for (int s = 0; s < nsets; ++s) {
+    vd_mc* mc = new (std::nothrow) vd_mc();
+    if (!mc) return fail(VD_ENOMEM);
+    mcs[s] = mc;
+    const int64_t n = N[s];
+    const int dd = d[s];
+    mc->st = ctx->st;
+    mc->N = n;
+    mc->d = dd;
+    mc->R = R;
+    mc->seed = seed;
+    mc->set = (uint32_t)s;
+    cudaError_t e = mc->bufs.alloc_n(&mc->X, (size_t)n * dd);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(mc->X, X[s], (size_t)n * dd * sizeof(double),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->st);
+    TreeView tv;
+    if (e == cudaSuccess) e = vd::build_tree(mc->X, n, dd, ctx->st, mc->bufs, &tv);
+    const int K = (int)std::min<int64_t>(std::max(vd::default_knn_k(dd), 1), std::max<int64_t>(n - 1, 1));
+    if (e == cudaSuccess) e = vd::build_knn(&tv, K, ctx->st, mc->bufs);
+    const int64_t cap = n * std::min<int64_t>(R, n - 1 + 2 * dd);
+    int64_t* cnt = nullptr;
+    if (e == cudaSuccess) e = mc->bufs.alloc_n(&mc->hit, (size_t)n * R);
+    if (e == cudaSuccess) e = mc->bufs.alloc_n(&mc->l, (size_t)n * R);
+    if (e == cudaSuccess) e = mc->bufs.alloc_n(&mc->V, (size_t)n);
+    if (e == cudaSuccess) e = mc->bufs.alloc_n(&cnt, (size_t)n);
+    if (e == cudaSuccess) e = mc->bufs.alloc_n(&mc->rowptr, (size_t)n + 1);
+    if (e == cudaSuccess) e = mc->bufs.alloc_n(&mc->col, (size_t)std::max<int64_t>(cap, 1));
+    if (e == cudaSuccess) e = mc->bufs.alloc_n(&mc->A, (size_t)std::max<int64_t>(cap, 1));
+    if (e == cudaErrorInvalidValue) return fail(set_err(ctx, VD_EINVAL, "set %d: non-finite coordinate", s));
+    if (e != cudaSuccess) return fail(cuda_err(ctx, e, "vd_mc_integrate_batch: set preparation"));
+    const double S = 2.0 * std::pow(M_PI, 0.5 * dd) / std::tgamma(0.5 * dd);
+    vd::SetDesc& D = desc[s];
+    D.tv = tv;
+    D.item0 = nitems;
+    D.set = (uint32_t)s;
+    D.hit = mc->hit;
+    D.l = mc->l;
+    D.V = mc->V;
+    D.cnt = cnt;
+    D.rowptr = mc->rowptr;
+    D.col = mc->col;
+    D.A = mc->A;
+    D.cV = S / ((double)dd * (double)R);
+    D.cA = S / (double)R;
+    nitems += n;
+    maxK = std::max(maxK, tv.K);
+    maxd = std::max(maxd, dd);
+  }
+  DevBufs tmp;
+  struct Guard {
+    DevBufs& b;
+    ~Guard() { b.release(); }
+  } guard{tmp};
+  vd::SetDesc* desc_dev = nullptr;
+  int64_t* nnz_dev = nullptr;
+  cudaError_t e = tmp.alloc_n(&desc_dev, nsets);
+  if (e == cudaSuccess) e = tmp.alloc_n(&nnz_dev, nsets);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(desc_dev, desc.data(), nsets * sizeof(vd::SetDesc), cudaMemcpyHostToDevice, ctx->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  if (e != cudaSuccess) return fail(cuda_err(ctx, e, "vd_mc_integrate_batch: descriptors"));
+  // the forward pass runs as one CUDA graph on a private stream (the context
+  // stream may be the legacy default stream, which cannot be captured)
+  cudaStream_t gs = nullptr;
+  cudaEvent_t ev = nullptr, ga = nullptr, gb = nullptr;
+  e = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev);
+  if (e == cudaSuccess) e = cudaEventCreate(&ga);
+  if (e == cudaSuccess) e = cudaEventCreate(&gb);
+  struct StreamGuard {
+    cudaStream_t s;
+    cudaEvent_t a, b, c;
+    ~StreamGuard() {
+      if (s) cudaStreamDestroy(s);
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+      if (c) cudaEventDestroy(c);
+    }
+  } sg{gs, ev, ga, gb};
+  if (e != cudaSuccess) return fail(cuda_err(ctx, e, "vd_mc_integrate_batch: stream"));
+  // autotuner: threads per block of the persistent kernel, per largest d
+  int& threads = ctx->batch_threads[std::min(maxd, 8)];
+  if (threads == 0) {
+    float best = INFINITY;
+    for (int th : {64, 128, 256}) {
+      cudaEventRecord(ga, gs);
+      e = vd::launch_mc_batch(desc_dev, nsets, nitems, maxd, maxK, R, seed, th, ctx->ctr, gs);
+      cudaEventRecord(gb, gs);
+      if (e == cudaSuccess) e = cudaEventSynchronize(gb);
+      if (e != cudaSuccess) return fail(cuda_err(ctx, e, "vd_mc_integrate_batch: autotune"));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ga, gb);
+      if (ms < best) {
+        best = ms;
+        threads = th;
+      }
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEventRecord(ev, ctx->st);
+  cudaStreamWaitEvent(gs, ev, 0);
+  e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), gs);
+    cudaError_t e2 = vd::launch_mc_batch(desc_dev, nsets, nitems, maxd, maxK, R, seed, threads, ctx->ctr, gs);
+    e = cudaStreamEndCapture(gs, &graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess) {
+    cudaEventRecord(ga, gs);
+    e = cudaGraphLaunch(exec, gs);
+    cudaEventRecord(gb, gs);
+  }
+  if (e == cudaSuccess) {
+    vd::k_gather_nnz<<<(nsets + 127) / 128, 128, 0, gs>>>(desc_dev, nsets, nnz_dev);
+    vd::count_launch();
+    e = cudaGetLastError();
+  }
+  std::vector<int64_t> nnz(nsets);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(nnz.data(), nnz_dev, nsets * sizeof(int64_t), cudaMemcpyDeviceToHost, gs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(gs);
+  float gms = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&gms, ga, gb);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(cuda_err(ctx, e, "vd_mc_integrate_batch: graph"));
+  Counters hc;
+  vd_status st2 = read_counters(ctx, &hc);
+  if (st2 == VD_OK) st2 = check_flags(ctx, hc);
+  if (st2 != VD_OK) return fail(st2);
+  for (int s = 0; s < nsets; ++s) {
+    mcs[s]->nnz = nnz[s];
+    mcs[s]->stats.rays = mcs[s]->N * R;
+    out[s] = mcs[s];
+  }
+  ctx->last.rays = nitems * R;
+  ctx->last.pairs_screened = (int64_t)hc.pairs;
+  ctx->last.rechecked = (int64_t)hc.rechecked;
+  ctx->last.fallback_rays = (int64_t)hc.aux0;
+  ctx->last.ms = gms;
+  ctx->last.raycast_ms = gms;
+  ctx->last.launches = vd::g_launches.load() - l0;
+  return VD_OK;
 }
 
 // ------------------------------------------------------------- vertices --

@@ -131,6 +131,28 @@ cudaError_t build_knn(TreeView* tv, int K, cudaStream_t st, DevBufs& bufs);
 int default_knn_k(int d);
 cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision,
                            Counters* ctr, cudaStream_t st, int64_t* nfallback = nullptr);
+// One point set of a batched MC launch (device array, one entry per set).
+struct SetDesc {
+  TreeView tv;          // nodes, tiles, candidate lists of the set
+  int64_t item0 = 0;    // first global cell index of the set
+  uint32_t set = 0;     // Philox set id
+  int32_t* hit = nullptr;  // N*R
+  double* l = nullptr;     // N*R
+  double* V = nullptr;     // N
+  int64_t* cnt = nullptr;  // N distinct hits per cell
+  int64_t* rowptr = nullptr;  // N+1
+  int32_t* col = nullptr;
+  double* A = nullptr;
+  double cV = 0.0, cA = 0.0;
+};
+
+// Batched forward pass over nsets sets (items = all cells of all sets), no
+// host synchronisation: cell kernel (brute-force binary64 finish for rays
+// the lists cannot certify), distinct-hit counts, per-set scans, fill.
+cudaError_t launch_mc_batch(const SetDesc* sets_dev, int nsets, int64_t nitems, int maxd, int maxK, int64_t R,
+                            uint64_t seed, int threads, Counters* ctr, cudaStream_t st);
+void mc_batch_dims(int threads, int maxd, int maxK, size_t* smem);
+
 // MC rays of all cells through the cell-centric kernel (candidate lists
 // required), leftovers through launch_raycast.  ro.fallback_list holds
 // 2 x (fallback_cap / 2) entries for (cell, ray) pairs.

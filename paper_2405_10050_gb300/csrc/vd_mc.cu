@@ -132,15 +132,9 @@ __device__ __forceinline__ int gather_rays(const int32_t* h, int64_t R, int32_t 
 }
 
 template <int D>
-__global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill(const double* X, int64_t N, int d, int64_t R,
-                                                           uint64_t seed, uint32_t set, const int32_t* hit,
-                                                           const double* l, const int64_t* rowptr, double cV,
-                                                           double cA, double* V, int32_t* col, double* A) {
-  __shared__ int32_t Ls[kMcWarps][kMcList];
-  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= N) return;
-  int32_t* L = Ls[threadIdx.x >> 5];
+__device__ void fill_item(const double* X, int d, int64_t i, int64_t R, uint64_t seed, uint32_t set,
+                          const int32_t* hit, const double* l, const int64_t* rowptr, double cV, double cA, double* V,
+                          int32_t* col, double* A, int32_t* L, int lane) {
   const int32_t* h = hit + i * R;
   const double* li = l + i * R;
   double vs = 0.0;
@@ -185,6 +179,101 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill(const double* X, int6
     ++q;
     prev = id;
     first = false;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill(const double* X, int64_t N, int d, int64_t R,
+                                                           uint64_t seed, uint32_t set, const int32_t* hit,
+                                                           const double* l, const int64_t* rowptr, double cV,
+                                                           double cA, double* V, int32_t* col, double* A) {
+  __shared__ int32_t Ls[kMcWarps][kMcList];
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;
+  fill_item<D>(X, d, i, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, Ls[threadIdx.x >> 5], lane);
+}
+
+// ---- batched reduction over many sets (items = all cells of all sets) ----
+__device__ __forceinline__ int find_set(const SetDesc* sets, int nsets, int64_t item) {
+  int lo = 0, hi = nsets - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (sets[mid].item0 <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_mc_count_batch(const SetDesc* sets, int nsets, int64_t nitems, int64_t R) {
+  const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (item >= nitems) return;
+  const SetDesc& S = sets[find_set(sets, nsets, item)];
+  const int64_t i = item - S.item0;
+  const int32_t* h = S.hit + i * R;
+  int64_t n = 0;
+  int32_t prev = 0;
+  bool first = true;
+  while (true) {
+    const int32_t id = next_id(h, R, prev, first, lane);
+    if (id == INT32_MAX) break;
+    ++n;
+    prev = id;
+    first = false;
+  }
+  if (lane == 0) S.cnt[i] = n;
+}
+
+// one block per set: rowptr = exclusive scan of the set's counts
+__global__ void k_scan_batch(const SetDesc* sets) {
+  const SetDesc& S = sets[blockIdx.x];
+  const int64_t n = S.tv.N;
+  __shared__ int64_t part[1024];
+  const int64_t seg = (n + 1023) / 1024;
+  const int64_t b = threadIdx.x * seg, e = min(n, b + seg);
+  int64_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += S.cnt[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int64_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t run = part[threadIdx.x] - s;
+  for (int64_t i = b; i < e; ++i) {
+    S.rowptr[i] = run;
+    run += S.cnt[i];
+  }
+  if (threadIdx.x == 1023) S.rowptr[n] = part[1023];
+}
+
+__global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill_batch(const SetDesc* sets, int nsets, int64_t nitems,
+                                                                 int64_t R, uint64_t seed) {
+  __shared__ int32_t Ls[kMcWarps][kMcList];
+  const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (item >= nitems) return;
+  const SetDesc& S = sets[find_set(sets, nsets, item)];
+  const int64_t i = item - S.item0;
+  int32_t* L = Ls[threadIdx.x >> 5];
+  switch (S.tv.d) {
+#define VD_FILL(DD)                                                                                              \
+  case DD:                                                                                                       \
+    fill_item<DD>(S.tv.X, S.tv.d, i, R, seed, S.set, S.hit, S.l, S.rowptr, S.cV, S.cA, S.V, S.col, S.A, L, lane); \
+    break;
+    VD_FILL(1)
+    VD_FILL(2)
+    VD_FILL(3)
+    VD_FILL(4)
+    VD_FILL(5)
+    VD_FILL(6)
+    default:
+      fill_item<8>(S.tv.X, S.tv.d, i, R, seed, S.set, S.hit, S.l, S.rowptr, S.cV, S.cA, S.V, S.col, S.A, L, lane);
+      break;
+#undef VD_FILL
   }
 }
 
@@ -330,6 +419,18 @@ cudaError_t adj_rows_d(const double* X, int64_t N, int d, int64_t R, uint64_t se
 }  // namespace
 
 double sphere_area(int d) { return 2.0 * std::pow(M_PI, 0.5 * d) / std::tgamma(0.5 * d); }
+
+cudaError_t mc_batch_reduce(const SetDesc* sets_dev, int nsets, int64_t nitems, int maxd, int64_t R, uint64_t seed,
+                            cudaStream_t st) {
+  (void)maxd;
+  k_mc_count_batch<<<nblk(nitems * 32, 128), 128, 0, st>>>(sets_dev, nsets, nitems, R);
+  count_launch();
+  k_scan_batch<<<nsets, 1024, 0, st>>>(sets_dev);
+  count_launch();
+  k_mc_fill_batch<<<nblk(nitems * 32, kMcWarps * 32), kMcWarps * 32, 0, st>>>(sets_dev, nsets, nitems, R, seed);
+  count_launch();
+  return cudaGetLastError();
+}
 
 // Counts the distinct hits per cell and writes rowptr (N+1); returns nnz.
 cudaError_t mc_rowptr(const int32_t* hit, int64_t N, int64_t R, int64_t* cnt_scratch, int64_t* rowptr,

@@ -23,11 +23,61 @@ namespace {
 constexpr int kCellThreads = 128;
 constexpr int kCellBuf = 8;  // candidates kept per ray
 
+// Shared memory of one cell: offsets [D][K], bounds, ids; per-thread buffers.
+__host__ __device__ inline size_t cell_smem(int D, int K, int threads) {
+  return (size_t)K * (D + 5) * 4 + (size_t)threads * kCellBuf * 8;
+}
+
+// Exact ray by brute force over all nodes (binary64, canonical order): the
+// finish of the rare MC rays the candidate list cannot certify in batched
+// launches (no host round trip).
 template <int D>
-__global__ void __launch_bounds__(kCellThreads) k_mc_cell(TreeView tr, int64_t R, uint64_t seed, uint32_t set,
-                                                          RayOut ro, Counters* ctr, unsigned long long* work,
-                                                          int32_t* fb_cell, int32_t* fb_ray, int64_t fb_cap) {
-  extern __shared__ __align__(16) float smem[];
+__device__ void bruteforce_ray(const TreeView& tr, int64_t i, const double* u64, const double* g64, double& bt,
+                               int& bc, int& bk) {
+  const int d = tr.d;
+  bt = INFINITY;
+  bc = 2;
+  bk = 0;
+  for (int64_t j = 0; j < tr.N; ++j) {
+    if (j == i) continue;
+    double w[D], den = 0.0, ww = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) w[a] = a < d ? __dadd_rn(tr.X[j * d + a], -g64[a]) : 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (a < d) den = __dadd_rn(den, __dmul_rn(u64[a], w[a]));
+    if (!(den > 0.0)) continue;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (a < d) ww = __dadd_rn(ww, __dmul_rn(w[a], w[a]));
+    const double t = __ddiv_rn(ww, __dmul_rn(2.0, den));
+    if (better(t, 0, (int)j, bt, bc, bk)) {
+      bt = t;
+      bc = 0;
+      bk = (int)j;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (a >= d || u64[a] == 0.0) continue;
+    const int s = u64[a] > 0.0 ? 1 : 0;
+    const double t = __ddiv_rn(__dadd_rn(s ? 1.0 : 0.0, -g64[a]), u64[a]);
+    if (better(t, 1, 2 * a + s, bt, bc, bk)) {
+      bt = t;
+      bc = 1;
+      bk = 2 * a + s;
+    }
+  }
+}
+
+// All R rays of cell i (see the file comment).  INLINE: rays the list cannot
+// certify are finished here by brute force; otherwise they are appended to
+// (fb_cell, fb_ray) for the tree walk.
+template <int D, int TH, bool INLINE>
+__device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t seed, uint32_t set, int32_t* hit_out,
+                          double* t_out, float* smem, Counters* ctr, int32_t* fb_cell, int32_t* fb_ray,
+                          int64_t fb_cap, unsigned long long& n_pairs, unsigned long long& n_rech,
+                          unsigned long long& n_brute) {
   const int K = tr.K;
   const int d = tr.d;
   float* sw = smem;                      // [D][K] binary32 offsets
@@ -36,9 +86,8 @@ __global__ void __launch_bounds__(kCellThreads) k_mc_cell(TreeView tr, int64_t R
   float* swn = snhi + K;                 // upper bound of |w|
   float* sflo = swn + K;                 // lower bound of |x_j - x_i|^2 in list order
   int32_t* sid = reinterpret_cast<int32_t*>(sflo + K);
-  int32_t* bid = sid + K;                // [kCellThreads][kCellBuf]
-  float* btl = reinterpret_cast<float*>(bid + kCellThreads * kCellBuf);
-  __shared__ int64_t s_cell;
+  int32_t* bid = sid + K;                // [TH][kCellBuf]
+  float* btl = reinterpret_cast<float*>(bid + TH * kCellBuf);
   const int tid = threadIdx.x;
   const float B = tr.coord_abs;
   const float gam = (float)(D + 1) * kU32 * 1.01f;
@@ -47,125 +96,122 @@ __global__ void __launch_bounds__(kCellThreads) k_mc_cell(TreeView tr, int64_t R
   const float e1 = 1.1f * (gam + 2.1f * kU32);  // |ww32 - |w|^2| <= e1 ww32
   int32_t* cb = bid + tid * kCellBuf;
   float* ct = btl + tid * kCellBuf;
-  unsigned long long n_pairs = 0, n_rech = 0;
-  while (true) {
-    if (tid == 0) s_cell = (int64_t)atomicAdd(work, 1ull);
-    __syncthreads();
-    const int64_t i = s_cell;
-    if (i >= tr.N) break;
-    const int n = tr.kcnt[i];
-    double g64[D];
-    float g32[D];
+  const int n = tr.kcnt[i];
+  double g64[D];
+  float g32[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    g64[k] = k < d ? tr.X[i * d + k] : 0.0;
+    g32[k] = k < d ? tr.X32[i * d + k] : 0.f;
+  }
+  for (int c = tid; c < n; c += TH) {
+    const int32_t id = tr.knn[i * K + c];
+    float ww = 0.f;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      g64[k] = k < d ? tr.X[i * d + k] : 0.0;
-      g32[k] = k < d ? tr.X32[i * d + k] : 0.f;
+      const float w = k < d ? __double2float_rn(tr.X[(int64_t)id * d + k] - g64[k]) : 0.f;
+      sw[k * K + c] = w;
+      ww = fmaf(w, w, ww);
     }
-    for (int c = tid; c < n; c += kCellThreads) {
-      const int32_t id = tr.knn[i * K + c];
-      float ww = 0.f;
+    snlo[c] = ww * (1.f - e1);
+    snhi[c] = ww * (1.f + e1);
+    swn[c] = sqrtf(ww) * (1.f + gam);
+    sflo[c] = true_d2_lower(ww32_of<D>(tr.X32 + (int64_t)id * d, 1, g32, d), gam, EW, D);
+    sid[c] = id;
+  }
+  const float cert_lo = true_d2_lower(tr.kcert[i], gam, EW, D);
+  __syncthreads();
+  for (int64_t k = tid; k < R; k += TH) {
+    double u64[D];
+    mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u64);
+    float u32[D], p0[D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const float w = k < d ? __double2float_rn(tr.X[(int64_t)id * d + k] - g64[k]) : 0.f;
-        sw[k * K + c] = w;
-        ww = fmaf(w, w, ww);
-      }
-      snlo[c] = ww * (1.f - e1);
-      snhi[c] = ww * (1.f + e1);
-      swn[c] = sqrtf(ww) * (1.f + gam);
-      sflo[c] = true_d2_lower(ww32_of<D>(tr.X32 + (int64_t)id * d, 1, g32, d), gam, EW, D);
-      sid[c] = id;
+    for (int q = 0; q < D; ++q) {
+      u32[q] = __double2float_rn(u64[q]);
+      p0[q] = 0.f;
     }
-    const float cert_lo = true_d2_lower(tr.kcert[i], gam, EW, D);
-    __syncthreads();
-    for (int64_t k = tid; k < R; k += kCellThreads) {
-      double u64[D];
-      mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u64);
-      float u32[D], p0[D];
+    // box faces: binary32 interval of (b - x_ia) / u_a
+    float T = INFINITY;
+    int nc = 0;
+    for (int a = 0; a < d; ++a) {
+      double ua64 = 0.0;
+      float ua = 0.f, va = 0.f;
 #pragma unroll
-      for (int q = 0; q < D; ++q) {
-        u32[q] = __double2float_rn(u64[q]);
-        p0[q] = 0.f;
+      for (int q = 0; q < D; ++q)
+        if (q == a) {
+          ua64 = u64[q];
+          ua = u32[q];
+          va = g32[q];
+        }
+      if (ua64 == 0.0 || ua == 0.f) continue;
+      const int s = ua64 > 0.0 ? 1 : 0;
+      const float nf = (s ? 1.f : 0.f) - va;
+      const float nfs = s ? nf : -nf;
+      const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
+      const float au = fabsf(ua);
+      const float lo_n = nfs - ef, hi_n = nfs + ef;
+      const float tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
+                                    : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
+      const float thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
+                                    : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
+      T = fminf(T, thi);
+      if (nc < kCellBuf) {
+        cb[nc] = face_id(a, s);
+        ct[nc] = tlo;
+        ++nc;
       }
-      // box faces: binary32 interval of (b - x_ia) / u_a
-      float T = INFINITY;
-      int nc = 0;
-      for (int a = 0; a < d; ++a) {
-        double ua64 = 0.0;
-        float ua = 0.f, va = 0.f;
+    }
+    Ball<D> ball;
+    make_ball<D>(g32, p0, u32, T, B, ball);
+    float far2 = far_radius2<D>(tr, ball, g32);
+    bool certified = false, overflow = false;
+    int c = 0;
+    for (; c < n; ++c) {
+      if (sflo[c] >= far2) {
+        certified = true;
+        break;
+      }
+      float den = 0.f;
 #pragma unroll
-        for (int q = 0; q < D; ++q)
-          if (q == a) {
-            ua64 = u64[q];
-            ua = u32[q];
-            va = g32[q];
-          }
-        if (ua64 == 0.0 || ua == 0.f) continue;
-        const int s = ua64 > 0.0 ? 1 : 0;
-        const float nf = (s ? 1.f : 0.f) - va;
-        const float nfs = s ? nf : -nf;
-        const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
-        const float au = fabsf(ua);
-        const float lo_n = nfs - ef, hi_n = nfs + ef;
-        const float tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
-                                      : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
-        const float thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
-                                      : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
-        T = fminf(T, thi);
+      for (int q = 0; q < D; ++q) den = fmaf(u32[q], sw[q * K + c], den);
+      const float e = a1 * swn[c];
+      const float dh = den + e;
+      const float nlo = snlo[c];
+      if (!(dh > 0.f) || nlo > 2.f * T * dh * (1.f + 8.f * kU32)) continue;
+      const float dl = den - e;
+      const float thi = dl > 0.f ? __fdiv_rn(snhi[c], 2.f * dl) * (1.f + 4.f * kU32) : INFINITY;
+      const float tlo = __fdiv_rn(nlo, 2.f * dh) * (1.f - 4.f * kU32);
+      if (thi < T) {
+        T = thi;
+        make_ball<D>(g32, p0, u32, T, B, ball);
+        far2 = far_radius2<D>(tr, ball, g32);
+      }
+      if (tlo <= T && !overflow) {
+        if (nc == kCellBuf) {  // drop entries the new bound has excluded
+          int m = 0;
+          for (int q = 0; q < kCellBuf; ++q)
+            if (ct[q] <= T) {
+              cb[m] = cb[q];
+              ct[m] = ct[q];
+              ++m;
+            }
+          nc = m;
+        }
         if (nc < kCellBuf) {
-          cb[nc] = face_id(a, s);
+          cb[nc] = sid[c];
           ct[nc] = tlo;
           ++nc;
+        } else {
+          overflow = true;
         }
       }
-      Ball<D> ball;
-      make_ball<D>(g32, p0, u32, T, B, ball);
-      float far2 = far_radius2<D>(tr, ball, g32);
-      bool certified = false, overflow = false;
-      int c = 0;
-      for (; c < n; ++c) {
-        if (sflo[c] >= far2) {
-          certified = true;
-          break;
-        }
-        float den = 0.f;
-#pragma unroll
-        for (int q = 0; q < D; ++q) den = fmaf(u32[q], sw[q * K + c], den);
-        const float e = a1 * swn[c];
-        const float dh = den + e;
-        const float nlo = snlo[c];
-        if (!(dh > 0.f) || nlo > 2.f * T * dh * (1.f + 8.f * kU32)) continue;
-        const float dl = den - e;
-        const float thi = dl > 0.f ? __fdiv_rn(snhi[c], 2.f * dl) * (1.f + 4.f * kU32) : INFINITY;
-        const float tlo = __fdiv_rn(nlo, 2.f * dh) * (1.f - 4.f * kU32);
-        if (thi < T) {
-          T = thi;
-          make_ball<D>(g32, p0, u32, T, B, ball);
-          far2 = far_radius2<D>(tr, ball, g32);
-        }
-        if (tlo <= T && !overflow) {
-          if (nc == kCellBuf) {  // drop entries the new bound has excluded
-            int m = 0;
-            for (int q = 0; q < kCellBuf; ++q)
-              if (ct[q] <= T) {
-                cb[m] = cb[q];
-                ct[m] = ct[q];
-                ++m;
-              }
-            nc = m;
-          }
-          if (nc < kCellBuf) {
-            cb[nc] = sid[c];
-            ct[nc] = tlo;
-            ++nc;
-          } else {
-            overflow = true;
-          }
-        }
-      }
-      n_pairs += (unsigned long long)c;
-      if (!certified) certified = cert_lo >= far2;
-      if (!certified || overflow) {
+    }
+    n_pairs += (unsigned long long)c;
+    if (!certified) certified = cert_lo >= far2;
+    double bt = INFINITY;
+    int bc = 2, bk = 0;
+    if (!certified || overflow) {
+      if (!INLINE) {
         const unsigned long long q = atomicAdd(&ctr->fallback, 1ull);
         if ((int64_t)q < fb_cap) {
           fb_cell[q] = (int32_t)i;
@@ -175,9 +221,10 @@ __global__ void __launch_bounds__(kCellThreads) k_mc_cell(TreeView tr, int64_t R
         }
         continue;
       }
+      ++n_brute;
+      bruteforce_ray<D>(tr, i, u64, g64, bt, bc, bk);
+    } else {
       // binary64 recheck of the survivors, canonical order
-      double bt = INFINITY;
-      int bc = 2, bk = 0;
       for (int q = 0; q < nc; ++q) {
         if (!(ct[q] <= T)) continue;
         const int32_t id = cb[q];
@@ -216,19 +263,90 @@ __global__ void __launch_bounds__(kCellThreads) k_mc_cell(TreeView tr, int64_t R
           }
         }
       }
-      ro.hit[i * R + k] = gen_from_key(bc, bk);
-      ro.t[i * R + k] = bt;
     }
-    __syncthreads();
+    hit_out[i * R + k] = gen_from_key(bc, bk);
+    t_out[i * R + k] = bt;
   }
+  __syncthreads();
+}
+
+template <int TH>
+__device__ __forceinline__ void flush_counters(Counters* ctr, unsigned long long n_pairs, unsigned long long n_rech,
+                                               unsigned long long n_brute) {
   for (int o = 16; o; o >>= 1) {
     n_pairs += __shfl_xor_sync(kFull, n_pairs, o);
     n_rech += __shfl_xor_sync(kFull, n_rech, o);
+    n_brute += __shfl_xor_sync(kFull, n_brute, o);
   }
-  if ((tid & 31) == 0) {
+  if ((threadIdx.x & 31) == 0) {
     atomicAdd(&ctr->pairs, n_pairs);
     atomicAdd(&ctr->rechecked, n_rech);
+    if (n_brute) atomicAdd(&ctr->aux0, n_brute);
   }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kCellThreads) k_mc_cell(TreeView tr, int64_t R, uint64_t seed, uint32_t set,
+                                                          RayOut ro, Counters* ctr, unsigned long long* work,
+                                                          int32_t* fb_cell, int32_t* fb_ray, int64_t fb_cap) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int64_t s_cell;
+  unsigned long long n_pairs = 0, n_rech = 0, n_brute = 0;
+  while (true) {
+    if (threadIdx.x == 0) s_cell = (int64_t)atomicAdd(work, 1ull);
+    __syncthreads();
+    const int64_t i = s_cell;
+    __syncthreads();
+    if (i >= tr.N) break;
+    cell_item<D, kCellThreads, false>(tr, i, R, seed, set, ro.hit, ro.t, smem, ctr, fb_cell, fb_ray, fb_cap,
+                                      n_pairs, n_rech, n_brute);
+  }
+  flush_counters<kCellThreads>(ctr, n_pairs, n_rech, n_brute);
+}
+
+// Batched: one persistent launch over every cell of every set; the item's
+// set is found by binary search over the sets' first items, the dimension
+// selects the instantiation.
+template <int TH>
+__global__ void __launch_bounds__(TH) k_mc_cell_batch(const SetDesc* sets, int nsets, int64_t nitems, int64_t R,
+                                                       uint64_t seed, Counters* ctr, unsigned long long* work) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int64_t s_item;
+  unsigned long long n_pairs = 0, n_rech = 0, n_brute = 0;
+  while (true) {
+    if (threadIdx.x == 0) s_item = (int64_t)atomicAdd(work, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    __syncthreads();
+    if (item >= nitems) break;
+    int lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (sets[mid].item0 <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const SetDesc& S = sets[lo];
+    const int64_t i = item - S.item0;
+    switch (S.tv.d) {
+#define VD_CASE(DD)                                                                                                \
+  case DD:                                                                                                         \
+    cell_item<DD, TH, true>(S.tv, i, R, seed, S.set, S.hit, S.l, smem, ctr, nullptr, nullptr, 0, n_pairs, n_rech, \
+                            n_brute);                                                                              \
+    break;
+      VD_CASE(1)
+      VD_CASE(2)
+      VD_CASE(3)
+      VD_CASE(4)
+      VD_CASE(5)
+      VD_CASE(6)
+      default:
+        cell_item<8, TH, true>(S.tv, i, R, seed, S.set, S.hit, S.l, smem, ctr, nullptr, nullptr, 0, n_pairs, n_rech,
+                               n_brute);
+        break;
+#undef VD_CASE
+    }
+  }
+  flush_counters<TH>(ctr, n_pairs, n_rech, n_brute);
 }
 
 template <int D>
@@ -238,13 +356,31 @@ cudaError_t launch_cell_d(const TreeView& tv, int64_t R, uint64_t seed, uint32_t
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t sm = (size_t)tv.K * (D + 5) * 4 + (size_t)kCellThreads * kCellBuf * 8;
+  const size_t sm = cell_smem(D, tv.K, kCellThreads);
   cudaFuncSetAttribute(k_mc_cell<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mc_cell<D>, kCellThreads, sm);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1), tv.N));
   cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
   k_mc_cell<D><<<(unsigned)grid, kCellThreads, sm, st>>>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int TH>
+cudaError_t launch_batch_th(const SetDesc* sets, int nsets, int64_t nitems, int maxK, int64_t R, uint64_t seed,
+                            Counters* ctr, cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t sm = cell_smem(8, maxK, TH);
+  cudaFuncSetAttribute(k_mc_cell_batch<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mc_cell_batch<TH>, TH, sm);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1), nitems));
+  unsigned long long* work = reinterpret_cast<unsigned long long*>(&ctr->aux1);
+  cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+  k_mc_cell_batch<TH><<<(unsigned)grid, TH, sm, st>>>(sets, nsets, nitems, R, seed, ctr, work);
   count_launch();
   return cudaGetLastError();
 }
@@ -295,5 +431,20 @@ cudaError_t launch_mc_cells(const TreeView& tv, int64_t R, uint64_t seed, uint32
   tv2.K = 0;
   return launch_raycast(tv2, rs, r2, precision, ctr, st, nullptr);
 }
+
+cudaError_t mc_batch_reduce(const SetDesc* sets_dev, int nsets, int64_t nitems, int maxd, int64_t R, uint64_t seed,
+                            cudaStream_t st);
+
+cudaError_t launch_mc_batch(const SetDesc* sets_dev, int nsets, int64_t nitems, int maxd, int maxK, int64_t R,
+                            uint64_t seed, int threads, Counters* ctr, cudaStream_t st) {
+  cudaError_t e;
+  if (threads <= 64) e = launch_batch_th<64>(sets_dev, nsets, nitems, maxK, R, seed, ctr, st);
+  else if (threads <= 128) e = launch_batch_th<128>(sets_dev, nsets, nitems, maxK, R, seed, ctr, st);
+  else e = launch_batch_th<256>(sets_dev, nsets, nitems, maxK, R, seed, ctr, st);
+  if (e != cudaSuccess) return e;
+  return mc_batch_reduce(sets_dev, nsets, nitems, maxd, R, seed, st);
+}
+
+void mc_batch_dims(int threads, int maxd, int maxK, size_t* smem) { *smem = cell_smem(8, maxK, threads); }
 
 }  // namespace vd

@@ -231,6 +231,27 @@ def vd_mc_get(mc, V=None, rowptr=None, col=None, A=None):
     return nnz.value
 
 
+def vd_mc_integrate_batch(ctx, Xs, rays_per_cell, seed):
+    """Batched MC over a list of node sets (torch CUDA tensors or numpy
+    arrays, all of one kind); returns one vd_mc handle per set."""
+    ptrs, keep, dev = [], [], None
+    for X in Xs:
+        p, dv, k = _ptr(X, np.float64)
+        if dev is None:
+            dev = dv
+        elif dev != dv:
+            raise ValueError("all sets must be on the same side (host or device)")
+        ptrs.append(p.value)
+        keep.append(k)
+    n = len(Xs)
+    Pa = (ctypes.c_void_p * n)(*ptrs)
+    Na = (ctypes.c_int64 * n)(*[X.shape[0] for X in Xs])
+    Da = (ctypes.c_int32 * n)(*[X.shape[1] for X in Xs])
+    outs = (ctypes.c_void_p * n)()
+    _check(ctx, load().vd_mc_integrate_batch(ctx, n, Pa, Na, Da, rays_per_cell, seed, outs, dev or 0))
+    return [ctypes.c_void_p(o) for o in outs]
+
+
 def vd_mc_rays(mc, hit, l):
     ph, dev, _ = _ptr(hit, np.int32)
     pl, _, _ = _ptr(l, np.float64)

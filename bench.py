@@ -246,6 +246,9 @@ def run_ours(args):
     if args.only_mc:  # the MC secondary measurement alone (profiling)
         print(json.dumps({"mc": run_mc(args, vd, torch.cuda.current_stream())}), flush=True)
         return
+    if args.only_batch:
+        print(json.dumps({"batch": run_batch(args, vd, torch.cuda.current_stream())}), flush=True)
+        return
     X = synth.uniform(args.N, args.d, seed=0)
     Xd = torch.tensor(X, device="cuda")
     stream = torch.cuda.current_stream()
@@ -445,6 +448,48 @@ def run_mc(args, vd, stream):
     return out
 
 
+BATCH_WORKLOAD = ("batched MC volumes + areas + adjoint: 512 sets, N log-uniform in [200, 20000], d uniform in "
+                  "{2..8}, half uniform, half 8-component Gaussian mixtures (sigma 0.05), 256 rays per cell")
+
+
+def run_batch(args, vd, stream):
+    """MC vol+grad cells/s on the batched workload (one persistent,
+    graph-captured forward launch over all sets, then the adjoint of each)."""
+    import torch
+    from paper_2405_10050_gb300 import VD_FP32, synth
+    sets = synth.batch_sets(args.batch_sets, seed=0)
+    Xd = [torch.tensor(X, device="cuda") for X, _ in sets]
+    ncell = sum(X.shape[0] for X, _ in sets)
+    R = args.batch_rays
+    cfg = vd.vd_config_default()
+    cfg.precision = VD_FP32
+    ctx = vd.vd_create(cfg, stream.cuda_stream)
+    for mc in vd.vd_mc_integrate_batch(ctx, Xd, R, 3):  # first call: autotune
+        vd.vd_mc_free(mc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mcs = vd.vd_mc_integrate_batch(ctx, Xd, R, 3)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    st = vd.vd_last_stats(ctx)
+    for mc, X in zip(mcs, Xd):
+        N, d = X.shape
+        nnz = vd.vd_mc_get(mc)
+        gX = torch.empty((N, d), dtype=torch.float64, device="cuda")
+        vd.vd_mc_adjoint(mc, torch.ones(N, dtype=torch.float64, device="cuda"),
+                         torch.ones(max(nnz, 1), dtype=torch.float64, device="cuda")[:nnz], gX)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for mc in mcs:
+        vd.vd_mc_free(mc)
+    vd.vd_destroy(ctx)
+    return {"workload": BATCH_WORKLOAD.replace("512", str(args.batch_sets)).replace("256 rays", f"{R} rays"),
+            "cells": ncell, "rays": ncell * R, "unit": "cells/s",
+            "value": ncell / (t2 - t0), "forward_graph_ms": st["ms"], "forward_call_s": t1 - t0,
+            "adjoint_s": t2 - t1, "rays_per_s_forward_graph": ncell * R / (st["ms"] / 1000.0),
+            "brute_force_rays": st["fallback_rays"], "launches_forward": st["launches"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -460,6 +505,9 @@ def main():
     ap.add_argument("--knn-k", type=int, default=0, help="candidate list length (0 automatic, -1 none)")
     ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--only-mc", action="store_true")
+    ap.add_argument("--only-batch", action="store_true")
+    ap.add_argument("--batch-sets", type=int, default=512)
+    ap.add_argument("--batch-rays", type=int, default=256)
     ap.add_argument("--mc-n", type=int, default=100000)
     ap.add_argument("--mc-rays", type=int, default=1024)
     args = ap.parse_args()

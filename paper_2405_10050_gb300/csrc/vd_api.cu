@@ -627,8 +627,20 @@ vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const*
   } guard{tmp};
   vd::SetDesc* desc_dev = nullptr;
   int64_t* nnz_dev = nullptr;
+  Counters* set_ctr = nullptr;
   cudaError_t e = tmp.alloc_n(&desc_dev, nsets);
   if (e == cudaSuccess) e = tmp.alloc_n(&nnz_dev, nsets);
+  if (e == cudaSuccess) e = tmp.alloc_n(&set_ctr, nsets);
+  for (int s = 0; s < nsets && e == cudaSuccess; ++s) {
+    vd::SetDesc& D = desc[s];
+    const int64_t rays = mcs[s]->N * R;
+    D.ctr = set_ctr + s;
+    D.fb_cap = std::max<int64_t>(rays / 4, 1024);
+    D.ov_cap = std::max<int64_t>(rays / 16, 1024);
+    if (e == cudaSuccess) e = tmp.alloc_n(&D.fb_cell, D.fb_cap);
+    if (e == cudaSuccess) e = tmp.alloc_n(&D.fb_ray, D.fb_cap);
+    if (e == cudaSuccess) e = tmp.alloc_n(&D.ov_list, D.ov_cap);
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(desc_dev, desc.data(), nsets * sizeof(vd::SetDesc), cudaMemcpyHostToDevice, ctx->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
@@ -658,7 +670,7 @@ vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const*
     float best = INFINITY;
     for (int th : {64, 128, 256}) {
       cudaEventRecord(ga, gs);
-      e = vd::launch_mc_batch(desc_dev, nsets, nitems, maxd, maxK, R, seed, th, ctx->ctr, gs);
+      e = vd::launch_mc_batch(desc_dev, desc.data(), nsets, nitems, maxd, maxK, R, seed, th, ctx->ctr, gs);
       cudaEventRecord(gb, gs);
       if (e == cudaSuccess) e = cudaEventSynchronize(gb);
       if (e != cudaSuccess) return fail(cuda_err(ctx, e, "vd_mc_integrate_batch: autotune"));
@@ -677,7 +689,8 @@ vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const*
   e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), gs);
-    cudaError_t e2 = vd::launch_mc_batch(desc_dev, nsets, nitems, maxd, maxK, R, seed, threads, ctx->ctr, gs);
+    cudaError_t e2 =
+        vd::launch_mc_batch(desc_dev, desc.data(), nsets, nitems, maxd, maxK, R, seed, threads, ctx->ctr, gs);
     e = cudaStreamEndCapture(gs, &graph);
     if (e == cudaSuccess) e = e2;
   }
@@ -704,6 +717,18 @@ vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const*
   vd_status st2 = read_counters(ctx, &hc);
   if (st2 == VD_OK) st2 = check_flags(ctx, hc);
   if (st2 != VD_OK) return fail(st2);
+  std::vector<Counters> hs(nsets);
+  e = cudaMemcpy(hs.data(), set_ctr, nsets * sizeof(Counters), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(cuda_err(ctx, e, "vd_mc_integrate_batch: counters"));
+  int64_t nfb = 0;
+  for (int s = 0; s < nsets; ++s) {
+    if ((st2 = check_flags(ctx, hs[s])) != VD_OK) return fail(st2);
+    if ((int64_t)hs[s].fallback > desc[s].fb_cap || (int64_t)hs[s].overflow > desc[s].ov_cap)
+      return fail(set_err(ctx, VD_EOVERFLOW, "set %d: work list overflow", s));
+    nfb += (int64_t)hs[s].fallback;
+    hc.pairs += hs[s].pairs;
+  }
+  hc.aux0 = (unsigned long long)nfb;
   for (int s = 0; s < nsets; ++s) {
     mcs[s]->nnz = nnz[s];
     mcs[s]->stats.rays = mcs[s]->N * R;

@@ -74,6 +74,9 @@ struct RaySource {
   uint32_t set = 0;
   int box = 1;
   int rpb = 32;                  // rays per warp batch (1..32), set by the launcher
+  // with R_dev set, the ray count is min(*R_dev, R), read on the device (the
+  // launch needs no host round trip), and the batch size is chosen there
+  const unsigned long long* R_dev = nullptr;
 };
 
 struct RayOut {
@@ -144,13 +147,21 @@ struct SetDesc {
   int32_t* col = nullptr;
   double* A = nullptr;
   double cV = 0.0, cA = 0.0;
+  Counters* ctr = nullptr;     // per-set counters (fallback, overflow, work)
+  int32_t* fb_cell = nullptr;  // rays the lists cannot certify: (cell, ray)
+  int32_t* fb_ray = nullptr;
+  int64_t fb_cap = 0;
+  int32_t* ov_list = nullptr;  // rays the binary32 screen could not settle
+  int64_t ov_cap = 0;
 };
 
 // Batched forward pass over nsets sets (items = all cells of all sets), no
 // host synchronisation: cell kernel (brute-force binary64 finish for rays
 // the lists cannot certify), distinct-hit counts, per-set scans, fill.
-cudaError_t launch_mc_batch(const SetDesc* sets_dev, int nsets, int64_t nitems, int maxd, int maxK, int64_t R,
-                            uint64_t seed, int threads, Counters* ctr, cudaStream_t st);
+cudaError_t launch_mc_batch(const SetDesc* sets_dev, const SetDesc* sets_host, int nsets, int64_t nitems, int maxd,
+                            int maxK, int64_t R, uint64_t seed, int threads, Counters* ctr, cudaStream_t st);
+// Tree-walk finish of one set's uncertified MC rays with device-side counts.
+cudaError_t launch_mc_fallback_dev(const SetDesc& S, int64_t R, uint64_t seed, cudaStream_t st);
 void mc_batch_dims(int threads, int maxd, int maxK, size_t* smem);
 
 // MC rays of all cells through the cell-centric kernel (candidate lists

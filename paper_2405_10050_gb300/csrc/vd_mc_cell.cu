@@ -10,7 +10,8 @@
 //              the node box, every later one is too;
 //   recheck    t_j = |w|^2 / (2 u.w) in binary64, canonical order, for the
 //              survivors (about one per ray), plus the box faces.
-// Rays the list cannot certify go to the generic tree walk.
+// Rays the list cannot certify go to the generic tree walk.  The batched
+// variant runs the cells of many point sets in one persistent launch.
 #include <algorithm>
 #include <cmath>
 
@@ -28,56 +29,13 @@ __host__ __device__ inline size_t cell_smem(int D, int K, int threads) {
   return (size_t)K * (D + 5) * 4 + (size_t)threads * kCellBuf * 8;
 }
 
-// Exact ray by brute force over all nodes (binary64, canonical order): the
-// finish of the rare MC rays the candidate list cannot certify in batched
-// launches (no host round trip).
-template <int D>
-__device__ void bruteforce_ray(const TreeView& tr, int64_t i, const double* u64, const double* g64, double& bt,
-                               int& bc, int& bk) {
-  const int d = tr.d;
-  bt = INFINITY;
-  bc = 2;
-  bk = 0;
-  for (int64_t j = 0; j < tr.N; ++j) {
-    if (j == i) continue;
-    double w[D], den = 0.0, ww = 0.0;
-#pragma unroll
-    for (int a = 0; a < D; ++a) w[a] = a < d ? __dadd_rn(tr.X[j * d + a], -g64[a]) : 0.0;
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-      if (a < d) den = __dadd_rn(den, __dmul_rn(u64[a], w[a]));
-    if (!(den > 0.0)) continue;
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-      if (a < d) ww = __dadd_rn(ww, __dmul_rn(w[a], w[a]));
-    const double t = __ddiv_rn(ww, __dmul_rn(2.0, den));
-    if (better(t, 0, (int)j, bt, bc, bk)) {
-      bt = t;
-      bc = 0;
-      bk = (int)j;
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    if (a >= d || u64[a] == 0.0) continue;
-    const int s = u64[a] > 0.0 ? 1 : 0;
-    const double t = __ddiv_rn(__dadd_rn(s ? 1.0 : 0.0, -g64[a]), u64[a]);
-    if (better(t, 1, 2 * a + s, bt, bc, bk)) {
-      bt = t;
-      bc = 1;
-      bk = 2 * a + s;
-    }
-  }
-}
-
-// All R rays of cell i (see the file comment).  INLINE: rays the list cannot
-// certify are finished here by brute force; otherwise they are appended to
-// (fb_cell, fb_ray) for the tree walk.
-template <int D, int TH, bool INLINE>
+// All R rays of cell i (see the file comment).  Rays the list cannot
+// certify are appended to (fb_cell, fb_ray) for the tree walk.
+template <int D, int TH>
 __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t seed, uint32_t set, int32_t* hit_out,
                           double* t_out, float* smem, Counters* ctr, int32_t* fb_cell, int32_t* fb_ray,
                           int64_t fb_cap, unsigned long long& n_pairs, unsigned long long& n_rech,
-                          unsigned long long& n_brute) {
+                          unsigned long long& n_brute, unsigned long long* fb_count) {
   const int K = tr.K;
   const int d = tr.d;
   float* sw = smem;                      // [D][K] binary32 offsets
@@ -211,18 +169,14 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
     double bt = INFINITY;
     int bc = 2, bk = 0;
     if (!certified || overflow) {
-      if (!INLINE) {
-        const unsigned long long q = atomicAdd(&ctr->fallback, 1ull);
-        if ((int64_t)q < fb_cap) {
-          fb_cell[q] = (int32_t)i;
-          fb_ray[q] = (int32_t)k;
-        } else {
-          atomicOr(&ctr->flags, kFlagQueue);
-        }
-        continue;
+      const unsigned long long q = atomicAdd(fb_count, 1ull);
+      if ((int64_t)q < fb_cap) {
+        fb_cell[q] = (int32_t)i;
+        fb_ray[q] = (int32_t)k;
+      } else {
+        atomicOr(&ctr->flags, kFlagQueue);
       }
-      ++n_brute;
-      bruteforce_ray<D>(tr, i, u64, g64, bt, bc, bk);
+      continue;
     } else {
       // binary64 recheck of the survivors, canonical order
       for (int q = 0; q < nc; ++q) {
@@ -298,8 +252,8 @@ __global__ void __launch_bounds__(kCellThreads) k_mc_cell(TreeView tr, int64_t R
     const int64_t i = s_cell;
     __syncthreads();
     if (i >= tr.N) break;
-    cell_item<D, kCellThreads, false>(tr, i, R, seed, set, ro.hit, ro.t, smem, ctr, fb_cell, fb_ray, fb_cap,
-                                      n_pairs, n_rech, n_brute);
+    cell_item<D, kCellThreads>(tr, i, R, seed, set, ro.hit, ro.t, smem, ctr, fb_cell, fb_ray, fb_cap,
+                                      n_pairs, n_rech, n_brute, &ctr->fallback);
   }
   flush_counters<kCellThreads>(ctr, n_pairs, n_rech, n_brute);
 }
@@ -328,10 +282,10 @@ __global__ void __launch_bounds__(TH) k_mc_cell_batch(const SetDesc* sets, int n
     const SetDesc& S = sets[lo];
     const int64_t i = item - S.item0;
     switch (S.tv.d) {
-#define VD_CASE(DD)                                                                                                \
-  case DD:                                                                                                         \
-    cell_item<DD, TH, true>(S.tv, i, R, seed, S.set, S.hit, S.l, smem, ctr, nullptr, nullptr, 0, n_pairs, n_rech, \
-                            n_brute);                                                                              \
+#define VD_CASE(DD)                                                                                              \
+  case DD:                                                                                                       \
+    cell_item<DD, TH>(S.tv, i, R, seed, S.set, S.hit, S.l, smem, ctr, S.fb_cell, S.fb_ray, S.fb_cap,      \
+                             n_pairs, n_rech, n_brute, &S.ctr->fallback);                                        \
     break;
       VD_CASE(1)
       VD_CASE(2)
@@ -340,8 +294,8 @@ __global__ void __launch_bounds__(TH) k_mc_cell_batch(const SetDesc* sets, int n
       VD_CASE(5)
       VD_CASE(6)
       default:
-        cell_item<8, TH, true>(S.tv, i, R, seed, S.set, S.hit, S.l, smem, ctr, nullptr, nullptr, 0, n_pairs, n_rech,
-                               n_brute);
+        cell_item<8, TH>(S.tv, i, R, seed, S.set, S.hit, S.l, smem, ctr, S.fb_cell, S.fb_ray, S.fb_cap,
+                                n_pairs, n_rech, n_brute, &S.ctr->fallback);
         break;
 #undef VD_CASE
     }
@@ -435,12 +389,17 @@ cudaError_t launch_mc_cells(const TreeView& tv, int64_t R, uint64_t seed, uint32
 cudaError_t mc_batch_reduce(const SetDesc* sets_dev, int nsets, int64_t nitems, int maxd, int64_t R, uint64_t seed,
                             cudaStream_t st);
 
-cudaError_t launch_mc_batch(const SetDesc* sets_dev, int nsets, int64_t nitems, int maxd, int maxK, int64_t R,
-                            uint64_t seed, int threads, Counters* ctr, cudaStream_t st) {
-  cudaError_t e;
+cudaError_t launch_mc_batch(const SetDesc* sets_dev, const SetDesc* sets_host, int nsets, int64_t nitems, int maxd,
+                            int maxK, int64_t R, uint64_t seed, int threads, Counters* ctr, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(sets_host[0].ctr, 0, sizeof(Counters) * nsets, st);
+  if (e != cudaSuccess) return e;
   if (threads <= 64) e = launch_batch_th<64>(sets_dev, nsets, nitems, maxK, R, seed, ctr, st);
   else if (threads <= 128) e = launch_batch_th<128>(sets_dev, nsets, nitems, maxK, R, seed, ctr, st);
   else e = launch_batch_th<256>(sets_dev, nsets, nitems, maxK, R, seed, ctr, st);
+  if (e != cudaSuccess) return e;
+  // rays the lists could not certify: tree walk per set, counts read on the
+  // device (a set without such rays costs two empty launches)
+  for (int s = 0; s < nsets && e == cudaSuccess; ++s) e = launch_mc_fallback_dev(sets_host[s], R, seed, st);
   if (e != cudaSuccess) return e;
   return mc_batch_reduce(sets_dev, nsets, nitems, maxd, R, seed, st);
 }

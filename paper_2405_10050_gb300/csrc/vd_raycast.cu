@@ -183,16 +183,21 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
   const float gam = (float)(D + 1) * kU32 * 1.01f;          // gamma_D for the FMA dot products
   const float EW = 4.01f * kU32 * B;                         // |w32_k - w_k|
   unsigned long long n_tiles = 0, n_pairs = 0, n_rech = 0, n_over = 0;
-  const int64_t R = rs.R;
+  int64_t R = rs.R;
+  int rpb = rs.rpb;
+  if (rs.R_dev) {
+    R = min((int64_t)*rs.R_dev, rs.R);
+    rpb = R < (int64_t)gridDim.x * kWpb * 64 ? 1 : 32;
+  }
   while (true) {
     unsigned long long b = 0;
     if (lane == 0) b = atomicAdd(work, 1ull);
     b = __shfl_sync(kFull, b, 0);
-    const int64_t b0 = (int64_t)b * rs.rpb;
+    const int64_t b0 = (int64_t)b * rpb;
     if (b0 >= R) break;
     // ---- set-up: one ray per lane ----
     const int64_t slot = b0 + lane;
-    const bool vr = lane < rs.rpb && slot < R;
+    const bool vr = lane < rpb && slot < R;
     const int64_t r = vr ? (subset ? (int64_t)subset[slot] : slot) : 0;
     if (vr) {
       double v[D], u[D];
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
     }
     __syncwarp();
     // ---- screening: the warp walks the tree for each ray ----
-    for (int rr = 0; rr < rs.rpb && b0 + rr < R; ++rr) {
+    for (int rr = 0; rr < rpb && b0 + rr < R; ++rr) {
       float u[D], gg[D], pp[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -486,15 +491,20 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_fp64(TreeView tr, RaySource r
   const float gam = (float)(D + 1) * kU32 * 1.01f;
   const float EW = 4.01f * kU32 * B;
   unsigned long long n_tiles = 0, n_pairs = 0;
-  const int64_t R = rs.R;
+  int64_t R = rs.R;
+  int rpb = rs.rpb;
+  if (rs.R_dev) {
+    R = min((int64_t)*rs.R_dev, rs.R);
+    rpb = R < (int64_t)gridDim.x * kWpb * 64 ? 1 : 32;
+  }
   while (true) {
     unsigned long long b = 0;
     if (lane == 0) b = atomicAdd(work, 1ull);
     b = __shfl_sync(kFull, b, 0);
-    const int64_t b0 = (int64_t)b * rs.rpb;
+    const int64_t b0 = (int64_t)b * rpb;
     if (b0 >= R) break;
     const int64_t slot = b0 + lane;
-    const bool vr = lane < rs.rpb && slot < R;
+    const bool vr = lane < rpb && slot < R;
     const int64_t r = vr ? (subset ? (int64_t)subset[slot] : slot) : 0;
     if (vr) {
       double v[D], u[D];
@@ -539,7 +549,7 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_fp64(TreeView tr, RaySource r
       S.bkey[lane] = bk;
     }
     __syncwarp();
-    for (int rr = 0; rr < rs.rpb && b0 + rr < R; ++rr) {
+    for (int rr = 0; rr < rpb && b0 + rr < R; ++rr) {
       double u[D], gg[D], pp[D];
       float u32[D], g32[D], p32[D];
 #pragma unroll
@@ -670,7 +680,7 @@ cudaError_t launch_ray_d(const TreeView& tv, const RaySource& rs, const RayOut& 
   // few rays (the tree-walk leftovers of the list scan): one ray per warp so
   // that they spread over the SMs; otherwise 32 rays per warp
   r2.rpb = nrays < (int64_t)nsm * 256 ? 1 : 32;
-  const int64_t batches = (nrays + r2.rpb - 1) / r2.rpb;
+  const int64_t batches = rs.R_dev ? (int64_t)nsm * 64 : (nrays + r2.rpb - 1) / r2.rpb;
   cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
   auto go = [&](auto kern, size_t sm) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -873,6 +883,34 @@ cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut
     e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rs, ro, VD_FP64, ctr, work, ro.overflow_list, n, false, st);
   }
   return e;
+}
+
+cudaError_t launch_mc_fallback_dev(const SetDesc& S, int64_t R, uint64_t seed, cudaStream_t st) {
+  TreeView tv = S.tv;
+  tv.K = 0;  // tree walk
+  RaySource rs;
+  rs.mode = 1;
+  rs.R = S.fb_cap;
+  rs.R_dev = &S.ctr->fallback;
+  rs.mc_cell = S.fb_cell;
+  rs.mc_ray = S.fb_ray;
+  rs.mc_rpc = R;
+  rs.seed = seed;
+  rs.set = S.set;
+  rs.box = 1;
+  RayOut ro;
+  ro.hit = S.hit;
+  ro.t = S.l;
+  ro.mc_rpc = R;
+  ro.overflow_list = S.ov_list;
+  ro.overflow_cap = S.ov_cap;
+  unsigned long long* work = reinterpret_cast<unsigned long long*>(&S.ctr->aux1);
+  cudaError_t e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rs, ro, VD_FP32, S.ctr, work, nullptr, S.fb_cap, false, st);
+  if (e != cudaSuccess) return e;
+  RaySource r2 = rs;
+  r2.R = S.ov_cap;
+  r2.R_dev = &S.ctr->overflow;
+  return VD_DISPATCH_D(tv.d, launch_ray_d, tv, r2, ro, VD_FP64, S.ctr, work, S.ov_list, S.ov_cap, false, st);
 }
 
 int default_knn_k(int d) {

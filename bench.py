@@ -401,17 +401,18 @@ MC_WORKLOAD = ("MC volumes + interface areas + adjoint, d=4, N=100000 iid unifor
 
 def run_mc(args, vd, stream):
     """Secondary line of the metric: MC vol+grad cells/s on the MC workload,
-    binary32-screened path vs plain binary64 path (same seeded directions,
-    identical per-ray hits required)."""
+    binary32-screened path, tensor-core (fp16 tcgen05) screened path and
+    plain binary64 path (same seeded directions, identical per-ray hits
+    required)."""
     import torch
-    from paper_2405_10050_gb300 import VD_FP32, VD_FP64, synth
+    from paper_2405_10050_gb300 import VD_FP32, VD_FP64, VD_TC16, synth
     N, d, R = args.mc_n, 4, args.mc_rays
     X = torch.tensor(synth.uniform(N, d, seed=0), device="cuda")
     gV = torch.ones(N, dtype=torch.float64, device="cuda")
     out = {"workload": MC_WORKLOAD.replace("100000", str(N)).replace("1024 rays", f"{R} rays"),
            "unit": "cells/s"}
     hits = {}
-    for name, prec in (("mixed", VD_FP32), ("fp64", VD_FP64)):
+    for name, prec in (("mixed", VD_FP32), ("tensor", VD_TC16), ("fp64", VD_FP64)):
         cfg = vd.vd_config_default()
         cfg.precision = prec
         ctx = vd.vd_create(cfg, stream.cuda_stream)
@@ -444,7 +445,8 @@ def run_mc(args, vd, stream):
                      "pairs_per_ray": st["pairs_screened"] / max(st["rays"], 1)}
     out["value"] = out["mixed"]["cells_per_s"]
     out["speedup_vs_fp64"] = out["mixed"]["cells_per_s"] / out["fp64"]["cells_per_s"]
-    out["hits_identical_to_fp64"] = bool(torch.equal(hits["mixed"], hits["fp64"]))
+    out["hits_identical_to_fp64"] = bool(torch.equal(hits["mixed"], hits["fp64"]) and
+                                         torch.equal(hits["tensor"], hits["fp64"]))
     return out
 
 

@@ -51,7 +51,9 @@ typedef enum {
   VD_FP64 = 0,  /* every (ray, node) pair in binary64                      */
   VD_FP32 = 1,  /* binary32 screening with a proven error margin, binary64
                    recheck of the survivors                                */
-  VD_BF16 = 2,  /* tensor-core bf16 screening, binary64 recheck            */
+  VD_TC16 = 2,  /* MC rays: u.w on the tensor cores (tcgen05, fp16 in,
+                   fp32 accumulate) with a proven error margin, binary64
+                   recheck; other calls treat it as VD_FP32              */
   VD_AUTO = 3   /* the library's autotuner picks among the above           */
 } vd_precision;
 

@@ -11,9 +11,9 @@ from __future__ import annotations
 import numpy as np
 
 from . import vd
-from .vd import NO_ID, VD_AUTO, VD_BF16, VD_FP32, VD_FP64, VDError
+from .vd import NO_ID, VD_AUTO, VD_TC16, VD_FP32, VD_FP64, VDError
 
-__all__ = ["vd", "Voronoi", "VoronoiMC", "MCResult", "NO_ID", "VD_FP64", "VD_FP32", "VD_BF16", "VD_AUTO",
+__all__ = ["vd", "Voronoi", "VoronoiMC", "MCResult", "NO_ID", "VD_FP64", "VD_FP32", "VD_TC16", "VD_AUTO",
            "VDError", "face_id"]
 
 

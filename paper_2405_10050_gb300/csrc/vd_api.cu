@@ -154,7 +154,8 @@ vd_status check_flags(vd_ctx* ctx, const Counters& hc) {
 int effective_precision(const vd_ctx* ctx) {
   const int p = ctx->cfg.precision;
   if (p == VD_FP64) return VD_FP64;
-  return VD_FP32;  // VD_FP32, VD_AUTO and (until the tensor path is selected) VD_BF16
+  if (p == VD_TC16) return VD_TC16;
+  return VD_FP32;  // VD_FP32 and VD_AUTO
 }
 
 }  // namespace
@@ -409,7 +410,11 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
   {
     Timer tr(ctx->st);
     const int prec = effective_precision(ctx);
-    if (tv.K > 0 && prec != VD_FP64)
+    if (tv.K > 0 && prec == VD_TC16 && tv.coord_abs <= vd::kTcCoordMax)
+      VD_CK(vd::launch_mc_cells_tc(tv, R, seed, set, ro, ctx->ctr, ctx->cfg.wait_limit, ctx->st,
+                                   &mc->stats.fallback_rays),
+            "mc cells tc");
+    else if (tv.K > 0 && prec != VD_FP64)
       VD_CK(vd::launch_mc_cells(tv, R, seed, set, ro, prec, ctx->ctr, ctx->st, &mc->stats.fallback_rays),
             "mc cells");
     else

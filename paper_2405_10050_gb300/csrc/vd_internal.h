@@ -169,6 +169,13 @@ void mc_batch_dims(int threads, int maxd, int maxK, size_t* smem);
 // 2 x (fallback_cap / 2) entries for (cell, ray) pairs.
 cudaError_t launch_mc_cells(const TreeView& tv, int64_t R, uint64_t seed, uint32_t set, const RayOut& ro,
                             int precision, Counters* ctr, cudaStream_t st, int64_t* nfallback);
+// Same contract with the u.w screening contraction on the tensor cores
+// (tcgen05, fp16 operands); needs coordinates within the fp16 range
+// (tv.coord_abs <= kTcCoordMax).  MMA completion waits poll at most
+// wait_limit times; a wait that gives up sets kFlagTimeout.
+constexpr float kTcCoordMax = 1.0e4f;
+cudaError_t launch_mc_cells_tc(const TreeView& tv, int64_t R, uint64_t seed, uint32_t set, const RayOut& ro,
+                               Counters* ctr, long long wait_limit, cudaStream_t st, int64_t* nfallback);
 cudaError_t launch_mc_directions(uint64_t seed, uint32_t set, int64_t cell0, int64_t ncells, int64_t R, int d,
                                  double* out, cudaStream_t st);
 

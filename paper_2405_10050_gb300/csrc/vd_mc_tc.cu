@@ -1,0 +1,431 @@
+// vd_mc_tc.cu -- cell-centric Monte Carlo RayCast with the u.w contraction
+// on the tensor cores (tcgen05).  Same method as vd_mc_cell.cu (Section 3.1,
+// Algorithm 3; candidate list of x_i, early exit, binary64 recheck), but the
+// denominators den_rc = u_r . w_c of a tile of 128 rays against 32 candidates
+// come from one `tcgen05.mma.kind::f16` (A = ray directions [128 x 16],
+// B = candidate offsets [32 x 16], fp16 operands with d padded to K = 16,
+// fp32 accumulation in tensor memory).  Each thread owns one ray (one
+// tensor-memory lane), reads its 32 den values with `tcgen05.ld` and runs the
+// interval screening with an error bound that covers the fp16 rounding of
+// both operands and the tensor-core accumulation.
+//
+// Operand layout in shared memory (no swizzle, K-major): element (row, k)
+// of a [rows x 16] fp16 matrix sits at byte (row/8)*256 + (k/8)*128 +
+// (row%8)*16 + (k%8)*2, i.e. 8x16-byte core matrices, 128 B apart along K
+// and 256 B apart along rows.
+#include <algorithm>
+#include <cmath>
+#include <cuda_fp16.h>
+
+#include "vd_ray_common.cuh"
+#include "vd_tc.cuh"
+
+namespace vd {
+
+namespace {
+
+constexpr int kTcThreads = 128;  // rays per tile = MMA M = tensor-memory lanes
+constexpr int kTcN = 32;         // candidates per MMA (MMA N, tensor-memory columns)
+constexpr int kTcBuf = 8;        // candidates kept per ray
+
+__host__ __device__ inline size_t tc_smem(int K) {
+  const size_t Kp = ((size_t)K + kTcN - 1) / kTcN * kTcN;
+  return Kp * 32 + (size_t)kTcThreads * 32 + Kp * 5 * 4 + (size_t)kTcThreads * kTcBuf * 8 +
+         (size_t)kTcThreads * (kTcN + 1) * 4;
+}
+
+__device__ __forceinline__ void store_row16(unsigned char* base, int row, const __half (&h)[16]) {
+  unsigned char* p = base + (row >> 3) * 256 + (row & 7) * 16;
+  *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(&h[0]);
+  *reinterpret_cast<uint4*>(p + 128) = *reinterpret_cast<const uint4*>(&h[8]);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t R, uint64_t seed, uint32_t set,
+                                                           RayOut ro, Counters* ctr, unsigned long long* work,
+                                                           int32_t* fb_cell, int32_t* fb_ray, int64_t fb_cap,
+                                                           long long wait_limit) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int64_t s_cell;
+  const int K = tr.K;
+  const int Kp = (K + kTcN - 1) / kTcN * kTcN;
+  unsigned char* B16 = smem;                          // [Kp x 16] fp16 candidate offsets
+  unsigned char* A16 = smem + (size_t)Kp * 32;        // [128 x 16] fp16 ray directions
+  float* snlo = reinterpret_cast<float*>(A16 + kTcThreads * 32);
+  float* snhi = snlo + Kp;
+  float* swn = snhi + Kp;
+  float* sflo = swn + Kp;
+  int32_t* sid = reinterpret_cast<int32_t*>(sflo + Kp);
+  int32_t* cb = reinterpret_cast<int32_t*>(sid + Kp) + threadIdx.x * kTcBuf;
+  float* ct = reinterpret_cast<float*>(reinterpret_cast<int32_t*>(sid + Kp) + kTcThreads * kTcBuf) +
+              threadIdx.x * kTcBuf;
+  // this thread's den row of the current chunk (stride kTcN + 1: no bank conflicts)
+  float* sden = reinterpret_cast<float*>(reinterpret_cast<int32_t*>(sid + Kp) + 2 * kTcThreads * kTcBuf) +
+                threadIdx.x * (kTcN + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int d = tr.d;
+  const float B = tr.coord_abs;
+  const float gam = (float)(D + 1) * kU32 * 1.01f;
+  const float EW = 4.01f * kU32 * B;
+  const float e1 = 1.1f * (gam + 2.1f * kU32);  // |ww32 - |w|^2| <= e1 ww32
+  // |den_mma - u.w| <= a1 |w| + a0 for |u| = 1:
+  //   binary32 then fp16 rounding of each u_k and w_k: relative 2^-11 + 2^-24,
+  //   plus an absolute 2^-25 below the fp16 normal range, which over the
+  //   d terms adds at most sqrt(d) 2^-25 (|w| + 1);
+  //   the products of two fp16 values are exact in fp32; the sum of the 16
+  //   products is charged 2^-16 of sum |u_k w_k| <= |w|, far above the
+  //   16 x 2^-23 of any fp32 accumulation order or rounding mode.
+  const float sq = sqrtf((float)D);
+  const float a1 = 1.1f * (0x1p-10f + 0x1p-22f + 0x1p-16f + sq * 0x1p-25f);
+  const float a0 = 1.1f * sq * 0x1p-25f;
+  const uint32_t idesc = tc::idesc_f16_f32(kTcThreads, kTcN);
+
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, kTcN);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = tmem_base;
+  const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16);
+  uint32_t phase = 0;
+  bool timed_out = false;
+  unsigned long long n_pairs = 0, n_rech = 0;
+  const uint64_t adesc = tc::smem_desc(A16, 128, 256);
+
+  while (!timed_out) {
+    if (tid == 0) s_cell = (int64_t)atomicAdd(work, 1ull);
+    __syncthreads();
+    const int64_t i = s_cell;
+    __syncthreads();
+    if (i >= tr.N) break;
+    const int n = tr.kcnt[i];
+    const int np = (n + kTcN - 1) / kTcN * kTcN;
+    double g64[D];
+    float g32[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      g64[k] = k < d ? tr.X[i * d + k] : 0.0;
+      g32[k] = k < d ? tr.X32[i * d + k] : 0.f;
+    }
+    // ---- stage the cell's candidate list: fp16 offsets + binary32 bounds ----
+    for (int c = tid; c < np; c += kTcThreads) {
+      __half h[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) h[k] = __float2half_rn(0.f);
+      if (c < n) {
+        const int32_t id = tr.knn[i * K + c];
+        float ww = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float w = k < d ? __double2float_rn(tr.X[(int64_t)id * d + k] - g64[k]) : 0.f;
+          ww = fmaf(w, w, ww);
+          if (k < 16) h[k] = __float2half_rn(w);
+        }
+        snlo[c] = ww * (1.f - e1);
+        snhi[c] = ww * (1.f + e1);
+        swn[c] = sqrtf(ww) * (1.f + gam);
+        sflo[c] = true_d2_lower(ww32_of<D>(tr.X32 + (int64_t)id * d, 1, g32, d), gam, EW, D);
+        sid[c] = id;
+      }
+      store_row16(B16, c, h);
+    }
+    const float cert_lo = true_d2_lower(tr.kcert[i], gam, EW, D);
+    // ---- rays, 128 per tile ----
+    for (int64_t t0 = 0; t0 < R; t0 += kTcThreads) {
+      const int64_t k = t0 + tid;
+      const bool valid = k < R;
+      double u64[D];
+      float u32[D], p0[D];
+      float T = INFINITY;
+      int nc = 0;
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        u64[q] = 0.0;
+        p0[q] = 0.f;
+      }
+      if (valid) mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u64);
+      __half hu[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) hu[q] = __float2half_rn(0.f);
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        u32[q] = __double2float_rn(u64[q]);
+        if (q < 16) hu[q] = __float2half_rn(u32[q]);
+      }
+      store_row16(A16, tid, hu);
+      if (valid) {  // box faces: binary32 interval of (b - x_ia) / u_a
+        for (int a = 0; a < d; ++a) {
+          double ua64 = 0.0;
+          float ua = 0.f, va = 0.f;
+#pragma unroll
+          for (int q = 0; q < D; ++q)
+            if (q == a) {
+              ua64 = u64[q];
+              ua = u32[q];
+              va = g32[q];
+            }
+          if (ua64 == 0.0 || ua == 0.f) continue;
+          const int s = ua64 > 0.0 ? 1 : 0;
+          const float nf = (s ? 1.f : 0.f) - va;
+          const float nfs = s ? nf : -nf;
+          const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
+          const float au = fabsf(ua);
+          const float lo_n = nfs - ef, hi_n = nfs + ef;
+          const float tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
+                                        : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
+          const float thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
+                                        : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
+          T = fminf(T, thi);
+          if (nc < kTcBuf) {
+            cb[nc] = face_id(a, s);
+            ct[nc] = tlo;
+            ++nc;
+          }
+        }
+      }
+      Ball<D> ball;
+      make_ball<D>(g32, p0, u32, T, B, ball);
+      float far2 = far_radius2<D>(tr, ball, g32);
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      bool certified = !valid, overflow = false;
+      int done = 0;  // candidates screened by this ray
+      for (int c0 = 0; c0 < np; c0 += kTcN) {
+        if (tid == 0) {
+          tc::fence_after_sync();
+          tc::mma_f16(tbase, adesc, tc::smem_desc(B16 + (size_t)c0 * 32, 128, 256), idesc, 0u);
+          tc::mma_commit(&mbar);
+        }
+        const bool ok = tc::mbar_wait(&mbar, phase, wait_limit);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+          timed_out = true;
+          break;
+        }
+        tc::fence_after_sync();
+        __syncwarp();
+        {
+          float den[kTcN];
+          tc::tmem_ld32(taddr, den);
+#pragma unroll
+          for (int j = 0; j < kTcN; ++j) sden[j] = den[j];
+        }
+        if (!certified) {
+          const int jn = min(kTcN, n - c0);
+#pragma unroll 1
+          for (int j = 0; j < jn; ++j) {
+            const int c = c0 + j;
+            if (sflo[c] >= far2) {
+              certified = true;
+              break;
+            }
+            done = c + 1;
+            const float e = fmaf(a1, swn[c], a0);
+            const float dj = sden[j];
+            const float dh = dj + e;
+            const float nlo = snlo[c];
+            if (!(dh > 0.f) || nlo > 2.f * T * dh * (1.f + 8.f * kU32)) continue;
+            const float dl = dj - e;
+            const float thi = dl > 0.f ? __fdiv_rn(snhi[c], 2.f * dl) * (1.f + 4.f * kU32) : INFINITY;
+            const float tlo = __fdiv_rn(nlo, 2.f * dh) * (1.f - 4.f * kU32);
+            if (thi < T) {
+              T = thi;
+              make_ball<D>(g32, p0, u32, T, B, ball);
+              far2 = far_radius2<D>(tr, ball, g32);
+            }
+            if (tlo <= T && !overflow) {
+              if (nc == kTcBuf) {
+                int m = 0;
+                for (int q = 0; q < kTcBuf; ++q)
+                  if (ct[q] <= T) {
+                    cb[m] = cb[q];
+                    ct[m] = ct[q];
+                    ++m;
+                  }
+                nc = m;
+              }
+              if (nc < kTcBuf) {
+                cb[nc] = sid[c];
+                ct[nc] = tlo;
+                ++nc;
+              } else {
+                overflow = true;
+              }
+            }
+          }
+        }
+        const bool more = !certified && (c0 + kTcN < n);
+        tc::fence_before_sync();
+        if (!__syncthreads_or(more)) break;
+      }
+      if (timed_out) break;
+      if (valid) {
+        n_pairs += (unsigned long long)done;
+        if (!certified) certified = cert_lo >= far2;
+        if (!certified || overflow) {
+          const unsigned long long q = atomicAdd(&ctr->fallback, 1ull);
+          if ((int64_t)q < fb_cap) {
+            fb_cell[q] = (int32_t)i;
+            fb_ray[q] = (int32_t)k;
+          } else {
+            atomicOr(&ctr->flags, kFlagQueue);
+          }
+        } else {
+          double bt = INFINITY;
+          int bc = 2, bk = 0;
+          for (int q = 0; q < nc; ++q) {
+            if (!(ct[q] <= T)) continue;
+            const int32_t id = cb[q];
+            ++n_rech;
+            if (id >= 0) {
+              double w[D], dn = 0.0, ww = 0.0;
+#pragma unroll
+              for (int a = 0; a < D; ++a) w[a] = a < d ? __dadd_rn(tr.X[(int64_t)id * d + a], -g64[a]) : 0.0;
+#pragma unroll
+              for (int a = 0; a < D; ++a)
+                if (a < d) dn = __dadd_rn(dn, __dmul_rn(u64[a], w[a]));
+              if (!(dn > 0.0)) continue;
+#pragma unroll
+              for (int a = 0; a < D; ++a)
+                if (a < d) ww = __dadd_rn(ww, __dmul_rn(w[a], w[a]));
+              const double t = __ddiv_rn(ww, __dmul_rn(2.0, dn));
+              if (better(t, 0, id, bt, bc, bk)) {
+                bt = t;
+                bc = 0;
+                bk = id;
+              }
+            } else {
+              const int a = face_axis(id), s = face_side(id);
+              double ua = 0.0, va = 0.0;
+#pragma unroll
+              for (int q2 = 0; q2 < D; ++q2)
+                if (q2 == a) {
+                  ua = u64[q2];
+                  va = g64[q2];
+                }
+              const double t = __ddiv_rn(__dadd_rn(s ? 1.0 : 0.0, -va), ua);
+              if (better(t, 1, 2 * a + s, bt, bc, bk)) {
+                bt = t;
+                bc = 1;
+                bk = 2 * a + s;
+              }
+            }
+          }
+          ro.hit[i * R + k] = gen_from_key(bc, bk);
+          ro.t[i * R + k] = bt;
+        }
+      }
+      __syncthreads();  // the next tile rewrites the A operand
+    }
+    __syncthreads();  // the next cell rewrites the B operand
+  }
+  if (timed_out) {
+    // give the in-flight MMA a bounded chance to finish before freeing its memory
+    tc::mbar_wait(&mbar, phase ^ 1u, wait_limit);
+    if (tid == 0) atomicOr(&ctr->flags, kFlagTimeout);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tbase, kTcN);
+  for (int o = 16; o; o >>= 1) {
+    n_pairs += __shfl_xor_sync(kFull, n_pairs, o);
+    n_rech += __shfl_xor_sync(kFull, n_rech, o);
+  }
+  if ((tid & 31) == 0) {
+    atomicAdd(&ctr->pairs, n_pairs);
+    atomicAdd(&ctr->rechecked, n_rech);
+  }
+}
+
+template <int D>
+cudaError_t launch_tc_d(const TreeView& tv, int64_t R, uint64_t seed, uint32_t set, const RayOut& ro, Counters* ctr,
+                        unsigned long long* work, int32_t* fb_cell, int32_t* fb_ray, int64_t fb_cap,
+                        long long wait_limit, cudaStream_t st) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t sm = tc_smem(tv.K);
+  cudaFuncSetAttribute(k_mc_cell_tc<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  // The occupancy API reports one block per SM for any kernel that allocates
+  // tensor memory; the resident count follows from registers, shared memory
+  // and warps, and 16 blocks of 32 columns fill the 512 tensor-memory columns.
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, k_mc_cell_tc<D>);
+  int smem_sm = 0, regs_sm = 0, warps_sm = 0;
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&warps_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  const int warps = kTcThreads / 32;
+  const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+  const int by_regs = regs_sm / std::max(1, regs_warp * warps);
+  const int by_smem = (int)(smem_sm / (sm + fa.sharedSizeBytes + 1024));
+  const int by_warps = warps_sm / 32 / warps;
+  const int occ = std::max(1, std::min(std::min(by_regs, by_smem), std::min(by_warps, 16)));
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * occ, tv.N));
+  cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+  k_mc_cell_tc<D><<<(unsigned)grid, kTcThreads, sm, st>>>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap,
+                                                           wait_limit > 0 ? wait_limit : (1ll << 22));
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Tensor-core variant of launch_mc_cells (same contract).
+cudaError_t launch_mc_cells_tc(const TreeView& tv, int64_t R, uint64_t seed, uint32_t set, const RayOut& ro,
+                               Counters* ctr, long long wait_limit, cudaStream_t st, int64_t* nfallback) {
+  unsigned long long* work = reinterpret_cast<unsigned long long*>(&ctr->aux1);
+  int32_t* fb_cell = ro.fallback_list;
+  int32_t* fb_ray = ro.fallback_list + ro.fallback_cap / 2;
+  const int64_t fb_cap = ro.fallback_cap / 2;
+  cudaMemsetAsync(&ctr->fallback, 0, sizeof(unsigned long long), st);
+  cudaError_t e;
+  switch (tv.d) {
+    case 1: e = launch_tc_d<1>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, wait_limit, st); break;
+    case 2: e = launch_tc_d<2>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, wait_limit, st); break;
+    case 3: e = launch_tc_d<3>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, wait_limit, st); break;
+    case 4: e = launch_tc_d<4>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, wait_limit, st); break;
+    case 5: e = launch_tc_d<5>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, wait_limit, st); break;
+    case 6: e = launch_tc_d<6>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, wait_limit, st); break;
+    case 7:
+    case 8: e = launch_tc_d<8>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, wait_limit, st); break;
+    case 9: case 10: case 11: case 12:
+      e = launch_tc_d<12>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, wait_limit, st);
+      break;
+    default: e = launch_tc_d<16>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, wait_limit, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  unsigned long long nfb = 0;
+  cudaMemcpyAsync(&nfb, &ctr->fallback, sizeof(nfb), cudaMemcpyDeviceToHost, st);
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  const int64_t n = std::min<int64_t>((int64_t)nfb, fb_cap);
+  if (nfallback) *nfallback += n;
+  if (n == 0) return cudaSuccess;
+  RaySource rs;
+  rs.mode = 1;
+  rs.R = n;
+  rs.mc_cell = fb_cell;
+  rs.mc_ray = fb_ray;
+  rs.mc_rpc = R;
+  rs.seed = seed;
+  rs.set = set;
+  rs.box = 1;
+  RayOut r2 = ro;
+  r2.fallback_list = nullptr;
+  r2.fallback_cap = 0;
+  TreeView tv2 = tv;
+  tv2.K = 0;
+  return launch_raycast(tv2, rs, r2, VD_FP32, ctr, st, nullptr);
+}
+
+}  // namespace vd

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 NO_ID = -(2**31)
-VD_FP64, VD_FP32, VD_BF16, VD_AUTO = 0, 1, 2, 3
+VD_FP64, VD_FP32, VD_TC16, VD_AUTO = 0, 1, 2, 3
 STATUS = {0: "VD_OK", -1: "VD_EINVAL", -2: "VD_ENOMEM", -3: "VD_ECUDA", -4: "VD_EDEGENERATE",
           -5: "VD_EHASHFULL", -6: "VD_EOVERFLOW", -7: "VD_ETIMEOUT"}
 

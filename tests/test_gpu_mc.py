@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from gpu_util import need_cuda
-from paper_2405_10050_gb300 import VD_FP32, VD_FP64, Voronoi, VoronoiMC, synth
+from paper_2405_10050_gb300 import VD_FP32, VD_FP64, VD_TC16, Voronoi, VoronoiMC, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -37,13 +37,27 @@ def _parity(orc, X, R, seed, prec):
     return vor, res, ref
 
 
-@pytest.mark.parametrize("prec", [VD_FP64, VD_FP32])
+@pytest.mark.parametrize("prec", [VD_FP64, VD_FP32, VD_TC16])
 @pytest.mark.parametrize("d,N,R", [(1, 100, 16), (2, 700, 64), (3, 2000, 64), (4, 1000, 64), (5, 600, 32),
                                    (8, 300, 32), (16, 200, 16)])
 def test_mc_parity(orc, prec, d, N, R):
     need_cuda()
     X = synth.uniform(N, d, seed=d)
     vor, res, ref = _parity(orc, X, R, seed=11 + d, prec=prec)
+    res.free()
+    vor.close()
+
+
+@pytest.mark.parametrize("d,N,R,scale", [(3, 3000, 200, 1.0), (4, 1500, 130, 1e-3), (6, 800, 96, 1.0),
+                                         (12, 300, 40, 1.0)])
+def test_mc_parity_tensor_cases(orc, d, N, R, scale):
+    """Tensor-core screening: clustered nodes, several 128-ray tiles per
+    cell with a ragged last tile (R not a multiple of 128), and a small-scale
+    set whose offsets fall below the fp16 normal range (the absolute error
+    floor of the bound)."""
+    need_cuda()
+    X = synth.gaussian_mixture(N, d, K=8, sigma=0.03, seed=d) * scale
+    vor, res, ref = _parity(orc, X, R, seed=7 + d, prec=VD_TC16)
     res.free()
     vor.close()
 

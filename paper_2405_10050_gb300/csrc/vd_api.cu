@@ -414,6 +414,10 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
       VD_CK(vd::launch_mc_cells_tc(tv, R, seed, set, ro, ctx->ctr, ctx->cfg.wait_limit, ctx->st,
                                    &mc->stats.fallback_rays),
             "mc cells tc");
+    else if (prec == VD_TC16 && tv.coord_abs <= vd::kTcCoordMax)
+      VD_CK(vd::launch_mc_walk_tc(tv, R, seed, set, ro, ctx->ctr, ctx->cfg.wait_limit, ctx->st,
+                                  &mc->stats.fallback_rays),
+            "mc walk tc");
     else if (tv.K > 0 && prec != VD_FP64)
       VD_CK(vd::launch_mc_cells(tv, R, seed, set, ro, prec, ctx->ctr, ctx->st, &mc->stats.fallback_rays),
             "mc cells");

@@ -176,6 +176,11 @@ cudaError_t launch_mc_cells(const TreeView& tv, int64_t R, uint64_t seed, uint32
 constexpr float kTcCoordMax = 1.0e4f;
 cudaError_t launch_mc_cells_tc(const TreeView& tv, int64_t R, uint64_t seed, uint32_t set, const RayOut& ro,
                                Counters* ctr, long long wait_limit, cudaStream_t st, int64_t* nfallback);
+// MC rays without candidate lists: block tree walk with the ball tests of
+// children and the leaf screening on the tensor cores; same contract as
+// launch_mc_cells_tc.
+cudaError_t launch_mc_walk_tc(const TreeView& tv, int64_t R, uint64_t seed, uint32_t set, const RayOut& ro,
+                              Counters* ctr, long long wait_limit, cudaStream_t st, int64_t* nfallback);
 cudaError_t launch_mc_directions(uint64_t seed, uint32_t set, int64_t cell0, int64_t ncells, int64_t R, int d,
                                  double* out, cudaStream_t st);
 

@@ -9,15 +9,10 @@
 // interval screening with an error bound that covers the fp16 rounding of
 // both operands and the tensor-core accumulation.
 //
-// Operand layout in shared memory (no swizzle, K-major): element (row, k)
-// of a [rows x 16] fp16 matrix sits at byte (row/8)*256 + (k/8)*128 +
-// (row%8)*16 + (k%8)*2, i.e. 8x16-byte core matrices, 128 B apart along K
-// and 256 B apart along rows.
 #include <algorithm>
 #include <cmath>
-#include <cuda_fp16.h>
 
-#include "vd_ray_common.cuh"
+#include "vd_mc_common.cuh"
 #include "vd_tc.cuh"
 
 namespace vd {
@@ -34,11 +29,6 @@ __host__ __device__ inline size_t tc_smem(int K) {
          (size_t)kTcThreads * (kTcN + 1) * 4;
 }
 
-__device__ __forceinline__ void store_row16(unsigned char* base, int row, const __half (&h)[16]) {
-  unsigned char* p = base + (row >> 3) * 256 + (row & 7) * 16;
-  *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(&h[0]);
-  *reinterpret_cast<uint4*>(p + 128) = *reinterpret_cast<const uint4*>(&h[8]);
-}
 
 template <int D>
 __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t R, uint64_t seed, uint32_t set,
@@ -70,16 +60,8 @@ __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t 
   const float gam = (float)(D + 1) * kU32 * 1.01f;
   const float EW = 4.01f * kU32 * B;
   const float e1 = 1.1f * (gam + 2.1f * kU32);  // |ww32 - |w|^2| <= e1 ww32
-  // |den_mma - u.w| <= a1 |w| + a0 for |u| = 1:
-  //   binary32 then fp16 rounding of each u_k and w_k: relative 2^-11 + 2^-24,
-  //   plus an absolute 2^-25 below the fp16 normal range, which over the
-  //   d terms adds at most sqrt(d) 2^-25 (|w| + 1);
-  //   the products of two fp16 values are exact in fp32; the sum of the 16
-  //   products is charged 2^-16 of sum |u_k w_k| <= |w|, far above the
-  //   16 x 2^-23 of any fp32 accumulation order or rounding mode.
-  const float sq = sqrtf((float)D);
-  const float a1 = 1.1f * (0x1p-10f + 0x1p-22f + 0x1p-16f + sq * 0x1p-25f);
-  const float a0 = 1.1f * sq * 0x1p-25f;
+  const TcBound eb = tc_bound(D);
+  const float a1 = eb.a1, a0 = eb.a0;
   const uint32_t idesc = tc::idesc_f16_f32(kTcThreads, kTcN);
 
   if (warp == 0) {
@@ -96,7 +78,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t 
   uint32_t phase = 0;
   bool timed_out = false;
   unsigned long long n_pairs = 0, n_rech = 0;
-  const uint64_t adesc = tc::smem_desc(A16, 128, 256);
+  const uint64_t adesc = tc::smem_desc(A16, tc::kLbo16, tc::kSbo16);
 
   while (!timed_out) {
     if (tid == 0) s_cell = (int64_t)atomicAdd(work, 1ull);
@@ -115,9 +97,9 @@ __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t 
     }
     // ---- stage the cell's candidate list: fp16 offsets + binary32 bounds ----
     for (int c = tid; c < np; c += kTcThreads) {
-      __half h[16];
+      float h[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) h[k] = __float2half_rn(0.f);
+      for (int k = 0; k < 16; ++k) h[k] = 0.f;
       if (c < n) {
         const int32_t id = tr.knn[i * K + c];
         float ww = 0.f;
@@ -125,7 +107,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t 
         for (int k = 0; k < D; ++k) {
           const float w = k < d ? __double2float_rn(tr.X[(int64_t)id * d + k] - g64[k]) : 0.f;
           ww = fmaf(w, w, ww);
-          if (k < 16) h[k] = __float2half_rn(w);
+          if (k < 16) h[k] = w;
         }
         snlo[c] = ww * (1.f - e1);
         snhi[c] = ww * (1.f + e1);
@@ -133,7 +115,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t 
         sflo[c] = true_d2_lower(ww32_of<D>(tr.X32 + (int64_t)id * d, 1, g32, d), gam, EW, D);
         sid[c] = id;
       }
-      store_row16(B16, c, h);
+      tc::store_row16(B16, c, h);
     }
     const float cert_lo = true_d2_lower(tr.kcert[i], gam, EW, D);
     // ---- rays, 128 per tile ----
@@ -150,45 +132,17 @@ __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t 
         p0[q] = 0.f;
       }
       if (valid) mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u64);
-      __half hu[16];
+      float hu[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) hu[q] = __float2half_rn(0.f);
+      for (int q = 0; q < 16; ++q) hu[q] = 0.f;
 #pragma unroll
       for (int q = 0; q < D; ++q) {
         u32[q] = __double2float_rn(u64[q]);
-        if (q < 16) hu[q] = __float2half_rn(u32[q]);
+        if (q < 16) hu[q] = u32[q];
       }
-      store_row16(A16, tid, hu);
-      if (valid) {  // box faces: binary32 interval of (b - x_ia) / u_a
-        for (int a = 0; a < d; ++a) {
-          double ua64 = 0.0;
-          float ua = 0.f, va = 0.f;
-#pragma unroll
-          for (int q = 0; q < D; ++q)
-            if (q == a) {
-              ua64 = u64[q];
-              ua = u32[q];
-              va = g32[q];
-            }
-          if (ua64 == 0.0 || ua == 0.f) continue;
-          const int s = ua64 > 0.0 ? 1 : 0;
-          const float nf = (s ? 1.f : 0.f) - va;
-          const float nfs = s ? nf : -nf;
-          const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
-          const float au = fabsf(ua);
-          const float lo_n = nfs - ef, hi_n = nfs + ef;
-          const float tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
-                                        : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
-          const float thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
-                                        : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
-          T = fminf(T, thi);
-          if (nc < kTcBuf) {
-            cb[nc] = face_id(a, s);
-            ct[nc] = tlo;
-            ++nc;
-          }
-        }
-      }
+      tc::store_row16(A16, tid, hu);
+      bool overflow = false;
+      if (valid) T = mc_faces<D>(u64, u32, g32, d, cb, ct, nc, kTcBuf, overflow);
       Ball<D> ball;
       make_ball<D>(g32, p0, u32, T, B, ball);
       float far2 = far_radius2<D>(tr, ball, g32);
@@ -196,12 +150,12 @@ __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t 
       tc::fence_before_sync();
       __syncthreads();
       tc::fence_after_sync();
-      bool certified = !valid, overflow = false;
+      bool certified = !valid;
       int done = 0;  // candidates screened by this ray
       for (int c0 = 0; c0 < np; c0 += kTcN) {
         if (tid == 0) {
           tc::fence_after_sync();
-          tc::mma_f16(tbase, adesc, tc::smem_desc(B16 + (size_t)c0 * 32, 128, 256), idesc, 0u);
+          tc::mma_f16(tbase, adesc, tc::smem_desc(B16 + (size_t)c0 * 32, tc::kLbo16, tc::kSbo16), idesc, 0u);
           tc::mma_commit(&mbar);
         }
         const bool ok = tc::mbar_wait(&mbar, phase, wait_limit);
@@ -241,25 +195,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t 
               make_ball<D>(g32, p0, u32, T, B, ball);
               far2 = far_radius2<D>(tr, ball, g32);
             }
-            if (tlo <= T && !overflow) {
-              if (nc == kTcBuf) {
-                int m = 0;
-                for (int q = 0; q < kTcBuf; ++q)
-                  if (ct[q] <= T) {
-                    cb[m] = cb[q];
-                    ct[m] = ct[q];
-                    ++m;
-                  }
-                nc = m;
-              }
-              if (nc < kTcBuf) {
-                cb[nc] = sid[c];
-                ct[nc] = tlo;
-                ++nc;
-              } else {
-                overflow = true;
-              }
-            }
+            if (!overflow) overflow = !mc_push(sid[c], tlo, T, cb, ct, nc, kTcBuf);
           }
         }
         const bool more = !certified && (c0 + kTcN < n);
@@ -279,48 +215,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t 
             atomicOr(&ctr->flags, kFlagQueue);
           }
         } else {
-          double bt = INFINITY;
-          int bc = 2, bk = 0;
-          for (int q = 0; q < nc; ++q) {
-            if (!(ct[q] <= T)) continue;
-            const int32_t id = cb[q];
-            ++n_rech;
-            if (id >= 0) {
-              double w[D], dn = 0.0, ww = 0.0;
-#pragma unroll
-              for (int a = 0; a < D; ++a) w[a] = a < d ? __dadd_rn(tr.X[(int64_t)id * d + a], -g64[a]) : 0.0;
-#pragma unroll
-              for (int a = 0; a < D; ++a)
-                if (a < d) dn = __dadd_rn(dn, __dmul_rn(u64[a], w[a]));
-              if (!(dn > 0.0)) continue;
-#pragma unroll
-              for (int a = 0; a < D; ++a)
-                if (a < d) ww = __dadd_rn(ww, __dmul_rn(w[a], w[a]));
-              const double t = __ddiv_rn(ww, __dmul_rn(2.0, dn));
-              if (better(t, 0, id, bt, bc, bk)) {
-                bt = t;
-                bc = 0;
-                bk = id;
-              }
-            } else {
-              const int a = face_axis(id), s = face_side(id);
-              double ua = 0.0, va = 0.0;
-#pragma unroll
-              for (int q2 = 0; q2 < D; ++q2)
-                if (q2 == a) {
-                  ua = u64[q2];
-                  va = g64[q2];
-                }
-              const double t = __ddiv_rn(__dadd_rn(s ? 1.0 : 0.0, -va), ua);
-              if (better(t, 1, 2 * a + s, bt, bc, bk)) {
-                bt = t;
-                bc = 1;
-                bk = 2 * a + s;
-              }
-            }
-          }
-          ro.hit[i * R + k] = gen_from_key(bc, bk);
-          ro.t[i * R + k] = bt;
+          mc_recheck<D>(tr.X, d, g64, u64, cb, ct, nc, T, ro.hit[i * R + k], ro.t[i * R + k], n_rech);
         }
       }
       __syncthreads();  // the next tile rewrites the A operand

@@ -4,6 +4,7 @@
 // completion through an mbarrier (bounded wait) and tensor-memory loads.
 #pragma once
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace vd {
@@ -99,6 +100,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long 
   }
   return false;
 }
+
+// Operand layout in shared memory (no swizzle, K-major, K = 16): element
+// (row, k) of a [rows x 16] fp16 matrix sits at byte (row/8)*256 +
+// (k/8)*128 + (row%8)*16 + (k%8)*2, i.e. 8 x 16-byte core matrices, 128 B
+// apart along K (leading-dimension offset) and 256 B apart along rows
+// (stride-dimension offset).  Writes one row.
+__device__ __forceinline__ uint32_t pack_f16x2(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);  // a in the low half
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ void store_row16(unsigned char* base, int row, const float (&w)[16]) {
+  unsigned char* p = base + (row >> 3) * 256 + (row & 7) * 16;
+  *reinterpret_cast<uint4*>(p) =
+      make_uint4(pack_f16x2(w[0], w[1]), pack_f16x2(w[2], w[3]), pack_f16x2(w[4], w[5]), pack_f16x2(w[6], w[7]));
+  *reinterpret_cast<uint4*>(p + 128) = make_uint4(pack_f16x2(w[8], w[9]), pack_f16x2(w[10], w[11]),
+                                                  pack_f16x2(w[12], w[13]), pack_f16x2(w[14], w[15]));
+}
+constexpr uint32_t kLbo16 = 128, kSbo16 = 256;
 
 // 32 consecutive fp32 columns of this thread's tensor-memory lane.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {

@@ -22,8 +22,8 @@ def test_directions_bitwise(orc, d):
     vor.close()
 
 
-def _parity(orc, X, R, seed, prec):
-    vor = Voronoi(X, precision=prec)
+def _parity(orc, X, R, seed, prec, knn_k=0):
+    vor = Voronoi(X, precision=prec, knn_k=knn_k)
     res = vor.mc_integrate(R, seed)
     ref = orc.mc_integrate(X, R, seed)
     hit, l = res.hit.cpu().numpy(), res.l.cpu().numpy()
@@ -58,6 +58,21 @@ def test_mc_parity_tensor_cases(orc, d, N, R, scale):
     need_cuda()
     X = synth.gaussian_mixture(N, d, K=8, sigma=0.03, seed=d) * scale
     vor, res, ref = _parity(orc, X, R, seed=7 + d, prec=VD_TC16)
+    res.free()
+    vor.close()
+
+
+@pytest.mark.parametrize("d,N,R,mix", [(3, 1500, 64, False), (5, 700, 32, True), (9, 400, 96, False),
+                                       (12, 300, 200, True), (16, 500, 64, True), (16, 33, 128, False)])
+def test_mc_parity_tensor_walk(orc, d, N, R, mix):
+    """Block tree walk with tensor-core ball tests and leaf screening (the
+    path of node sets without candidate lists): 1, 2 and 4 cells per ray
+    tile (R = 96 or 200, 64, 32), ragged last tiles, a set of one tile and
+    one more node."""
+    need_cuda()
+    X = synth.gaussian_mixture(N, d, K=4, sigma=0.1, seed=d) if mix else synth.uniform(N, d, seed=d)
+    vor, res, ref = _parity(orc, X, R, seed=21 + d, prec=VD_TC16, knn_k=-1)
+    assert res.stats["tiles_visited"] > 0
     res.free()
     vor.close()
 

@@ -37,32 +37,82 @@ namespace {
 
 constexpr int kWt = 128;          // threads = rays per tile = MMA M
 constexpr int kWtBuf = 8;         // candidates kept per ray
-constexpr int kWtStk = kFan * kMaxLev;  // > 1 + 31 (levels - 1): DFS stack bound
+constexpr int kGroups = 4;        // 32-row B groups (32 tensor-memory columns each) per round
+constexpr int kWtStk = kFan * kMaxLev * kGroups;  // stack bound for rounds of up to kGroups entries
 
 struct WalkSmem {
   unsigned char A16[kWt * 32];       // ray directions, fp16, K-major core matrices
-  unsigned char B16[kWt * 32];       // up to 4 x 32 rows of offsets
-  float r_lo[kWt];                   // leaf: |w|^2 lower bound; internal: |m - g|^2 lower bound
-  float r_hi[kWt];                   // leaf: |w|^2 upper bound; internal: rho (rounded up)
-  float r_wn[kWt];                   // upper bound of |w|
-  int32_t r_id[kWt];                 // leaf: node id or kNoId; internal: child index or -1
+  unsigned char B16[kWt * 32];       // kGroups x 32 rows of offsets
+  // per staged row, x = threshold, y = additive term of the test against den = u.w:
+  //   leaf (node j):  x = lower bound of |w|^2 (+inf if absent), y = error bound of den;
+  //                   t_j <= T possible iff den + y > 0 and x <= 2 T (den + y) (1 + 8u)
+  //   internal child: x = |m - g|^2 - rho^2 rounded down (+inf if absent),
+  //                   y = err(den) + rho rounded up; needed iff x <= 2 T (den + y)
+  float2 r_ae[kWt];
+  float r_hi[kWt];                   // leaf: |w|^2 upper bound; internal: |m - g|^2 (sort key)
+  int32_t r_id[kWt];                 // leaf: node id or kNoId
+  float e_w[kGroups][16];            // popped entry's own box: centre - g (binary32)
+  float e_lo[kGroups], e_rho[kGroups], e_wn[kGroups];
   int32_t cb[kWt * kWtBuf];
   float ct[kWt * kWtBuf];
   float den[kWt * 33];
   int32_t stk[kWtStk];
+  int32_t ent[kGroups];              // entries popped this round
+  uint32_t mask[kGroups];            // children wanted by any ray, per popped internal entry
   double g64[4][16];
+  float g32[4][16];
   int32_t cell[4];
 };
 
 __device__ __forceinline__ int wenc(int lev, int64_t idx) { return (lev << 27) | (int)idx; }
 
-// Stages the 32 rows of cell slot `slot` for tree node (lev, idx): offsets
-// from g of the 32 leaf nodes (lev 0) or of the 32 children's box centres.
+// Binary32 error model of the staged offsets: each component of
+// w32 = fl(x32 - g32) is within EW of the exact x - g (x32, g32 the nearest
+// binary32 of x and g), ww32 = fma chain of w32^2 within gamma_D of |w32|^2.
+struct WalkEps {
+  float gam;   // gamma_D of the fma chains
+  float EW;    // per-component absolute error of w32
+  float eabs;  // sqrt(D) EW (1.01): |u.(w32 - w)| for |u| <= 1
+  float a1, a0;  // MMA den: |den - u.w| <= a1 |w32| + a0 (a0 includes eabs)
+};
+
+// Upper bound of the exact |w|^2 from ww32.
+__device__ __forceinline__ float d2_upper(float ww, const WalkEps& ep) {
+  const float t = sqrtf(ww) * (1.f + ep.gam) + ep.eabs;
+  return t * t * (1.f + 4.f * kU32);
+}
+
+// Stages the 32 rows of group grp (cell slot `slot`) for tree node
+// (lev, idx): offsets from g of the 32 leaf nodes (lev 0) or of the 32
+// children's box centres, and the node's own box (centre offset, radius).
+// All in binary32 with directed rounding where a bound is formed.
 template <int D>
-__device__ __forceinline__ void stage_rows(const TreeView& tr, WalkSmem& S, int slot, int lane, int lev, int64_t idx,
-                                           float gam, float e1) {
+__device__ __forceinline__ void stage_rows(const TreeView& tr, WalkSmem& S, int grp, int slot, int lane, int lev,
+                                           int64_t idx, const WalkEps& ep) {
   const int d = tr.d;
-  const int row = slot * 32 + lane;
+  const int row = grp * 32 + lane;
+  {  // the node's own box, one dimension per lane
+    const int64_t bi = tr.off[lev] + idx;
+    float w = 0.f, h2 = 0.f;
+    if (lane < d) {
+      const float lo = tr.blo32[lane * tr.total + bi], hi = tr.bhi32[lane * tr.total + bi];
+      const float m = 0.5f * (lo + hi);
+      const float h = fmaxf(__fsub_ru(m, lo), __fsub_ru(hi, m));
+      h2 = __fmul_ru(h, h);
+      w = m - S.g32[slot][lane];
+    }
+    float ww = w * w;
+    for (int o = 16; o; o >>= 1) {
+      ww += __shfl_xor_sync(kFull, ww, o);
+      h2 = __fadd_ru(h2, __shfl_xor_sync(kFull, h2, o));
+    }
+    if (lane < 16) S.e_w[grp][lane] = w;
+    if (lane == 0) {
+      S.e_lo[grp] = true_d2_lower(ww, ep.gam, ep.EW, D);
+      S.e_rho[grp] = __fsqrt_ru(h2);
+      S.e_wn[grp] = sqrtf(ww) * (1.f + ep.gam);
+    }
+  }
   float w[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) w[k] = 0.f;
@@ -74,45 +124,47 @@ __device__ __forceinline__ void stage_rows(const TreeView& tr, WalkSmem& S, int 
 #pragma unroll
       for (int k = 0; k < D; ++k)
         if (k < d) {
-          w[k] = __double2float_rn(tr.x64[(idx * d + k) * kFan + lane] - S.g64[slot][k]);
+          w[k] = tr.x32[(idx * d + k) * kFan + lane] - S.g32[slot][k];
           ww = fmaf(w[k], w[k], ww);
         }
-      S.r_lo[row] = ww * (1.f - e1);
-      S.r_hi[row] = ww * (1.f + e1);
-      S.r_wn[row] = sqrtf(ww) * (1.f + gam);
+      S.r_ae[row] = make_float2(true_d2_lower(ww, ep.gam, ep.EW, D), fmaf(ep.a1, sqrtf(ww) * (1.f + ep.gam), ep.a0));
+      S.r_hi[row] = d2_upper(ww, ep);
       S.r_id[row] = id;
     } else {
+      S.r_ae[row] = make_float2(INFINITY, 1.f);
       S.r_id[row] = kNoId;
     }
   } else {
     const int64_t c = idx * kFan + lane;
     if (cell != kNoId && c < tr.cnt[lev - 1]) {
       const int64_t bi = tr.off[lev - 1] + c;
-      float ww = 0.f;
-      double r2 = 0.0;
+      float ww = 0.f, r2 = 0.f;
 #pragma unroll
       for (int k = 0; k < D; ++k)
         if (k < d) {
-          const double lo = tr.blo64[k * tr.total + bi], hi = tr.bhi64[k * tr.total + bi];
-          const double m = 0.5 * (lo + hi);
-          const double h = fmax(m - lo, hi - m);
-          r2 = fma(h, h, r2);
-          w[k] = __double2float_rn(m - S.g64[slot][k]);
+          const float lo = tr.blo32[k * tr.total + bi], hi = tr.bhi32[k * tr.total + bi];
+          const float m = 0.5f * (lo + hi);
+          const float h = fmaxf(__fsub_ru(m, lo), __fsub_ru(hi, m));
+          r2 = __fmaf_ru(h, h, r2);
+          w[k] = m - S.g32[slot][k];
           ww = fmaf(w[k], w[k], ww);
         }
-      S.r_lo[row] = ww * (1.f - e1);
-      S.r_hi[row] = __double2float_ru(sqrt(r2) * (1.0 + 1e-14));
-      S.r_wn[row] = sqrtf(ww) * (1.f + gam);
-      S.r_id[row] = (int32_t)c;
+      const float d2lo = true_d2_lower(ww, ep.gam, ep.EW, D);
+      const float rho = __fsqrt_ru(r2);
+      const float err = fmaf(ep.a1, sqrtf(ww) * (1.f + ep.gam), ep.a0);
+      // |u| <= 1 + 2^-40 after the binary64 normalisation
+      S.r_ae[row] = make_float2(__fsub_rd(d2lo, __fmul_ru(rho, rho)), __fadd_ru(err, __fmul_ru(rho, 1.0000001f)));
+      S.r_hi[row] = d2lo;
     } else {
-      S.r_id[row] = -1;
+      S.r_ae[row] = make_float2(INFINITY, 0.f);
+      S.r_hi[row] = INFINITY;
     }
   }
   tc::store_row16(S.B16, row, w);
 }
 
 template <int D>
-__global__ void __launch_bounds__(kWt) k_mc_walk_tc(TreeView tr, int64_t R, int cpt, uint64_t seed, uint32_t set,
+__global__ void __launch_bounds__(kWt, 4) k_mc_walk_tc(TreeView tr, int64_t R, int cpt, uint64_t seed, uint32_t set,
                                                     RayOut ro, Counters* ctr, unsigned long long* work,
                                                     int32_t* fb_cell, int32_t* fb_ray, int64_t fb_cap,
                                                     long long wait_limit) {
@@ -122,18 +174,25 @@ __global__ void __launch_bounds__(kWt) k_mc_walk_tc(TreeView tr, int64_t R, int 
   __shared__ uint32_t tmem_base;
   __shared__ int64_t s_item;
   __shared__ int s_sp;
-  __shared__ uint32_t s_mask;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int d = tr.d;
-  const float gam = (float)(D + 1) * kU32 * 1.01f;
-  const float e1 = 1.1f * (gam + 2.1f * kU32);
-  const TcBound eb = tc_bound(D);
+  WalkEps ep;
+  ep.gam = (float)(D + 1) * kU32 * 1.01f;
+  ep.EW = 4.01f * kU32 * tr.coord_abs;
+  ep.eabs = sqrtf((float)D) * ep.EW * 1.01f;
+  const float gam = ep.gam;
+  {
+    const TcBound eb = tc_bound(D);
+    ep.a1 = eb.a1;
+    ep.a0 = eb.a0 + ep.eabs;
+  }
   const int Rt = cpt > 1 ? (int)R : kWt;               // rays of one cell in a tile
   const int64_t tpc = cpt > 1 ? 1 : (R + kWt - 1) / kWt;  // tiles per cell
   const int64_t nitems = cpt > 1 ? (tr.N + cpt - 1) / cpt : tr.N * tpc;
   const int slot = tid / Rt;
-  const uint32_t ncols = 32u * (uint32_t)cpt;
-  const uint32_t idesc = tc::idesc_f16_f32(kWt, 32 * cpt);
+  const int P = kGroups / cpt;  // entries per round
+  const uint32_t ncols = 32u * kGroups;
+  const float a1f = 1.1f * (gam + 2.1f * kU32);  // binary32 dot product of u and w: error <= a1f |w|
   int32_t* cb = S.cb + tid * kWtBuf;
   float* ct = S.ct + tid * kWtBuf;
   float* sden = S.den + tid * 33;
@@ -142,16 +201,14 @@ __global__ void __launch_bounds__(kWt) k_mc_walk_tc(TreeView tr, int64_t R, int 
     tc::tmem_alloc(&tmem_base, ncols);
     tc::tmem_relinquish();
   }
-  if (tid == 0) {
-    tc::mbar_init(&mbar, 1);
-    s_mask = 0;
-  }
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  if (tid < kGroups) S.mask[tid] = 0;
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = tmem_base;
-  const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(slot * 32);
+  const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16);
   const uint64_t adesc = tc::smem_desc(S.A16, tc::kLbo16, tc::kSbo16);
   const uint64_t bdesc = tc::smem_desc(S.B16, tc::kLbo16, tc::kSbo16);
   uint32_t phase = 0;
@@ -169,7 +226,9 @@ __global__ void __launch_bounds__(kWt) k_mc_walk_tc(TreeView tr, int64_t R, int 
       const int s = tid >> 4, k = tid & 15;
       const int64_t q = q0 + s;
       const int32_t c = q < tr.N ? tr.ids[q] : kNoId;
-      S.g64[s][k] = (c != kNoId && k < d) ? tr.X[(int64_t)c * d + k] : 0.0;
+      const double gk = (c != kNoId && k < d) ? tr.X[(int64_t)c * d + k] : 0.0;
+      S.g64[s][k] = gk;
+      S.g32[s][k] = __double2float_rn(gk);
       if (k == 0) S.cell[s] = c;
     }
     if (tid == 0) {
@@ -186,7 +245,7 @@ __global__ void __launch_bounds__(kWt) k_mc_walk_tc(TreeView tr, int64_t R, int 
 #pragma unroll
     for (int q = 0; q < D; ++q) {
       u64[q] = 0.0;
-      g32[q] = __double2float_rn(S.g64[slot][q < 16 ? q : 0]);
+      g32[q] = S.g32[slot][q];
     }
     if (valid) mc_direction<D>(seed, set, (uint32_t)cell, (uint32_t)k, d, u64);
 #pragma unroll
@@ -201,21 +260,23 @@ __global__ void __launch_bounds__(kWt) k_mc_walk_tc(TreeView tr, int64_t R, int 
     int nc = 0;
     bool overflow = false;
     if (valid) T = mc_faces<D>(u64, u32, g32, d, cb, ct, nc, kWtBuf, overflow);
-    // ---- block walk ----
+    // ---- block walk: each round pops up to P entries ----
     while (true) {
       const int sp = s_sp;
       if (sp == 0) break;
-      const int e = S.stk[sp - 1];
-      const int lev = e >> 27;
-      const int64_t idx = e & ((1 << 27) - 1);
-      if (warp < cpt) stage_rows<D>(tr, S, warp, lane, lev, idx, gam, e1);
+      const int np = min(P, sp);
+      if (warp < np * cpt) {
+        const int e = S.stk[sp - 1 - warp / cpt];
+        if (lane == 0 && warp % cpt == 0) S.ent[warp / cpt] = e;
+        stage_rows<D>(tr, S, warp, warp % cpt, lane, e >> 27, e & ((1 << 27) - 1), ep);
+      }
       tc::fence_proxy_async();
       tc::fence_before_sync();
-      __syncthreads();  // rows staged; everyone has read the stack top
+      __syncthreads();  // rows staged; everyone has read the stack
       if (tid == 0) {
-        s_sp = sp - 1;
+        s_sp = sp - np;
         tc::fence_after_sync();
-        tc::mma_f16(tbase, adesc, bdesc, idesc, 0u);
+        tc::mma_f16(tbase, adesc, bdesc, tc::idesc_f16_f32(kWt, 32 * np * cpt), 0u);
         tc::mma_commit(&mbar);
       }
       const bool ok = tc::mbar_wait(&mbar, phase, wait_limit);
@@ -226,73 +287,94 @@ __global__ void __launch_bounds__(kWt) k_mc_walk_tc(TreeView tr, int64_t R, int 
       }
       tc::fence_after_sync();
       __syncwarp();
-      {
+      for (int p = 0; p < np; ++p) {
+        const int grp = p * cpt + slot;
+        const int r0 = grp * 32;
+        const int e = S.ent[p];
         float v[32];
-        tc::tmem_ld32(taddr, v);
+        tc::tmem_ld32(taddr + (uint32_t)(grp * 32), v);
+        // does this ray still need the entry?  ball of T around g + T u
+        // against the sphere of the entry's own box, binary32 dot product
+        bool need = valid;
+        if (need) {
+          float sdot = 0.f;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) sden[j] = v[j];
-      }
-      const int r0 = slot * 32;
-      if (lev == 0) {
-        if (valid) {
-          ++n_tiles;
-          n_pairs += 32;
-#pragma unroll 1
-          for (int j = 0; j < 32; ++j) {
-            const int32_t id = S.r_id[r0 + j];
-            if (id == kNoId) continue;
-            const float dj = sden[j];
-            const float e = fmaf(eb.a1, S.r_wn[r0 + j], eb.a0);
-            const float dh = dj + e;
-            const float nlo = S.r_lo[r0 + j];
-            if (!(dh > 0.f) || nlo > 2.f * T * dh * (1.f + 8.f * kU32)) continue;
-            const float dl = dj - e;
-            const float thi = dl > 0.f ? __fdiv_rn(S.r_hi[r0 + j], 2.f * dl) * (1.f + 4.f * kU32) : INFINITY;
-            const float tlo = __fdiv_rn(nlo, 2.f * dh) * (1.f - 4.f * kU32);
-            if (thi < T) T = thi;
-            if (!overflow) overflow = !mc_push(id, tlo, T, cb, ct, nc, kWtBuf);
-          }
+          for (int q = 0; q < D; ++q) sdot = fmaf(u32[q], S.e_w[grp][q], sdot);
+          const float rho = S.e_rho[grp];
+          const float qv = __fadd_ru(__fadd_ru(sdot, fmaf(a1f, S.e_wn[grp], ep.eabs)), __fmul_ru(rho, 1.0000001f));
+          const float lhs = __fsub_rd(S.e_lo[grp], __fmul_ru(rho, rho));
+          need = !(lhs > __fmul_ru(2.f * T, qv));
         }
-      } else {
-        uint32_t m = 0;
-        if (valid) {
-          const float T2 = 2.f * T;
-#pragma unroll 1
-          for (int j = 0; j < 32; ++j) {
-            if (S.r_id[r0 + j] < 0) continue;
-            const float rho = S.r_hi[r0 + j];
-            const float e = fmaf(eb.a1, S.r_wn[r0 + j], eb.a0);
-            // |u| <= 1 + 2^-40 after the binary64 normalisation
-            const float q = __fadd_ru(__fadd_ru(sden[j], e), __fmul_ru(rho, 1.0000001f));
-            const float lhs = __fsub_rd(S.r_lo[r0 + j], __fmul_ru(rho, rho));
-            if (!(lhs > __fmul_ru(T2, q))) m |= 1u << j;
+        if ((e >> 27) == 0) {
+          uint32_t pass = 0;
+          if (need) {
+            ++n_tiles;
+            n_pairs += 32;
+            const float T2u = 2.f * T * (1.f + 10.f * kU32);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float2 ae = S.r_ae[r0 + j];
+              const float dh = v[j] + ae.y;
+              if (dh > 0.f && !(ae.x > T2u * dh)) pass |= 1u << j;
+            }
           }
+          if (pass) {  // rare: exact interval test with the current bound
+#pragma unroll
+            for (int j = 0; j < 32; ++j) sden[j] = v[j];
+            while (pass) {
+              const int j = __ffs(pass) - 1;
+              pass &= pass - 1;
+              const float2 ae = S.r_ae[r0 + j];
+              const float dj = sden[j];
+              const float dh = dj + ae.y;
+              if (ae.x > 2.f * T * dh * (1.f + 8.f * kU32)) continue;
+              const float dl = dj - ae.y;
+              const float thi = dl > 0.f ? __fdiv_rn(S.r_hi[r0 + j], 2.f * dl) * (1.f + 4.f * kU32) : INFINITY;
+              const float tlo = __fdiv_rn(ae.x, 2.f * dh) * (1.f - 4.f * kU32);
+              if (thi < T) T = thi;
+              if (!overflow) overflow = !mc_push(S.r_id[r0 + j], tlo, T, cb, ct, nc, kWtBuf);
+            }
+          }
+        } else {
+          uint32_t m = 0;
+          if (need) {
+            const float T2 = 2.f * T;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float2 ae = S.r_ae[r0 + j];
+              if (!(ae.x > __fmul_ru(T2, __fadd_ru(v[j], ae.y)))) m |= 1u << j;
+            }
+          }
+          m = __reduce_or_sync(kFull, m);
+          if (lane == 0 && m) atomicOr(&S.mask[p], m);
         }
-        m = __reduce_or_sync(kFull, m);
-        if (lane == 0 && m) atomicOr(&s_mask, m);
       }
       tc::fence_before_sync();
       __syncthreads();
-      if (lev > 0) {
-        if (warp == 0) {
-          const uint32_t m = s_mask;
-          // nearest child (to the first cell of the tile) on top
-          float key = (m >> lane) & 1u ? S.r_lo[lane] : INFINITY;
+      if (warp == 0) {
+        // children of the popped internal entries, the first entry's on top,
+        // each entry's children nearest (to the tile's first cell) on top
+        for (int p = np - 1; p >= 0; --p) {
+          const int e = S.ent[p];
+          if ((e >> 27) == 0) continue;
+          const uint32_t m = S.mask[p];
+          float key = (m >> lane) & 1u ? S.r_hi[p * cpt * 32 + lane] : INFINITY;
           int val = lane;
           warp_sort(key, val);
           const int n = __popc(m);
           const int base = s_sp;
           if (lane < n && base + n - 1 - lane < kWtStk)
-            S.stk[base + n - 1 - lane] = wenc(lev - 1, idx * kFan + val);
+            S.stk[base + n - 1 - lane] = wenc((e >> 27) - 1, (int64_t)(e & ((1 << 27) - 1)) * kFan + val);
           __syncwarp();
           if (lane == 0) {
             if (base + n > kWtStk) atomicOr(&ctr->flags, kFlagStack);
             s_sp = min(base + n, kWtStk);
-            s_mask = 0;
+            S.mask[p] = 0;
           }
+          __syncwarp();
         }
-        __syncthreads();
       }
+      __syncthreads();
     }
     if (timed_out) break;
     if (valid) {
@@ -305,10 +387,11 @@ __global__ void __launch_bounds__(kWt) k_mc_walk_tc(TreeView tr, int64_t R, int 
           atomicOr(&ctr->flags, kFlagQueue);
         }
       } else {
-        double g64[D];
+        double g64[D], uu[D];
 #pragma unroll
         for (int q = 0; q < D; ++q) g64[q] = q < d ? S.g64[slot][q] : 0.0;
-        mc_recheck<D>(tr.X, d, g64, u64, cb, ct, nc, T, ro.hit[(int64_t)cell * R + k],
+        mc_direction<D>(seed, set, (uint32_t)cell, (uint32_t)k, d, uu);  // drawn again: same bits
+        mc_recheck<D>(tr.X, d, g64, uu, cb, ct, nc, T, ro.hit[(int64_t)cell * R + k],
                       ro.t[(int64_t)cell * R + k], n_rech);
       }
     }
@@ -357,7 +440,7 @@ cudaError_t launch_walk_d(const TreeView& tv, int64_t R, int cpt, uint64_t seed,
   const int by_regs = regs_sm / std::max(1, regs_warp * warps);
   const int by_smem = (int)(smem_sm / (sm + fa.sharedSizeBytes + 1024));
   const int by_thr = thr_sm / kWt;
-  const int by_tmem = 16 / cpt;
+  const int by_tmem = 512 / (32 * kGroups);
   const int occ = std::max(1, std::min(std::min(by_regs, by_smem), std::min(by_thr, by_tmem)));
   const int64_t nitems = cpt > 1 ? (tv.N + cpt - 1) / cpt : tv.N * ((R + kWt - 1) / kWt);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * occ, nitems));

@@ -7,6 +7,12 @@ recheck.  The metric is raycasts per second of that traversal; the same
 workload on the plain binary64 path is timed beside it, and its vertex
 tuples must equal the screened path's bit for bit.
 
+Secondary lines in the same JSON object: "mc" (MC volumes + areas + adjoint,
+d=4, N=100,000, 1024 rays per cell; binary32-screened, tensor-core screened
+and binary64 paths) and "highd" (the same at d=16, N=200,000 mixture nodes,
+64 rays per cell; tensor-core walk vs binary32 tree walk).  --only-batch
+times the batched MC workload (512 point sets).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 With --gpus N > 1 (launched by torchrun) every rank runs an independent
@@ -246,6 +252,9 @@ def run_ours(args):
     if args.only_mc:  # the MC secondary measurement alone (profiling)
         print(json.dumps({"mc": run_mc(args, vd, torch.cuda.current_stream())}), flush=True)
         return
+    if args.only_highd:
+        print(json.dumps({"highd": run_highd(args, vd, torch.cuda.current_stream())}), flush=True)
+        return
     if args.only_batch:
         print(json.dumps({"batch": run_batch(args, vd, torch.cuda.current_stream())}), flush=True)
         return
@@ -361,6 +370,9 @@ def run_ours(args):
     mc = None
     if not args.no_mc:
         mc = run_mc(args, vd, stream)
+    highd = None
+    if not args.no_highd:
+        highd = run_highd(args, vd, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -388,7 +400,7 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": "raycasts/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "mc": mc}
+                "mc": mc, "highd": highd}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -450,6 +462,61 @@ def run_mc(args, vd, stream):
     return out
 
 
+HIGHD_WORKLOAD = ("MC volumes + interface areas + adjoint, d=16, N=200000 from a 32-component Gaussian mixture "
+                  "(centres U[0,1]^16, sigma 0.1, redrawn outside the cube; seed 0), 64 rays per cell")
+
+
+def run_highd(args, vd, stream):
+    """MC vol+grad cells/s on the high-dimensional workload: tensor-core walk
+    (tcgen05 ball tests and leaf screening) vs the binary32 tree walk, same
+    seeded directions, identical per-ray hits required."""
+    import torch
+    from paper_2405_10050_gb300 import VD_FP32, VD_FP64, VD_TC16, synth
+    N, d, R = args.highd_n, 16, 64
+    X = torch.tensor(synth.gaussian_mixture(N, d, K=32, sigma=0.1, seed=0), device="cuda")
+    gV = torch.ones(N, dtype=torch.float64, device="cuda")
+    out = {"workload": HIGHD_WORKLOAD.replace("200000", str(N)), "unit": "cells/s"}
+    legs = [("tensor", VD_TC16), ("mixed", VD_FP32)] + ([("fp64", VD_FP64)] if args.highd_fp64 else [])
+    hits = {}
+    for name, prec in legs:
+        cfg = vd.vd_config_default()
+        cfg.precision = prec
+        ctx = vd.vd_create(cfg, stream.cuda_stream)
+        gX = torch.empty((N, d), dtype=torch.float64, device="cuda")
+
+        def step():
+            vd.vd_set_nodes(ctx, X)
+            m = vd.vd_mc_integrate(ctx, R, 5)
+            nnz = vd.vd_mc_get(m)
+            gA = torch.ones(max(nnz, 1), dtype=torch.float64, device="cuda")
+            vd.vd_mc_adjoint(m, gV, gA[:nnz], gX)
+            return m
+
+        vd.vd_mc_free(step())
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = vd.vd_mc_stats(m)
+        h = torch.empty((N, R), dtype=torch.int32, device="cuda")
+        vd.vd_mc_rays(m, h, None)
+        hits[name] = h
+        vd.vd_mc_free(m)
+        vd.vd_destroy(ctx)
+        out[name] = {"cells_per_s": N / (ms / 1000.0), "rays_per_s": N * R / (ms / 1000.0), "ms_per_step": ms,
+                     "raycast_ms": st["raycast_ms"], "tile_visits_per_ray": st["tiles_visited"] / max(st["rays"], 1),
+                     "tree_walk_rays": st["fallback_rays"]}
+    out["value"] = out["tensor"]["cells_per_s"]
+    out["speedup_vs_mixed"] = out["tensor"]["cells_per_s"] / out["mixed"]["cells_per_s"]
+    if "fp64" in out:
+        out["speedup_vs_fp64"] = out["tensor"]["cells_per_s"] / out["fp64"]["cells_per_s"]
+    out["hits_identical"] = all(bool(torch.equal(hits[a], hits["tensor"])) for a in hits)
+    return out
+
+
 BATCH_WORKLOAD = ("batched MC volumes + areas + adjoint: 512 sets, N log-uniform in [200, 20000], d uniform in "
                   "{2..8}, half uniform, half 8-component Gaussian mixtures (sigma 0.05), 256 rays per cell")
 
@@ -508,6 +575,10 @@ def main():
     ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--only-mc", action="store_true")
     ap.add_argument("--only-batch", action="store_true")
+    ap.add_argument("--no-highd", action="store_true")
+    ap.add_argument("--only-highd", action="store_true")
+    ap.add_argument("--highd-fp64", action="store_true", help="also time the binary64 path (about 25 s)")
+    ap.add_argument("--highd-n", type=int, default=200000)
     ap.add_argument("--batch-sets", type=int, default=512)
     ap.add_argument("--batch-rays", type=int, default=256)
     ap.add_argument("--mc-n", type=int, default=100000)

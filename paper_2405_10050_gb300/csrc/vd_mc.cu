@@ -9,7 +9,11 @@
 //   a_k  = l^{d-1} / |u_a|                               (face on axis a)
 // The reductions are deterministic: a warp owns a cell, visits the distinct
 // hit ids of the row in ascending order and sums each one's terms with a
-// fixed lane-strided order and butterfly.
+// fixed lane-strided order and butterfly.  When the row has few rays per hit
+// id (nnz > R / 8, e.g. high d), the warp instead computes the terms of 32
+// rays at a time, one per lane, and adds them to their entries in ascending
+// ray order (lanes split the components of the adjoint's vectors); which of
+// the two orders a row uses depends only on (nnz, R).
 //
 // Adjoint (directions and argmins held fixed): for a node hit
 //   dl/dx_j = (w - l u) / (u.w) = -dl/dx_i,
@@ -53,6 +57,20 @@ __device__ __forceinline__ int32_t next_id(const int32_t* h, int64_t R, int32_t 
   for (int o = 16; o; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o));
   return best;
 }
+
+// position of hit id in the row's ascending ids col[q0 .. q0 + n)
+__device__ __forceinline__ int64_t entry_of(const int32_t* col, int64_t q0, int64_t n, int32_t id) {
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    if (col[q0 + mid] < id) lo = mid + 1;
+    else hi = mid;
+  }
+  return q0 + lo;
+}
+
+// rows with nnz * kFewRays > R take the ray-parallel order
+constexpr int kFewRays = 8;
 
 template <int D>
 __device__ __forceinline__ double node_area_term(const double* X, int d, int64_t i, int32_t j, double ld) {
@@ -131,10 +149,25 @@ __device__ __forceinline__ int gather_rays(const int32_t* h, int64_t R, int32_t 
   return m;
 }
 
+// Area term of ray k of cell i that hit id.
+template <int D>
+__device__ __forceinline__ double area_term(const double* X, int d, int64_t i, int64_t k, int32_t id, double lk,
+                                            uint64_t seed, uint32_t set) {
+  if (id >= 0) return node_area_term<D>(X, d, i, id, ipow_d(lk, d));
+  double u[D];
+  mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
+  const int a = face_axis(id);
+  double ua = 0.0;
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+    if (c == a) ua = u[c];
+  return __ddiv_rn(ipow_d(lk, d - 1), fabs(ua));
+}
+
 template <int D>
 __device__ void fill_item(const double* X, int d, int64_t i, int64_t R, uint64_t seed, uint32_t set,
                           const int32_t* hit, const double* l, const int64_t* rowptr, double cV, double cA, double* V,
-                          int32_t* col, double* A, int32_t* L, int lane) {
+                          int32_t* col, double* A, int32_t* L, double* Ts, int32_t* Es, int lane) {
   const int32_t* h = hit + i * R;
   const double* li = l + i * R;
   double vs = 0.0;
@@ -144,6 +177,35 @@ __device__ void fill_item(const double* X, int d, int64_t i, int64_t R, uint64_t
   int64_t q = rowptr[i];
   int32_t prev = 0;
   bool first = true;
+  const int64_t q0 = q, nnz = rowptr[i + 1] - q0;
+  if (nnz * kFewRays > R) {  // few rays per id: terms ray-parallel, sums in ascending ray order
+    while (true) {
+      const int32_t id = next_id(h, R, prev, first, lane);
+      if (id == INT32_MAX) break;
+      if (lane == 0) {
+        col[q] = id;
+        A[q] = 0.0;
+      }
+      ++q;
+      prev = id;
+      first = false;
+    }
+    __syncwarp();
+    for (int64_t k0 = 0; k0 < R; k0 += 32) {
+      const int64_t k = k0 + lane;
+      if (k < R) {
+        const int32_t id = h[k];
+        Es[lane] = (int32_t)(entry_of(col, q0, nnz, id) - q0);
+        Ts[lane] = area_term<D>(X, d, i, k, id, li[k], seed, set);
+      }
+      __syncwarp();
+      if (lane == 0)
+        for (int r = 0; r < 32 && k0 + r < R; ++r) A[q0 + Es[r]] = __dadd_rn(A[q0 + Es[r]], Ts[r]);
+      __syncwarp();
+    }
+    for (int64_t e = q0 + lane; e < q0 + nnz; e += 32) A[e] = __dmul_rn(cA, A[e]);
+    return;
+  }
   while (true) {
     const int32_t id = next_id(h, R, prev, first, lane);
     if (id == INT32_MAX) break;
@@ -153,21 +215,7 @@ __device__ void fill_item(const double* X, int d, int64_t i, int64_t R, uint64_t
       const int m = gather_rays(h, R, id, &k0, L, lane);
       for (int p = lane; p < m; p += 32) {
         const int32_t k = L[p];
-        const double lk = li[k];
-        double term;
-        if (id >= 0) {
-          term = node_area_term<D>(X, d, i, id, ipow_d(lk, d));
-        } else {
-          double u[D];
-          mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
-          const int a = face_axis(id);
-          double ua = 0.0;
-#pragma unroll
-          for (int c = 0; c < D; ++c)
-            if (c == a) ua = u[c];
-          term = __ddiv_rn(ipow_d(lk, d - 1), fabs(ua));
-        }
-        s = __dadd_rn(s, term);
+        s = __dadd_rn(s, area_term<D>(X, d, i, k, id, li[k], seed, set));
       }
       __syncwarp();
     }
@@ -188,10 +236,13 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill(const double* X, int6
                                                            const double* l, const int64_t* rowptr, double cV,
                                                            double cA, double* V, int32_t* col, double* A) {
   __shared__ int32_t Ls[kMcWarps][kMcList];
+  __shared__ double Ts[kMcWarps][32];
+  __shared__ int32_t Es[kMcWarps][32];
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= N) return;
-  fill_item<D>(X, d, i, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, Ls[threadIdx.x >> 5], lane);
+  const int w = threadIdx.x >> 5;
+  fill_item<D>(X, d, i, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, Ls[w], Ts[w], Es[w], lane);
 }
 
 // ---- batched reduction over many sets (items = all cells of all sets) ----
@@ -253,16 +304,21 @@ __global__ void k_scan_batch(const SetDesc* sets) {
 __global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill_batch(const SetDesc* sets, int nsets, int64_t nitems,
                                                                  int64_t R, uint64_t seed) {
   __shared__ int32_t Ls[kMcWarps][kMcList];
+  __shared__ double Tss[kMcWarps][32];
+  __shared__ int32_t Ess[kMcWarps][32];
   const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (item >= nitems) return;
   const SetDesc& S = sets[find_set(sets, nsets, item)];
   const int64_t i = item - S.item0;
   int32_t* L = Ls[threadIdx.x >> 5];
+  double* Ts = Tss[threadIdx.x >> 5];
+  int32_t* Es = Ess[threadIdx.x >> 5];
   switch (S.tv.d) {
 #define VD_FILL(DD)                                                                                              \
   case DD:                                                                                                       \
-    fill_item<DD>(S.tv.X, S.tv.d, i, R, seed, S.set, S.hit, S.l, S.rowptr, S.cV, S.cA, S.V, S.col, S.A, L, lane); \
+    fill_item<DD>(S.tv.X, S.tv.d, i, R, seed, S.set, S.hit, S.l, S.rowptr, S.cV, S.cA, S.V, S.col, S.A, L, Ts, Es, \
+                  lane);                                                                                        \
     break;
     VD_FILL(1)
     VD_FILL(2)
@@ -271,15 +327,63 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill_batch(const SetDesc* 
     VD_FILL(5)
     VD_FILL(6)
     default:
-      fill_item<8>(S.tv.X, S.tv.d, i, R, seed, S.set, S.hit, S.l, S.rowptr, S.cV, S.cA, S.V, S.col, S.A, L, lane);
+      fill_item<8>(S.tv.X, S.tv.d, i, R, seed, S.set, S.hit, S.l, S.rowptr, S.cV, S.cA, S.V, S.col, S.A, L, Ts, Es,
+                   lane);
       break;
 #undef VD_FILL
   }
 }
 
+// Adds to acc the contribution of ray k of cell i (hit id, length lk) to
+// dLoss/dx: for a node hit the vector along w (the row entry's P), for a face
+// hit the component on the face's axis (x_i's own term).
+template <int D>
+__device__ __forceinline__ void adj_contrib(const double* X, int d, int64_t i, int64_t k, int32_t id, double lk,
+                                            double gVi, double gAij, double cV, double cA, uint64_t seed,
+                                            uint32_t set, double (&acc)[D]) {
+  double u[D];
+  mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
+  const double ld1 = ipow_d(lk, d - 1), ld = ipow_d(lk, d);
+  if (id >= 0) {
+    double w[D], den = 0.0, ww = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) w[c] = c < d ? __dadd_rn(X[(int64_t)id * d + c], -X[i * d + c]) : 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      if (c < d) den = __dadd_rn(den, __dmul_rn(u[c], w[c]));
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      if (c < d) ww = __dadd_rn(ww, __dmul_rn(w[c], w[c]));
+    const double inw = rsqrt(ww);
+    const double iden = 1.0 / den;
+    const double c1 = 2.0 * (double)d * ld1 * inw, c2 = 2.0 * ld * inw * inw * inw;
+    const double kV = gVi * cV * (double)d * ld1, kA = gAij * cA;
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      if (c < d) {
+        const double dl = (w[c] - lk * u[c]) * iden;
+        acc[c] += kV * dl + kA * (c1 * dl - c2 * w[c]);
+      }
+  } else {
+    const int a = face_axis(id);
+    double ua = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      if (c == a) ua = u[c];
+    const double dl = -1.0 / ua;
+    const double dadl = (d >= 2) ? (double)(d - 1) * ipow_d(lk, d - 2) / fabs(ua) : 0.0;
+    const double G = gVi * cV * (double)d * ld1 * dl + gAij * cA * dadl * dl;
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      if (c == a) acc[c] += G;
+  }
+}
+
 // Row pass of the adjoint: P[q][*] = sum over the rays of cell i that hit
 // col[q] of dLoss/dw (node) ; own[i][*] = face terms of x_i.  The rays of a
-// column are gathered first so the binary64 work runs on full warps.
+// column are gathered first so the binary64 work runs on full warps; rows
+// with few rays per entry compute 32 rays at once and add them per entry in
+// ascending ray order, the lanes splitting the components.
 template <int D>
 __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, int64_t N, int d, int64_t R,
                                                                uint64_t seed, uint32_t set, const int32_t* hit,
@@ -288,17 +392,59 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
                                                                const double* gV, const double* gA, double* P,
                                                                double* own) {
   __shared__ int32_t Ls[kMcWarps][kMcList];
+  __shared__ double Cs[kMcWarps][32][D + 1];
+  __shared__ int32_t Es[kMcWarps][32];
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= N) return;
-  int32_t* L = Ls[threadIdx.x >> 5];
+  const int wb = threadIdx.x >> 5;
+  int32_t* L = Ls[wb];
   const int32_t* h = hit + i * R;
   const double* li = l + i * R;
   const double gVi = gV[i];
+  const int64_t q0 = rowptr[i], nnz = rowptr[i + 1] - q0;
+  if (nnz * kFewRays > R) {
+    for (int64_t e = lane; e < nnz * d; e += 32) P[q0 * d + e] = 0.0;
+    __syncwarp();
+    for (int64_t k0 = 0; k0 < R; k0 += 32) {
+      const int64_t k = k0 + lane;
+      if (k < R) {
+        const int32_t id = h[k];
+        const int64_t q = entry_of(col, q0, nnz, id);
+        double v[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) v[c] = 0.0;
+        adj_contrib<D>(X, d, i, k, id, li[k], gVi, gA ? gA[q] : 0.0, cV, cA, seed, set, v);
+#pragma unroll
+        for (int c = 0; c < D; ++c) Cs[wb][lane][c] = v[c];
+        Es[wb][lane] = (int32_t)(q - q0);
+      }
+      __syncwarp();
+      if (lane < d)
+        for (int r = 0; r < 32 && k0 + r < R; ++r) {
+          double* pe = P + (q0 + Es[wb][r]) * d + lane;
+          *pe += Cs[wb][r][lane];
+        }
+      __syncwarp();
+    }
+    if (lane < d) {  // x_i's own term: minus its node entries, plus its face entries, in entry order
+      double o = 0.0;
+      for (int64_t e = 0; e < nnz; ++e) {
+        const double v = P[(q0 + e) * d + lane];
+        o = col[q0 + e] >= 0 ? o - v : o + v;
+      }
+      own[i * d + lane] = o;
+    }
+    __syncwarp();
+    for (int64_t e = lane; e < nnz; e += 32)
+      if (col[q0 + e] < 0)
+        for (int c = 0; c < d; ++c) P[(q0 + e) * d + c] = 0.0;
+    return;
+  }
   double faceacc[D];
 #pragma unroll
   for (int c = 0; c < D; ++c) faceacc[c] = 0.0;
-  for (int64_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+  for (int64_t q = q0; q < q0 + nnz; ++q) {
     const int32_t id = col[q];
     const double gAij = gA ? gA[q] : 0.0;
     double acc[D];
@@ -309,43 +455,7 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
       const int m = gather_rays(h, R, id, &k0, L, lane);
       for (int p = lane; p < m; p += 32) {
         const int32_t k = L[p];
-        double u[D];
-        mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
-        const double lk = li[k];
-        const double ld1 = ipow_d(lk, d - 1), ld = ipow_d(lk, d);
-        if (id >= 0) {
-          double w[D], den = 0.0, ww = 0.0;
-#pragma unroll
-          for (int c = 0; c < D; ++c) w[c] = c < d ? __dadd_rn(X[(int64_t)id * d + c], -X[i * d + c]) : 0.0;
-#pragma unroll
-          for (int c = 0; c < D; ++c)
-            if (c < d) den = __dadd_rn(den, __dmul_rn(u[c], w[c]));
-#pragma unroll
-          for (int c = 0; c < D; ++c)
-            if (c < d) ww = __dadd_rn(ww, __dmul_rn(w[c], w[c]));
-          const double inw = rsqrt(ww);
-          const double iden = 1.0 / den;
-          const double c1 = 2.0 * (double)d * ld1 * inw, c2 = 2.0 * ld * inw * inw * inw;
-          const double kV = gVi * cV * (double)d * ld1, kA = gAij * cA;
-#pragma unroll
-          for (int c = 0; c < D; ++c)
-            if (c < d) {
-              const double dl = (w[c] - lk * u[c]) * iden;
-              acc[c] += kV * dl + kA * (c1 * dl - c2 * w[c]);
-            }
-        } else {
-          const int a = face_axis(id);
-          double ua = 0.0;
-#pragma unroll
-          for (int c = 0; c < D; ++c)
-            if (c == a) ua = u[c];
-          const double dl = -1.0 / ua;
-          const double dadl = (d >= 2) ? (double)(d - 1) * ipow_d(lk, d - 2) / fabs(ua) : 0.0;
-          const double G = gVi * cV * (double)d * ld1 * dl + gAij * cA * dadl * dl;
-#pragma unroll
-          for (int c = 0; c < D; ++c)
-            if (c == a) acc[c] += G;
-        }
+        adj_contrib<D>(X, d, i, k, id, li[k], gVi, gAij, cV, cA, seed, set, acc);
       }
       __syncwarp();
     }

@@ -77,10 +77,12 @@ def test_mc_parity_tensor_walk(orc, d, N, R, mix):
     vor.close()
 
 
-@pytest.mark.parametrize("d", [2, 3, 4])
-def test_adjoint_parity(orc, d):
+@pytest.mark.parametrize("d,N,R", [(2, 300, 32), (3, 300, 32), (4, 300, 32), (2, 200, 512), (3, 150, 256),
+                                   (9, 120, 16)])
+def test_adjoint_parity(orc, d, N, R):
+    """Rows with many rays per hit id (R = 256, 512: rays gathered per id) and
+    rows with few (R = 16, 32: 32 rays at a time, summed per entry)."""
     torch = need_cuda()
-    N, R = 300, 32
     X = synth.uniform(N, d, seed=50 + d)
     vor, res, ref = _parity(orc, X, R, seed=3, prec=VD_FP32)
     rng = np.random.default_rng(d)

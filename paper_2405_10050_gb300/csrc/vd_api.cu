@@ -20,9 +20,9 @@ cudaError_t mc_fill(const double* X, int64_t N, int d, int64_t R, uint64_t seed,
 cudaError_t mc_adjoint(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
                        const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, int64_t nnz,
                        const double* gV, const double* gA, double* gX, DevBufs& scratch, cudaStream_t st);
-cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, DevBufs& out_bufs,
-                              int32_t** tuples, double** coords, int64_t* nv, vd_stats* stats, Counters* ctr,
-                              cudaStream_t st, char* err, size_t errlen);
+cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, Workspace& ws,
+                              DevBufs& out_bufs, int32_t** tuples, double** coords, int64_t* nv, vd_stats* stats,
+                              Counters* ctr, cudaStream_t st, char* err, size_t errlen);
 }  // namespace vd
 
 namespace vd {
@@ -46,6 +46,7 @@ struct vd_ctx {
   Counters* ctr = nullptr;  // device
   DevBufs own;
   int batch_threads[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // autotuned block size by largest d
+  vd::Workspace trav_ws;  // traversal tables and level buffers, reused across vd_vertices calls
 };
 
 struct vd_mesh {
@@ -212,6 +213,7 @@ void vd_destroy(vd_ctx* ctx) {
   cudaStreamSynchronize(ctx->st);
   ctx->node_bufs.release();
   ctx->own.release();
+  ctx->trav_ws.release();
   delete ctx;
 }
 
@@ -768,7 +770,7 @@ vd_status vd_vertices(vd_ctx* ctx, vd_mesh** out) {
   const long long l0 = vd::g_launches.load();
   Timer tm(ctx->st);
   char err[256] = {0};
-  cudaError_t e = vd::traverse_vertices(ctx->tree, effective_precision(ctx), ctx->cfg, m->bufs, &m->tuples,
+  cudaError_t e = vd::traverse_vertices(ctx->tree, effective_precision(ctx), ctx->cfg, ctx->trav_ws, m->bufs, &m->tuples,
                                         &m->coords, &m->nv, &m->stats, ctx->ctr, ctx->st, err, sizeof(err));
   m->stats.ms = tm.stop();
   m->stats.launches = vd::g_launches.load() - l0;

@@ -3,6 +3,7 @@
 #pragma once
 #include <atomic>
 #include <cstdint>
+#include <utility>
 #include <vector>
 #include <cuda_runtime.h>
 
@@ -125,6 +126,36 @@ struct DevBufs {
   }
 };
 
+// Device buffers kept across calls: slot k holds one buffer that is
+// reallocated only when a call needs more than it holds, so repeated calls of
+// the same size make no cudaMalloc / cudaFree (which synchronise the device).
+struct Workspace {
+  std::vector<std::pair<void*, size_t>> slots;
+  cudaError_t get(int slot, size_t bytes, void** p) {
+    if (bytes == 0) bytes = 16;
+    if ((int)slots.size() <= slot) slots.resize(slot + 1, {nullptr, 0});
+    auto& s = slots[slot];
+    if (s.second < bytes) {
+      if (s.first) cudaFree(s.first);
+      s = {nullptr, 0};
+      cudaError_t e = cudaMalloc(&s.first, bytes);
+      if (e != cudaSuccess) return e;
+      s.second = bytes;
+    }
+    *p = s.first;
+    return cudaSuccess;
+  }
+  template <class T>
+  cudaError_t get_n(int slot, size_t n, T** p) {
+    return get(slot, n * sizeof(T), reinterpret_cast<void**>(p));
+  }
+  void release() {
+    for (auto& s : slots)
+      if (s.first) cudaFree(s.first);
+    slots.clear();
+  }
+};
+
 // ---- launchers (defined in the .cu files) --------------------------------
 // Builds the tree of X_dev (N x d, device) into buffers owned by `bufs`.
 cudaError_t build_tree(const double* X_dev, int64_t N, int d, cudaStream_t st, DevBufs& bufs, TreeView* tv);
@@ -134,6 +165,12 @@ cudaError_t build_knn(TreeView* tv, int K, cudaStream_t st, DevBufs& bufs);
 int default_knn_k(int d);
 cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision,
                            Counters* ctr, cudaStream_t st, int64_t* nfallback = nullptr);
+// Same result with no host synchronisation: the ray count may live on the
+// device (rs.R_dev, at most rs.R), and the tree-walk and binary64 follow-up
+// launches read their counts (ctr->fallback, ctr->overflow) on the device.
+// The caller zeroes ctr->fallback and ctr->overflow before the call.
+cudaError_t launch_raycast_async(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision,
+                                 Counters* ctr, cudaStream_t st);
 // One point set of a batched MC launch (device array, one entry per set).
 struct SetDesc {
   TreeView tv;          // nodes, tiles, candidate lists of the set

@@ -885,6 +885,29 @@ cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut
   return e;
 }
 
+cudaError_t launch_raycast_async(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision,
+                                 Counters* ctr, cudaStream_t st) {
+  if (rs.R <= 0) return cudaSuccess;
+  unsigned long long* work = reinterpret_cast<unsigned long long*>(&ctr->aux1);
+  const bool list = tv.K > 0 && ro.fallback_list != nullptr;
+  cudaError_t e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rs, ro, precision, ctr, work, nullptr, rs.R, list, st);
+  if (e != cudaSuccess) return e;
+  if (list) {  // rays the lists could not certify: tree walk, count on the device
+    RaySource r2 = rs;
+    r2.R = ro.fallback_cap;
+    r2.R_dev = &ctr->fallback;
+    e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, r2, ro, precision, ctr, work, ro.fallback_list, ro.fallback_cap,
+                      false, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (precision == VD_FP64 || ro.overflow_list == nullptr) return cudaSuccess;
+  RaySource r3 = rs;  // rays whose candidate buffer overflowed: binary64 path
+  r3.R = ro.overflow_cap;
+  r3.R_dev = &ctr->overflow;
+  return VD_DISPATCH_D(tv.d, launch_ray_d, tv, r3, ro, VD_FP64, ctr, work, ro.overflow_list, ro.overflow_cap, false,
+                       st);
+}
+
 cudaError_t launch_mc_fallback_dev(const SetDesc& S, int64_t R, uint64_t seed, cudaStream_t st) {
   TreeView tv = S.tv;
   tv.K = 0;  // tree walk

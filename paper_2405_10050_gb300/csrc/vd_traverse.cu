@@ -361,11 +361,11 @@ __global__ void k_expand(Tables T, const double* X, const int32_t* frontier, int
 }
 
 // Phase 1 of the commit: claim the tuple's slot for this ray (or find it).
-__global__ void k_commit_claim(Tables T, const int32_t* reta, const int32_t* hit, int64_t nr, int32_t* cand,
-                               int64_t* cslot, unsigned* flags) {
+__global__ void k_commit_claim(Tables T, const int32_t* reta, const int32_t* hit, int64_t nr,
+                               const unsigned long long* nr_dev, int32_t* cand, int64_t* cslot, unsigned* flags) {
   const int d = T.d, L = d + 1;
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= nr) return;
+  if (r >= (nr_dev ? min(nr, (int64_t)*nr_dev) : nr)) return;
   int32_t sig[VD_MAX_D + 1];
   for (int a = 0; a < d; ++a) sig[a] = reta[r * d + a];
   sig[d] = hit[r];
@@ -399,10 +399,11 @@ __global__ void k_commit_claim(Tables T, const int32_t* reta, const int32_t* hit
 // Phase 2: winners get vertex ids, coordinates, frontier slots and edges.
 template <int D>
 __global__ void k_commit_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot, int64_t nr,
-                                int32_t* next, unsigned long long* nnext, unsigned* flags) {
+                                const unsigned long long* nr_dev, int32_t* next, unsigned long long* nnext,
+                                unsigned* flags) {
   const int d = T.d, L = d + 1;
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= nr || cslot[r] < 0) return;
+  if (r >= (nr_dev ? min(nr, (int64_t)*nr_dev) : nr) || cslot[r] < 0) return;
   const unsigned long long v = atomicAdd(T.nv, 1ull);
   if ((int64_t)v >= T.vcap) {
     atomicOr(flags, kFlagHashFull);
@@ -573,9 +574,10 @@ void launch_expand(Tables T, const double* X, const int32_t* front, int64_t nf, 
 }
 
 template <int D>
-void launch_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot, int64_t nr, int32_t* next,
-                   unsigned long long* nnext, unsigned* flags, cudaStream_t st) {
-  k_commit_finish<D><<<nb(nr), 256, 0, st>>>(T, X, cand, cslot, nr, next, nnext, flags);
+void launch_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot, int64_t nr,
+                   const unsigned long long* nr_dev, int32_t* next, unsigned long long* nnext, unsigned* flags,
+                   cudaStream_t st) {
+  k_commit_finish<D><<<nb(nr), 256, 0, st>>>(T, X, cand, cslot, nr, nr_dev, next, nnext, flags);
   count_launch();
 }
 
@@ -609,23 +611,23 @@ static double vertices_per_cell(int d) {
   return v;
 }
 
-cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, DevBufs& out_bufs,
-                              int32_t** tuples_out, double** coords_out, int64_t* nv_out, vd_stats* stats,
-                              Counters* ctr, cudaStream_t st, char* err, size_t errlen) {
+cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, Workspace& ws,
+                              DevBufs& out_bufs, int32_t** tuples_out, double** coords_out, int64_t* nv_out,
+                              vd_stats* stats, Counters* ctr, cudaStream_t st, char* err, size_t errlen) {
   const int d = tv.d;
   const int L = d + 1;
   const int64_t N = tv.N;
   cudaError_t e;
-  DevBufs tb;
-  struct Guard {
-    DevBufs& b;
-    ~Guard() { b.release(); }
-  } guard{tb};
 #define VD_TRY(x)                     \
   do {                                \
     e = (x);                          \
     if (e != cudaSuccess) return e;   \
   } while (0)
+  // workspace slots
+  enum {
+    kVt, kVx, kVslot, kEt, kEcnt, kEslot, kCnts, kRo, kRd, kRt, kReta, kRhit, kCand, kCslot, kOvl, kFbl, kSnode,
+    kSsig, kSm, kAlive, kSr, kFront, kNext, kPerm, kPtmp, kKeys, kKtmp, kCounts, kOrand
+  };
   int64_t vcap = cfg.hash_capacity > 0 ? cfg.hash_capacity
                                        : (int64_t)std::min(2.0e9, std::max(1.0e5, 2.0 * N * vertices_per_cell(d) / L +
                                                                                        64.0 * (1 << std::min(d, 16)) +
@@ -639,14 +641,14 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   T.ecap = ecap;
   T.vhmask = vh - 1;
   T.ehmask = eh - 1;
-  VD_TRY(tb.alloc_n(&T.vt, (size_t)vcap * L));
-  VD_TRY(tb.alloc_n(&T.vx, (size_t)vcap * d));
-  VD_TRY(tb.alloc_n(&T.vslot, (size_t)vh));
-  VD_TRY(tb.alloc_n(&T.et, (size_t)ecap * d));
-  VD_TRY(tb.alloc_n(&T.ecnt, (size_t)ecap));
-  VD_TRY(tb.alloc_n(&T.eslot, (size_t)eh));
+  VD_TRY(ws.get_n(kVt, (size_t)vcap * L, &T.vt));
+  VD_TRY(ws.get_n(kVx, (size_t)vcap * d, &T.vx));
+  VD_TRY(ws.get_n(kVslot, (size_t)vh, &T.vslot));
+  VD_TRY(ws.get_n(kEt, (size_t)ecap * d, &T.et));
+  VD_TRY(ws.get_n(kEcnt, (size_t)ecap, &T.ecnt));
+  VD_TRY(ws.get_n(kEslot, (size_t)eh, &T.eslot));
   unsigned long long* cnts = nullptr;  // nv, ne, nrays, nnext
-  VD_TRY(tb.alloc_n(&cnts, 4));
+  VD_TRY(ws.get_n(kCnts, 4, &cnts));
   T.nv = cnts + 0;
   T.ne = cnts + 1;
   unsigned* flags = &ctr->flags;
@@ -654,39 +656,27 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   k_fill_i32<<<nb(vh), 256, 0, st>>>(T.vslot, vh, kEmpty); count_launch();
   k_fill_i32<<<nb(eh), 256, 0, st>>>(T.eslot, eh, kEmpty); count_launch();
 
-  // level buffers, grown on demand
+  // per-level ray buffers (contents live for one level; grown between levels)
   int64_t rcap = 0;
   double *ro = nullptr, *rd = nullptr, *rt = nullptr;
   int32_t *reta = nullptr, *rhit = nullptr, *cand = nullptr;
   int64_t* cslot = nullptr;
   int32_t *ovl = nullptr, *fbl = nullptr;
-  int64_t ovcap = 0;
   auto grow = [&](int64_t need) -> cudaError_t {
     if (need <= rcap) return cudaSuccess;
-    int64_t c = std::max<int64_t>(need, rcap * 2);
-    c = std::max<int64_t>(c, 4096);
-    for (void* p : {(void*)ro, (void*)rd, (void*)rt, (void*)reta, (void*)rhit, (void*)cand, (void*)cslot,
-                    (void*)ovl, (void*)fbl}) {
-      if (!p) continue;
-      cudaFree(p);
-      tb.ptrs.erase(std::remove(tb.ptrs.begin(), tb.ptrs.end(), p), tb.ptrs.end());
-    }
-    rcap = c;
-    ovcap = c;
+    const int64_t c = std::max<int64_t>({need, rcap * 2, 4096});
     cudaError_t ee;
-    if ((ee = tb.alloc_n(&ro, (size_t)c * d)) || (ee = tb.alloc_n(&rd, (size_t)c * d)) ||
-        (ee = tb.alloc_n(&rt, (size_t)c)) || (ee = tb.alloc_n(&reta, (size_t)c * L)) ||
-        (ee = tb.alloc_n(&rhit, (size_t)c)) ||
-        (ee = tb.alloc_n(&cand, (size_t)c * L)) || (ee = tb.alloc_n(&cslot, (size_t)c)) ||
-        (ee = tb.alloc_n(&ovl, (size_t)c)) || (ee = tb.alloc_n(&fbl, (size_t)c)))
+    if ((ee = ws.get_n(kRo, (size_t)c * d, &ro)) || (ee = ws.get_n(kRd, (size_t)c * d, &rd)) ||
+        (ee = ws.get_n(kRt, (size_t)c, &rt)) || (ee = ws.get_n(kReta, (size_t)c * L, &reta)) ||
+        (ee = ws.get_n(kRhit, (size_t)c, &rhit)) || (ee = ws.get_n(kCand, (size_t)c * L, &cand)) ||
+        (ee = ws.get_n(kCslot, (size_t)c, &cslot)) || (ee = ws.get_n(kOvl, (size_t)c, &ovl)) ||
+        (ee = ws.get_n(kFbl, (size_t)c, &fbl)))
       return ee;
+    rcap = c;
     return cudaSuccess;
   };
-  auto read_flags = [&](unsigned* hf) -> cudaError_t {
-    cudaError_t ee = cudaMemcpyAsync(hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
-    if (ee == cudaSuccess) ee = cudaStreamSynchronize(st);
-    return ee;
-  };
+  // the widest level of a traversal holds a small fraction of all vertices
+  VD_TRY(grow(std::min<int64_t>(vcap * L, std::max<int64_t>(4096, vcap * L / 16))));
   cudaEvent_t ev0, ev1;
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
@@ -699,10 +689,12 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   } evg{ev0, ev1};
   double raycast_ms = 0.0;
   int64_t nfallback = 0;
-  auto run_rays = [&](int64_t nr, int stride) -> cudaError_t {
+  // casts the level's rays (count on the device if nr_dev != nullptr, at most nr)
+  auto cast = [&](int64_t nr, const unsigned long long* nr_dev, int stride) -> cudaError_t {
     RaySource rs;
     rs.mode = 0;
     rs.R = nr;
+    rs.R_dev = nr_dev;
     rs.origins = ro;
     rs.dirs = rd;
     rs.eta = reta;
@@ -712,32 +704,34 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     rout.hit = rhit;
     rout.t = rt;
     rout.overflow_list = ovl;
-    rout.overflow_cap = ovcap;
+    rout.overflow_cap = rcap;
     rout.fallback_list = fbl;
     rout.fallback_cap = rcap;
     cudaError_t ee = cudaMemsetAsync(&ctr->overflow, 0, sizeof(unsigned long long), st);
+    if (ee == cudaSuccess) ee = cudaMemsetAsync(&ctr->fallback, 0, sizeof(unsigned long long), st);
     if (ee != cudaSuccess) return ee;
     cudaEventRecord(ev0, st);
-    ee = launch_raycast(tv, rs, rout, precision, ctr, st, &nfallback);
+    ee = launch_raycast_async(tv, rs, rout, precision, ctr, st);
     cudaEventRecord(ev1, st);
-    if (ee == cudaSuccess) ee = cudaEventSynchronize(ev1);
-    float ms = 0.f;
-    if (ee == cudaSuccess) cudaEventElapsedTime(&ms, ev0, ev1);
-    raycast_ms += ms;
     return ee;
+  };
+  // after the stream has been synchronised
+  auto account = [&](const unsigned long long* fb_host) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) raycast_ms += ms;
+    nfallback += (int64_t)std::min<unsigned long long>(*fb_host, (unsigned long long)rcap);
   };
 
   // ---- seeds by Descent ----
   const int64_t ns = std::min<int64_t>(N, 64);
-  VD_TRY(grow(std::max<int64_t>(ns, 4096)));
   int32_t *snode = nullptr, *ssig = nullptr;
   int *sm = nullptr, *alive = nullptr;
   double* sr = nullptr;
-  VD_TRY(tb.alloc_n(&snode, ns));
-  VD_TRY(tb.alloc_n(&ssig, (size_t)ns * (VD_MAX_D + 1)));
-  VD_TRY(tb.alloc_n(&sm, ns));
-  VD_TRY(tb.alloc_n(&alive, ns));
-  VD_TRY(tb.alloc_n(&sr, (size_t)ns * VD_MAX_D));
+  VD_TRY(ws.get_n(kSnode, ns, &snode));
+  VD_TRY(ws.get_n(kSsig, (size_t)ns * (VD_MAX_D + 1), &ssig));
+  VD_TRY(ws.get_n(kSm, ns, &sm));
+  VD_TRY(ws.get_n(kAlive, ns, &alive));
+  VD_TRY(ws.get_n(kSr, (size_t)ns * VD_MAX_D, &sr));
   {
     std::vector<int32_t> hn(ns), hsig(ns * (VD_MAX_D + 1), kNoId);
     std::vector<int> hm(ns, 1), ha(ns, 1);
@@ -750,7 +744,6 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     VD_TRY(cudaMemcpyAsync(sm, hm.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
     VD_TRY(cudaMemcpyAsync(alive, ha.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
     std::vector<double> hr(ns * VD_MAX_D, 0.0);
-    std::vector<double> hx(ns * d);
     for (int64_t s = 0; s < ns; ++s)
       VD_TRY(cudaMemcpyAsync(hr.data() + s * VD_MAX_D, tv.X + (int64_t)hn[s] * d, d * sizeof(double),
                              cudaMemcpyDeviceToHost, st));
@@ -761,32 +754,32 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   for (int step = 0; step < d; ++step) {
     k_descent_dir<<<nb(ns, 64), 64, 0, st>>>(tv.X, d, ns, snode, ssig, sm, sr, step, ro, rd, reta, alive); count_launch();
     VD_TRY(cudaGetLastError());
-    VD_TRY(run_rays(ns, L));
+    VD_TRY(cast(ns, nullptr, L));
     raycasts += ns;
     k_descent_update<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, sr, rd, rhit, rt, alive); count_launch();
     VD_TRY(cudaGetLastError());
   }
   k_descent_cand<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, alive, reta, rhit); count_launch();
-  // insert the seeds as the first level
+  // frontiers: each holds the vertices created by one level (at most vcap)
   int32_t *front = nullptr, *next = nullptr;
-  int64_t fcap = std::max<int64_t>(ns, 4096);
-  VD_TRY(tb.alloc_n(&front, fcap));
-  VD_TRY(tb.alloc_n(&next, fcap));
+  VD_TRY(ws.get_n(kFront, (size_t)vcap, &front));
+  VD_TRY(ws.get_n(kNext, (size_t)vcap, &next));
   unsigned long long* nrays = cnts + 2;
   unsigned long long* nnext = cnts + 3;
   VD_TRY(cudaMemsetAsync(nnext, 0, sizeof(unsigned long long), st));
-  k_commit_claim<<<nb(ns), 256, 0, st>>>(T, reta, rhit, ns, cand, cslot, flags); count_launch();
+  k_commit_claim<<<nb(ns), 256, 0, st>>>(T, reta, rhit, ns, nullptr, cand, cslot, flags); count_launch();
   // seeds that did not reach a vertex were marked with hit = kNoId: clear the
   // degenerate flag they raised (a missing seed is not an error)
   {
     unsigned hf = 0;
-    VD_TRY(read_flags(&hf));
+    VD_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    VD_TRY(cudaStreamSynchronize(st));
     if (hf & kFlagDegenerate) {
       unsigned clr = hf & ~kFlagDegenerate;
       VD_TRY(cudaMemcpyAsync(flags, &clr, sizeof(unsigned), cudaMemcpyHostToDevice, st));
     }
   }
-  VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, ns, front, nnext, flags, st);
+  VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, ns, nullptr, front, nnext, flags, st);
   unsigned long long hn2[4];
   VD_TRY(cudaMemcpyAsync(hn2, cnts, sizeof(hn2), cudaMemcpyDeviceToHost, st));
   VD_TRY(cudaStreamSynchronize(st));
@@ -795,6 +788,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     snprintf(err, errlen, "Descent found no seed vertex");
     return cudaErrorUnknown;
   }
+  // ---- levels: one host synchronisation each (the next frontier's size) ----
   int64_t levels = 0;
   const int64_t max_levels = cfg.max_levels > 0 ? cfg.max_levels : (int64_t)1 << 20;
   while (nf > 0) {
@@ -803,42 +797,23 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
       return cudaErrorUnknown;
     }
     ++levels;
-    VD_TRY(grow(nf * L));
-    if (fcap < nf * L) {
-      // the next frontier holds at most one vertex per ray
-      int32_t* nn = nullptr;
-      VD_TRY(tb.alloc_n(&nn, (size_t)nf * L));
-      tb.ptrs.erase(std::remove(tb.ptrs.begin(), tb.ptrs.end(), (void*)next), tb.ptrs.end());
-      cudaFree(next);
-      next = nn;
-      fcap = nf * L;
-      // front must hold nf*L too for the swap below
-      int32_t* nfb = nullptr;
-      VD_TRY(tb.alloc_n(&nfb, (size_t)fcap));
-      VD_TRY(cudaMemcpyAsync(nfb, front, nf * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-      tb.ptrs.erase(std::remove(tb.ptrs.begin(), tb.ptrs.end(), (void*)front), tb.ptrs.end());
-      VD_TRY(cudaStreamSynchronize(st));
-      cudaFree(front);
-      front = nfb;
-    }
+    const int64_t ncap = nf * L;  // at most one ray per (frontier vertex, edge)
+    VD_TRY(grow(ncap));
     VD_TRY(cudaMemsetAsync(cnts + 2, 0, 2 * sizeof(unsigned long long), st));
     VD_TRAV_D(d, launch_expand, T, tv.X, front, nf, ro, rd, reta, nrays, rcap, flags, st);
     VD_TRY(cudaGetLastError());
-    unsigned long long hr = 0;
-    VD_TRY(cudaMemcpyAsync(&hr, nrays, sizeof(hr), cudaMemcpyDeviceToHost, st));
-    VD_TRY(cudaStreamSynchronize(st));
-    const int64_t nr = std::min<int64_t>((int64_t)hr, rcap);
-    if (nr > 0) {
-      VD_TRY(run_rays(nr, d));
-      raycasts += nr;
-      k_commit_claim<<<nb(nr), 256, 0, st>>>(T, reta, rhit, nr, cand, cslot, flags); count_launch();
-      VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, nr, next, nnext, flags, st);
-      VD_TRY(cudaGetLastError());
-    }
-    unsigned long long hc[4];
+    VD_TRY(cast(ncap, nrays, d));
+    k_commit_claim<<<nb(ncap), 256, 0, st>>>(T, reta, rhit, ncap, nrays, cand, cslot, flags); count_launch();
+    VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, ncap, nrays, next, nnext, flags, st);
+    VD_TRY(cudaGetLastError());
+    unsigned long long hc[5];
     unsigned hf = 0;
-    VD_TRY(cudaMemcpyAsync(hc, cnts, sizeof(hc), cudaMemcpyDeviceToHost, st));
-    VD_TRY(read_flags(&hf));
+    VD_TRY(cudaMemcpyAsync(hc, cnts, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    VD_TRY(cudaMemcpyAsync(hc + 4, &ctr->fallback, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    VD_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    VD_TRY(cudaStreamSynchronize(st));
+    account(hc + 4);
+    raycasts += (int64_t)std::min<unsigned long long>(hc[2], (unsigned long long)rcap);
     if (hf & (kFlagHashFull | kFlagQueue | kFlagDegenerate | kFlagCandOverflow | kFlagBadInput)) break;
     nf = (int64_t)hc[3];
     std::swap(front, next);
@@ -853,12 +828,12 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   uint32_t* counts = nullptr;
   unsigned long long* orand = nullptr;
   const int64_t nvv = std::max<int64_t>(nv, 1);
-  VD_TRY(tb.alloc_n(&perm, nvv));
-  VD_TRY(tb.alloc_n(&ptmp, nvv));
-  VD_TRY(tb.alloc_n(&keys, nvv));
-  VD_TRY(tb.alloc_n(&ktmp, nvv));
-  VD_TRY(tb.alloc_n(&counts, (size_t)256 * (nvv / 4096 + 2)));
-  VD_TRY(tb.alloc_n(&orand, 2));
+  VD_TRY(ws.get_n(kPerm, nvv, &perm));
+  VD_TRY(ws.get_n(kPtmp, nvv, &ptmp));
+  VD_TRY(ws.get_n(kKeys, nvv, &keys));
+  VD_TRY(ws.get_n(kKtmp, nvv, &ktmp));
+  VD_TRY(ws.get_n(kCounts, (size_t)256 * (nvv / 4096 + 2), &counts));
+  VD_TRY(ws.get_n(kOrand, 2, &orand));
   k_iota<<<nb(nvv), 256, 0, st>>>(perm, nv); count_launch();
   for (int c = d; c >= 0; --c) {
     k_col_keys<<<nb(nvv), 256, 0, st>>>(T.vt, L, c, perm, nv, keys, ptmp); count_launch();

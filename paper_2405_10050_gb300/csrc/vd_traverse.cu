@@ -317,35 +317,74 @@ __device__ void edge_increment(const Tables& T, const int32_t* eta, unsigned* fl
 }
 
 // ---- level kernels ----------------------------------------------------------
-template <int D>
-__global__ void k_expand(Tables T, const double* X, const int32_t* frontier, int64_t nf, double* ro, double* rd,
-                         int32_t* reta, unsigned long long* nrays, int64_t rcap, unsigned* flags) {
+// Warp-aggregated append: returns this lane's slot in a list whose length
+// is *n (lanes with want == false get -1).
+__device__ __forceinline__ long long warp_append(bool want, unsigned long long* n) {
+  const unsigned m = __ballot_sync(__activemask(), want);
+  if (!want) return -1;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(n, (unsigned long long)__popc(m));
+  base = __shfl_sync(m, base, leader);
+  return (long long)(base + __popc(m & ((1u << lane) - 1u)));
+}
+
+// Expansion, pass 1: every (frontier vertex, dropped generator) whose edge
+// holds a node and has fewer than two known endpoints is appended to the
+// level's work list (cheap hash lookups; pass 2 then runs the binary64
+// SearchDirection on full warps).
+__global__ void k_expand_mark(Tables T, const int32_t* frontier, int64_t nf, int64_t* items,
+                              unsigned long long* nitems, int64_t rcap, unsigned* flags) {
   const int d = T.d;
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= nf * (d + 1)) return;
+  bool want = false;
+  if (q < nf * (d + 1)) {
+    const int64_t f = q / (d + 1);
+    const int drop = (int)(q % (d + 1));
+    const int32_t v = frontier[f];
+    int32_t eta[VD_MAX_D];
+    int m = 0, hasnode = 0;
+    for (int a = 0; a <= d; ++a)
+      if (a != drop) {
+        const int32_t g = T.vt[(int64_t)v * (d + 1) + a];
+        eta[m++] = g;
+        hasnode |= g >= 0;
+      }
+    want = hasnode && edge_count(T, eta) < 2;
+  }
+  const long long r = warp_append(want, nitems);
+  if (r < 0) return;
+  if (r >= rcap) {
+    atomicOr(flags, kFlagQueue);
+    return;
+  }
+  items[r] = q;
+}
+
+// Expansion, pass 2: ray r of the level from the r-th work item: origin =
+// the vertex, direction = SearchDirection, eta = the edge (reference node
+// first).
+template <int D>
+__global__ void k_expand_dir(Tables T, const double* X, const int32_t* frontier, const int64_t* items,
+                             const unsigned long long* nitems, int64_t rcap, double* ro, double* rd, int32_t* reta,
+                             unsigned* flags) {
+  const int d = T.d;
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= min(rcap, (int64_t)*nitems)) return;
+  const int64_t q = items[r];
   const int64_t f = q / (d + 1);
   const int drop = (int)(q % (d + 1));
   const int32_t v = frontier[f];
   int32_t sig[D + 1], eta[D];
   for (int a = 0; a <= d; ++a) sig[a] = T.vt[(int64_t)v * (d + 1) + a];
-  int m = 0, hasnode = 0;
+  int m = 0;
   for (int a = 0; a <= d; ++a)
-    if (a != drop) {
-      eta[m] = sig[a];
-      hasnode |= sig[a] >= 0;
-      ++m;
-    }
-  if (!hasnode) return;
-  if (edge_count(T, eta) >= 2) return;
+    if (a != drop) eta[m++] = sig[a];
   double u[D];
   if (!search_direction<D>(X, d, sig, drop, u)) {
     atomicOr(flags, kFlagDegenerate);
-    return;
-  }
-  const unsigned long long r = atomicAdd(nrays, 1ull);
-  if ((int64_t)r >= rcap) {
-    atomicOr(flags, kFlagQueue);
-    return;
+    for (int a = 0; a < d; ++a) u[a] = 0.0;  // casts to nothing; the commit flags it again
   }
   // eta row: reference node g (first node of eta) first
   int gpos = 0;
@@ -360,19 +399,18 @@ __global__ void k_expand(Tables T, const double* X, const int32_t* frontier, int
   }
 }
 
-// Phase 1 of the commit: claim the tuple's slot for this ray (or find it).
-__global__ void k_commit_claim(Tables T, const int32_t* reta, const int32_t* hit, int64_t nr,
-                               const unsigned long long* nr_dev, int32_t* cand, int64_t* cslot, unsigned* flags) {
+// Phase 1 of the commit: claim the tuple's slot for ray r (or find it);
+// true if this ray owns a new vertex.
+__device__ bool claim_slot(const Tables& T, const int32_t* reta, const int32_t* hit, int64_t r, int32_t* cand,
+                           int64_t* cslot, unsigned* flags) {
   const int d = T.d, L = d + 1;
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= (nr_dev ? min(nr, (int64_t)*nr_dev) : nr)) return;
   int32_t sig[VD_MAX_D + 1];
   for (int a = 0; a < d; ++a) sig[a] = reta[r * d + a];
   sig[d] = hit[r];
   cslot[r] = -1;
   if (sig[d] == kNoId) {
     atomicOr(flags, kFlagDegenerate);
-    return;
+    return false;
   }
   sort_small(sig, L);
   for (int a = 0; a < L; ++a) cand[r * L + a] = sig[a];
@@ -384,26 +422,38 @@ __global__ void k_commit_claim(Tables T, const int32_t* reta, const int32_t* hit
       s = atomicCAS(&T.vslot[h], kEmpty, kRayTag | (int32_t)r);
       if (s == kEmpty) {
         cslot[r] = (int64_t)h;  // this ray owns the new vertex
-        return;
+        return true;
       }
       __threadfence();
     }
     __threadfence();  // the other ray's tuple was published before its claim
     const volatile int32_t* other = (s & kRayTag) ? (cand + (int64_t)(s & ~kRayTag) * L) : (T.vt + (int64_t)s * L);
-    if (tuple_eq(other, sig, L)) return;  // known vertex or claimed by another ray
+    if (tuple_eq(other, sig, L)) return false;  // known vertex or claimed by another ray
     h = (h + 1) & (uint64_t)T.vhmask;
   }
   atomicOr(flags, kFlagHashFull);
+  return false;
+}
+
+// Rays that own a new vertex are appended to win[] (count *nwin).
+__global__ void k_commit_claim(Tables T, const int32_t* reta, const int32_t* hit, int64_t nr,
+                               const unsigned long long* nr_dev, int32_t* cand, int64_t* cslot, int32_t* win,
+                               unsigned long long* nwin, unsigned* flags) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool owns = r < (nr_dev ? min(nr, (int64_t)*nr_dev) : nr) && claim_slot(T, reta, hit, r, cand, cslot, flags);
+  const long long p = warp_append(owns, nwin);
+  if (p >= 0) win[p] = (int32_t)r;
 }
 
 // Phase 2: winners get vertex ids, coordinates, frontier slots and edges.
 template <int D>
-__global__ void k_commit_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot, int64_t nr,
-                                const unsigned long long* nr_dev, int32_t* next, unsigned long long* nnext,
-                                unsigned* flags) {
+__global__ void k_commit_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot,
+                                const int32_t* win, int64_t nwcap, const unsigned long long* nwin, int32_t* next,
+                                unsigned long long* nnext, unsigned* flags) {
   const int d = T.d, L = d + 1;
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= (nr_dev ? min(nr, (int64_t)*nr_dev) : nr) || cslot[r] < 0) return;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= min(nwcap, (int64_t)*nwin)) return;
+  const int64_t r = win[p];
   const unsigned long long v = atomicAdd(T.nv, 1ull);
   if ((int64_t)v >= T.vcap) {
     atomicOr(flags, kFlagHashFull);
@@ -566,18 +616,24 @@ __global__ void k_gather_out(const int32_t* vt, const double* vx, int d, const i
 
 inline unsigned nb(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
+// The level's rays: nf frontier vertices -> work list -> ray arrays (count
+// *nrays on the device, at most min(nf (d+1), rcap)).
 template <int D>
-void launch_expand(Tables T, const double* X, const int32_t* front, int64_t nf, double* ro, double* rd, int32_t* reta,
-                   unsigned long long* nrays, int64_t rcap, unsigned* flags, cudaStream_t st) {
-  k_expand<D><<<nb(nf * (T.d + 1), 128), 128, 0, st>>>(T, X, front, nf, ro, rd, reta, nrays, rcap, flags);
+void launch_expand(Tables T, const double* X, const int32_t* front, int64_t nf, int64_t* items, double* ro,
+                   double* rd, int32_t* reta, unsigned long long* nrays, int64_t rcap, unsigned* flags,
+                   cudaStream_t st) {
+  const int64_t n = nf * (T.d + 1);
+  k_expand_mark<<<nb(n), 256, 0, st>>>(T, front, nf, items, nrays, rcap, flags);
+  count_launch();
+  k_expand_dir<D><<<nb(std::min(n, rcap), 128), 128, 0, st>>>(T, X, front, items, nrays, rcap, ro, rd, reta, flags);
   count_launch();
 }
 
 template <int D>
-void launch_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot, int64_t nr,
-                   const unsigned long long* nr_dev, int32_t* next, unsigned long long* nnext, unsigned* flags,
-                   cudaStream_t st) {
-  k_commit_finish<D><<<nb(nr), 256, 0, st>>>(T, X, cand, cslot, nr, nr_dev, next, nnext, flags);
+void launch_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot, const int32_t* win,
+                   int64_t nwcap, const unsigned long long* nwin, int32_t* next, unsigned long long* nnext,
+                   unsigned* flags, cudaStream_t st) {
+  k_commit_finish<D><<<nb(nwcap), 256, 0, st>>>(T, X, cand, cslot, win, nwcap, nwin, next, nnext, flags);
   count_launch();
 }
 
@@ -626,7 +682,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   // workspace slots
   enum {
     kVt, kVx, kVslot, kEt, kEcnt, kEslot, kCnts, kRo, kRd, kRt, kReta, kRhit, kCand, kCslot, kOvl, kFbl, kSnode,
-    kSsig, kSm, kAlive, kSr, kFront, kNext, kPerm, kPtmp, kKeys, kKtmp, kCounts, kOrand
+    kSsig, kSm, kAlive, kSr, kFront, kNext, kPerm, kPtmp, kKeys, kKtmp, kCounts, kOrand, kItems, kWin
   };
   int64_t vcap = cfg.hash_capacity > 0 ? cfg.hash_capacity
                                        : (int64_t)std::min(2.0e9, std::max(1.0e5, 2.0 * N * vertices_per_cell(d) / L +
@@ -647,12 +703,12 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   VD_TRY(ws.get_n(kEt, (size_t)ecap * d, &T.et));
   VD_TRY(ws.get_n(kEcnt, (size_t)ecap, &T.ecnt));
   VD_TRY(ws.get_n(kEslot, (size_t)eh, &T.eslot));
-  unsigned long long* cnts = nullptr;  // nv, ne, nrays, nnext
-  VD_TRY(ws.get_n(kCnts, 4, &cnts));
+  unsigned long long* cnts = nullptr;  // nv, ne, nrays, nnext, nwin
+  VD_TRY(ws.get_n(kCnts, 5, &cnts));
   T.nv = cnts + 0;
   T.ne = cnts + 1;
   unsigned* flags = &ctr->flags;
-  VD_TRY(cudaMemsetAsync(cnts, 0, 4 * sizeof(unsigned long long), st));
+  VD_TRY(cudaMemsetAsync(cnts, 0, 5 * sizeof(unsigned long long), st));
   k_fill_i32<<<nb(vh), 256, 0, st>>>(T.vslot, vh, kEmpty); count_launch();
   k_fill_i32<<<nb(eh), 256, 0, st>>>(T.eslot, eh, kEmpty); count_launch();
 
@@ -660,8 +716,8 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   int64_t rcap = 0;
   double *ro = nullptr, *rd = nullptr, *rt = nullptr;
   int32_t *reta = nullptr, *rhit = nullptr, *cand = nullptr;
-  int64_t* cslot = nullptr;
-  int32_t *ovl = nullptr, *fbl = nullptr;
+  int64_t *cslot = nullptr, *items = nullptr;
+  int32_t *ovl = nullptr, *fbl = nullptr, *win = nullptr;
   auto grow = [&](int64_t need) -> cudaError_t {
     if (need <= rcap) return cudaSuccess;
     const int64_t c = std::max<int64_t>({need, rcap * 2, 4096});
@@ -670,7 +726,8 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
         (ee = ws.get_n(kRt, (size_t)c, &rt)) || (ee = ws.get_n(kReta, (size_t)c * L, &reta)) ||
         (ee = ws.get_n(kRhit, (size_t)c, &rhit)) || (ee = ws.get_n(kCand, (size_t)c * L, &cand)) ||
         (ee = ws.get_n(kCslot, (size_t)c, &cslot)) || (ee = ws.get_n(kOvl, (size_t)c, &ovl)) ||
-        (ee = ws.get_n(kFbl, (size_t)c, &fbl)))
+        (ee = ws.get_n(kFbl, (size_t)c, &fbl)) || (ee = ws.get_n(kItems, (size_t)c, &items)) ||
+        (ee = ws.get_n(kWin, (size_t)c, &win)))
       return ee;
     rcap = c;
     return cudaSuccess;
@@ -766,8 +823,9 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   VD_TRY(ws.get_n(kNext, (size_t)vcap, &next));
   unsigned long long* nrays = cnts + 2;
   unsigned long long* nnext = cnts + 3;
-  VD_TRY(cudaMemsetAsync(nnext, 0, sizeof(unsigned long long), st));
-  k_commit_claim<<<nb(ns), 256, 0, st>>>(T, reta, rhit, ns, nullptr, cand, cslot, flags); count_launch();
+  unsigned long long* nwin = cnts + 4;
+  VD_TRY(cudaMemsetAsync(nnext, 0, 2 * sizeof(unsigned long long), st));
+  k_commit_claim<<<nb(ns), 256, 0, st>>>(T, reta, rhit, ns, nullptr, cand, cslot, win, nwin, flags); count_launch();
   // seeds that did not reach a vertex were marked with hit = kNoId: clear the
   // degenerate flag they raised (a missing seed is not an error)
   {
@@ -779,7 +837,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
       VD_TRY(cudaMemcpyAsync(flags, &clr, sizeof(unsigned), cudaMemcpyHostToDevice, st));
     }
   }
-  VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, ns, nullptr, front, nnext, flags, st);
+  VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, ns, nwin, front, nnext, flags, st);
   unsigned long long hn2[4];
   VD_TRY(cudaMemcpyAsync(hn2, cnts, sizeof(hn2), cudaMemcpyDeviceToHost, st));
   VD_TRY(cudaStreamSynchronize(st));
@@ -799,12 +857,14 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     ++levels;
     const int64_t ncap = nf * L;  // at most one ray per (frontier vertex, edge)
     VD_TRY(grow(ncap));
-    VD_TRY(cudaMemsetAsync(cnts + 2, 0, 2 * sizeof(unsigned long long), st));
-    VD_TRAV_D(d, launch_expand, T, tv.X, front, nf, ro, rd, reta, nrays, rcap, flags, st);
+    VD_TRY(cudaMemsetAsync(cnts + 2, 0, 3 * sizeof(unsigned long long), st));
+    VD_TRAV_D(d, launch_expand, T, tv.X, front, nf, items, ro, rd, reta, nrays, rcap, flags, st);
     VD_TRY(cudaGetLastError());
-    VD_TRY(cast(ncap, nrays, d));
-    k_commit_claim<<<nb(ncap), 256, 0, st>>>(T, reta, rhit, ncap, nrays, cand, cslot, flags); count_launch();
-    VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, ncap, nrays, next, nnext, flags, st);
+    const int64_t rmax = std::min(ncap, rcap);
+    VD_TRY(cast(rmax, nrays, d));
+    k_commit_claim<<<nb(rmax), 256, 0, st>>>(T, reta, rhit, rmax, nrays, cand, cslot, win, nwin, flags);
+    count_launch();
+    VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, rmax, nwin, next, nnext, flags, st);
     VD_TRY(cudaGetLastError());
     unsigned long long hc[5];
     unsigned hf = 0;

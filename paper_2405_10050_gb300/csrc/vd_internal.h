@@ -75,6 +75,9 @@ struct RaySource {
   uint32_t set = 0;
   int box = 1;
   int rpb = 32;                  // rays per warp batch (1..32), set by the launcher
+  // the ray's output t already holds an upper bound of its hit distance (left
+  // there by the list scan that could not certify the ray): start from it
+  int t_hint = 0;
   // with R_dev set, the ray count is min(*R_dev, R), read on the device (the
   // launch needs no host round trip), and the batch size is chosen there
   const unsigned long long* R_dev = nullptr;

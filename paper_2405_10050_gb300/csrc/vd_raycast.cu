@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
           }
         }
       }
+      if (rs.t_hint) T = fminf(T, (float)ro.t[out_pos(rs, ro, r)]);
       S.T[lane] = T;
       S.ncand[lane] = nc;
     }
@@ -411,6 +412,7 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
         const unsigned long long k = atomicAdd(&ctr->fallback, 1ull);
         if ((int64_t)k < ro.fallback_cap) ro.fallback_list[k] = (int32_t)r;
         else atomicOr(&ctr->flags, kFlagQueue);
+        ro.t[op] = (double)S.T[lane];  // the list's bound seeds the tree walk
       } else if (nc < 0) {
         const unsigned long long k = atomicAdd(&ctr->overflow, 1ull);
         if ((int64_t)k < ro.overflow_cap) ro.overflow_list[k] = (int32_t)r;
@@ -867,8 +869,11 @@ cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut
     if (e != cudaSuccess) return e;
     const int64_t n = std::min<int64_t>((int64_t)nfb, ro.fallback_cap);
     if (nfallback) *nfallback += n;
-    if (n > 0)
-      e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rs, ro, precision, ctr, work, ro.fallback_list, n, false, st);
+    if (n > 0) {
+      RaySource rf = rs;
+      rf.t_hint = 1;
+      e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rf, ro, precision, ctr, work, ro.fallback_list, n, false, st);
+    }
   } else {
     e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, rs, ro, precision, ctr, work, nullptr, rs.R, false, st);
   }
@@ -896,6 +901,7 @@ cudaError_t launch_raycast_async(const TreeView& tv, const RaySource& rs, const 
     RaySource r2 = rs;
     r2.R = ro.fallback_cap;
     r2.R_dev = &ctr->fallback;
+    r2.t_hint = 1;
     e = VD_DISPATCH_D(tv.d, launch_ray_d, tv, r2, ro, precision, ctr, work, ro.fallback_list, ro.fallback_cap,
                       false, st);
     if (e != cudaSuccess) return e;

@@ -596,12 +596,16 @@ __global__ void k_iota(int32_t* p, int64_t n) {
   if (i < n) p[i] = (int32_t)i;
 }
 
-__global__ void k_col_keys(const int32_t* vt, int L, int c, const int32_t* perm, int64_t n, uint64_t* keys,
-                           int32_t* vals) {
+// keys[i] = tuple columns c0 .. c1 of vertex perm[i], each shifted by `off`
+// to be non-negative and packed `bits` wide, column c0 most significant.
+__global__ void k_col_keys(const int32_t* vt, int L, int c0, int c1, int bits, int32_t off, const int32_t* perm,
+                           int64_t n, uint64_t* keys, int32_t* vals) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int32_t v = perm[i];
-  keys[i] = (uint64_t)((uint32_t)vt[(int64_t)v * L + c] ^ 0x80000000u);
+  uint64_t k = 0;
+  for (int c = c0; c <= c1; ++c) k = (k << bits) | (uint64_t)(uint32_t)(vt[(int64_t)v * L + c] + off);
+  keys[i] = k;
   vals[i] = v;
 }
 
@@ -895,8 +899,15 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   VD_TRY(ws.get_n(kCounts, (size_t)256 * (nvv / 4096 + 2), &counts));
   VD_TRY(ws.get_n(kOrand, 2, &orand));
   k_iota<<<nb(nvv), 256, 0, st>>>(perm, nv); count_launch();
-  for (int c = d; c >= 0; --c) {
-    k_col_keys<<<nb(nvv), 256, 0, st>>>(T.vt, L, c, perm, nv, keys, ptmp); count_launch();
+  // ids + (2d + 1) lie in [0, N + 2d + 1): pack as many columns per 64-bit key
+  // as fit and sort the groups of columns last to first (stable LSD)
+  const int32_t off = 2 * d + 1;
+  int bits = 1;
+  while (((int64_t)1 << bits) < N + off) ++bits;
+  const int per = std::max(1, 64 / bits);
+  for (int c1 = d; c1 >= 0; c1 -= per) {
+    const int c0 = std::max(0, c1 - per + 1);
+    k_col_keys<<<nb(nvv), 256, 0, st>>>(T.vt, L, c0, c1, bits, off, perm, nv, keys, ptmp); count_launch();
     VD_TRY(radix_sort_u64(keys, ptmp, ktmp, perm, nv, counts, orand, st));
     VD_TRY(cudaMemcpyAsync(perm, ptmp, nv * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   }

@@ -58,6 +58,18 @@ __device__ __forceinline__ float true_d2_lower(float ww, float gam, float EW, in
   return fmaxf(l, 0.f);
 }
 
+// A binary32 squared distance ww32 >= ww_exit(f) implies
+// true_d2_lower(ww32) >= f: with a = 1 - 2 gam, b = 2.02 sqrt(D) EW,
+// c = D EW^2 the bound is a s^2 - b s - c at s = sqrt(ww32), increasing for
+// s > b / (2a); its root for f, squared, is inflated by 2^-12 to cover the
+// rounding of this evaluation.
+__device__ __forceinline__ float ww_exit(float f, float gam, float EW, int D) {
+  if (!(f < INFINITY)) return INFINITY;
+  const float a = 1.f - 2.f * gam, b = 2.02f * sqrtf((float)D) * EW, c = (float)D * EW * EW;
+  const float s = (b + sqrtf(fmaf(b, b, 4.f * a * (c + fmaxf(f, 0.f))))) / (2.f * a);
+  return s * s * (1.f + 0x1p-12f);
+}
+
 // Squared radius around g that holds every node of the ball: nodes lie in
 // the node box, so only the part of the ball inside it matters; the farthest
 // point from g of that part is bounded through its axis-aligned box

@@ -480,6 +480,284 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
 }
 
 // ------------------------------------------------------------------------
+// VD_FP32 over the candidate lists, one thread per ray: each thread scans its
+// reference node's sorted list by itself (the warp-per-ray kernel above
+// spends warp-wide reductions on every 32 candidates, this one only plain
+// per-thread arithmetic), with the same binary32 bounds, the same early exit
+// (a candidate whose distance from g exceeds the reach of the current ball
+// ends the scan) and the same binary64 recheck.
+// ------------------------------------------------------------------------
+constexpr int kThrRays = 128;  // threads (rays in flight) per block
+
+template <int D>
+__global__ void __launch_bounds__(kThrRays) k_ray_list_thr(TreeView tr, RaySource rs, RayOut ro, Counters* ctr,
+                                                           unsigned long long* work) {
+  __shared__ int32_t s_cid[kThrRays][kCmax];
+  __shared__ float s_ctlo[kThrRays][kCmax];
+  __shared__ int32_t s_eta[kThrRays][D + 1];
+  const int tid = threadIdx.x, lane = tid & 31;
+  int32_t* cid = s_cid[tid];
+  float* ctlo = s_ctlo[tid];
+  int32_t* eta = s_eta[tid];
+  const int d = tr.d;
+  const float B = tr.coord_abs;
+  const float gam = (float)(D + 1) * kU32 * 1.01f;
+  const float EW = 4.01f * kU32 * B;
+  unsigned long long n_pairs = 0, n_rech = 0, n_over = 0;
+  const int64_t R = rs.R_dev ? min((int64_t)*rs.R_dev, rs.R) : rs.R;
+  while (true) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(work, 1ull);
+    b = __shfl_sync(kFull, b, 0);
+    const int64_t slot = (int64_t)b * 32 + lane;
+    if ((int64_t)b * 32 >= R) break;
+    if (slot >= R) continue;
+    const int64_t r = slot;
+    // ---- set-up ----
+    double v[D], u[D];
+    int m;
+    {
+      int32_t e[D + 1];
+      load_ray<D>(tr, rs, r, v, u, e, m);
+      if (m < 1 || e[0] < 0 || e[0] >= tr.N) {
+        atomicOr(&ctr->flags, kFlagBadInput);
+        m = 1;
+        e[0] = 0;
+      }
+      for (int q = 0; q <= D; ++q) eta[q] = q < m ? e[q] : kNoId;
+    }
+    const int32_t g = eta[0];
+    float u32[D], g32[D], p32[D];
+    float U1 = 0.f, P1 = 0.f, P2s = 0.f;
+    bool hasp = false;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double gk = k < d ? tr.X[(int64_t)g * d + k] : 0.0;
+      const double pk = __dadd_rn(v[k], -gk);
+      u32[k] = __double2float_rn(u[k]);
+      g32[k] = __double2float_rn(gk);
+      p32[k] = __double2float_rn(pk);
+      U1 += fabsf(u32[k]);
+      const float pa = fabsf(__double2float_ru(fabs(pk)));
+      P1 += pa;
+      P2s = fmaf(pa, pa, P2s);
+      hasp |= (pk != 0.0);
+    }
+    U1 *= 1.0001f;
+    P1 *= 1.0001f;
+    const float P2 = sqrtf(P2s) * 1.0001f;
+    const float a0 = 1.1f * EW * U1;
+    const float a1 = 1.1f * (gam + kU32);
+    const float b0c = 1.1f * ((float)D * EW * EW + 2.f * EW * P1);
+    const float b2 = 1.1f * (2.f * sqrtf((float)D) * EW + 2.f * (gam + kU32) * P2);
+    float T = INFINITY;
+    int nc = 0;
+    bool overflow = false;
+    if (rs.box) {
+      for (int a = 0; a < d; ++a) {
+        float ua = 0.f;
+        double ua64 = 0.0, va64 = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          if (k == a) {
+            ua = u32[k];
+            ua64 = u[k];
+            va64 = v[k];
+          }
+        if (ua64 == 0.0 || ua == 0.f) continue;
+        const int sd = ua64 > 0.0 ? 1 : 0;
+        const int32_t fid = face_id(a, sd);
+        bool ex = false;
+        for (int q = 0; q < m; ++q) ex |= (eta[q] == fid);
+        if (ex) continue;
+        const float va = __double2float_rn(va64);
+        const float nf = (sd ? 1.f : 0.f) - va;
+        const float nfs = sd ? nf : -nf;
+        const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
+        const float au = fabsf(ua);
+        const float lo_n = nfs - ef, hi_n = nfs + ef;
+        const float tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
+                                      : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
+        const float thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
+                                      : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
+        T = fminf(T, thi);
+        if (nc < kCmax) {
+          cid[nc] = fid;
+          ctlo[nc] = tlo;
+          ++nc;
+        } else {
+          overflow = true;
+        }
+      }
+    }
+    Ball<D> ball;
+    make_ball<D>(g32, p32, u32, T, B, ball);
+    float far2 = far_radius2<D>(tr, ball, g32);
+    float wwx = ww_exit(far2, gam, EW, D);
+    // ---- list scan ----
+    const int32_t* lst = tr.knn + (int64_t)g * tr.K;
+    const int n = tr.kcnt[g];
+    bool certified = false;
+    int c = 0;
+    // software pipeline: the next candidate's id and coordinates are loaded
+    // while this one is screened, the id after that one further ahead
+    int32_t nid = n > 0 ? lst[0] : 0;
+    int32_t nnid = n > 1 ? lst[1] : 0;
+    float xn[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xn[k] = (k < d && n > 0) ? tr.X32[(int64_t)nid * d + k] : 0.f;
+    for (; c < n; ++c) {
+      const int32_t id = nid;
+      float xc[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) xc[k] = xn[k];
+      nid = nnid;
+      if (c + 2 < n) nnid = lst[c + 2];
+      if (c + 1 < n) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) xn[k] = k < d ? tr.X32[(int64_t)nid * d + k] : 0.f;
+      }
+      float w[D];
+      float den = 0.f, ww = 0.f, pw = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        w[k] = (k < d) ? xc[k] - g32[k] : 0.f;
+        den = fmaf(u32[k], w[k], den);
+        ww = fmaf(w[k], w[k], ww);
+      }
+      if (ww >= wwx) {  // then true_d2_lower(ww) >= far2: this and every later node lie outside
+        certified = true;
+        break;
+      }
+      if (hasp) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) pw = fmaf(p32[k], w[k], pw);
+      }
+      const float num = fmaf(-2.f, pw, ww);
+      const float wn = sqrtf(ww) * (1.f + gam);
+      const float Eden = fmaf(a1, wn, a0);
+      const float dh = den + Eden;
+      if (!(dh > 0.f)) continue;
+      const float Enum = fmaf(1.1f * kU32, fabsf(num), fmaf(1.1f * gam, ww, fmaf(b2, wn, b0c)));
+      const float nlo = num - Enum;
+      if (!(nlo <= 0.f || nlo <= 2.f * T * dh * (1.f + 8.f * kU32))) continue;
+      bool ok = true;  // the generators of eta are excluded by id
+      for (int q = 0; q < m; ++q) ok &= (id != eta[q]);
+      if (!ok) continue;
+      const float dl = den - Eden;
+      const float nhi = num + Enum;
+      float thi = INFINITY, tlo = -INFINITY;
+      if (dl > 0.f)
+        thi = nhi >= 0.f ? __fdiv_rn(nhi, 2.f * dl) * (1.f + 4.f * kU32)
+                         : __fdiv_rn(nhi, 2.f * dh) * (1.f - 4.f * kU32);
+      if (nlo > 0.f) tlo = __fdiv_rn(nlo, 2.f * dh) * (1.f - 4.f * kU32);
+      if (thi < T) {
+        T = thi;
+        make_ball<D>(g32, p32, u32, T, B, ball);
+        far2 = far_radius2<D>(tr, ball, g32);
+        wwx = ww_exit(far2, gam, EW, D);
+      }
+      if (!overflow && tlo <= T) {
+        if (nc == kCmax) {  // drop entries the bound has excluded
+          int k2 = 0;
+          for (int q = 0; q < kCmax; ++q)
+            if (ctlo[q] <= T) {
+              cid[k2] = cid[q];
+              ctlo[k2] = ctlo[q];
+              ++k2;
+            }
+          nc = k2;
+        }
+        if (nc < kCmax) {
+          cid[nc] = id;
+          ctlo[nc] = tlo;
+          ++nc;
+        } else {
+          overflow = true;
+        }
+      }
+    }
+    n_pairs += (unsigned long long)c;
+    if (!certified) certified = true_d2_lower(tr.kcert[g], gam, EW, D) >= far2;
+    const int64_t op = out_pos(rs, ro, r);
+    if (!certified) {  // finished by the tree walk, from the bound found so far
+      const unsigned long long k = atomicAdd(&ctr->fallback, 1ull);
+      if ((int64_t)k < ro.fallback_cap) ro.fallback_list[k] = (int32_t)r;
+      else atomicOr(&ctr->flags, kFlagQueue);
+      ro.t[op] = (double)T;
+      continue;
+    }
+    if (overflow) {  // redone on the binary64 path
+      const unsigned long long k = atomicAdd(&ctr->overflow, 1ull);
+      if ((int64_t)k < ro.overflow_cap) ro.overflow_list[k] = (int32_t)r;
+      else atomicOr(&ctr->flags, kFlagCandOverflow);
+      ++n_over;
+      ro.hit[op] = kNoId;
+      ro.t[op] = NAN;
+      continue;
+    }
+    // ---- binary64 recheck, canonical order ----
+    double bt = INFINITY;
+    int bc = 2, bk = 0;
+    for (int q = 0; q < nc; ++q) {
+      if (!(ctlo[q] <= T)) continue;
+      const int32_t id = cid[q];
+      ++n_rech;
+      if (id >= 0) {
+        double den = 0.0, ww = 0.0, pw = 0.0, w[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          w[k] = k < d ? __dadd_rn(tr.X[(int64_t)id * d + k], -tr.X[(int64_t)g * d + k]) : 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          if (k < d) den = __dadd_rn(den, __dmul_rn(u[k], w[k]));
+        if (!(den > 0.0)) continue;
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          if (k < d) ww = __dadd_rn(ww, __dmul_rn(w[k], w[k]));
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          if (k < d) pw = __dadd_rn(pw, __dmul_rn(__dadd_rn(v[k], -tr.X[(int64_t)g * d + k]), w[k]));
+        const double num = __dadd_rn(ww, -__dmul_rn(2.0, pw));
+        const double t = __ddiv_rn(num, __dmul_rn(2.0, den));
+        if (better(t, 0, id, bt, bc, bk)) {
+          bt = t;
+          bc = 0;
+          bk = id;
+        }
+      } else {
+        const int a = face_axis(id), sd = face_side(id);
+        double ua = 0.0, va = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          if (k == a) {
+            ua = u[k];
+            va = v[k];
+          }
+        const double t = __ddiv_rn(__dadd_rn(sd ? 1.0 : 0.0, -va), ua);
+        if (better(t, 1, 2 * a + sd, bt, bc, bk)) {
+          bt = t;
+          bc = 1;
+          bk = 2 * a + sd;
+        }
+      }
+    }
+    ro.hit[op] = gen_from_key(bc, bk);
+    ro.t[op] = bt;
+    if (ro.screen_err) ro.screen_err[op] = (bt > 0.0 && bt < INFINITY) ? (float)((T - bt) / bt) : 0.f;
+  }
+  for (int o = 16; o; o >>= 1) {
+    n_pairs += __shfl_xor_sync(kFull, n_pairs, o);
+    n_rech += __shfl_xor_sync(kFull, n_rech, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&ctr->pairs, n_pairs);
+    atomicAdd(&ctr->rechecked, n_rech);
+  }
+  (void)n_over;
+}
+
+// ------------------------------------------------------------------------
 // VD_FP64: every pair in binary64, canonical order
 // ------------------------------------------------------------------------
 template <int D, bool LIST>
@@ -696,6 +974,13 @@ cudaError_t launch_ray_d(const TreeView& tv, const RaySource& rs, const RayOut& 
   if (precision == VD_FP64) {
     if (list) go(k_ray_fp64<D, true>, sizeof(WarpF64<D>) * kWpb);
     else go(k_ray_fp64<D, false>, sizeof(WarpF64<D>) * kWpb);
+  } else if (list && subset == nullptr) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ray_list_thr<D>, kThrRays, 0);
+    const int64_t want = rs.R_dev ? (int64_t)nsm * std::max(occ, 1) : (nrays + kThrRays - 1) / kThrRays;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1), want));
+    k_ray_list_thr<D><<<(unsigned)grid, kThrRays, 0, st>>>(tv, r2, ro, ctr, work);
+    count_launch();
   } else {
     if (list) go(k_ray_mixed<D, true>, sizeof(WarpMixed<D>) * kWpb);
     else go(k_ray_mixed<D, false>, sizeof(WarpMixed<D>) * kWpb);

@@ -50,6 +50,7 @@ struct Tables {
   int32_t* eslot;    // [ehcap]
   int64_t ehmask;
   unsigned long long* ne;
+  int edet;          // edge entries indexed v (d+1) + q (ecap >= vcap (d+1))
 };
 
 __device__ __forceinline__ uint64_t mix64(uint64_t h) {
@@ -280,8 +281,10 @@ __device__ int edge_count(const Tables& T, const int32_t* eta) {
   return 0;
 }
 
-// G[eta] += 1, inserting eta if absent.
-__device__ void edge_increment(const Tables& T, const int32_t* eta, unsigned* flags) {
+// G[eta] += 1, inserting eta if absent.  A new entry takes index `entry`
+// (edge q of vertex v: v (d+1) + q, no shared counter) when entry >= 0, else
+// the next index of the shared counter.
+__device__ void edge_increment(const Tables& T, const int32_t* eta, int64_t entry, unsigned* flags) {
   const int L = T.d;
   uint64_t h = hash_tuple(eta, L) & (uint64_t)T.ehmask;
   int32_t mine = kEmpty;
@@ -289,7 +292,7 @@ __device__ void edge_increment(const Tables& T, const int32_t* eta, unsigned* fl
     int32_t s = vslot_load(&T.eslot[h]);
     if (s == kEmpty) {
       if (mine == kEmpty) {
-        const unsigned long long e = atomicAdd(T.ne, 1ull);
+        const unsigned long long e = entry >= 0 ? (unsigned long long)entry : atomicAdd(T.ne, 1ull);
         if ((int64_t)e >= T.ecap) {
           atomicOr(flags, kFlagHashFull);
           return;
@@ -334,15 +337,15 @@ __device__ __forceinline__ long long warp_append(bool want, unsigned long long* 
 // holds a node and has fewer than two known endpoints is appended to the
 // level's work list (cheap hash lookups; pass 2 then runs the binary64
 // SearchDirection on full warps).
-__global__ void k_expand_mark(Tables T, const int32_t* frontier, int64_t nf, int64_t* items,
-                              unsigned long long* nitems, int64_t rcap, unsigned* flags) {
+__global__ void k_expand_mark(Tables T, int64_t f0, int64_t nf, int64_t* items, unsigned long long* nitems,
+                              int64_t rcap, unsigned* flags) {
   const int d = T.d;
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool want = false;
   if (q < nf * (d + 1)) {
     const int64_t f = q / (d + 1);
     const int drop = (int)(q % (d + 1));
-    const int32_t v = frontier[f];
+    const int64_t v = f0 + f;
     int32_t eta[VD_MAX_D];
     int m = 0, hasnode = 0;
     for (int a = 0; a <= d; ++a)
@@ -366,7 +369,7 @@ __global__ void k_expand_mark(Tables T, const int32_t* frontier, int64_t nf, int
 // the vertex, direction = SearchDirection, eta = the edge (reference node
 // first).
 template <int D>
-__global__ void k_expand_dir(Tables T, const double* X, const int32_t* frontier, const int64_t* items,
+__global__ void k_expand_dir(Tables T, const double* X, int64_t f0, const int64_t* items,
                              const unsigned long long* nitems, int64_t rcap, double* ro, double* rd, int32_t* reta,
                              unsigned* flags) {
   const int d = T.d;
@@ -375,7 +378,7 @@ __global__ void k_expand_dir(Tables T, const double* X, const int32_t* frontier,
   const int64_t q = items[r];
   const int64_t f = q / (d + 1);
   const int drop = (int)(q % (d + 1));
-  const int32_t v = frontier[f];
+  const int64_t v = f0 + f;
   int32_t sig[D + 1], eta[D];
   for (int a = 0; a <= d; ++a) sig[a] = T.vt[(int64_t)v * (d + 1) + a];
   int m = 0;
@@ -446,15 +449,16 @@ __global__ void k_commit_claim(Tables T, const int32_t* reta, const int32_t* hit
 }
 
 // Phase 2: winners get vertex ids, coordinates, frontier slots and edges.
+// New vertex ids are consecutive, so the next frontier is the id range the
+// level added.
 template <int D>
 __global__ void k_commit_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot,
-                                const int32_t* win, int64_t nwcap, const unsigned long long* nwin, int32_t* next,
-                                unsigned long long* nnext, unsigned* flags) {
+                                const int32_t* win, int64_t nwcap, const unsigned long long* nwin, unsigned* flags) {
   const int d = T.d, L = d + 1;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= min(nwcap, (int64_t)*nwin)) return;
   const int64_t r = win[p];
-  const unsigned long long v = atomicAdd(T.nv, 1ull);
+  const long long v = warp_append(true, T.nv);
   if ((int64_t)v >= T.vcap) {
     atomicOr(flags, kFlagHashFull);
     return;
@@ -467,7 +471,6 @@ __global__ void k_commit_finish(Tables T, const double* X, const int32_t* cand, 
   for (int a = 0; a < d; ++a) T.vx[(int64_t)v * d + a] = x[a];
   __threadfence();
   T.vslot[cslot[r]] = (int32_t)v;
-  next[atomicAdd(nnext, 1ull)] = (int32_t)v;
   for (int q = 0; q <= d; ++q) {
     int32_t eta[D];
     int m = 0, hasnode = 0;
@@ -476,7 +479,7 @@ __global__ void k_commit_finish(Tables T, const double* X, const int32_t* cand, 
         eta[m++] = sig[a];
         hasnode |= sig[a] >= 0;
       }
-    if (hasnode) edge_increment(T, eta, flags);
+    if (hasnode) edge_increment(T, eta, T.edet ? (int64_t)v * L + q : -1, flags);
   }
 }
 
@@ -623,21 +626,19 @@ inline unsigned nb(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(
 // The level's rays: nf frontier vertices -> work list -> ray arrays (count
 // *nrays on the device, at most min(nf (d+1), rcap)).
 template <int D>
-void launch_expand(Tables T, const double* X, const int32_t* front, int64_t nf, int64_t* items, double* ro,
-                   double* rd, int32_t* reta, unsigned long long* nrays, int64_t rcap, unsigned* flags,
-                   cudaStream_t st) {
+void launch_expand(Tables T, const double* X, int64_t f0, int64_t nf, int64_t* items, double* ro, double* rd,
+                   int32_t* reta, unsigned long long* nrays, int64_t rcap, unsigned* flags, cudaStream_t st) {
   const int64_t n = nf * (T.d + 1);
-  k_expand_mark<<<nb(n), 256, 0, st>>>(T, front, nf, items, nrays, rcap, flags);
+  k_expand_mark<<<nb(n), 256, 0, st>>>(T, f0, nf, items, nrays, rcap, flags);
   count_launch();
-  k_expand_dir<D><<<nb(std::min(n, rcap), 128), 128, 0, st>>>(T, X, front, items, nrays, rcap, ro, rd, reta, flags);
+  k_expand_dir<D><<<nb(std::min(n, rcap), 128), 128, 0, st>>>(T, X, f0, items, nrays, rcap, ro, rd, reta, flags);
   count_launch();
 }
 
 template <int D>
 void launch_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot, const int32_t* win,
-                   int64_t nwcap, const unsigned long long* nwin, int32_t* next, unsigned long long* nnext,
-                   unsigned* flags, cudaStream_t st) {
-  k_commit_finish<D><<<nb(nwcap), 256, 0, st>>>(T, X, cand, cslot, win, nwcap, nwin, next, nnext, flags);
+                   int64_t nwcap, const unsigned long long* nwin, unsigned* flags, cudaStream_t st) {
+  k_commit_finish<D><<<nb(nwcap), 256, 0, st>>>(T, X, cand, cslot, win, nwcap, nwin, flags);
   count_launch();
 }
 
@@ -693,12 +694,16 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
                                                                                        64.0 * (1 << std::min(d, 16)) +
                                                                                        8.0 * N * d));
   vcap = std::min<int64_t>(vcap, (int64_t)1 << 30);
-  const int64_t ecap = std::min<int64_t>((int64_t)1 << 30, vcap * L / 2 + vcap / 4 + 1024);
-  const int64_t vh = pow2_at_least(2 * vcap), eh = pow2_at_least(2 * ecap);
+  // expected edges ~ V (d+1) / 2; entries indexed v (d+1) + q while that fits
+  const int64_t ehint = std::min<int64_t>((int64_t)1 << 30, vcap * L / 2 + vcap / 4 + 1024);
+  const bool edet = vcap * L < ((int64_t)1 << 31);
+  const int64_t ecap = edet ? vcap * L : ehint;
+  const int64_t vh = pow2_at_least(2 * vcap), eh = pow2_at_least(2 * ehint);
   Tables T;
   T.d = d;
   T.vcap = vcap;
   T.ecap = ecap;
+  T.edet = edet ? 1 : 0;
   T.vhmask = vh - 1;
   T.ehmask = eh - 1;
   VD_TRY(ws.get_n(kVt, (size_t)vcap * L, &T.vt));
@@ -707,7 +712,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   VD_TRY(ws.get_n(kEt, (size_t)ecap * d, &T.et));
   VD_TRY(ws.get_n(kEcnt, (size_t)ecap, &T.ecnt));
   VD_TRY(ws.get_n(kEslot, (size_t)eh, &T.eslot));
-  unsigned long long* cnts = nullptr;  // nv, ne, nrays, nnext, nwin
+  unsigned long long* cnts = nullptr;  // nv, ne, nrays, (unused), nwin
   VD_TRY(ws.get_n(kCnts, 5, &cnts));
   T.nv = cnts + 0;
   T.ne = cnts + 1;
@@ -821,14 +826,10 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     VD_TRY(cudaGetLastError());
   }
   k_descent_cand<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, alive, reta, rhit); count_launch();
-  // frontiers: each holds the vertices created by one level (at most vcap)
-  int32_t *front = nullptr, *next = nullptr;
-  VD_TRY(ws.get_n(kFront, (size_t)vcap, &front));
-  VD_TRY(ws.get_n(kNext, (size_t)vcap, &next));
+  // a level's frontier is the id range of the vertices the previous level added
   unsigned long long* nrays = cnts + 2;
-  unsigned long long* nnext = cnts + 3;
   unsigned long long* nwin = cnts + 4;
-  VD_TRY(cudaMemsetAsync(nnext, 0, 2 * sizeof(unsigned long long), st));
+  VD_TRY(cudaMemsetAsync(nwin, 0, sizeof(unsigned long long), st));
   k_commit_claim<<<nb(ns), 256, 0, st>>>(T, reta, rhit, ns, nullptr, cand, cslot, win, nwin, flags); count_launch();
   // seeds that did not reach a vertex were marked with hit = kNoId: clear the
   // degenerate flag they raised (a missing seed is not an error)
@@ -841,11 +842,12 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
       VD_TRY(cudaMemcpyAsync(flags, &clr, sizeof(unsigned), cudaMemcpyHostToDevice, st));
     }
   }
-  VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, ns, nwin, front, nnext, flags, st);
+  VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, ns, nwin, flags, st);
   unsigned long long hn2[4];
   VD_TRY(cudaMemcpyAsync(hn2, cnts, sizeof(hn2), cudaMemcpyDeviceToHost, st));
   VD_TRY(cudaStreamSynchronize(st));
-  int64_t nf = (int64_t)hn2[3];
+  int64_t f0 = 0;
+  int64_t nf = std::min<int64_t>((int64_t)hn2[0], vcap);
   if (nf == 0) {
     snprintf(err, errlen, "Descent found no seed vertex");
     return cudaErrorUnknown;
@@ -862,13 +864,13 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     const int64_t ncap = nf * L;  // at most one ray per (frontier vertex, edge)
     VD_TRY(grow(ncap));
     VD_TRY(cudaMemsetAsync(cnts + 2, 0, 3 * sizeof(unsigned long long), st));
-    VD_TRAV_D(d, launch_expand, T, tv.X, front, nf, items, ro, rd, reta, nrays, rcap, flags, st);
+    VD_TRAV_D(d, launch_expand, T, tv.X, f0, nf, items, ro, rd, reta, nrays, rcap, flags, st);
     VD_TRY(cudaGetLastError());
     const int64_t rmax = std::min(ncap, rcap);
     VD_TRY(cast(rmax, nrays, d));
     k_commit_claim<<<nb(rmax), 256, 0, st>>>(T, reta, rhit, rmax, nrays, cand, cslot, win, nwin, flags);
     count_launch();
-    VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, rmax, nwin, next, nnext, flags, st);
+    VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, rmax, nwin, flags, st);
     VD_TRY(cudaGetLastError());
     unsigned long long hc[5];
     unsigned hf = 0;
@@ -879,8 +881,9 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     account(hc + 4);
     raycasts += (int64_t)std::min<unsigned long long>(hc[2], (unsigned long long)rcap);
     if (hf & (kFlagHashFull | kFlagQueue | kFlagDegenerate | kFlagCandOverflow | kFlagBadInput)) break;
-    nf = (int64_t)hc[3];
-    std::swap(front, next);
+    const int64_t nv_now = std::min<int64_t>((int64_t)hc[0], vcap);
+    nf = nv_now - (f0 + nf);
+    f0 = nv_now - nf;
   }
   unsigned long long hc[4];
   VD_TRY(cudaMemcpyAsync(hc, cnts, sizeof(hc), cudaMemcpyDeviceToHost, st));

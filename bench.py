@@ -363,7 +363,7 @@ def run_ours(args):
     achieved = rays * flops_per_ray / (rc_ms / 1000.0) / 1e12 if rc_ms > 0 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": (achieved / peak_tflops) if achieved else None, "traffic": None,
-                "kernel": "k_ray_mixed<5> (binary32 screening + binary64 recheck)",
+                "kernel": "k_ray_list_thr<5> + tree-walk follow-up (binary32 screening + binary64 recheck)",
                 "peak_source": f"FP32 lanes x 2 x sm_max_mhz ({src} peaks file)",
                 "algorithmic_flops_per_ray": flops_per_ray, "raycast_ms_per_step": rc_ms / args.steps}
 

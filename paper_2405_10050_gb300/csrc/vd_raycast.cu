@@ -1000,11 +1000,87 @@ cudaError_t launch_ray_d(const TreeView& tv, const RaySource& rs, const RayOut& 
 constexpr int kKnnCap = 2048;
 constexpr int kKnnWpb = 4;
 
+constexpr int kKnnTies = 64;
+
 struct WarpKnn {
   float key[kKnnCap];
   int32_t id[kKnnCap];
   int stk[kStk];
+  int hist[256];
+  int32_t tie[kKnnTies];
 };
+
+// Bitonic sort of S.key/S.id[0, P) by (key, id), P a power of two.
+__device__ __forceinline__ void knn_sort(WarpKnn& S, int P, int lane) {
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = lane; i < P / 2; i += 32) {
+        const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
+        const bool asc = (lo & size) == 0;
+        const float ka = S.key[lo], kb = S.key[hi];
+        const int32_t ia = S.id[lo], ib = S.id[hi];
+        const bool gt = ka > kb || (ka == kb && ia > ib);
+        if (asc == gt) {
+          S.key[lo] = kb;
+          S.key[hi] = ka;
+          S.id[lo] = ib;
+          S.id[hi] = ia;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Key of rank k (0-based) among S.key[0, n) (non-negative floats, whose bit
+// patterns order like the values): most-significant-byte-first radix select.
+__device__ __forceinline__ float knn_select(WarpKnn& S, int n, int k, int lane) {
+  uint32_t prefix = 0, high = 0;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int b = lane; b < 256; b += 32) S.hist[b] = 0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const uint32_t bits = __float_as_uint(S.key[i]);
+      if ((bits & high) == prefix) atomicAdd(&S.hist[(bits >> shift) & 255u], 1);
+    }
+    __syncwarp();
+    int c[8], tot = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      c[j] = S.hist[lane * 8 + j];
+      tot += c[j];
+    }
+    int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int excl = incl - tot;
+    const bool mine = k >= excl && k < incl;
+    const unsigned who = __ballot_sync(kFull, mine);
+    const int src = __ffs(who) - 1;
+    int digit = 0, before = 0;
+    if (mine) {
+      int run = excl;
+      for (int j = 0; j < 8; ++j) {
+        if (k < run + c[j]) {
+          digit = lane * 8 + j;
+          before = run;
+          break;
+        }
+        run += c[j];
+      }
+    }
+    digit = __shfl_sync(kFull, digit, src);
+    before = __shfl_sync(kFull, before, src);
+    k -= before;
+    prefix |= (uint32_t)digit << shift;
+    high |= 255u << shift;
+    __syncwarp();
+  }
+  return __uint_as_float(prefix);
+}
 
 template <int D>
 __global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, float r0, float rmax, int32_t* knn,
@@ -1066,36 +1142,75 @@ __global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, 
       }
       continue;
     }
+    // keep the K smallest by (key, id): select the key of rank K, keep the
+    // smaller keys and the smallest ids among the keys equal to it, then
+    // sort only those K
+    int n_sort = count;
+    float cert = r * r;
+    if (count > K) {
+      const float tk = knn_select(S, count, K, lane);
+      cert = tk;
+      int nless = 0, ntie = 0;
+      for (int c0 = 0; c0 < count; c0 += 32) {
+        const int c = c0 + lane;
+        const float kc = c < count ? S.key[c] : INFINITY;
+        const int32_t ic = c < count ? S.id[c] : 0;
+        const bool less = kc < tk, tie = kc == tk;
+        const unsigned lm = __ballot_sync(kFull, less), tm = __ballot_sync(kFull, tie);
+        __syncwarp();
+        if (less) {
+          const int pos = nless + __popc(lm & lt);
+          S.key[pos] = kc;
+          S.id[pos] = ic;
+        }
+        if (tie) {
+          const int pos = ntie + __popc(tm & lt);
+          if (pos < kKnnTies) S.tie[pos] = ic;
+        }
+        nless += __popc(lm);
+        ntie += __popc(tm);
+        __syncwarp();
+      }
+      const int need = K - nless;  // 1 <= need <= ntie
+      if (ntie > kKnnTies) {       // massive ties: no list for this node, tree walk only
+        if (lane == 0) {
+          kcnt[g] = 0;
+          kcert[g] = 0.f;
+        }
+        __syncwarp();
+        continue;
+      }
+      if (lane == 0) {  // the need smallest ids among the ties (usually one)
+        for (int a = 1; a < ntie; ++a) {
+          const int32_t x = S.tie[a];
+          int b = a - 1;
+          while (b >= 0 && S.tie[b] > x) {
+            S.tie[b + 1] = S.tie[b];
+            --b;
+          }
+          S.tie[b + 1] = x;
+        }
+        for (int a = 0; a < need; ++a) {
+          S.key[nless + a] = tk;
+          S.id[nless + a] = S.tie[a];
+        }
+      }
+      __syncwarp();
+      n_sort = K;
+    }
     int P = 1;
-    while (P < count) P <<= 1;
-    for (int i = count + lane; i < P; i += 32) {
+    while (P < n_sort) P <<= 1;
+    for (int i = n_sort + lane; i < P; i += 32) {
       S.key[i] = INFINITY;
       S.id[i] = INT32_MAX;
     }
     __syncwarp();
-    for (int size = 2; size <= P; size <<= 1) {
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int i = lane; i < P / 2; i += 32) {
-          const int lo = 2 * stride * (i / stride) + (i % stride), hi = lo + stride;
-          const bool asc = (lo & size) == 0;
-          const float ka = S.key[lo], kb = S.key[hi];
-          const int32_t ia = S.id[lo], ib = S.id[hi];
-          const bool gt = ka > kb || (ka == kb && ia > ib);
-          if (asc == gt) {
-            S.key[lo] = kb;
-            S.key[hi] = ka;
-            S.id[lo] = ib;
-            S.id[hi] = ia;
-          }
-        }
-        __syncwarp();
-      }
-    }
+    knn_sort(S, P, lane);
     const int nk = min(count, K);
     for (int c = lane; c < nk; c += 32) knn[g * K + c] = S.id[c];
     if (lane == 0) {
       kcnt[g] = nk;
-      kcert[g] = count > K ? S.key[K] : r * r;
+      kcert[g] = cert;
     }
     __syncwarp();
   }

@@ -215,11 +215,13 @@ __device__ void fill_item(const double* X, int d, int64_t i, int64_t R, uint64_t
       const int m = gather_rays(h, R, id, &k0, L, lane);
       for (int p = lane; p < m; p += 32) {
         const int32_t k = L[p];
-        s = __dadd_rn(s, area_term<D>(X, d, i, k, id, li[k], seed, set));
+        // node hit: the factor 2 / |x_j - x_i| is applied once per id below
+        s = __dadd_rn(s, id >= 0 ? ipow_d(li[k], d) : area_term<D>(X, d, i, k, id, li[k], seed, set));
       }
       __syncwarp();
     }
     s = warp_sum_d(s);
+    if (id >= 0) s = node_area_term<D>(X, d, i, id, s);
     if (lane == 0) {
       col[q] = id;
       A[q] = __dmul_rn(cA, s);
@@ -450,17 +452,58 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
     double acc[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) acc[c] = 0.0;
-    int64_t k0 = 0;
-    while (k0 < R) {
-      const int m = gather_rays(h, R, id, &k0, L, lane);
-      for (int p = lane; p < m; p += 32) {
-        const int32_t k = L[p];
-        adj_contrib<D>(X, d, i, k, id, li[k], gVi, gAij, cV, cA, seed, set, acc);
-      }
-      __syncwarp();
-    }
+    if (id >= 0) {
+      // node hit: every ray adds a_k w - b_k u_k (w = x_j - x_i is the entry's),
+      // so the rays accumulate the scalar sum of a_k and the vector of b_k u_k
+      double w[D], ww = 0.0;
 #pragma unroll
-    for (int c = 0; c < D; ++c) acc[c] = warp_sum_d(acc[c]);
+      for (int c = 0; c < D; ++c) w[c] = c < d ? __dadd_rn(X[(int64_t)id * d + c], -X[i * d + c]) : 0.0;
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        if (c < d) ww = __dadd_rn(ww, __dmul_rn(w[c], w[c]));
+      const double inw = rsqrt(ww);
+      const double kA = gAij * cA;
+      const double cwa = 2.0 * (double)d * inw, cwb = 2.0 * inw * inw * inw;
+      double asum = 0.0, bu[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) bu[c] = 0.0;
+      int64_t k0 = 0;
+      while (k0 < R) {
+        const int m = gather_rays(h, R, id, &k0, L, lane);
+        for (int p = lane; p < m; p += 32) {
+          const int32_t k = L[p];
+          const double lk = li[k];
+          double u[D];
+          mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
+          double den = 0.0;
+#pragma unroll
+          for (int c = 0; c < D; ++c)
+            if (c < d) den = __dadd_rn(den, __dmul_rn(u[c], w[c]));
+          const double ld1 = ipow_d(lk, d - 1), ld = ld1 * lk;
+          const double g = (gVi * cV * (double)d * ld1 + kA * cwa * ld1) / den;  // coefficient of dl
+          asum += g - kA * cwb * ld;
+          const double b = g * lk;
+#pragma unroll
+          for (int c = 0; c < D; ++c) bu[c] += b * u[c];
+        }
+        __syncwarp();
+      }
+      asum = warp_sum_d(asum);
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc[c] = c < d ? asum * w[c] - warp_sum_d(bu[c]) : 0.0;
+    } else {
+      int64_t k0 = 0;
+      while (k0 < R) {
+        const int m = gather_rays(h, R, id, &k0, L, lane);
+        for (int p = lane; p < m; p += 32) {
+          const int32_t k = L[p];
+          adj_contrib<D>(X, d, i, k, id, li[k], gVi, gAij, cV, cA, seed, set, acc);
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc[c] = warp_sum_d(acc[c]);
+    }
     if (id >= 0) {
       if (lane == 0)
         for (int c = 0; c < d; ++c) P[q * d + c] = acc[c];

@@ -16,10 +16,12 @@ namespace vd {
 cudaError_t mc_rowptr(const int32_t* hit, int64_t N, int64_t R, int64_t* cnt_scratch, int64_t* rowptr,
                       int64_t* nnz_host, cudaStream_t st);
 cudaError_t mc_fill(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set, const int32_t* hit,
-                    const double* l, const int64_t* rowptr, double* V, int32_t* col, double* A, cudaStream_t st);
+                    const double* l, const int64_t* rowptr, double* V, int32_t* col, double* A, const double* U,
+                    cudaStream_t st);
 cudaError_t mc_adjoint(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
                        const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, int64_t nnz,
-                       const double* gV, const double* gA, double* gX, DevBufs& scratch, cudaStream_t st);
+                       const double* gV, const double* gA, double* gX, const double* U, DevBufs& scratch,
+                       cudaStream_t st);
 cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, Workspace& ws,
                               DevBufs& out_bufs, int32_t** tuples, double** coords, int64_t* nv, vd_stats* stats,
                               Counters* ctr, cudaStream_t st, char* err, size_t errlen);
@@ -47,6 +49,7 @@ struct vd_ctx {
   DevBufs own;
   int batch_threads[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // autotuned block size by largest d
   vd::Workspace trav_ws;  // traversal tables and level buffers, reused across vd_vertices calls
+  vd::Workspace mc_ws;    // MC work lists, reused across vd_mc_integrate calls
 };
 
 struct vd_mesh {
@@ -69,6 +72,7 @@ struct vd_mc {
   double* X = nullptr;
   int32_t* hit = nullptr;
   double* l = nullptr;
+  double* u = nullptr;  // ray directions kept from the forward pass (or null: drawn again)
   double* V = nullptr;
   int64_t* rowptr = nullptr;
   int32_t* col = nullptr;
@@ -214,6 +218,7 @@ void vd_destroy(vd_ctx* ctx) {
   ctx->node_bufs.release();
   ctx->own.release();
   ctx->trav_ws.release();
+  ctx->mc_ws.release();
   delete ctx;
 }
 
@@ -380,17 +385,18 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
   VD_CK(mc->bufs.alloc_n(&mc->l, (size_t)N * R), "mc alloc");
   VD_CK(mc->bufs.alloc_n(&mc->V, (size_t)N), "mc alloc");
   VD_CK(mc->bufs.alloc_n(&mc->rowptr, (size_t)N + 1), "mc alloc");
-  DevBufs tmp;
-  struct Guard {
-    DevBufs& b;
-    ~Guard() { b.release(); }
-  } guard{tmp};
   int32_t *ovl = nullptr, *fbl = nullptr;
   int64_t* cnt = nullptr;
   const int64_t ovcap = std::max<int64_t>(4096, N * R / 64);
-  VD_CK(tmp.alloc_n(&ovl, ovcap), "alloc");
-  VD_CK(tmp.alloc_n(&fbl, N * R), "alloc");
-  VD_CK(tmp.alloc_n(&cnt, N), "alloc");
+  VD_CK(ctx->mc_ws.get_n(0, ovcap, &ovl), "alloc");
+  VD_CK(ctx->mc_ws.get_n(1, N * R, &fbl), "alloc");
+  VD_CK(ctx->mc_ws.get_n(2, N, &cnt), "alloc");
+  const int prec = effective_precision(ctx);
+  // the cell kernels keep each ray's binary64 direction for the fill and the
+  // adjoint (8 d bytes per ray) unless that would exceed 16 GiB
+  const bool cells = tv.K > 0 && prec != VD_FP64;
+  if (cells && (double)N * R * d * 8.0 <= 16.0 * (1ull << 30))
+    VD_CK(mc->bufs.alloc_n(&mc->u, (size_t)N * R * d), "mc alloc");
   vd::RaySource rs;
   rs.mode = 1;
   rs.R = N * R;
@@ -406,12 +412,12 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
   ro.overflow_cap = ovcap;
   ro.fallback_list = fbl;
   ro.fallback_cap = N * R;
+  ro.u = mc->u;
   VD_CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->st), "memset");
   const long long l0 = vd::g_launches.load();
   Timer tm(ctx->st);
   {
     Timer tr(ctx->st);
-    const int prec = effective_precision(ctx);
     if (tv.K > 0 && prec == VD_TC16 && tv.coord_abs <= vd::kTcCoordMax)
       VD_CK(vd::launch_mc_cells_tc(tv, R, seed, set, ro, ctx->ctr, ctx->cfg.wait_limit, ctx->st,
                                    &mc->stats.fallback_rays),
@@ -432,7 +438,8 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
   mc->nnz = nnz;
   VD_CK(mc->bufs.alloc_n(&mc->col, (size_t)std::max<int64_t>(nnz, 1)), "mc alloc");
   VD_CK(mc->bufs.alloc_n(&mc->A, (size_t)std::max<int64_t>(nnz, 1)), "mc alloc");
-  VD_CK(vd::mc_fill(Xd, N, d, R, seed, set, mc->hit, mc->l, mc->rowptr, mc->V, mc->col, mc->A, ctx->st), "mc fill");
+  VD_CK(vd::mc_fill(Xd, N, d, R, seed, set, mc->hit, mc->l, mc->rowptr, mc->V, mc->col, mc->A, mc->u, ctx->st),
+        "mc fill");
   mc->stats.ms = tm.stop();
   mc->stats.launches = vd::g_launches.load() - l0;
   Counters hc;
@@ -532,7 +539,7 @@ vd_status vd_mc_adjoint(const vd_mc* mc, const double* gV, const double* gA, dou
   if (e == cudaSuccess && !on_device) e = tmp.alloc_n(&gXd, (size_t)mc->N * mc->d);
   if (e == cudaSuccess)
     e = vd::mc_adjoint(mc->X, mc->N, mc->d, mc->R, mc->seed, mc->set, mc->hit, mc->l, mc->rowptr, mc->col, mc->nnz,
-                       gVd, gAd, gXd, tmp, mc->st);
+                       gVd, gAd, gXd, mc->u, tmp, mc->st);
   if (e == cudaSuccess && !on_device)
     e = cudaMemcpyAsync(gX, gXd, (size_t)mc->N * mc->d * sizeof(double), cudaMemcpyDeviceToHost, mc->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(mc->st);

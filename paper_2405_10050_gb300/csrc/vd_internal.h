@@ -92,6 +92,7 @@ struct RayOut {
   int64_t overflow_cap = 0;
   int32_t* fallback_list = nullptr;  // rays the candidate lists could not certify
   int64_t fallback_cap = 0;
+  double* u = nullptr;  // MC cell kernels: each ray's binary64 direction (row cell * mc_rpc + ray, d values)
 };
 
 struct Counters {

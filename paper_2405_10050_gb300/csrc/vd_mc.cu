@@ -58,6 +58,20 @@ __device__ __forceinline__ int32_t next_id(const int32_t* h, int64_t R, int32_t 
   return best;
 }
 
+// Direction of ray k of cell i: read from the forward pass's copy U (row
+// i R + k, d values) when it was kept, else drawn again (the same bits).
+template <int D>
+__device__ __forceinline__ void ray_dir(const double* U, uint64_t seed, uint32_t set, int64_t i, int64_t k, int64_t R,
+                                        int d, double (&u)[D]) {
+  if (U) {
+    const double* p = U + (i * R + k) * d;
+#pragma unroll
+    for (int c = 0; c < D; ++c) u[c] = c < d ? p[c] : 0.0;
+  } else {
+    mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
+  }
+}
+
 // position of hit id in the row's ascending ids col[q0 .. q0 + n)
 __device__ __forceinline__ int64_t entry_of(const int32_t* col, int64_t q0, int64_t n, int32_t id) {
   int64_t lo = 0, hi = n - 1;
@@ -152,10 +166,10 @@ __device__ __forceinline__ int gather_rays(const int32_t* h, int64_t R, int32_t 
 // Area term of ray k of cell i that hit id.
 template <int D>
 __device__ __forceinline__ double area_term(const double* X, int d, int64_t i, int64_t k, int32_t id, double lk,
-                                            uint64_t seed, uint32_t set) {
+                                            uint64_t seed, uint32_t set, const double* U, int64_t R) {
   if (id >= 0) return node_area_term<D>(X, d, i, id, ipow_d(lk, d));
   double u[D];
-  mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
+  ray_dir<D>(U, seed, set, i, k, R, d, u);
   const int a = face_axis(id);
   double ua = 0.0;
 #pragma unroll
@@ -167,7 +181,8 @@ __device__ __forceinline__ double area_term(const double* X, int d, int64_t i, i
 template <int D>
 __device__ void fill_item(const double* X, int d, int64_t i, int64_t R, uint64_t seed, uint32_t set,
                           const int32_t* hit, const double* l, const int64_t* rowptr, double cV, double cA, double* V,
-                          int32_t* col, double* A, int32_t* L, double* Ts, int32_t* Es, int lane) {
+                          int32_t* col, double* A, int32_t* L, double* Ts, int32_t* Es, int lane,
+                          const double* U = nullptr) {
   const int32_t* h = hit + i * R;
   const double* li = l + i * R;
   double vs = 0.0;
@@ -196,7 +211,7 @@ __device__ void fill_item(const double* X, int d, int64_t i, int64_t R, uint64_t
       if (k < R) {
         const int32_t id = h[k];
         Es[lane] = (int32_t)(entry_of(col, q0, nnz, id) - q0);
-        Ts[lane] = area_term<D>(X, d, i, k, id, li[k], seed, set);
+        Ts[lane] = area_term<D>(X, d, i, k, id, li[k], seed, set, U, R);
       }
       __syncwarp();
       if (lane == 0)
@@ -216,7 +231,7 @@ __device__ void fill_item(const double* X, int d, int64_t i, int64_t R, uint64_t
       for (int p = lane; p < m; p += 32) {
         const int32_t k = L[p];
         // node hit: the factor 2 / |x_j - x_i| is applied once per id below
-        s = __dadd_rn(s, id >= 0 ? ipow_d(li[k], d) : area_term<D>(X, d, i, k, id, li[k], seed, set));
+        s = __dadd_rn(s, id >= 0 ? ipow_d(li[k], d) : area_term<D>(X, d, i, k, id, li[k], seed, set, U, R));
       }
       __syncwarp();
     }
@@ -236,7 +251,8 @@ template <int D>
 __global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill(const double* X, int64_t N, int d, int64_t R,
                                                            uint64_t seed, uint32_t set, const int32_t* hit,
                                                            const double* l, const int64_t* rowptr, double cV,
-                                                           double cA, double* V, int32_t* col, double* A) {
+                                                           double cA, double* V, int32_t* col, double* A,
+                                                           const double* U) {
   __shared__ int32_t Ls[kMcWarps][kMcList];
   __shared__ double Ts[kMcWarps][32];
   __shared__ int32_t Es[kMcWarps][32];
@@ -244,7 +260,7 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill(const double* X, int6
   const int lane = threadIdx.x & 31;
   if (i >= N) return;
   const int w = threadIdx.x >> 5;
-  fill_item<D>(X, d, i, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, Ls[w], Ts[w], Es[w], lane);
+  fill_item<D>(X, d, i, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, Ls[w], Ts[w], Es[w], lane, U);
 }
 
 // ---- batched reduction over many sets (items = all cells of all sets) ----
@@ -342,9 +358,9 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill_batch(const SetDesc* 
 template <int D>
 __device__ __forceinline__ void adj_contrib(const double* X, int d, int64_t i, int64_t k, int32_t id, double lk,
                                             double gVi, double gAij, double cV, double cA, uint64_t seed,
-                                            uint32_t set, double (&acc)[D]) {
+                                            uint32_t set, const double* U, int64_t R, double (&acc)[D]) {
   double u[D];
-  mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
+  ray_dir<D>(U, seed, set, i, k, R, d, u);
   const double ld1 = ipow_d(lk, d - 1), ld = ipow_d(lk, d);
   if (id >= 0) {
     double w[D], den = 0.0, ww = 0.0;
@@ -392,7 +408,7 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
                                                                const double* l, const int64_t* rowptr,
                                                                const int32_t* col, double cV, double cA,
                                                                const double* gV, const double* gA, double* P,
-                                                               double* own) {
+                                                               double* own, const double* U) {
   __shared__ int32_t Ls[kMcWarps][kMcList];
   __shared__ double Cs[kMcWarps][32][D + 1];
   __shared__ int32_t Es[kMcWarps][32];
@@ -416,7 +432,7 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
         double v[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) v[c] = 0.0;
-        adj_contrib<D>(X, d, i, k, id, li[k], gVi, gA ? gA[q] : 0.0, cV, cA, seed, set, v);
+        adj_contrib<D>(X, d, i, k, id, li[k], gVi, gA ? gA[q] : 0.0, cV, cA, seed, set, U, R, v);
 #pragma unroll
         for (int c = 0; c < D; ++c) Cs[wb][lane][c] = v[c];
         Es[wb][lane] = (int32_t)(q - q0);
@@ -474,7 +490,7 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
           const int32_t k = L[p];
           const double lk = li[k];
           double u[D];
-          mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u);
+          ray_dir<D>(U, seed, set, i, k, R, d, u);
           double den = 0.0;
 #pragma unroll
           for (int c = 0; c < D; ++c)
@@ -497,7 +513,7 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
         const int m = gather_rays(h, R, id, &k0, L, lane);
         for (int p = lane; p < m; p += 32) {
           const int32_t k = L[p];
-          adj_contrib<D>(X, d, i, k, id, li[k], gVi, gAij, cV, cA, seed, set, acc);
+          adj_contrib<D>(X, d, i, k, id, li[k], gVi, gAij, cV, cA, seed, set, U, R, acc);
         }
         __syncwarp();
       }
@@ -555,17 +571,21 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (
 template <int D>
 cudaError_t fill_d(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set, const int32_t* hit,
                    const double* l, const int64_t* rowptr, double cV, double cA, double* V, int32_t* col, double* A,
-                   cudaStream_t st) {
-  k_mc_fill<D><<<nblk(N * 32, kMcWarps * 32), kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A); count_launch();
+                   const double* U, cudaStream_t st) {
+  k_mc_fill<D><<<nblk(N * 32, kMcWarps * 32), kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V,
+                                                                      col, A, U);
+  count_launch();
   return cudaGetLastError();
 }
 
 template <int D>
 cudaError_t adj_rows_d(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
                        const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, double cV,
-                       double cA, const double* gV, const double* gA, double* P, double* own, cudaStream_t st) {
-  k_mc_adj_rows<D><<<nblk(N * 32, kMcWarps * 32), kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P,
-                                                       own); count_launch();
+                       double cA, const double* gV, const double* gA, double* P, double* own, const double* U,
+                       cudaStream_t st) {
+  k_mc_adj_rows<D><<<nblk(N * 32, kMcWarps * 32), kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col,
+                                                                          cV, cA, gV, gA, P, own, U);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -597,17 +617,19 @@ cudaError_t mc_rowptr(const int32_t* hit, int64_t N, int64_t R, int64_t* cnt_scr
 }
 
 cudaError_t mc_fill(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set, const int32_t* hit,
-                    const double* l, const int64_t* rowptr, double* V, int32_t* col, double* A, cudaStream_t st) {
+                    const double* l, const int64_t* rowptr, double* V, int32_t* col, double* A, const double* U,
+                    cudaStream_t st) {
   const double S = sphere_area(d);
   const double cV = S / ((double)d * (double)R), cA = S / (double)R;
-  if (d <= 4) return fill_d<4>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, st);
-  if (d <= 8) return fill_d<8>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, st);
-  return fill_d<16>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, st);
+  if (d <= 4) return fill_d<4>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, U, st);
+  if (d <= 8) return fill_d<8>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, U, st);
+  return fill_d<16>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, U, st);
 }
 
 cudaError_t mc_adjoint(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
                        const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, int64_t nnz,
-                       const double* gV, const double* gA, double* gX, DevBufs& scratch, cudaStream_t st) {
+                       const double* gV, const double* gA, double* gX, const double* U, DevBufs& scratch,
+                       cudaStream_t st) {
   const double S = sphere_area(d);
   const double cV = S / ((double)d * (double)R), cA = S / (double)R;
   double *P = nullptr, *own = nullptr;
@@ -622,9 +644,9 @@ cudaError_t mc_adjoint(const double* X, int64_t N, int d, int64_t R, uint64_t se
       (e = scratch.alloc_n(&vtmp, nn)) || (e = scratch.alloc_n(&counts, (size_t)256 * (nn / 4096 + 2))) ||
       (e = scratch.alloc_n(&orand, 2)))
     return e;
-  if (d <= 4) e = adj_rows_d<4>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P, own, st);
-  else if (d <= 8) e = adj_rows_d<8>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P, own, st);
-  else e = adj_rows_d<16>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P, own, st);
+  if (d <= 4) e = adj_rows_d<4>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P, own, U, st);
+  else if (d <= 8) e = adj_rows_d<8>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P, own, U, st);
+  else e = adj_rows_d<16>(X, N, d, R, seed, set, hit, l, rowptr, col, cV, cA, gV, gA, P, own, U, st);
   if (e != cudaSuccess) return e;
   k_mc_col_keys<<<nblk(nnz, 256), 256, 0, st>>>(col, nnz, keys, vals); count_launch();
   e = radix_sort_u64(keys, vals, ktmp, vtmp, nnz, counts, orand, st);

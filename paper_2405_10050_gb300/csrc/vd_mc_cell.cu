@@ -35,7 +35,7 @@ template <int D, int TH>
 __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t seed, uint32_t set, int32_t* hit_out,
                           double* t_out, float* smem, Counters* ctr, int32_t* fb_cell, int32_t* fb_ray,
                           int64_t fb_cap, unsigned long long& n_pairs, unsigned long long& n_rech,
-                          unsigned long long& n_brute, unsigned long long* fb_count) {
+                          unsigned long long& n_brute, unsigned long long* fb_count, double* u_out) {
   const int K = tr.K;
   const int d = tr.d;
   float* sw = smem;                      // [D][K] binary32 offsets
@@ -82,6 +82,11 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
   for (int64_t k = tid; k < R; k += TH) {
     double u64[D];
     mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u64);
+    if (u_out) {
+#pragma unroll
+      for (int q = 0; q < D; ++q)
+        if (q < d) u_out[(i * R + k) * d + q] = u64[q];
+    }
     float u32[D], p0[D];
 #pragma unroll
     for (int q = 0; q < D; ++q) {
@@ -253,7 +258,7 @@ __global__ void __launch_bounds__(kCellThreads) k_mc_cell(TreeView tr, int64_t R
     __syncthreads();
     if (i >= tr.N) break;
     cell_item<D, kCellThreads>(tr, i, R, seed, set, ro.hit, ro.t, smem, ctr, fb_cell, fb_ray, fb_cap,
-                                      n_pairs, n_rech, n_brute, &ctr->fallback);
+                                      n_pairs, n_rech, n_brute, &ctr->fallback, ro.u);
   }
   flush_counters<kCellThreads>(ctr, n_pairs, n_rech, n_brute);
 }
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(TH) k_mc_cell_batch(const SetDesc* sets, int n
 #define VD_CASE(DD)                                                                                              \
   case DD:                                                                                                       \
     cell_item<DD, TH>(S.tv, i, R, seed, S.set, S.hit, S.l, smem, ctr, S.fb_cell, S.fb_ray, S.fb_cap,      \
-                             n_pairs, n_rech, n_brute, &S.ctr->fallback);                                        \
+                             n_pairs, n_rech, n_brute, &S.ctr->fallback, nullptr);                               \
     break;
       VD_CASE(1)
       VD_CASE(2)
@@ -295,7 +300,7 @@ __global__ void __launch_bounds__(TH) k_mc_cell_batch(const SetDesc* sets, int n
       VD_CASE(6)
       default:
         cell_item<8, TH>(S.tv, i, R, seed, S.set, S.hit, S.l, smem, ctr, S.fb_cell, S.fb_ray, S.fb_cap,
-                                n_pairs, n_rech, n_brute, &S.ctr->fallback);
+                                n_pairs, n_rech, n_brute, &S.ctr->fallback, nullptr);
         break;
 #undef VD_CASE
     }

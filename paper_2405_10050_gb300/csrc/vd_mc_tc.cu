@@ -131,7 +131,14 @@ __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t 
         u64[q] = 0.0;
         p0[q] = 0.f;
       }
-      if (valid) mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u64);
+      if (valid) {
+        mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u64);
+        if (ro.u) {
+#pragma unroll
+          for (int q = 0; q < D; ++q)
+            if (q < d) ro.u[(i * R + k) * d + q] = u64[q];
+        }
+      }
       float hu[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) hu[q] = 0.f;

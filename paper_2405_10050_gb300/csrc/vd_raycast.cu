@@ -992,7 +992,7 @@ cudaError_t launch_ray_d(const TreeView& tv, const RaySource& rs, const RayOut& 
 // Candidate lists: for node g, the K nearest other nodes sorted by the
 // binary32 squared distance ww32 (the same expression the list scan
 // evaluates).  A warp gathers every node with ww32 <= r^2 by a tree walk
-// (r adapted until more than K but at most kKnnCap nodes are found, or r
+// (r adapted until more than K but at most `cap` nodes are found, or r
 // covers all nodes), sorts them (bitonic, in shared memory), keeps K, and
 // records kcert = the (K+1)-th smallest ww32 (or r^2): every node missing
 // from the list has ww32 >= kcert.
@@ -1002,13 +1002,24 @@ constexpr int kKnnWpb = 4;
 
 constexpr int kKnnTies = 64;
 
+// One warp's shared memory: fixed part, then `cap` keys and `cap` ids (cap =
+// the gather capacity of the launch, a power of two <= kKnnCap).
 struct WarpKnn {
-  float key[kKnnCap];
-  int32_t id[kKnnCap];
-  int stk[kStk];
-  int hist[256];
-  int32_t tie[kKnnTies];
+  int* stk;      // [kStk]
+  int* hist;     // [256]
+  int32_t* tie;  // [kKnnTies]
+  float* key;    // [cap]
+  int32_t* id;   // [cap]
 };
+constexpr size_t kKnnFixed = (sizeof(int) * (kStk + 256 + kKnnTies) + 15) / 16 * 16;
+__host__ __device__ inline size_t knn_warp_bytes(int cap) { return kKnnFixed + (size_t)cap * 8; }
+// Capacity of the gather for list length K: room for a ball about four
+// times the list.
+inline int knn_cap(int K) {
+  int c = 256;
+  while (c < 4 * K && c < kKnnCap) c <<= 1;
+  return c;
+}
 
 // Bitonic sort of S.key/S.id[0, P) by (key, id), P a power of two.
 __device__ __forceinline__ void knn_sort(WarpKnn& S, int P, int lane) {
@@ -1083,11 +1094,17 @@ __device__ __forceinline__ float knn_select(WarpKnn& S, int n, int k, int lane) 
 }
 
 template <int D>
-__global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, float r0, float rmax, int32_t* knn,
-                                                            int32_t* kcnt, float* kcert) {
+__global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, int cap, float r0, float rmax,
+                                                            int32_t* knn, int32_t* kcnt, float* kcert) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  WarpKnn& S = reinterpret_cast<WarpKnn*>(smem_raw)[wib];
+  unsigned char* wbase = smem_raw + knn_warp_bytes(cap) * wib;
+  WarpKnn S;
+  S.stk = reinterpret_cast<int*>(wbase);
+  S.hist = S.stk + kStk;
+  S.tie = S.hist + 256;
+  S.key = reinterpret_cast<float*>(wbase + kKnnFixed);
+  S.id = reinterpret_cast<int32_t*>(S.key + cap);
   const int d = tr.d;
   const unsigned lt = (1u << lane) - 1u;
   for (int64_t g = (int64_t)blockIdx.x * kKnnWpb + wib; g < tr.N; g += (int64_t)gridDim.x * kKnnWpb) {
@@ -1096,7 +1113,7 @@ __global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, 
     for (int k = 0; k < D; ++k) g32[k] = k < d ? tr.X32[g * d + k] : 0.f;
     float r = r0;
     int count = 0;
-    const float target = fminf(1.5f * (float)K + 32.f, 0.75f * (float)kKnnCap);
+    const float target = fminf(1.5f * (float)K + 32.f, 0.75f * (float)cap);
     for (int attempt = 0; attempt < 64; ++attempt) {
       Ball<D> ball;
 #pragma unroll
@@ -1113,7 +1130,7 @@ __global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, 
         const unsigned m = __ballot_sync(kFull, in);
         if (in) {
           const int pos = count + __popc(m & lt);
-          if (pos < kKnnCap) {
+          if (pos < cap) {
             S.key[pos] = ww;
             S.id[pos] = id;
           }
@@ -1124,7 +1141,7 @@ __global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, 
       unsigned long long dummy = 0;
       walk<D>(tr, S.stk, ball, lane, leaf, dummy);
       // aim the ball at about `target` nodes: count scales like r^d
-      if (count > kKnnCap) {
+      if (count > cap) {
         r *= fminf(0.9f, __powf(target / (float)count, 1.f / (float)d));
         continue;
       }
@@ -1135,7 +1152,7 @@ __global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, 
       }
       break;
     }
-    if (count > kKnnCap) {  // unresolvable (massive duplicates): no list, tree walk only
+    if (count > cap) {  // unresolvable (massive duplicates): no list, tree walk only
       if (lane == 0) {
         kcnt[g] = 0;
         kcert[g] = 0.f;
@@ -1227,13 +1244,14 @@ cudaError_t launch_knn_d(TreeView* tv, int K, float r0, float rmax, int32_t* knn
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t sm = sizeof(WarpKnn) * kKnnWpb;
+  const int cap = knn_cap(K);
+  const size_t sm = knn_warp_bytes(cap) * kKnnWpb;
   cudaFuncSetAttribute(k_knn_build<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_knn_build<D>, kKnnWpb * 32, sm);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1) * 4,
                                                                (tv->N + kKnnWpb - 1) / kKnnWpb));
-  k_knn_build<D><<<(unsigned)grid, kKnnWpb * 32, sm, st>>>(*tv, K, r0, rmax, knn, kcnt, kcert);
+  k_knn_build<D><<<(unsigned)grid, kKnnWpb * 32, sm, st>>>(*tv, K, cap, r0, rmax, knn, kcnt, kcert);
   count_launch();
   return cudaGetLastError();
 }
@@ -1381,7 +1399,7 @@ cudaError_t build_knn(TreeView* tv, int K, cudaStream_t st, DevBufs& bufs) {
     }
   }
   const double vball = std::pow(M_PI, 0.5 * d) / std::tgamma(0.5 * d + 1.0);
-  const float r0 = (float)std::pow(std::min(1.5 * K + 32, 0.75 * kKnnCap) * vol / ((double)N * vball), 1.0 / d);
+  const float r0 = (float)std::pow(std::min(1.5 * K + 32, 0.75 * knn_cap(K)) * vol / ((double)N * vball), 1.0 / d);
   const float rmax = (float)std::sqrt(diag2) * 1.01f + 1e-6f;
   e = VD_DISPATCH_D(d, launch_knn_d, tv, K, std::min(r0, rmax), rmax, knn, kcnt, kcert, st);
   if (e != cudaSuccess) return e;

@@ -65,3 +65,26 @@ def test_vertex_invariants_larger(orc):
         dist = np.linalg.norm(X - r, axis=1)
         R = dist[nodes[0]]
         assert np.min(dist) >= R * (1 - 1e-12)
+
+
+def test_context_reuse_across_sizes(orc):
+    """One context, node sets of growing and shrinking size and dimension:
+    the traversal and MC work buffers kept in the context are reused or
+    grown, and every result still equals the oracle's."""
+    need_cuda()
+    vor = Voronoi(synth.uniform(900, 3, seed=1), precision=VD_FP32)
+    try:
+        for X in [synth.uniform(900, 3, seed=1), synth.uniform(40, 2, seed=2), synth.uniform(2500, 3, seed=3),
+                  synth.gaussian_mixture(150, 4, 4, 0.1, seed=4), synth.uniform(900, 3, seed=1)]:
+            vor.set_nodes(X)
+            t1, c1, _ = vor.vertices()
+            t0, c0, _ = orc.vertices(X)
+            assert np.array_equal(t1.cpu().numpy(), t0) and np.array_equal(c1.cpu().numpy(), c0)
+            R = 48 if X.shape[0] < 1000 else 16
+            res = vor.mc_integrate(R, 9)
+            ref = orc.mc_integrate(X, R, 9)
+            assert np.array_equal(res.hit.cpu().numpy(), ref.hit)
+            assert np.array_equal(res.l.cpu().numpy(), ref.l)
+            res.free()
+    finally:
+        vor.close()

@@ -6,8 +6,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "vd_dev.cuh"
@@ -50,6 +52,7 @@ struct vd_ctx {
   int batch_threads[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // autotuned block size by largest d
   vd::Workspace trav_ws;  // traversal tables and level buffers, reused across vd_vertices calls
   vd::Workspace mc_ws;    // MC work lists, reused across vd_mc_integrate calls
+  vd::Workspace batch_ws; // batched MC: trees, candidate lists, work lists of all sets (one block)
 };
 
 struct vd_mesh {
@@ -73,6 +76,7 @@ struct vd_mc {
   int32_t* hit = nullptr;
   double* l = nullptr;
   double* u = nullptr;  // ray directions kept from the forward pass (or null: drawn again)
+  std::shared_ptr<void> pool;  // batched sets: one device block shared by all of a batch's results
   double* V = nullptr;
   int64_t* rowptr = nullptr;
   int32_t* col = nullptr;
@@ -219,6 +223,7 @@ void vd_destroy(vd_ctx* ctx) {
   ctx->own.release();
   ctx->trav_ws.release();
   ctx->mc_ws.release();
+  ctx->batch_ws.release();
   delete ctx;
 }
 
@@ -517,7 +522,18 @@ vd_status vd_mc_rays(const vd_mc* mc, int32_t* hit, double* l, int32_t on_device
 
 vd_status vd_mc_adjoint(const vd_mc* mc, const double* gV, const double* gA, double* gX, int32_t on_device) {
   if (!mc || !gX || (!gV && !gA)) return VD_EINVAL;
+  // scratch of up to 1 GiB comes from a block this thread keeps for its next
+  // calls (many small adjoints, e.g. of a batch, then allocate nothing)
+  static thread_local vd::Workspace tl_ws;
+  const size_t nn = (size_t)std::max<int64_t>(mc->nnz, 1), n = (size_t)mc->N, dd = (size_t)mc->d;
+  const size_t need = 256 * 16 + nn * dd * 8 + n * dd * 8 * 2 + nn * 24 + 1024 * (nn / 4096 + 2) + n * 8 * 2 + nn * 8;
+  vd::Arena arena;
+  if (need <= ((size_t)1 << 30)) {
+    void* b = nullptr;
+    if (tl_ws.get(0, need, &b) == cudaSuccess) arena = vd::Arena{static_cast<char*>(b), need, 0};
+  }
   DevBufs tmp;
+  tmp.arena = &arena;
   const double *gVd = gV, *gAd = gA;
   double* gXd = gX;
   double* zeroV = nullptr;
@@ -575,6 +591,67 @@ vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const*
   if (nsets == 0) return VD_OK;
   std::vector<vd_mc*> mcs(nsets, nullptr);
   std::vector<vd::SetDesc> desc(nsets);
+  // Device memory in two blocks instead of ~25 allocations per set: the
+  // results every set keeps (X, per-ray hits and lengths, V, CSR) in one
+  // block shared by the sets' vd_mc objects (freed with the last of them),
+  // and everything only the forward pass needs (trees, candidate lists,
+  // counts, work lists) in a per-context arena reused by later calls.
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  std::vector<int> Ks(nsets);
+  std::vector<size_t> prep_set(nsets);
+  size_t keep_bytes = 0;
+  for (int s = 0; s < nsets; ++s) {
+    const int64_t n = N[s];
+    const int dd = d[s];
+    Ks[s] = (int)std::min<int64_t>(std::max(vd::default_knn_k(dd), 1), std::max<int64_t>(n - 1, 1));
+    const int64_t cap = n * std::min<int64_t>(R, n - 1 + 2 * dd);
+    keep_bytes += al(n * dd * 8) + al(n * R * 4) + al(n * R * 8) + al(n * 8) + al((n + 1) * 8) +
+                  al(std::max<int64_t>(cap, 1) * 4) + al(std::max<int64_t>(cap, 1) * 8);
+    const int64_t ntl = (n + 31) / 32;
+    prep_set[s] = al(ntl * 32 * dd * 12) + al(ntl * 32 * 4) + 2 * al((ntl + ntl / 16 + 8) * dd * 24) +
+                  al(n * 24 + 65536) + al(n * 8) * 2 + al(n * 4) * 2 + al((size_t)n * Ks[s] * 4) + al(n * 8) +
+                  al(n * dd * 4) + al(n * 8) + 40 * 256;
+  }
+  void* keep_base = nullptr;
+  if (cudaMalloc(&keep_base, keep_bytes) != cudaSuccess)
+    return set_err(ctx, VD_ENOMEM, "vd_mc_integrate_batch: %zu bytes for the results", keep_bytes);
+  std::shared_ptr<void> keep(keep_base, [](void* p) { cudaFree(p); });
+  vd::Arena keep_arena{static_cast<char*>(keep_base), keep_bytes, 0};
+  // set preparation runs on several host threads, each with its own stream
+  // and its own slice of the arena (the tree and list builds wait on the
+  // device a few times per set; threads overlap those waits)
+  const int T = std::max(1, std::min(nsets, 8));
+  std::vector<size_t> slice(T, (size_t)1 << 16);
+  for (int s = 0; s < nsets; ++s) slice[s % T] += prep_set[s];
+  size_t prep_bytes = 0;
+  for (int t = 0; t < T; ++t) prep_bytes += al(slice[t]);
+  char* prep_base = nullptr;
+  {
+    void* pb = nullptr;
+    if (ctx->batch_ws.get(0, prep_bytes, &pb) == cudaSuccess) prep_base = static_cast<char*>(pb);
+  }
+  std::vector<vd::Arena> arenas(T);
+  std::vector<DevBufs> preps(T);
+  {
+    size_t off = 0;
+    for (int t = 0; t < T; ++t) {
+      if (prep_base) arenas[t] = vd::Arena{prep_base + off, slice[t], 0};
+      off += al(slice[t]);
+      preps[t].arena = &arenas[t];
+    }
+  }
+  vd::Arena misc_arena;  // descriptors and work lists, after the per-thread slices
+  DevBufs prep;          // owns whatever outgrew an arena; freed at the end
+  struct PrepGuard {
+    DevBufs& b;
+    std::vector<DevBufs>& v;
+    cudaStream_t st;
+    ~PrepGuard() {
+      cudaStreamSynchronize(st);
+      b.release();
+      for (auto& x : v) x.release();
+    }
+  } prep_guard{prep, preps, ctx->st};
   auto fail = [&](vd_status st) {
     cudaStreamSynchronize(ctx->st);
     for (vd_mc* m : mcs)
@@ -588,7 +665,7 @@ vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const*
   const long long l0 = vd::g_launches.load();
   int64_t nitems = 0;
   int maxK = 1, maxd = 1;
-  // node preparation of every set (tree + candidate lists), result buffers
+  // results: carved from the shared block in set order
   for (int s = 0; s < nsets; ++s) {
     vd_mc* mc = new (std::nothrow) vd_mc();
     if (!mc) return fail(VD_ENOMEM);
@@ -601,48 +678,84 @@ vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const*
     mc->R = R;
     mc->seed = seed;
     mc->set = (uint32_t)s;
-    cudaError_t e = mc->bufs.alloc_n(&mc->X, (size_t)n * dd);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(mc->X, X[s], (size_t)n * dd * sizeof(double),
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->st);
-    TreeView tv;
-    if (e == cudaSuccess) e = vd::build_tree(mc->X, n, dd, ctx->st, mc->bufs, &tv);
-    const int K = (int)std::min<int64_t>(std::max(vd::default_knn_k(dd), 1), std::max<int64_t>(n - 1, 1));
-    if (e == cudaSuccess) e = vd::build_knn(&tv, K, ctx->st, mc->bufs);
+    mc->pool = keep;
     const int64_t cap = n * std::min<int64_t>(R, n - 1 + 2 * dd);
-    int64_t* cnt = nullptr;
-    if (e == cudaSuccess) e = mc->bufs.alloc_n(&mc->hit, (size_t)n * R);
-    if (e == cudaSuccess) e = mc->bufs.alloc_n(&mc->l, (size_t)n * R);
-    if (e == cudaSuccess) e = mc->bufs.alloc_n(&mc->V, (size_t)n);
-    if (e == cudaSuccess) e = mc->bufs.alloc_n(&cnt, (size_t)n);
-    if (e == cudaSuccess) e = mc->bufs.alloc_n(&mc->rowptr, (size_t)n + 1);
-    if (e == cudaSuccess) e = mc->bufs.alloc_n(&mc->col, (size_t)std::max<int64_t>(cap, 1));
-    if (e == cudaSuccess) e = mc->bufs.alloc_n(&mc->A, (size_t)std::max<int64_t>(cap, 1));
-    if (e == cudaErrorInvalidValue) return fail(set_err(ctx, VD_EINVAL, "set %d: non-finite coordinate", s));
-    if (e != cudaSuccess) return fail(cuda_err(ctx, e, "vd_mc_integrate_batch: set preparation"));
+    DevBufs kb;
+    kb.arena = &keep_arena;
+    cudaError_t e = kb.alloc_n(&mc->X, (size_t)n * dd);
+    if (e == cudaSuccess) e = kb.alloc_n(&mc->hit, (size_t)n * R);
+    if (e == cudaSuccess) e = kb.alloc_n(&mc->l, (size_t)n * R);
+    if (e == cudaSuccess) e = kb.alloc_n(&mc->V, (size_t)n);
+    if (e == cudaSuccess) e = kb.alloc_n(&mc->rowptr, (size_t)n + 1);
+    if (e == cudaSuccess) e = kb.alloc_n(&mc->col, (size_t)std::max<int64_t>(cap, 1));
+    if (e == cudaSuccess) e = kb.alloc_n(&mc->A, (size_t)std::max<int64_t>(cap, 1));
+    mc->bufs.ptrs = kb.ptrs;  // empty unless the block was too small
+    if (e != cudaSuccess) return fail(cuda_err(ctx, e, "vd_mc_integrate_batch: result buffers"));
     const double S = 2.0 * std::pow(M_PI, 0.5 * dd) / std::tgamma(0.5 * dd);
     vd::SetDesc& D = desc[s];
-    D.tv = tv;
     D.item0 = nitems;
     D.set = (uint32_t)s;
     D.hit = mc->hit;
     D.l = mc->l;
     D.V = mc->V;
-    D.cnt = cnt;
     D.rowptr = mc->rowptr;
     D.col = mc->col;
     D.A = mc->A;
     D.cV = S / ((double)dd * (double)R);
     D.cA = S / (double)R;
     nitems += n;
-    maxK = std::max(maxK, tv.K);
     maxd = std::max(maxd, dd);
   }
-  DevBufs tmp;
-  struct Guard {
-    DevBufs& b;
-    ~Guard() { b.release(); }
-  } guard{tmp};
+  // node preparation of every set (tree + candidate lists)
+  std::vector<cudaError_t> terr(T, cudaSuccess);
+  std::vector<int> tbad(T, -1);
+  cudaStreamSynchronize(ctx->st);
+  auto work = [&](int t) {
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    for (int s = t; s < nsets && e == cudaSuccess; s += T) {
+      vd_mc* mc = mcs[s];
+      e = cudaMemcpyAsync(mc->X, X[s], (size_t)mc->N * mc->d * sizeof(double),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+      TreeView tv;
+      if (e == cudaSuccess) e = vd::build_tree(mc->X, mc->N, mc->d, st, preps[t], &tv);
+      if (e == cudaSuccess) e = vd::build_knn(&tv, Ks[s], st, preps[t]);
+      int64_t* cnt = nullptr;
+      if (e == cudaSuccess) e = preps[t].alloc_n(&cnt, (size_t)mc->N);
+      desc[s].tv = tv;
+      desc[s].cnt = cnt;
+      if (e != cudaSuccess) tbad[t] = s;
+    }
+    if (st) {
+      const cudaError_t e2 = cudaStreamSynchronize(st);
+      if (e == cudaSuccess) e = e2;
+      cudaStreamDestroy(st);
+    }
+    terr[t] = e;
+  };
+  {
+    std::vector<std::thread> pool;
+    for (int t = 1; t < T; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto& th : pool) th.join();
+  }
+  for (int t = 0; t < T; ++t) {
+    if (terr[t] == cudaErrorInvalidValue)
+      return fail(set_err(ctx, VD_EINVAL, "set %d: non-finite coordinate", tbad[t]));
+    if (terr[t] != cudaSuccess) return fail(cuda_err(ctx, terr[t], "vd_mc_integrate_batch: set preparation"));
+  }
+  for (int s = 0; s < nsets; ++s) maxK = std::max(maxK, desc[s].tv.K);
+  {  // descriptors and per-set work lists from one more block
+    size_t mb = al(nsets * sizeof(vd::SetDesc)) + al(nsets * 8) + al(nsets * sizeof(Counters)) + 4096;
+    for (int s = 0; s < nsets; ++s) {
+      const int64_t rays = mcs[s]->N * R;
+      mb += 2 * al(std::max<int64_t>(rays / 4, 1024) * 4) + al(std::max<int64_t>(rays / 16, 1024) * 4);
+    }
+    void* p = nullptr;
+    if (ctx->batch_ws.get(1, mb, &p) == cudaSuccess) misc_arena = vd::Arena{static_cast<char*>(p), mb, 0};
+    prep.arena = &misc_arena;
+  }
+  DevBufs& tmp = prep;
   vd::SetDesc* desc_dev = nullptr;
   int64_t* nnz_dev = nullptr;
   Counters* set_ctr = nullptr;

@@ -113,11 +113,27 @@ extern std::atomic<long long> g_launches;
 inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // Device allocations owned by one library object, released together.
+// Bump allocator over one preallocated device block: many small buffers
+// without a cudaMalloc each (and without cudaFree, which synchronises).
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0, off = 0;
+  void* take(size_t bytes) {
+    const size_t b = (bytes + 255) / 256 * 256;
+    if (!base || off + b > cap) return nullptr;
+    void* p = base + off;
+    off += b;
+    return p;
+  }
+};
+
 struct DevBufs {
   std::vector<void*> ptrs;
+  Arena* arena = nullptr;  // if set, buffers come from it while it has room
   cudaError_t alloc(void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (arena && (*p = arena->take(bytes)) != nullptr) return cudaSuccess;
     cudaError_t e = cudaMalloc(p, bytes);
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;

@@ -295,6 +295,7 @@ cudaError_t build_tree(const double* X, int64_t N, int d, cudaStream_t st, DevBu
   }
   // scratch (freed at the end)
   DevBufs scratch;
+  scratch.arena = bufs.arena;
   const int nb_bounds = std::min(nblocks(N, 256), 256);
   double *part = nullptr, *bounds = nullptr;
   uint64_t *keys = nullptr, *ktmp = nullptr;

@@ -181,6 +181,7 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
       } else {
         atomicOr(&ctr->flags, kFlagQueue);
       }
+      t_out[i * R + k] = (double)T;  // the bound found so far seeds the tree walk
       continue;
     } else {
       // binary64 recheck of the survivors, canonical order
@@ -383,6 +384,7 @@ cudaError_t launch_mc_cells(const TreeView& tv, int64_t R, uint64_t seed, uint32
   rs.seed = seed;
   rs.set = set;
   rs.box = 1;
+  rs.t_hint = 1;
   RayOut r2 = ro;
   r2.fallback_list = nullptr;  // tree walk directly
   r2.fallback_cap = 0;

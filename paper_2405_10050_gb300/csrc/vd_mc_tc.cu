@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t 
           } else {
             atomicOr(&ctr->flags, kFlagQueue);
           }
+          ro.t[i * R + k] = (double)T;  // the bound found so far seeds the tree walk
         } else {
           mc_recheck<D>(tr.X, d, g64, u64, cb, ct, nc, T, ro.hit[i * R + k], ro.t[i * R + k], n_rech);
         }
@@ -322,6 +323,7 @@ cudaError_t launch_mc_cells_tc(const TreeView& tv, int64_t R, uint64_t seed, uin
   rs.seed = seed;
   rs.set = set;
   rs.box = 1;
+  rs.t_hint = 1;
   RayOut r2 = ro;
   r2.fallback_list = nullptr;
   r2.fallback_cap = 0;

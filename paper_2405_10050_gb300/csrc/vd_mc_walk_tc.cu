@@ -386,6 +386,7 @@ __global__ void __launch_bounds__(kWt, 4) k_mc_walk_tc(TreeView tr, int64_t R, i
         } else {
           atomicOr(&ctr->flags, kFlagQueue);
         }
+        ro.t[(int64_t)cell * R + k] = (double)T;  // the bound found so far seeds the tree walk
       } else {
         double g64[D], uu[D];
 #pragma unroll
@@ -497,6 +498,7 @@ cudaError_t launch_mc_walk_tc(const TreeView& tv, int64_t R, uint64_t seed, uint
   rs.seed = seed;
   rs.set = set;
   rs.box = 1;
+  rs.t_hint = 1;
   RayOut r2 = ro;
   r2.fallback_list = nullptr;
   r2.fallback_cap = 0;

@@ -1339,6 +1339,7 @@ cudaError_t launch_mc_fallback_dev(const SetDesc& S, int64_t R, uint64_t seed, c
   rs.mode = 1;
   rs.R = S.fb_cap;
   rs.R_dev = &S.ctr->fallback;
+  rs.t_hint = 1;  // the cell kernel left each ray's bound in its output t
   rs.mc_cell = S.fb_cell;
   rs.mc_ray = S.fb_ray;
   rs.mc_rpc = R;

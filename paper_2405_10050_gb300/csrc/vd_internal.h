@@ -40,6 +40,7 @@ struct TreeView {
   const float* bhi32 = nullptr;  // [d][total], rounded up
   const double* blo64 = nullptr; // [d][total]
   const double* bhi64 = nullptr;
+  const float* rho32 = nullptr;  // [total] radius of the node's points around its binary32 box centre
   const float* x32 = nullptr;    // [ntiles][d][32], nearest binary32 of x
   const double* x64 = nullptr;   // [ntiles][d][32]
   const int32_t* ids = nullptr;  // [ntiles][32], kNoId for padding

@@ -109,7 +109,7 @@ __device__ __forceinline__ void stage_rows(const TreeView& tr, WalkSmem& S, int 
     if (lane < 16) S.e_w[grp][lane] = w;
     if (lane == 0) {
       S.e_lo[grp] = true_d2_lower(ww, ep.gam, ep.EW, D);
-      S.e_rho[grp] = __fsqrt_ru(h2);
+      S.e_rho[grp] = tr.rho32 ? fminf(__fsqrt_ru(h2), tr.rho32[bi]) : __fsqrt_ru(h2);
       S.e_wn[grp] = sqrtf(ww) * (1.f + ep.gam);
     }
   }
@@ -150,7 +150,7 @@ __device__ __forceinline__ void stage_rows(const TreeView& tr, WalkSmem& S, int 
           ww = fmaf(w[k], w[k], ww);
         }
       const float d2lo = true_d2_lower(ww, ep.gam, ep.EW, D);
-      const float rho = __fsqrt_ru(r2);
+      const float rho = tr.rho32 ? fminf(__fsqrt_ru(r2), tr.rho32[bi]) : __fsqrt_ru(r2);
       const float err = fmaf(ep.a1, sqrtf(ww) * (1.f + ep.gam), ep.a0);
       // |u| <= 1 + 2^-40 after the binary64 normalisation
       S.r_ae[row] = make_float2(__fsub_rd(d2lo, __fmul_ru(rho, rho)), __fadd_ru(err, __fmul_ru(rho, 1.0000001f)));

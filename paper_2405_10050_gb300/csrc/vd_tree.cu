@@ -233,6 +233,48 @@ __global__ void k_level_bbox(int d, int64_t total, int64_t off_child, int64_t n_
   }
 }
 
+// Radius of each node's points around the binary32 centre of its box,
+// m = 0.5 (lo32 + hi32) rounded to nearest in binary32 (the centre the
+// tensor-core walk uses), rounded up: leaves from their points, parents as
+// max over children of |m_child - m| + rho_child.  In high d the points of a
+// box stay far from its corners, so this radius is well below the box's
+// half-diagonal.
+__global__ void k_leaf_rho(const double* x64, int64_t ntiles, int d, int64_t total, int64_t off, const float* lo32,
+                           const float* hi32, float* rho) {
+  const int64_t tile = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (tile >= ntiles) return;
+  double r2 = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const float m = 0.5f * (lo32[k * total + off + tile] + hi32[k * total + off + tile]);
+    const double w = x64[(tile * d + k) * kTile + lane] - (double)m;  // pads duplicate a valid node
+    r2 = fma(w, w, r2);
+  }
+  for (int s = 16; s; s >>= 1) r2 = fmax(r2, __shfl_xor_sync(kFull, r2, s));
+  if (lane == 0) rho[off + tile] = f32_up(sqrt(r2) * (1.0 + 1e-14));
+}
+
+__global__ void k_level_rho(int d, int64_t total, int64_t off_child, int64_t n_child, int64_t off_par, int64_t n_par,
+                            const float* lo32, const float* hi32, float* rho) {
+  const int64_t par = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (par >= n_par) return;
+  const int64_t c = par * kFan + lane;
+  double r = 0.0;
+  if (c < n_child) {
+    double q2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+      const float mp = 0.5f * (lo32[k * total + off_par + par] + hi32[k * total + off_par + par]);
+      const float mc = 0.5f * (lo32[k * total + off_child + c] + hi32[k * total + off_child + c]);
+      const double w = (double)mc - (double)mp;
+      q2 = fma(w, w, q2);
+    }
+    r = sqrt(q2) * (1.0 + 1e-14) + (double)rho[off_child + c];
+  }
+  for (int s = 16; s; s >>= 1) r = fmax(r, __shfl_xor_sync(kFull, r, s));
+  if (lane == 0) rho[off_par + par] = f32_up(r * (1.0 + 1e-14));
+}
+
 inline int nblocks(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t - 1) / t); }
 
 }  // namespace
@@ -326,7 +368,7 @@ cudaError_t build_tree(const double* X, int64_t N, int d, cudaStream_t st, DevBu
   e = radix_sort_u64(keys, vals, ktmp, vtmp, N, counts, orand, st);
   if (e != cudaSuccess) { scratch.release(); return e; }
   double *x64 = nullptr, *lo64 = nullptr, *hi64 = nullptr;
-  float *x32 = nullptr, *lo32 = nullptr, *hi32 = nullptr;
+  float *x32 = nullptr, *lo32 = nullptr, *hi32 = nullptr, *rho32 = nullptr;
   int32_t* ids = nullptr;
   if ((e = bufs.alloc_n(&x64, (size_t)t.ntiles * d * kTile)) != cudaSuccess ||
       (e = bufs.alloc_n(&x32, (size_t)t.ntiles * d * kTile)) != cudaSuccess ||
@@ -334,7 +376,8 @@ cudaError_t build_tree(const double* X, int64_t N, int d, cudaStream_t st, DevBu
       (e = bufs.alloc_n(&lo64, (size_t)t.total * d)) != cudaSuccess ||
       (e = bufs.alloc_n(&hi64, (size_t)t.total * d)) != cudaSuccess ||
       (e = bufs.alloc_n(&lo32, (size_t)t.total * d)) != cudaSuccess ||
-      (e = bufs.alloc_n(&hi32, (size_t)t.total * d)) != cudaSuccess) {
+      (e = bufs.alloc_n(&hi32, (size_t)t.total * d)) != cudaSuccess ||
+      (e = bufs.alloc_n(&rho32, (size_t)t.total)) != cudaSuccess) {
     scratch.release();
     return e;
   }
@@ -344,6 +387,13 @@ cudaError_t build_tree(const double* X, int64_t N, int d, cudaStream_t st, DevBu
   for (int L = 1; L < t.nlev; ++L)
     k_level_bbox<<<nblocks(t.cnt[L] * 32, 256), 256, 0, st>>>(d, t.total, t.off[L - 1], t.cnt[L - 1], t.off[L],
                                                                 t.cnt[L], lo64, hi64, lo32, hi32); count_launch();
+  k_leaf_rho<<<nblocks(t.ntiles * 32, 256), 256, 0, st>>>(x64, t.ntiles, d, t.total, t.off[0], lo32, hi32, rho32);
+  count_launch();
+  for (int L = 1; L < t.nlev; ++L) {
+    k_level_rho<<<nblocks(t.cnt[L] * 32, 256), 256, 0, st>>>(d, t.total, t.off[L - 1], t.cnt[L - 1], t.off[L],
+                                                               t.cnt[L], lo32, hi32, rho32);
+    count_launch();
+  }
   e = cudaStreamSynchronize(st);
   scratch.release();
   if (e != cudaSuccess) return e;
@@ -355,6 +405,7 @@ cudaError_t build_tree(const double* X, int64_t N, int d, cudaStream_t st, DevBu
   t.bhi64 = hi64;
   t.blo32 = lo32;
   t.bhi32 = hi32;
+  t.rho32 = rho32;
   *tv = t;
   return cudaSuccess;
 #undef VD_TRY

@@ -114,24 +114,32 @@ def _barrier(ws):
         dist.barrier()
 
 
-def _max_over_ranks(x, ws):
+def _reduce_over_ranks(x, ws, op):
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def _max_over_ranks(x, ws):
+    import torch.distributed as dist
+    return _reduce_over_ranks(x, ws, dist.ReduceOp.MAX)
 
 
 def _sum_over_ranks(x, ws):
-    if ws == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce_over_ranks(x, ws, dist.ReduceOp.SUM)
+
+
+def replica_value(units, seconds, ws):
+    """Whole-job throughput of N independent replicas: every rank's units
+    over the slowest rank's time (the replicas start together after a
+    barrier)."""
+    return _sum_over_ranks(units, ws) / _max_over_ranks(seconds, ws)
 
 
 def edge_rays_from_mesh(orc, X, tuples, coords, n, seed=0):
@@ -302,8 +310,7 @@ def run_ours(args):
     _barrier(ws)
     ms = e0.elapsed_time(e1)
     ms_max = _max_over_ranks(ms, ws)
-    rays_all = _sum_over_ranks(rays, ws)
-    value = rays_all / (ms_max / 1000.0)
+    value = replica_value(rays, ms / 1000.0, ws)
     nv = vd.vd_mesh_count(last)
     tup = torch.empty((nv, args.d + 1), dtype=torch.int32, device="cuda")
     crd = torch.empty((nv, args.d), dtype=torch.float64, device="cuda")
@@ -349,7 +356,7 @@ def run_ours(args):
         vd.vd_mesh_free(m)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_value = _sum_over_ranks(e2e_rays, ws) / _max_over_ranks(e2e_s, ws)
+    e2e_value = replica_value(e2e_rays, e2e_s, ws)
     h2d = Xh.nbytes
     d2h = th.nbytes + ch.nbytes
 

@@ -232,7 +232,9 @@ __global__ void __launch_bounds__(kTcThreads) k_mc_cell_tc(TreeView tr, int64_t 
   }
   if (timed_out) {
     // give the in-flight MMA a bounded chance to finish before freeing its memory
-    tc::mbar_wait(&mbar, phase ^ 1u, wait_limit);
+    // the MMA still in flight must finish before its tensor memory is freed:
+    // this wait has its own generous bound, whatever limit gave up above
+    tc::mbar_wait(&mbar, phase ^ 1u, wait_limit > (1ll << 24) ? wait_limit : (1ll << 24));
     if (tid == 0) atomicOr(&ctr->flags, kFlagTimeout);
   }
   tc::fence_before_sync();

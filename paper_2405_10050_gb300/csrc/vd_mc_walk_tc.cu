@@ -399,7 +399,9 @@ __global__ void __launch_bounds__(kWt, 4) k_mc_walk_tc(TreeView tr, int64_t R, i
     __syncthreads();  // the next tile rewrites A, g and the stack
   }
   if (timed_out) {
-    tc::mbar_wait(&mbar, phase ^ 1u, wait_limit);
+    // the MMA still in flight must finish before its tensor memory is freed:
+    // this wait has its own generous bound, whatever limit gave up above
+    tc::mbar_wait(&mbar, phase ^ 1u, wait_limit > (1ll << 24) ? wait_limit : (1ll << 24));
     if (tid == 0) atomicOr(&ctr->flags, kFlagTimeout);
   }
   tc::fence_before_sync();

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from gpu_util import need_cuda
-from paper_2405_10050_gb300 import VD_FP32, VD_FP64, VD_TC16, Voronoi, VoronoiMC, synth
+from paper_2405_10050_gb300 import VD_FP32, VD_FP64, VD_TC16, Voronoi, VoronoiMC, synth, vd
 
 pytestmark = pytest.mark.gpu
 
@@ -112,3 +112,30 @@ def test_autograd_function(orc):
     g0 = orc.mc_adjoint(X.detach().cpu().numpy(), R, 5, ref.hit, ref.l, ref.rowptr, ref.col, wV.cpu().numpy(),
                         wA.cpu().numpy())
     assert np.max(np.abs(X.grad.cpu().numpy() - g0)) <= 1e-10 * np.max(np.abs(g0))
+
+
+@pytest.mark.parametrize("d,N,R", [(3, 400, 64), (10, 300, 64)])
+def test_tensor_wait_limit(orc, d, N, R):
+    """Bounded waits of the tensor-core kernels: with a limit of one poll the
+    MMA-completion wait gives up, the kernel waits (with its own bound) for
+    the MMA still in flight, frees its tensor memory and reports the timeout
+    through a status flag; the call fails with VD_ETIMEOUT (or succeeds if
+    the MMA was already done) and the device stays usable."""
+    torch = need_cuda()
+    X = synth.uniform(N, d, seed=d)
+    cfg = vd.vd_config_default()
+    cfg.precision = VD_TC16
+    cfg.wait_limit = 1
+    ctx = vd.vd_create(cfg, torch.cuda.current_stream().cuda_stream)
+    try:
+        vd.vd_set_nodes(ctx, torch.tensor(X, device="cuda"))
+        try:
+            vd.vd_mc_free(vd.vd_mc_integrate(ctx, R, 5))
+        except vd.VDError as e:
+            assert e.status == -7  # VD_ETIMEOUT
+    finally:
+        vd.vd_destroy(ctx)
+    torch.cuda.synchronize()
+    vor, res, ref = _parity(orc, X, R, seed=5, prec=VD_TC16)
+    res.free()
+    vor.close()

@@ -116,11 +116,12 @@ def test_autograd_function(orc):
 
 @pytest.mark.parametrize("d,N,R", [(3, 400, 64), (10, 300, 64)])
 def test_tensor_wait_limit(orc, d, N, R):
-    """Bounded waits of the tensor-core kernels: with a limit of one poll the
-    MMA-completion wait gives up, the kernel waits (with its own bound) for
-    the MMA still in flight, frees its tensor memory and reports the timeout
-    through a status flag; the call fails with VD_ETIMEOUT (or succeeds if
-    the MMA was already done) and the device stays usable."""
+    """Bounded waits of the tensor-core kernels with a limit of one poll: each
+    poll (mbarrier try_wait) may suspend the thread until the MMA completes
+    or a hardware time limit passes, so the call either completes or gives
+    up; giving up, the kernel waits (with its own bound) for the MMA still in
+    flight, frees its tensor memory and reports VD_ETIMEOUT.  Either way the
+    device stays usable and a normal call afterwards is exact."""
     torch = need_cuda()
     X = synth.uniform(N, d, seed=d)
     cfg = vd.vd_config_default()

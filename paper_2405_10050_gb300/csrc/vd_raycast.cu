@@ -169,6 +169,34 @@ __device__ __forceinline__ void walk(const TreeView& tr, int* stk, Ball<D>& ball
   }
 }
 
+// Same walk for a fixed ball (candidate-list gathering): every box that meets
+// the ball is visited, in no particular order, so children are pushed
+// without sorting.
+template <int D, class Leaf>
+__device__ __forceinline__ void walk_fixed(const TreeView& tr, int* stk, const Ball<D>& ball, int lane, Leaf&& leaf) {
+  int sp = 0;
+  if (lane == 0) stk[0] = enc(tr.nlev - 1, 0);
+  sp = 1;
+  __syncwarp();
+  while (sp > 0) {
+    const int e = stk[--sp];
+    __syncwarp();
+    const int lev = e >> 27;
+    const int64_t idx = e & ((1 << 27) - 1);
+    if (lev == 0) {
+      if (leaf_alive<D>(tr, idx, ball, lane)) leaf(idx);
+      continue;
+    }
+    const int64_t child = idx * kFan + lane;
+    const bool in = child < tr.cnt[lev - 1] && box_dist2<D>(tr, lev - 1, child, ball) * (1.f - 2e-6f) <= ball.lim2;
+    const unsigned m = __ballot_sync(kFull, in);
+    const int pos = sp + __popc(m & ((1u << lane) - 1u));
+    if (in && pos < kStk) stk[pos] = enc(lev - 1, child);
+    sp = min(sp + __popc(m), kStk);
+    __syncwarp();
+  }
+}
+
 // ------------------------------------------------------------------------
 // VD_FP32: binary32 screening + binary64 recheck
 // ------------------------------------------------------------------------
@@ -1138,8 +1166,7 @@ __global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, 
         count += __popc(m);
         __syncwarp();
       };
-      unsigned long long dummy = 0;
-      walk<D>(tr, S.stk, ball, lane, leaf, dummy);
+      walk_fixed<D>(tr, S.stk, ball, lane, leaf);
       // aim the ball at about `target` nodes: count scales like r^d
       if (count > cap) {
         r *= fminf(0.9f, __powf(target / (float)count, 1.f / (float)d));

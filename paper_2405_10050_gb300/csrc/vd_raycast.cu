@@ -183,8 +183,8 @@ __device__ __forceinline__ void walk_fixed(const TreeView& tr, int* stk, const B
     __syncwarp();
     const int lev = e >> 27;
     const int64_t idx = e & ((1 << 27) - 1);
-    if (lev == 0) {
-      if (leaf_alive<D>(tr, idx, ball, lane)) leaf(idx);
+    if (lev == 0) {  // pushed only if its box meets the ball, which does not change
+      leaf(idx);
       continue;
     }
     const int64_t child = idx * kFan + lane;

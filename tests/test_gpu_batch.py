@@ -76,3 +76,37 @@ def test_batch_rejects_high_dimension():
             vd.vd_mc_integrate_batch(ctx, [synth.uniform(10, 9, seed=0)], 8, 1)
     finally:
         vd.vd_destroy(ctx)
+
+
+def test_batch_host_inputs_and_errors(orc):
+    """Sets given as host arrays (copied on the preparation threads' own
+    streams); a set with a non-finite coordinate fails the whole call with
+    VD_EINVAL and leaves the context usable."""
+    torch = need_cuda()
+    Xs = [synth.uniform(300 + 37 * s, 2 + s % 5, seed=20 + s) for s in range(11)]
+    R, seed = 16, 5
+    ctx = vd.vd_create(None, torch.cuda.current_stream().cuda_stream)
+    try:
+        mcs = vd.vd_mc_integrate_batch(ctx, Xs, R, seed)
+        for s in (0, 5, 10):
+            X = Xs[s]
+            hit = np.empty((X.shape[0], R), np.int32)
+            l = np.empty((X.shape[0], R))
+            vd.vd_mc_rays(mcs[s], hit, l)
+            ref = orc.mc_integrate(X, R, seed, set_id=s)
+            assert np.array_equal(hit, ref.hit) and np.array_equal(l, ref.l)
+        for mc in mcs:
+            vd.vd_mc_free(mc)
+        bad = [X.copy() for X in Xs[:4]]
+        bad[2][7, 1] = np.nan
+        with pytest.raises(vd.VDError) as ei:
+            vd.vd_mc_integrate_batch(ctx, bad, R, seed)
+        assert ei.value.status == -1  # VD_EINVAL
+        mcs = vd.vd_mc_integrate_batch(ctx, Xs[:3], R, seed)
+        hit = np.empty((Xs[1].shape[0], R), np.int32)
+        vd.vd_mc_rays(mcs[1], hit, None)
+        assert np.array_equal(hit, orc.mc_integrate(Xs[1], R, seed, set_id=1).hit)
+        for mc in mcs:
+            vd.vd_mc_free(mc)
+    finally:
+        vd.vd_destroy(ctx)

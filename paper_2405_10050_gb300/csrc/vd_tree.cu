@@ -23,8 +23,13 @@ __global__ void k_bounds_partial(const double* X, int64_t N, int d, double* part
     double lo = INFINITY, hi = -INFINITY;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
       const double x = X[i * d + k];
-      lo = fmin(lo, x);
-      hi = fmax(hi, x);
+      if (isfinite(x)) {
+        lo = fmin(lo, x);
+        hi = fmax(hi, x);
+      } else {  // NaN or infinity: infinite bounds, which the host reports
+        lo = -INFINITY;
+        hi = INFINITY;
+      }
     }
     slo[threadIdx.x] = lo;
     shi[threadIdx.x] = hi;

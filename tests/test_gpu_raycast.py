@@ -135,6 +135,11 @@ def test_invalid_arguments_are_rejected():
             vd.vd_set_nodes(ctx, np.zeros((4, 17)))
         with pytest.raises(VDError):
             vd.vd_set_nodes(ctx, np.array([[0.1, np.nan]]))
+        Xb = synth.uniform(500, 3, seed=1)
+        for v in (np.nan, np.inf):
+            Xb[123, 2] = v
+            with pytest.raises(VDError):  # one non-finite coordinate among many
+                vd.vd_set_nodes(ctx, Xb)
         vd.vd_set_nodes(ctx, synth.uniform(10, 2, seed=0))
         with pytest.raises(VDError):  # eta rows longer than d + 1
             vd.vd_raycast(ctx, np.zeros((1, 2)), np.array([[1.0, 0.0]]), np.zeros((1, 4), np.int32),

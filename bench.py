@@ -40,6 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "raycasts/s and MC vol+grad cells/s: mixed vs FP64 path, same GB300, exact hits"
 WORKLOAD = "exhaustive vertex traversal, d=5, N=20000 iid uniform in [0,1]^5 (seed 0), clipped to the cube"
 NEIGHBOURS_D5 = 95  # neighbours per cell in d = 5 (the paper's table of vertices and neighbours per cell)
+RAYCAST_DRAM_BYTES_PER_STEP = 639.4e6  # ncu dram__bytes_read + write of k_ray_list_thr<5>, one traversal
 
 
 def _peaks():
@@ -368,8 +369,12 @@ def run_ours(args):
     pairs = NEIGHBOURS_D5 + 2 * args.d
     flops_per_ray = pairs * (2 * args.d + 6)
     achieved = rays * flops_per_ray / (rc_ms / 1000.0) / 1e12 if rc_ms > 0 else None
+    # DRAM bytes of the list RayCast per traversal of this workload, from one ncu capture of the current
+    # kernel (profiles/traversal_d5_n20000_launches.md); the ray I/O alone is ~573 MB
+    traffic = RAYCAST_DRAM_BYTES_PER_STEP if (args.N, args.d, args.knn_k) == (20000, 5, 0) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": (achieved / peak_tflops) if achieved else None, "traffic": None,
+                "frac": (achieved / peak_tflops) if achieved else None, "traffic": traffic,
+                "traffic_unit": "bytes per step (all list-RayCast launches of one traversal)",
                 "kernel": "k_ray_list_thr<5> + tree-walk follow-up (binary32 screening + binary64 recheck)",
                 "peak_source": f"FP32 lanes x 2 x sm_max_mhz ({src} peaks file)",
                 "algorithmic_flops_per_ray": flops_per_ray, "raycast_ms_per_step": rc_ms / args.steps}

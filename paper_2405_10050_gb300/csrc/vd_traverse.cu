@@ -453,7 +453,8 @@ __global__ void k_commit_claim(Tables T, const int32_t* reta, const int32_t* hit
 // level added.
 template <int D>
 __global__ void k_commit_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot,
-                                const int32_t* win, int64_t nwcap, const unsigned long long* nwin, unsigned* flags) {
+                                const int32_t* win, int64_t nwcap, const unsigned long long* nwin, int32_t* vids,
+                                unsigned* flags) {
   const int d = T.d, L = d + 1;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= min(nwcap, (int64_t)*nwin)) return;
@@ -461,6 +462,7 @@ __global__ void k_commit_finish(Tables T, const double* X, const int32_t* cand, 
   const long long v = warp_append(true, T.nv);
   if ((int64_t)v >= T.vcap) {
     atomicOr(flags, kFlagHashFull);
+    vids[p] = -1;
     return;
   }
   int32_t sig[D + 1];
@@ -471,16 +473,29 @@ __global__ void k_commit_finish(Tables T, const double* X, const int32_t* cand, 
   for (int a = 0; a < d; ++a) T.vx[(int64_t)v * d + a] = x[a];
   __threadfence();
   T.vslot[cslot[r]] = (int32_t)v;
-  for (int q = 0; q <= d; ++q) {
-    int32_t eta[D];
-    int m = 0, hasnode = 0;
-    for (int a = 0; a <= d; ++a)
-      if (a != q) {
-        eta[m++] = sig[a];
-        hasnode |= sig[a] >= 0;
-      }
-    if (hasnode) edge_increment(T, eta, T.edet ? (int64_t)v * L + q : -1, flags);
-  }
+  vids[p] = (int32_t)v;
+}
+
+// Edge counters of the level's new vertices: one thread per (vertex, edge),
+// so the dependent hash probes of the d + 1 edges run side by side.
+__global__ void k_commit_edges(Tables T, const int32_t* vids, int64_t nwcap, const unsigned long long* nwin,
+                               unsigned* flags) {
+  const int d = T.d, L = d + 1;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = t / L;
+  const int q = (int)(t % L);
+  if (p >= min(nwcap, (int64_t)*nwin)) return;
+  const int32_t v = vids[p];
+  if (v < 0) return;
+  int32_t eta[VD_MAX_D];
+  int m = 0, hasnode = 0;
+  for (int a = 0; a <= d; ++a)
+    if (a != q) {
+      const int32_t g = T.vt[(int64_t)v * L + a];
+      eta[m++] = g;
+      hasnode |= g >= 0;
+    }
+  if (hasnode) edge_increment(T, eta, T.edet ? (int64_t)v * L + q : -1, flags);
 }
 
 // ---- Descent seeding ----------------------------------------------------------
@@ -637,8 +652,10 @@ void launch_expand(Tables T, const double* X, int64_t f0, int64_t nf, int64_t* i
 
 template <int D>
 void launch_finish(Tables T, const double* X, const int32_t* cand, const int64_t* cslot, const int32_t* win,
-                   int64_t nwcap, const unsigned long long* nwin, unsigned* flags, cudaStream_t st) {
-  k_commit_finish<D><<<nb(nwcap), 256, 0, st>>>(T, X, cand, cslot, win, nwcap, nwin, flags);
+                   int64_t nwcap, const unsigned long long* nwin, int32_t* vids, unsigned* flags, cudaStream_t st) {
+  k_commit_finish<D><<<nb(nwcap), 256, 0, st>>>(T, X, cand, cslot, win, nwcap, nwin, vids, flags);
+  count_launch();
+  k_commit_edges<<<nb(nwcap * (T.d + 1)), 256, 0, st>>>(T, vids, nwcap, nwin, flags);
   count_launch();
 }
 
@@ -687,7 +704,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   // workspace slots
   enum {
     kVt, kVx, kVslot, kEt, kEcnt, kEslot, kCnts, kRo, kRd, kRt, kReta, kRhit, kCand, kCslot, kOvl, kFbl, kSnode,
-    kSsig, kSm, kAlive, kSr, kFront, kNext, kPerm, kPtmp, kKeys, kKtmp, kCounts, kOrand, kItems, kWin
+    kSsig, kSm, kAlive, kSr, kFront, kNext, kPerm, kPtmp, kKeys, kKtmp, kCounts, kOrand, kItems, kWin, kVids
   };
   int64_t vcap = cfg.hash_capacity > 0 ? cfg.hash_capacity
                                        : (int64_t)std::min(2.0e9, std::max(1.0e5, 2.0 * N * vertices_per_cell(d) / L +
@@ -726,7 +743,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   double *ro = nullptr, *rd = nullptr, *rt = nullptr;
   int32_t *reta = nullptr, *rhit = nullptr, *cand = nullptr;
   int64_t *cslot = nullptr, *items = nullptr;
-  int32_t *ovl = nullptr, *fbl = nullptr, *win = nullptr;
+  int32_t *ovl = nullptr, *fbl = nullptr, *win = nullptr, *vids = nullptr;
   auto grow = [&](int64_t need) -> cudaError_t {
     if (need <= rcap) return cudaSuccess;
     const int64_t c = std::max<int64_t>({need, rcap * 2, 4096});
@@ -736,7 +753,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
         (ee = ws.get_n(kRhit, (size_t)c, &rhit)) || (ee = ws.get_n(kCand, (size_t)c * L, &cand)) ||
         (ee = ws.get_n(kCslot, (size_t)c, &cslot)) || (ee = ws.get_n(kOvl, (size_t)c, &ovl)) ||
         (ee = ws.get_n(kFbl, (size_t)c, &fbl)) || (ee = ws.get_n(kItems, (size_t)c, &items)) ||
-        (ee = ws.get_n(kWin, (size_t)c, &win)))
+        (ee = ws.get_n(kWin, (size_t)c, &win)) || (ee = ws.get_n(kVids, (size_t)c, &vids)))
       return ee;
     rcap = c;
     return cudaSuccess;
@@ -842,7 +859,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
       VD_TRY(cudaMemcpyAsync(flags, &clr, sizeof(unsigned), cudaMemcpyHostToDevice, st));
     }
   }
-  VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, ns, nwin, flags, st);
+  VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, ns, nwin, vids, flags, st);
   unsigned long long hn2[4];
   VD_TRY(cudaMemcpyAsync(hn2, cnts, sizeof(hn2), cudaMemcpyDeviceToHost, st));
   VD_TRY(cudaStreamSynchronize(st));
@@ -870,7 +887,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     VD_TRY(cast(rmax, nrays, d));
     k_commit_claim<<<nb(rmax), 256, 0, st>>>(T, reta, rhit, rmax, nrays, cand, cslot, win, nwin, flags);
     count_launch();
-    VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, rmax, nwin, flags, st);
+    VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, rmax, nwin, vids, flags, st);
     VD_TRY(cudaGetLastError());
     unsigned long long hc[5];
     unsigned hf = 0;

@@ -704,7 +704,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   // workspace slots
   enum {
     kVt, kVx, kVslot, kEt, kEcnt, kEslot, kCnts, kRo, kRd, kRt, kReta, kRhit, kCand, kCslot, kOvl, kFbl, kSnode,
-    kSsig, kSm, kAlive, kSr, kFront, kNext, kPerm, kPtmp, kKeys, kKtmp, kCounts, kOrand, kItems, kWin, kVids
+    kSsig, kSm, kAlive, kSr, kPerm, kPtmp, kKeys, kKtmp, kCounts, kOrand, kItems, kWin, kVids
   };
   int64_t vcap = cfg.hash_capacity > 0 ? cfg.hash_capacity
                                        : (int64_t)std::min(2.0e9, std::max(1.0e5, 2.0 * N * vertices_per_cell(d) / L +

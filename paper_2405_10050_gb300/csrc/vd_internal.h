@@ -54,6 +54,8 @@ struct TreeView {
   const int32_t* kcnt = nullptr;  // [N] entries in use
   const float* kcert = nullptr;   // [N]
   const float* X32 = nullptr;     // [N][d] nearest binary32 of X, id order
+  const float4* X32v = nullptr;   // d <= 8: [N][x32q] the same, rows zero padded to 16-byte vectors
+  int x32q = 0;
   float root_lo[16] = {};         // bounding box of all nodes (binary32, outward)
   float root_hi[16] = {};
 };

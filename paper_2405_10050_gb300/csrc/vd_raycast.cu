@@ -67,10 +67,9 @@ struct WarpF64 {
 
 __device__ __forceinline__ int enc(int lev, int64_t idx) { return (lev << 27) | (int)idx; }
 
-// Loads ray r of the source: origin v, direction u, eta (m ids, eta[0] = g).
+// Origin v and direction u of ray r of the source.
 template <int D>
-__device__ __forceinline__ void load_ray(const TreeView& tr, const RaySource& rs, int64_t r, double v[D], double u[D],
-                                         int32_t eta[D + 1], int& m) {
+__device__ __forceinline__ void load_vu(const TreeView& tr, const RaySource& rs, int64_t r, double v[D], double u[D]) {
   const int d = tr.d;
   if (rs.mode == 0) {
 #pragma unroll
@@ -78,6 +77,21 @@ __device__ __forceinline__ void load_ray(const TreeView& tr, const RaySource& rs
       v[k] = k < d ? rs.origins[r * d + k] : 0.0;
       u[k] = k < d ? rs.dirs[r * d + k] : 0.0;
     }
+  } else {
+    const int32_t cell = rs.mc_cell ? rs.mc_cell[r] : (int32_t)(r / rs.mc_rpc);
+    const int32_t k = rs.mc_cell ? rs.mc_ray[r] : (int32_t)(r % rs.mc_rpc);
+    mc_direction<D>(rs.seed, rs.set, (uint32_t)cell, (uint32_t)k, d, u);
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = k < d ? tr.X[(int64_t)cell * d + k] : 0.0;
+  }
+}
+
+// Loads ray r of the source: origin v, direction u, eta (m ids, eta[0] = g).
+template <int D>
+__device__ __forceinline__ void load_ray(const TreeView& tr, const RaySource& rs, int64_t r, double v[D], double u[D],
+                                         int32_t eta[D + 1], int& m) {
+  load_vu<D>(tr, rs, r, v, u);
+  if (rs.mode == 0) {
     m = 0;
     for (int q = 0; q < rs.eta_stride && q < D + 1; ++q) {
       const int32_t e = rs.eta[r * rs.eta_stride + q];
@@ -85,12 +99,7 @@ __device__ __forceinline__ void load_ray(const TreeView& tr, const RaySource& rs
       eta[m++] = e;
     }
   } else {
-    const int32_t cell = rs.mc_cell ? rs.mc_cell[r] : (int32_t)(r / rs.mc_rpc);
-    const int32_t k = rs.mc_cell ? rs.mc_ray[r] : (int32_t)(r % rs.mc_rpc);
-    mc_direction<D>(rs.seed, rs.set, (uint32_t)cell, (uint32_t)k, d, u);
-#pragma unroll
-    for (int k = 0; k < D; ++k) v[k] = k < d ? tr.X[(int64_t)cell * d + k] : 0.0;
-    eta[0] = cell;
+    eta[0] = rs.mc_cell ? rs.mc_cell[r] : (int32_t)(r / rs.mc_rpc);
     m = 1;
   }
 }
@@ -517,9 +526,43 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
 // ------------------------------------------------------------------------
 constexpr int kThrRays = 128;  // threads (rays in flight) per block
 
+// Binary32 coordinates of node id (zeros when !valid): from the rows padded
+// to 16-byte vectors where they exist (d <= 8), else one by one.
 template <int D>
-__global__ void __launch_bounds__(kThrRays) k_ray_list_thr(TreeView tr, RaySource rs, RayOut ro, Counters* ctr,
-                                                           unsigned long long* work) {
+__device__ __forceinline__ void load_x32(const TreeView& tr, int32_t id, bool valid, float (&x)[D]) {
+  if constexpr (D <= 8) {
+    if (tr.X32v != nullptr) {
+      constexpr int Q = (D + 3) / 4;
+      const float4* row = tr.X32v + (int64_t)id * tr.x32q;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        const float4 f = (valid && j < tr.x32q) ? row[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float e[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (4 * j + k < D) x[4 * j + k] = e[k];
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) x[k] = (valid && k < tr.d) ? tr.X32[(int64_t)id * tr.d + k] : 0.f;
+}
+
+// Upper bound of the norm from the binary32 sum of squares ww, with the same
+// margin (1 + gam) as sqrtf(ww) (1 + gam) plus 2^-20 for the reciprocal square
+// root (documented error 2 ulp) and the product; 0 for ww = 0, inf for
+// ww = inf.
+__device__ __forceinline__ float norm_up(float ww, float gam) {
+  const float s = ww < INFINITY ? fmaxf(ww * rsqrtf(ww), 0.f) : INFINITY;
+  return s * (1.f + gam + 0x1p-20f);
+}
+
+// Six blocks per SM at d <= 6 (80 registers): nothing binary64 stays live
+// through the scan (the recheck loads the ray again).
+template <int D>
+__global__ void __launch_bounds__(kThrRays, (D <= 6 ? 6 : D <= 8 ? 4 : 3))
+    k_ray_list_thr(TreeView tr, RaySource rs, RayOut ro, Counters* ctr, unsigned long long* work) {
   __shared__ int32_t s_cid[kThrRays][kCmax];
   __shared__ float s_ctlo[kThrRays][kCmax];
   __shared__ int32_t s_eta[kThrRays][D + 1];
@@ -531,7 +574,7 @@ __global__ void __launch_bounds__(kThrRays) k_ray_list_thr(TreeView tr, RaySourc
   const float B = tr.coord_abs;
   const float gam = (float)(D + 1) * kU32 * 1.01f;
   const float EW = 4.01f * kU32 * B;
-  unsigned long long n_pairs = 0, n_rech = 0, n_over = 0;
+  unsigned n_pairs = 0, n_rech = 0;  // per thread; added up in 64 bits at the end
   const int64_t R = rs.R_dev ? min((int64_t)*rs.R_dev, rs.R) : rs.R;
   while (true) {
     unsigned long long b = 0;
@@ -618,10 +661,18 @@ __global__ void __launch_bounds__(kThrRays) k_ray_list_thr(TreeView tr, RaySourc
         }
       }
     }
-    Ball<D> ball;
-    make_ball<D>(g32, p32, u32, T, B, ball);
-    float far2 = far_radius2<D>(tr, ball, g32);
-    float wwx = ww_exit(far2, gam, EW, D);
+    // reach of the ball of the current T and the squared-distance threshold
+    // beyond which a list entry (and every later one) lies outside it
+    float far2, wwx;
+    bool stale = false;
+    auto refresh = [&]() {
+      Ball<D> ball;
+      make_ball<D>(g32, p32, u32, T, B, ball);
+      far2 = far_radius2<D>(tr, ball, g32);
+      wwx = ww_exit(far2, gam, EW, D);
+      stale = false;
+    };
+    refresh();
     // ---- list scan ----
     const int32_t* lst = tr.knn + (int64_t)g * tr.K;
     const int n = tr.kcnt[g];
@@ -632,19 +683,20 @@ __global__ void __launch_bounds__(kThrRays) k_ray_list_thr(TreeView tr, RaySourc
     int32_t nid = n > 0 ? lst[0] : 0;
     int32_t nnid = n > 1 ? lst[1] : 0;
     float xn[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) xn[k] = (k < d && n > 0) ? tr.X32[(int64_t)nid * d + k] : 0.f;
+    load_x32<D>(tr, nid, n > 0, xn);
     for (; c < n; ++c) {
+      // a lowered T is used by the screening at once; the exit threshold
+      // follows every fourth entry, in step on all lanes (a threshold from a
+      // larger T is still valid: a node that can beat the smaller T lies in
+      // the ball of the larger one; it only ends the scan a little later)
+      if (stale && (c & 3) == 0) refresh();
       const int32_t id = nid;
       float xc[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) xc[k] = xn[k];
       nid = nnid;
       if (c + 2 < n) nnid = lst[c + 2];
-      if (c + 1 < n) {
-#pragma unroll
-        for (int k = 0; k < D; ++k) xn[k] = k < d ? tr.X32[(int64_t)nid * d + k] : 0.f;
-      }
+      load_x32<D>(tr, nid, c + 1 < n, xn);
       float w[D];
       float den = 0.f, ww = 0.f, pw = 0.f;
 #pragma unroll
@@ -662,7 +714,7 @@ __global__ void __launch_bounds__(kThrRays) k_ray_list_thr(TreeView tr, RaySourc
         for (int k = 0; k < D; ++k) pw = fmaf(p32[k], w[k], pw);
       }
       const float num = fmaf(-2.f, pw, ww);
-      const float wn = sqrtf(ww) * (1.f + gam);
+      const float wn = norm_up(ww, gam);
       const float Eden = fmaf(a1, wn, a0);
       const float dh = den + Eden;
       if (!(dh > 0.f)) continue;
@@ -681,9 +733,7 @@ __global__ void __launch_bounds__(kThrRays) k_ray_list_thr(TreeView tr, RaySourc
       if (nlo > 0.f) tlo = __fdiv_rn(nlo, 2.f * dh) * (1.f - 4.f * kU32);
       if (thi < T) {
         T = thi;
-        make_ball<D>(g32, p32, u32, T, B, ball);
-        far2 = far_radius2<D>(tr, ball, g32);
-        wwx = ww_exit(far2, gam, EW, D);
+        stale = true;
       }
       if (!overflow && tlo <= T) {
         if (nc == kCmax) {  // drop entries the bound has excluded
@@ -705,8 +755,11 @@ __global__ void __launch_bounds__(kThrRays) k_ray_list_thr(TreeView tr, RaySourc
         }
       }
     }
-    n_pairs += (unsigned long long)c;
-    if (!certified) certified = true_d2_lower(tr.kcert[g], gam, EW, D) >= far2;
+    n_pairs += (unsigned)c;
+    if (!certified) {
+      if (stale) refresh();
+      certified = true_d2_lower(tr.kcert[g], gam, EW, D) >= far2;
+    }
     const int64_t op = out_pos(rs, ro, r);
     if (!certified) {  // finished by the tree walk, from the bound found so far
       const unsigned long long k = atomicAdd(&ctr->fallback, 1ull);
@@ -719,12 +772,12 @@ __global__ void __launch_bounds__(kThrRays) k_ray_list_thr(TreeView tr, RaySourc
       const unsigned long long k = atomicAdd(&ctr->overflow, 1ull);
       if ((int64_t)k < ro.overflow_cap) ro.overflow_list[k] = (int32_t)r;
       else atomicOr(&ctr->flags, kFlagCandOverflow);
-      ++n_over;
       ro.hit[op] = kNoId;
       ro.t[op] = NAN;
       continue;
     }
     // ---- binary64 recheck, canonical order ----
+    load_vu<D>(tr, rs, r, v, u);  // loaded again rather than kept in registers through the scan
     double bt = INFINITY;
     int bc = 2, bk = 0;
     for (int q = 0; q < nc; ++q) {
@@ -774,15 +827,15 @@ __global__ void __launch_bounds__(kThrRays) k_ray_list_thr(TreeView tr, RaySourc
     ro.t[op] = bt;
     if (ro.screen_err) ro.screen_err[op] = (bt > 0.0 && bt < INFINITY) ? (float)((T - bt) / bt) : 0.f;
   }
+  unsigned long long sp = n_pairs, sr = n_rech;
   for (int o = 16; o; o >>= 1) {
-    n_pairs += __shfl_xor_sync(kFull, n_pairs, o);
-    n_rech += __shfl_xor_sync(kFull, n_rech, o);
+    sp += __shfl_xor_sync(kFull, sp, o);
+    sr += __shfl_xor_sync(kFull, sr, o);
   }
   if (lane == 0) {
-    atomicAdd(&ctr->pairs, n_pairs);
-    atomicAdd(&ctr->rechecked, n_rech);
+    atomicAdd(&ctr->pairs, sp);
+    atomicAdd(&ctr->rechecked, sr);
   }
-  (void)n_over;
 }
 
 // ------------------------------------------------------------------------
@@ -1265,6 +1318,15 @@ __global__ void k_to_f32(const double* X, int64_t n, float* out) {
   if (i < n) out[i] = __double2float_rn(X[i]);
 }
 
+// out[i][j] = binary32 of X[i][j] for j < d, 0 for d <= j < 4q.
+__global__ void k_to_f32v(const double* X, int64_t N, int d, int q, float* out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= N * q * 4) return;
+  const int64_t i = t / (4 * q);
+  const int j = (int)(t - i * 4 * q);
+  out[t] = j < d ? __double2float_rn(X[i * d + j]) : 0.f;
+}
+
 template <int D>
 cudaError_t launch_knn_d(TreeView* tv, int K, float r0, float rmax, int32_t* knn, int32_t* kcnt, float* kcert,
                          cudaStream_t st) {
@@ -1406,6 +1468,15 @@ cudaError_t build_knn(TreeView* tv, int K, cudaStream_t st, DevBufs& bufs) {
   k_to_f32<<<(unsigned)((N * d + 255) / 256), 256, 0, st>>>(tv->X, N * d, X32);
   count_launch();
   tv->X32 = X32;
+  if (d <= 8) {  // the same coordinates in rows of 16-byte vectors, zero padded
+    const int q = (d + 3) / 4;
+    float4* X32v = nullptr;
+    if ((e = bufs.alloc_n(&X32v, (size_t)N * q))) return e;
+    k_to_f32v<<<(unsigned)((N * q * 4 + 255) / 256), 256, 0, st>>>(tv->X, N, d, q, reinterpret_cast<float*>(X32v));
+    count_launch();
+    tv->X32v = X32v;
+    tv->x32q = q;
+  }
   // initial radius: about 2K nodes expected in the ball for the node density
   // of the bounding box of the root
   double vol = 1.0, diag2 = 0.0;

@@ -55,6 +55,12 @@ def lib():
         L.or_mc_reduce.argtypes = [P, i64, i32, i64, u64, u32, P, P, P, P, P, P, i64]
         L.or_mc_eval_fixed.argtypes = [P, i64, i32, i64, u64, u32, P, P, P, P, P]
         L.or_mc_adjoint.argtypes = [P, i64, i32, i64, u64, u32, P, P, P, P, P, P, P]
+        L.or_func_eval.restype = ctypes.c_double
+        L.or_func_eval.argtypes = [i32, i32, P, i32, P]
+        L.or_mc_tsample.restype = ctypes.c_double
+        L.or_mc_tsample.argtypes = [u64, u32, u32, u32, u32]
+        L.or_mc_tsamples.argtypes = [u64, u32, i64, i64, i64, P]
+        L.or_mc_integrals.argtypes = [P, i64, i32, i64, u64, u32, i64, P, P, P, P, P, i32, i32, P, i64, P, P]
         L.or_vertex_coords.restype = ctypes.c_int
         L.or_vertex_coords.argtypes = [P, i32, P, P]
         L.or_search_direction.restype = ctypes.c_int
@@ -241,3 +247,59 @@ def vertices(X, seed_node: int = 0, max_vertices: int | None = None):
     order = np.lexsort(tuples.T[::-1])
     return tuples[order], coords[order], {"raycasts": int(stats[0]), "rediscoveries": int(stats[1]),
                                           "ties": int(stats[2])}
+
+
+# --- Monte Carlo function integrals -------------------------------------------
+def func_code(f, d: int):
+    """f as (kind, axis, coef): ("one",), ("poly2", c0, b, q) or ("sin_sq", axis)."""
+    coef = np.zeros(1 + 2 * d)
+    if f[0] == "one":
+        return 0, 0, coef
+    if f[0] == "poly2":
+        coef[0] = f[1]
+        coef[1:1 + d] = np.asarray(f[2], dtype=np.float64)[:d]
+        coef[1 + d:] = np.asarray(f[3], dtype=np.float64)[:d]
+        return 1, 0, coef
+    if f[0] == "sin_sq":
+        return 2, int(f[1]), coef
+    raise ValueError(f)
+
+
+def func_eval(f, y):
+    """f at the points y (n x d), by the oracle's evaluation."""
+    y = _f64(np.atleast_2d(y))
+    kind, axis, coef = func_code(f, y.shape[1])
+    return np.array([lib().or_func_eval(kind, axis, _p(coef), y.shape[1], _p(np.ascontiguousarray(r)))
+                     for r in y])
+
+
+def mc_tsamples(seed: int, set_id: int, N: int, R: int, m: int) -> np.ndarray:
+    """t_ks of cells 0..N-1 (N x R x m)."""
+    out = np.empty((N, R, m))
+    lib().or_mc_tsamples(seed, set_id, N, R, m, _p(out))
+    return out
+
+
+def mc_integrals(X, R: int, seed: int, cells, hit, l, rowptr, col, f, m: int, set_id: int = 0):
+    """Algorithm 3's F_V (per cell) and F_d (per CSR entry) for the given
+    cells: hit, l are their rows (len(cells) x R), rowptr/col their CSR rows
+    (rowptr local, starting at 0).  Returns (FV, Fd)."""
+    X = _f64(X)
+    N, d = X.shape
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    hit = np.ascontiguousarray(hit, dtype=np.int32).reshape(len(cells), R)
+    l = _f64(l).reshape(len(cells), R)
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    kind, axis, coef = func_code(f, d)
+    FV = np.empty(len(cells))
+    Fd = np.empty(max(int(rowptr[-1]), 1))
+    lib().or_mc_integrals(_p(X), N, d, R, seed, set_id, len(cells), _p(cells), _p(hit), _p(l), _p(rowptr), _p(col),
+                          kind, axis, _p(coef), m, _p(FV), _p(Fd))
+    return FV, Fd[:int(rowptr[-1])]
+
+
+def mc_integrals_all(X, R: int, seed: int, res: MCResult, f, m: int, set_id: int = 0):
+    """F_V and F_d of every cell of an oracle MC run."""
+    N = X.shape[0]
+    return mc_integrals(X, R, seed, np.arange(N), res.hit, res.l, res.rowptr, res.col, f, m, set_id)

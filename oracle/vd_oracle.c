@@ -468,6 +468,94 @@ void or_mc_adjoint(const double* X, int64_t N, int d, int64_t R, uint64_t seed, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Monte Carlo integrals of a function f over the cell boundaries and the    */
+/* cell volumes (Section 3.1, Eqs. mc-help1 and full_MC_integration,         */
+/* Algorithm 3), from the rays of a finished run (directions, hits, l):      */
+/*   F_d[i][j] = S_{d-1}/R sum_{k: hit j} f(r_k) a_k,  r_k = x_i + l_k u_k,  */
+/*               a_k the area term of A above (so f = 1 gives A exactly);    */
+/*   F_V[i]    = S_{d-1}/(R m) sum_k sum_{s<m} f(y_ks) t_ks^{d-1} l_k^d,     */
+/*               y_ks = x_i + (t_ks l_k) u_k,  t_ks ~ U(0,1).                */
+/* F_V is the polar change of variables around x_i, dV = l^d t^{d-1} dt dS   */
+/* over the sphere and t in (0,1), with the normalisation of Algorithm 3:    */
+/* the mean of t^{d-1} over uniform t is 1/d, so f = 1 estimates the volume. */
+/* t_ks = (w + 1/2) 2^-32 with w word (s mod 4) of Philox4x32-10 at counter  */
+/* (2^31 + s div 4, k, cell, set), key (seed low, seed high): counters the   */
+/* directions (block < 4) never use.  Sums run over k, then s, in order.     */
+/* f (kind, axis, coef = c0, b[0..d), q[0..d)):                              */
+/*   kind 0: f = 1;                                                          */
+/*   kind 1: f = c0 + sum_a b_a y_a + sum_a q_a y_a^2, left to right, the    */
+/*           linear terms first;                                             */
+/*   kind 2: f = sin(y_axis^2) (the integrand of the paper's Section 4).    */
+/* ------------------------------------------------------------------------ */
+double or_func_eval(int kind, int axis, const double* coef, int d, const double* y) {
+  if (kind == 1) {
+    double s = coef[0];
+    for (int a = 0; a < d; ++a) s = s + coef[1 + a] * y[a];
+    for (int a = 0; a < d; ++a) s = s + coef[1 + d + a] * (y[a] * y[a]);
+    return s;
+  }
+  if (kind == 2) return sin(y[axis] * y[axis]);
+  return 1.0;
+}
+
+double or_mc_tsample(uint64_t seed, uint32_t set, uint32_t cell, uint32_t ray, uint32_t s) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t ctr[4] = {0x80000000u + (s >> 2), ray, cell, set}, o[4];
+  or_philox4x32_10(ctr, key, o);
+  return ((double)o[s & 3] + 0.5) * 0x1p-32;
+}
+
+/* Cells cells[0..ncells): their rays' hit and l in rows of R (hit, l), their  */
+/* CSR rows in rowptr (local, rowptr[0] = 0) and col; writes FV[c] and the    */
+/* row entries of Fd. */
+void or_mc_integrals(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set, int64_t ncells,
+                     const int64_t* cells, const int32_t* hit, const double* l, const int64_t* rowptr,
+                     const int32_t* col, int kind, int axis, const double* coef, int64_t m, double* FV,
+                     double* Fd) {
+  (void)N;
+  const double S = or_sphere_area(d);
+  const double cA = S / (double)R, cV = S / ((double)R * (double)m);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t c = 0; c < ncells; ++c) {
+    const int64_t i = cells[c];
+    const double* xi = X + i * d;
+    const int32_t* h = hit + c * R;
+    const double* lc = l + c * R;
+    for (int64_t q = rowptr[c]; q < rowptr[c + 1]; ++q) Fd[q] = 0.0;
+    double fv = 0.0;
+    for (int64_t k = 0; k < R; ++k) {
+      double u[OR_MAXD], r[OR_MAXD], y[OR_MAXD];
+      or_mc_direction(seed, set, (uint32_t)i, (uint32_t)k, d, u);
+      const double lk = lc[k];
+      for (int a = 0; a < d; ++a) r[a] = xi[a] + lk * u[a];
+      int64_t lo = rowptr[c], hi = rowptr[c + 1];
+      while (hi - lo > 1) { /* the hit id's entry in the row */
+        int64_t mid = (lo + hi) / 2;
+        if (col[mid] <= h[k]) lo = mid; else hi = mid;
+      }
+      Fd[lo] = Fd[lo] + or_func_eval(kind, axis, coef, d, r) * area_term(X, d, i, h[k], lk, u);
+      const double ld = ipow(lk, d);
+      for (int64_t s2 = 0; s2 < m; ++s2) {
+        const double t = or_mc_tsample(seed, set, (uint32_t)i, (uint32_t)k, (uint32_t)s2);
+        const double tl = t * lk;
+        for (int a = 0; a < d; ++a) y[a] = xi[a] + tl * u[a];
+        const double w = ipow(t, d - 1) * ld;
+        fv = fv + or_func_eval(kind, axis, coef, d, y) * w;
+      }
+    }
+    FV[c] = cV * fv;
+    for (int64_t q = rowptr[c]; q < rowptr[c + 1]; ++q) Fd[q] = cA * Fd[q];
+  }
+}
+
+void or_mc_tsamples(uint64_t seed, uint32_t set, int64_t ncells, int64_t R, int64_t m, double* out) {
+  for (int64_t i = 0; i < ncells; ++i)
+    for (int64_t k = 0; k < R; ++k)
+      for (int64_t s = 0; s < m; ++s)
+        out[(i * R + k) * m + s] = or_mc_tsample(seed, set, (uint32_t)i, (uint32_t)k, (uint32_t)s);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Vertices: Algorithm 2 (VoronoiGraph) with the box faces as generators.   */
 /* ------------------------------------------------------------------------ */
 

@@ -31,7 +31,9 @@ def _polygon_area_centroid_3d(P):
 
 
 def exact_cells(X: np.ndarray, face_id):
-    """Per cell i: dict(volume=..., facets={gen_id: (area, centroid)})."""
+    """Per cell i: dict(volume=..., facets={gen_id: (area, centroid)},
+    facet_pts={gen_id: the facet's vertices (d = 2: its two end points)},
+    centroid=the cell's centroid)."""
     N, d = X.shape
     assert d in (2, 3)
     cells = []
@@ -49,6 +51,7 @@ def exact_cells(X: np.ndarray, face_id):
         verts = hs.intersections
         vol = ConvexHull(verts).volume
         facets = {}
+        facet_pts = {}
         dual = hs.dual_facets
         for h in range(H.shape[0]):
             on = [v for v in range(len(verts)) if h in dual[v]]
@@ -63,6 +66,7 @@ def exact_cells(X: np.ndarray, face_id):
                 if length < 1e-14:
                     continue
                 facets[int(ids[h])] = (length, P.mean(axis=0))
+                facet_pts[int(ids[h])] = P[[np.argmin(P @ (P[-1] - P[0])), np.argmax(P @ (P[-1] - P[0]))]]
             else:
                 if len(P) < 3:
                     continue
@@ -70,8 +74,24 @@ def exact_cells(X: np.ndarray, face_id):
                 if area < 1e-14:
                     continue
                 facets[int(ids[h])] = (area, cen)
-        cells.append({"volume": vol, "facets": facets})
+                facet_pts[int(ids[h])] = P
+        cells.append({"volume": vol, "facets": facets, "facet_pts": facet_pts,
+                      "centroid": _fan_centroid(verts, X[i])})
     return cells
+
+
+def _fan_centroid(verts, p0):
+    """Centroid of the convex hull of verts, from simplices fanned out of the
+    interior point p0 over the hull's boundary facets."""
+    d = verts.shape[1]
+    hull = ConvexHull(verts)
+    vol, cen = 0.0, np.zeros(d)
+    for simp in hull.simplices:
+        P = verts[simp]
+        v = abs(np.linalg.det(P - p0)) / float(np.prod(np.arange(1, d + 1)))
+        vol += v
+        cen += v * (P.sum(axis=0) + p0) / (d + 1)
+    return cen / vol
 
 
 def facet_height(X, i, gid, face_axis_side):

@@ -423,6 +423,28 @@ MC_WORKLOAD = ("MC volumes + interface areas + adjoint, d=4, N=100000 iid unifor
                "1024 rays per cell")
 
 
+def time_integrals(vd, m, N, R, msamp, stream, reps=3):
+    """Algorithm 3's function integrals F_V (msamp samples per ray) and F_d of
+    f = sin(x_1^2) on the rays of a finished MC run: CUDA-event time of one
+    vd_mc_integrals call (device outputs), mean of reps after one warm-up."""
+    import torch
+    nnz = vd.vd_mc_get(m)
+    FV = torch.empty(N, dtype=torch.float64, device="cuda")
+    Fd = torch.empty(max(nnz, 1), dtype=torch.float64, device="cuda")
+    f = vd.func_sin_sq(0)
+    vd.vd_mc_integrals(m, f, msamp, FV, Fd[:nnz])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        vd.vd_mc_integrals(m, f, msamp, FV, Fd[:nnz])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"f": "sin(x_1^2)", "samples_per_ray": msamp, "ms": ms, "cells_per_s": N / (ms / 1000.0),
+            "volume_samples_per_s": N * R * msamp / (ms / 1000.0)}
+
+
 def run_mc(args, vd, stream):
     """Secondary line of the metric: MC vol+grad cells/s on the MC workload,
     binary32-screened path, tensor-core (fp16 tcgen05) screened path and
@@ -462,11 +484,13 @@ def run_mc(args, vd, stream):
         h = torch.empty((N, R), dtype=torch.int32, device="cuda")
         vd.vd_mc_rays(m, h, None)
         hits[name] = h
-        vd.vd_mc_free(m)
-        vd.vd_destroy(ctx)
         out[name] = {"cells_per_s": N / (ms / 1000.0), "rays_per_s": N * R / (ms / 1000.0), "ms_per_step": ms,
                      "raycast_ms": st["raycast_ms"], "tree_walk_rays": st["fallback_rays"],
                      "pairs_per_ray": st["pairs_screened"] / max(st["rays"], 1)}
+        if name == "mixed":
+            out["integrals"] = time_integrals(vd, m, N, R, args.mc_m, stream)
+        vd.vd_mc_free(m)
+        vd.vd_destroy(ctx)
     out["value"] = out["mixed"]["cells_per_s"]
     out["speedup_vs_fp64"] = out["mixed"]["cells_per_s"] / out["fp64"]["cells_per_s"]
     out["hits_identical_to_fp64"] = bool(torch.equal(hits["mixed"], hits["fp64"]) and
@@ -595,6 +619,7 @@ def main():
     ap.add_argument("--batch-rays", type=int, default=256)
     ap.add_argument("--mc-n", type=int, default=100000)
     ap.add_argument("--mc-rays", type=int, default=1024)
+    ap.add_argument("--mc-m", type=int, default=2, help="samples per ray of the function-integral timing")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -173,6 +173,34 @@ vd_status vd_mc_rays(const vd_mc* mc, int32_t* hit, double* l, int32_t on_device
 /* Adjoint of the estimator with directions and argmins held fixed:
  * gX = sum_i gV_i dV_i/dX + sum_ij gA_ij dA_ij/dX (N x d float64). */
 vd_status vd_mc_adjoint(const vd_mc* mc, const double* gV, const double* gA, double* gX, int32_t on_device);
+/* Monte Carlo integrals of a function f over the cells (Section 3.1, Eqs.
+ * mc-help1 and full_MC_integration, Algorithm 3), from the rays of a
+ * finished vd_mc_integrate (its directions, hit ids and lengths):
+ *   Fd_ij = S_{d-1}/R sum_{k: hit j} f(r_k) l_k^{d-1} / |n_ij . u_k|,
+ *           r_k = x_i + l_k u_k the ray's hit point (f = 1 gives A_ij);
+ *   FV_i  = S_{d-1}/(R m) sum_k sum_{s<m} f(x_i + t_ks l_k u_k) t_ks^{d-1} l_k^d,
+ *           m samples t_ks ~ U(0,1) along each ray (f = 1 estimates V_i).
+ * t_ks = (w + 1/2) 2^-32, w = word (s mod 4) of Philox4x32-10 at counter
+ * (2^31 + s div 4, k, i, set), key (seed low, seed high) of the run.
+ * Everything in binary64; the sums are deterministic (fixed order).
+ * FV: N float64; Fd: nnz float64 in the order of vd_mc_get's col.  Either
+ * may be NULL.  m >= 1 (ignored when FV is NULL). */
+typedef enum {
+  VD_F_ONE = 0,    /* f = 1                                               */
+  VD_F_POLY2 = 1,  /* f = c0 + sum_a b[a] y_a + sum_a q[a] y_a^2, binary64,
+                      linear terms first, each sum left to right          */
+  VD_F_SIN_SQ = 2  /* f = sin(y_axis^2), the integrand of Section 4       */
+} vd_func_kind;
+
+typedef struct {
+  int32_t kind;           /* vd_func_kind                                   */
+  int32_t axis;           /* VD_F_SIN_SQ: 0 <= axis < d                     */
+  double c0;              /* VD_F_POLY2 coefficients (entries >= d unused)  */
+  double b[VD_MAX_D];
+  double q[VD_MAX_D];
+} vd_func;
+
+vd_status vd_mc_integrals(const vd_mc* mc, const vd_func* f, int64_t m, double* FV, double* Fd, int32_t on_device);
 vd_status vd_mc_stats(const vd_mc* mc, vd_stats* out);
 int64_t vd_mc_count(const vd_mc* mc);
 void vd_mc_free(vd_mc* mc);

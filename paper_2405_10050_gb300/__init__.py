@@ -37,6 +37,16 @@ class MCResult:
         vd.vd_mc_adjoint(self._mc, gV.to(torch.float64).contiguous(), gA.to(torch.float64).contiguous(), gX)
         return gX
 
+    def integrals(self, f, m: int = 2):
+        """Algorithm 3's function integrals of f (a vd.vd_func, e.g.
+        vd.func_sin_sq(0)): F_V per cell (N) and F_d per CSR entry (aligned
+        with col), m samples along each ray for F_V (library kernels)."""
+        import torch
+        FV = torch.empty(self.V.shape[0], dtype=torch.float64, device="cuda")
+        Fd = torch.empty(max(self.A.shape[0], 1), dtype=torch.float64, device="cuda")
+        vd.vd_mc_integrals(self._mc, f, m, FV, Fd)
+        return FV, Fd[:self.A.shape[0]]
+
     def free(self):
         if self._mc is not None:
             vd.vd_mc_free(self._mc)

@@ -24,6 +24,9 @@ cudaError_t mc_adjoint(const double* X, int64_t N, int d, int64_t R, uint64_t se
                        const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, int64_t nnz,
                        const double* gV, const double* gA, double* gX, const double* U, DevBufs& scratch,
                        cudaStream_t st);
+cudaError_t mc_integrals(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
+                         const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col,
+                         const double* U, const vd_func& f, int64_t m, double* FV, double* Fd, cudaStream_t st);
 cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, Workspace& ws,
                               DevBufs& out_bufs, int32_t** tuples, double** coords, int64_t* nv, vd_stats* stats,
                               Counters* ctr, cudaStream_t st, char* err, size_t errlen);
@@ -558,6 +561,32 @@ vd_status vd_mc_adjoint(const vd_mc* mc, const double* gV, const double* gA, dou
                        gVd, gAd, gXd, mc->u, tmp, mc->st);
   if (e == cudaSuccess && !on_device)
     e = cudaMemcpyAsync(gX, gXd, (size_t)mc->N * mc->d * sizeof(double), cudaMemcpyDeviceToHost, mc->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(mc->st);
+  cudaStreamSynchronize(mc->st);
+  tmp.release();
+  return e == cudaSuccess ? VD_OK : (e == cudaErrorMemoryAllocation ? VD_ENOMEM : VD_ECUDA);
+}
+
+vd_status vd_mc_integrals(const vd_mc* mc, const vd_func* f, int64_t m, double* FV, double* Fd, int32_t on_device) {
+  if (!mc || !f || (!FV && !Fd)) return VD_EINVAL;
+  if (f->kind != VD_F_ONE && f->kind != VD_F_POLY2 && f->kind != VD_F_SIN_SQ) return VD_EINVAL;
+  if (f->kind == VD_F_SIN_SQ && (f->axis < 0 || f->axis >= mc->d)) return VD_EINVAL;
+  if (FV && (m < 1 || m > ((int64_t)1 << 32))) return VD_EINVAL;  // sample blocks s / 4 below 2^31
+  if (!FV) m = 1;
+  DevBufs tmp;
+  double *FVd = FV, *Fdd = Fd;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    if (FV) e = tmp.alloc_n(&FVd, (size_t)mc->N);
+    if (e == cudaSuccess && Fd) e = tmp.alloc_n(&Fdd, (size_t)std::max<int64_t>(mc->nnz, 1));
+  }
+  if (e == cudaSuccess)
+    e = vd::mc_integrals(mc->X, mc->N, mc->d, mc->R, mc->seed, mc->set, mc->hit, mc->l, mc->rowptr, mc->col, mc->u, *f,
+                         m, FVd, Fdd, mc->st);
+  if (e == cudaSuccess && !on_device && FV)
+    e = cudaMemcpyAsync(FV, FVd, (size_t)mc->N * sizeof(double), cudaMemcpyDeviceToHost, mc->st);
+  if (e == cudaSuccess && !on_device && Fd && mc->nnz > 0)
+    e = cudaMemcpyAsync(Fd, Fdd, (size_t)mc->nnz * sizeof(double), cudaMemcpyDeviceToHost, mc->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(mc->st);
   cudaStreamSynchronize(mc->st);
   tmp.release();

@@ -263,6 +263,136 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill(const double* X, int6
   fill_item<D>(X, d, i, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, Ls[w], Ts[w], Es[w], lane, U);
 }
 
+// ---- function integrals F_d, F_V (Algorithm 3's F and F_V) ----
+// f at y in binary64, in the operation order include/vd.h states.
+template <int D>
+__device__ __forceinline__ double func_at(const vd_func& f, int d, const double (&y)[D]) {
+  if (f.kind == VD_F_POLY2) {
+    double s = f.c0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (a < d) s = __dadd_rn(s, __dmul_rn(f.b[a], y[a]));
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (a < d) s = __dadd_rn(s, __dmul_rn(f.q[a], __dmul_rn(y[a], y[a])));
+    return s;
+  }
+  if (f.kind == VD_F_SIN_SQ) {
+    double ya = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (a == f.axis) ya = y[a];
+    return sin(__dmul_rn(ya, ya));
+  }
+  return 1.0;
+}
+
+// y = x_i + s u (per component, product then sum)
+template <int D>
+__device__ __forceinline__ void ray_point(const double* X, int d, int64_t i, double s, const double (&u)[D],
+                                          double (&y)[D]) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) y[a] = a < d ? __dadd_rn(X[i * d + a], __dmul_rn(s, u[a])) : 0.0;
+}
+
+// l^{d-1} / |u_a| of a ray that hit the face id (the area term of a face hit)
+template <int D>
+__device__ __forceinline__ double face_term(double lk, int d, int32_t id, const double (&u)[D]) {
+  const int a = face_axis(id);
+  double ua = 0.0;
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+    if (c == a) ua = u[c];
+  return __ddiv_rn(ipow_d(lk, d - 1), fabs(ua));
+}
+
+// One warp per cell.  F_V: lanes take rays k = lane, lane + 32, ..., each
+// its m samples in order (four t per Philox call), then a butterfly.  F_d:
+// the two orders of the area fill above with each ray's term multiplied by
+// f at its hit point, so f = 1 reproduces A bit for bit.
+template <int D>
+__global__ void __launch_bounds__(kMcWarps * 32) k_mc_func(const double* X, int64_t N, int d, int64_t R,
+                                                           uint64_t seed, uint32_t set, const int32_t* hit,
+                                                           const double* l, const int64_t* rowptr,
+                                                           const int32_t* col, const double* U, vd_func f,
+                                                           int64_t m, double cV, double cA, double* FV, double* Fd) {
+  __shared__ int32_t Ls[kMcWarps][kMcList];
+  __shared__ double Ts[kMcWarps][32];
+  __shared__ int32_t Es[kMcWarps][32];
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (i >= N) return;
+  const int32_t* h = hit + i * R;
+  const double* li = l + i * R;
+  if (FV) {
+    double fv = 0.0;
+    for (int64_t k = lane; k < R; k += 32) {
+      double u[D], y[D];
+      ray_dir<D>(U, seed, set, i, k, R, d, u);
+      const double lk = li[k];
+      const double ld = ipow_d(lk, d);
+      for (int64_t s0 = 0; s0 < m; s0 += 4) {
+        uint32_t c[4] = {0x80000000u + (uint32_t)(s0 >> 2), (uint32_t)k, (uint32_t)i, set};
+        philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (s0 + q >= m) break;
+          const double t = __dmul_rn(__dadd_rn((double)c[q], 0.5), 0x1p-32);  // (w + 1/2) 2^-32, exact
+          ray_point<D>(X, d, i, __dmul_rn(t, lk), u, y);
+          fv = __dadd_rn(fv, __dmul_rn(func_at<D>(f, d, y), __dmul_rn(ipow_d(t, d - 1), ld)));
+        }
+      }
+    }
+    fv = warp_sum_d(fv);
+    if (lane == 0) FV[i] = __dmul_rn(cV, fv);
+  }
+  if (!Fd) return;
+  const int64_t q0 = rowptr[i], nnz = rowptr[i + 1] - q0;
+  if (nnz * kFewRays > R) {  // few rays per id: terms ray-parallel, sums in ascending ray order
+    for (int64_t e = q0 + lane; e < q0 + nnz; e += 32) Fd[e] = 0.0;
+    __syncwarp();
+    for (int64_t k0 = 0; k0 < R; k0 += 32) {
+      const int64_t k = k0 + lane;
+      if (k < R) {
+        const int32_t id = h[k];
+        double u[D], r[D];
+        ray_dir<D>(U, seed, set, i, k, R, d, u);
+        ray_point<D>(X, d, i, li[k], u, r);
+        const double a = id >= 0 ? node_area_term<D>(X, d, i, id, ipow_d(li[k], d)) : face_term<D>(li[k], d, id, u);
+        Es[w][lane] = (int32_t)(entry_of(col, q0, nnz, id) - q0);
+        Ts[w][lane] = __dmul_rn(func_at<D>(f, d, r), a);
+      }
+      __syncwarp();
+      if (lane == 0)
+        for (int r2 = 0; r2 < 32 && k0 + r2 < R; ++r2) Fd[q0 + Es[w][r2]] = __dadd_rn(Fd[q0 + Es[w][r2]], Ts[w][r2]);
+      __syncwarp();
+    }
+    for (int64_t e = q0 + lane; e < q0 + nnz; e += 32) Fd[e] = __dmul_rn(cA, Fd[e]);
+    return;
+  }
+  for (int64_t e = q0; e < q0 + nnz; ++e) {
+    const int32_t id = col[e];
+    double s = 0.0;
+    int64_t k0 = 0;
+    while (k0 < R) {
+      const int mm = gather_rays(h, R, id, &k0, Ls[w], lane);
+      for (int p = lane; p < mm; p += 32) {
+        const int32_t k = Ls[w][p];
+        double u[D], r[D];
+        ray_dir<D>(U, seed, set, i, k, R, d, u);
+        ray_point<D>(X, d, i, li[k], u, r);
+        // node hit: the factor 2 / |x_j - x_i| is applied once per id below
+        const double a = id >= 0 ? ipow_d(li[k], d) : face_term<D>(li[k], d, id, u);
+        s = __dadd_rn(s, __dmul_rn(func_at<D>(f, d, r), a));
+      }
+      __syncwarp();
+    }
+    s = warp_sum_d(s);
+    if (id >= 0) s = node_area_term<D>(X, d, i, id, s);
+    if (lane == 0) Fd[e] = __dmul_rn(cA, s);
+  }
+}
+
 // ---- batched reduction over many sets (items = all cells of all sets) ----
 __device__ __forceinline__ int find_set(const SetDesc* sets, int nsets, int64_t item) {
   int lo = 0, hi = nsets - 1;
@@ -624,6 +754,22 @@ cudaError_t mc_fill(const double* X, int64_t N, int d, int64_t R, uint64_t seed,
   if (d <= 4) return fill_d<4>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, U, st);
   if (d <= 8) return fill_d<8>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, U, st);
   return fill_d<16>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, U, st);
+}
+
+cudaError_t mc_integrals(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
+                         const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col,
+                         const double* U, const vd_func& f, int64_t m, double* FV, double* Fd, cudaStream_t st) {
+  const double S = sphere_area(d);
+  const double cV = S / ((double)R * (double)m), cA = S / (double)R;
+  const unsigned g = nblk(N * 32, kMcWarps * 32);
+  if (d <= 4)
+    k_mc_func<4><<<g, kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, U, f, m, cV, cA, FV, Fd);
+  else if (d <= 8)
+    k_mc_func<8><<<g, kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, U, f, m, cV, cA, FV, Fd);
+  else
+    k_mc_func<16><<<g, kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, U, f, m, cV, cA, FV, Fd);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t mc_adjoint(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,

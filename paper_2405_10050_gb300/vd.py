@@ -33,6 +33,34 @@ class vd_config(ctypes.Structure):
                 ("rays_per_block", ctypes.c_int32)]
 
 
+VD_F_ONE, VD_F_POLY2, VD_F_SIN_SQ = 0, 1, 2
+
+
+class vd_func(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("axis", ctypes.c_int32), ("c0", ctypes.c_double),
+                ("b", ctypes.c_double * 16), ("q", ctypes.c_double * 16)]
+
+
+def func_one():
+    """f = 1."""
+    return vd_func(kind=VD_F_ONE)
+
+
+def func_poly2(c0, b=(), q=()):
+    """f = c0 + sum_a b[a] y_a + sum_a q[a] y_a^2."""
+    f = vd_func(kind=VD_F_POLY2, c0=float(c0))
+    for a, v in enumerate(b):
+        f.b[a] = float(v)
+    for a, v in enumerate(q):
+        f.q[a] = float(v)
+    return f
+
+
+def func_sin_sq(axis=0):
+    """f = sin(y_axis^2)."""
+    return vd_func(kind=VD_F_SIN_SQ, axis=int(axis))
+
+
 class vd_stats(ctypes.Structure):
     _fields_ = [("rays", ctypes.c_int64), ("tiles_visited", ctypes.c_int64), ("pairs_screened", ctypes.c_int64),
                 ("rechecked", ctypes.c_int64), ("fallback_rays", ctypes.c_int64), ("overflow_rays", ctypes.c_int64),
@@ -46,7 +74,7 @@ class vd_stats(ctypes.Structure):
 EXPORTS = ["vd_kernel_launches", "vd_config_default", "vd_create", "vd_destroy", "vd_last_error", "vd_status_str", "vd_set_precision",
            "vd_last_stats", "vd_set_nodes", "vd_raycast", "vd_vertices", "vd_mesh_count", "vd_mesh_dim",
            "vd_mesh_copy", "vd_mesh_stats", "vd_mesh_free", "vd_mc_integrate", "vd_mc_get", "vd_mc_rays",
-           "vd_mc_adjoint", "vd_mc_stats", "vd_mc_count", "vd_mc_free", "vd_mc_directions",
+           "vd_mc_adjoint", "vd_mc_integrals", "vd_mc_stats", "vd_mc_count", "vd_mc_free", "vd_mc_directions",
            "vd_mc_integrate_batch", "vd_raycast_noalloc"]
 
 _lib = None
@@ -89,6 +117,7 @@ def load(build_if_missing: bool = True):
         "vd_mc_get": (i32, [P, P, P, P, P, P, i32]),
         "vd_mc_rays": (i32, [P, P, P, i32]),
         "vd_mc_adjoint": (i32, [P, P, P, P, i32]),
+        "vd_mc_integrals": (i32, [P, P, i64, P, P, i32]),
         "vd_mc_stats": (i32, [P, P]),
         "vd_mc_count": (i64, [P]),
         "vd_mc_free": (None, [P]),
@@ -263,6 +292,15 @@ def vd_mc_adjoint(mc, gV, gA, gX):
     pa, dev2, k2 = _ptr(gA, np.float64)
     px, dev3, k3 = _ptr(gX, np.float64)
     _check(None, load().vd_mc_adjoint(mc, pv, pa, px, dev3))
+
+
+def vd_mc_integrals(mc, f, m, FV=None, Fd=None):
+    """Algorithm 3's F_V (N) and F_d (nnz, vd_mc_get's col order) of f
+    (a vd_func) with m samples per ray."""
+    pv, dev, k1 = _ptr(FV, np.float64)
+    pd, dev2, k2 = _ptr(Fd, np.float64)
+    dev = dev if dev is not None else (dev2 or 0)
+    _check(None, load().vd_mc_integrals(mc, ctypes.byref(f), int(m), pv, pd, dev))
 
 
 def vd_mc_stats(mc):

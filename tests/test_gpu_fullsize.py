@@ -8,7 +8,8 @@ benchmark times, on outputs the oracle computes one by one:
   of the set; every edge of the whole set has exactly two endpoints and each
   cube corner appears once;
 * Monte Carlo (Algorithm 3), N = 100000 uniform nodes in [0,1]^4, 1024 rays
-  per cell, and N = 200000 nodes in [0,1]^16 from a 32-component Gaussian
+  per cell (with the function integrals F_V, F_d of sin(x_1^2), 2 samples
+  per ray, on sampled cells), and N = 200000 nodes in [0,1]^16 from a 32-component Gaussian
   mixture (sigma 0.1), 64 rays per cell: sampled rays equal the oracle's
   brute-force RayCast (hit id and l bit for bit), and the binary32, tensor
   core and binary64 paths agree on every ray;
@@ -108,6 +109,24 @@ def _mc_sample_check(orc, X, R, seed, hit, l, cells, rays_per_cell, rng, set_id=
         assert np.array_equal(l[row, ks], t0), (i, set_id)
 
 
+def _integrals_sample_check(orc, X, R, seed, res, cells, idx, m=2):
+    """Algorithm 3's F_V and F_d of f = sin(x_1^2) (m samples per ray) of the
+    whole set, compared on the sampled cells with the oracle's sums over the
+    same rays (within 1e-12 relative: every term is positive)."""
+    FV, Fd = res.integrals(vd.func_sin_sq(0), m)
+    rp = res.rowptr.cpu().numpy()
+    col = res.col.cpu().numpy()
+    Fd = Fd.cpu().numpy()
+    lrp = np.concatenate([[0], np.cumsum([rp[i + 1] - rp[i] for i in cells])])
+    lcol = np.concatenate([col[rp[i]:rp[i + 1]] for i in cells])
+    FV0, Fd0 = orc.mc_integrals(X, R, seed, cells, res.hit[idx].cpu().numpy(), res.l[idx].cpu().numpy(), lrp, lcol,
+                                ("sin_sq", 0), m)
+    FVs = FV[idx].cpu().numpy()
+    Fds = np.concatenate([Fd[rp[i]:rp[i + 1]] for i in cells])
+    assert np.all(np.abs(FVs - FV0) <= 1e-12 * np.abs(FV0) + 1e-300)
+    assert np.all(np.abs(Fds - Fd0) <= 1e-12 * np.abs(Fd0) + 1e-300)
+
+
 def _mc_full(X, R, seed, prec):
     vor = Voronoi(X, precision=prec)
     return vor, vor.mc_integrate(R, seed)
@@ -130,6 +149,7 @@ def test_mc_d4_n100000(orc):
             l = res.l[idx].cpu().numpy()
             _mc_sample_check(orc, X, R, seed, h[:2], l[:2], cells[:2], R, rng)
             _mc_sample_check(orc, X, R, seed, h[2:], l[2:], cells[2:], 48, rng)
+            _integrals_sample_check(orc, X, R, seed, res, cells, idx)
         else:
             assert torch.equal(res.hit, base.hit) and torch.equal(res.l, base.l)
             assert torch.equal(res.rowptr, base.rowptr) and torch.equal(res.col, base.col)

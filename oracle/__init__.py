@@ -61,6 +61,7 @@ def lib():
         L.or_mc_tsample.argtypes = [u64, u32, u32, u32, u32]
         L.or_mc_tsamples.argtypes = [u64, u32, i64, i64, i64, P]
         L.or_mc_integrals.argtypes = [P, i64, i32, i64, u64, u32, i64, P, P, P, P, P, i32, i32, P, i64, P, P]
+        L.or_hmc.argtypes = [P, i64, i32, P, P, P, P, P, i64, i32, i32, P, P, P, P, P]
         L.or_vertex_coords.restype = ctypes.c_int
         L.or_vertex_coords.argtypes = [P, i32, P, P]
         L.or_search_direction.restype = ctypes.c_int
@@ -303,3 +304,23 @@ def mc_integrals_all(X, R: int, seed: int, res: MCResult, f, m: int, set_id: int
     """F_V and F_d of every cell of an oracle MC run."""
     N = X.shape[0]
     return mc_integrals(X, R, seed, np.arange(N), res.hit, res.l, res.rowptr, res.col, f, m, set_id)
+
+
+def hmc(X, rowptr, col, A, tuples, coords, f):
+    """Section 3.3's heuristic MC: V_H (N), F_H (nnz), I_H (N) and the vertex
+    count K (nnz) of every CSR entry, from areas A and the diagram's vertices."""
+    X = _f64(X)
+    N, d = X.shape
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    A = _f64(A)
+    tuples = np.ascontiguousarray(tuples, dtype=np.int32).reshape(-1, d + 1)
+    coords = _f64(coords).reshape(-1, d)
+    kind, axis, coef = func_code(f, d)
+    nnz = int(rowptr[-1])
+    VH, IH = np.empty(N), np.empty(N)
+    FH = np.empty(max(nnz, 1))
+    K = np.empty(max(nnz, 1), np.int64)
+    lib().or_hmc(_p(X), N, d, _p(rowptr), _p(col), _p(A), _p(tuples), _p(coords), tuples.shape[0], kind, axis,
+                 _p(coef), _p(VH), _p(FH), _p(IH), _p(K))
+    return VH, FH[:nnz], IH, K[:nnz]

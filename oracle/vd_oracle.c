@@ -556,6 +556,97 @@ void or_mc_tsamples(uint64_t seed, uint32_t set, int64_t ncells, int64_t R, int6
 }
 
 /* ------------------------------------------------------------------------ */
+/* Heuristic Monte-Carlo integration (Section 3.3): from interface areas     */
+/* A_ij (the CSR of an MC run, or exact ones) and the vertices of the        */
+/* diagram (sorted tuples and coordinates, from the traversal):              */
+/*   V_i  = (1/d) sum_j h_ij A_ij   (h_ij = |x_j - x_i|/2, or the distance   */
+/*          from x_i to the box face j);                                     */
+/*   F_ij = (d/(d+1)) (1/K_ij) sum_k f(nu_k) A_ij + (1/(d+1)) f(y_ij) A_ij   */
+/*          over the K_ij vertices nu_k whose tuple holds both i and j, and  */
+/*          their mean y_ij;                                                 */
+/*   I_i  = sum_j (h_ij/d) ((d/(d+1)) F_ij + (1/(d+1)) A_ij f(x_i)), the     */
+/*          cone rule of Eq. (leibniz-int) over the pyramid with base facet  */
+/*          ij and apex x_i (height h_ij).                                   */
+/* Sums over k run in ascending vertex order, sums over j in CSR order.      */
+/* F_ij = 0 for an entry with no vertex (K_ij = 0).                          */
+/* In binary64: y = (sum nu) / K per axis, mean f = (sum f) / K,             */
+/* F = (cd * mean f + c1 * f(y)) * A with cd = d/(d+1), c1 = 1/(d+1);        */
+/* I sums (h / d) * (cd * F + c1 * (A * f(x_i))); V = (sum h A) / d.         */
+/* ------------------------------------------------------------------------ */
+static int64_t find_entry(const int64_t* rowptr, const int32_t* col, int64_t i, int32_t j) {
+  int64_t lo = rowptr[i], hi = rowptr[i + 1];
+  while (lo < hi) {
+    int64_t mid = (lo + hi) / 2;
+    if (col[mid] < j) lo = mid + 1; else hi = mid;
+  }
+  return (lo < rowptr[i + 1] && col[lo] == j) ? lo : -1;
+}
+
+void or_hmc(const double* X, int64_t N, int d, const int64_t* rowptr, const int32_t* col, const double* A,
+            const int32_t* tuples, const double* coords, int64_t nv, int kind, int axis, const double* coef,
+            double* VH, double* FH, double* IH, int64_t* K_out) {
+  const int64_t nnz = rowptr[N];
+  int64_t* K = (int64_t*)calloc((size_t)(nnz > 0 ? nnz : 1), sizeof(int64_t));
+  double* fs = (double*)calloc((size_t)(nnz > 0 ? nnz : 1), sizeof(double));
+  double* ys = (double*)calloc((size_t)(nnz > 0 ? nnz : 1) * d, sizeof(double));
+  const double cd = (double)d / (double)(d + 1), c1 = 1.0 / (double)(d + 1);
+  for (int64_t v = 0; v < nv; ++v) {
+    const int32_t* sg = tuples + v * (d + 1);
+    const double* nu = coords + v * d;
+    const double fnu = or_func_eval(kind, axis, coef, d, nu);
+    for (int a = 0; a <= d; ++a) {
+      if (sg[a] < 0 || sg[a] >= N) continue;
+      for (int b = 0; b <= d; ++b) {
+        if (b == a) continue;
+        const int64_t e = find_entry(rowptr, col, sg[a], sg[b]);
+        if (e < 0) continue;
+        K[e] += 1;
+        fs[e] = fs[e] + fnu;
+        for (int c = 0; c < d; ++c) ys[e * d + c] = ys[e * d + c] + nu[c];
+      }
+    }
+  }
+  for (int64_t e = 0; e < nnz; ++e) {
+    double F = 0.0;
+    if (K[e] > 0) {
+      double y[OR_MAXD];
+      for (int c = 0; c < d; ++c) y[c] = ys[e * d + c] / (double)K[e];
+      const double mf = fs[e] / (double)K[e];
+      F = (cd * mf + c1 * or_func_eval(kind, axis, coef, d, y)) * A[e];
+    }
+    if (FH) FH[e] = F;
+    fs[e] = F;  /* kept for the cells */
+    if (K_out) K_out[e] = K[e];
+  }
+  for (int64_t i = 0; i < N; ++i) {
+    const double* xi = X + i * d;
+    const double fxi = or_func_eval(kind, axis, coef, d, xi);
+    double vh = 0.0, ih = 0.0;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int32_t j = col[e];
+      double h;
+      if (j >= 0) {
+        double ww = 0.0;
+        for (int c = 0; c < d; ++c) {
+          double w = X[(int64_t)j * d + c] - xi[c];
+          ww = ww + w * w;
+        }
+        h = 0.5 * sqrt(ww);
+      } else {
+        h = face_side(j) ? 1.0 - xi[face_axis(j)] : xi[face_axis(j)];
+      }
+      vh = vh + h * A[e];
+      ih = ih + (h / (double)d) * (cd * fs[e] + c1 * (A[e] * fxi));
+    }
+    if (VH) VH[i] = vh / (double)d;
+    if (IH) IH[i] = ih;
+  }
+  free(K);
+  free(fs);
+  free(ys);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Vertices: Algorithm 2 (VoronoiGraph) with the box faces as generators.   */
 /* ------------------------------------------------------------------------ */
 

@@ -10,7 +10,9 @@ tuples must equal the screened path's bit for bit.
 Secondary lines in the same JSON object: "mc" (MC volumes + areas + adjoint,
 d=4, N=100,000, 1024 rays per cell; binary32-screened, tensor-core screened
 and binary64 paths) and "highd" (the same at d=16, N=200,000 mixture nodes,
-64 rays per cell; tensor-core walk vs binary32 tree walk).  --only-batch
+64 rays per cell; tensor-core walk vs binary32 tree walk), "mc.integrals"
+(Algorithm 3's function integrals on the d=4 rays) and "hmc" (heuristic MC
+integrals, Section 3.3, on the traversal workload's diagram).  --only-batch
 times the batched MC workload (512 point sets).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -264,6 +266,9 @@ def run_ours(args):
     if args.only_highd:
         print(json.dumps({"highd": run_highd(args, vd, torch.cuda.current_stream())}), flush=True)
         return
+    if args.only_hmc:
+        print(json.dumps({"hmc": run_hmc(args, vd, torch.cuda.current_stream())}), flush=True)
+        return
     if args.only_batch:
         print(json.dumps({"batch": run_batch(args, vd, torch.cuda.current_stream())}), flush=True)
         return
@@ -385,6 +390,9 @@ def run_ours(args):
     highd = None
     if not args.no_highd:
         highd = run_highd(args, vd, stream)
+    hmc = None
+    if not args.no_hmc:
+        hmc = run_hmc(args, vd, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -412,7 +420,7 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": "raycasts/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "mc": mc, "highd": highd}
+                "mc": mc, "highd": highd, "hmc": hmc}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -500,6 +508,54 @@ def run_mc(args, vd, stream):
 
 HIGHD_WORKLOAD = ("MC volumes + interface areas + adjoint, d=16, N=200000 from a 32-component Gaussian mixture "
                   "(centres U[0,1]^16, sigma 0.1, redrawn outside the cube; seed 0), 64 rays per cell")
+
+
+HMC_WORKLOAD = ("integrals of sin(x_1^2) over the cells and interfaces, d=5, N=20000 iid uniform in [0,1]^5 "
+                "(seed 0): heuristic MC (Section 3.3) from the areas of 1024 rays per cell and the diagram's "
+                "vertices, beside the MC integrals of Algorithm 3 (2 samples per ray) on the same rays")
+
+
+def run_hmc(args, vd, stream, reps=3):
+    """Heuristic MC integration: CUDA-event time of one vd_hmc_integrals call
+    (interface lists, sorted per interface, interface and cell integrals;
+    device outputs), mean of reps after one warm-up, with the MC function
+    integrals of the same rays timed the same way."""
+    import torch
+    from paper_2405_10050_gb300 import VD_FP32, synth
+    N, d, R = args.N, args.d, 1024
+    X = torch.tensor(synth.uniform(N, d, seed=0), device="cuda")
+    cfg = vd.vd_config_default()
+    cfg.precision = VD_FP32
+    ctx = vd.vd_create(cfg, stream.cuda_stream)
+    vd.vd_set_nodes(ctx, X)
+    mesh = vd.vd_vertices(ctx)
+    m = vd.vd_mc_integrate(ctx, R, 7)
+    nnz = vd.vd_mc_get(m)
+    VH = torch.empty(N, dtype=torch.float64, device="cuda")
+    IH = torch.empty(N, dtype=torch.float64, device="cuda")
+    FH = torch.empty(max(nnz, 1), dtype=torch.float64, device="cuda")
+    f = vd.func_sin_sq(0)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms = timed(lambda: vd.vd_hmc_integrals(m, mesh, f, VH, FH[:nnz], IH))
+    ms_mc = timed(lambda: vd.vd_mc_integrals(m, f, 2, VH, FH[:nnz]))
+    out = {"workload": HMC_WORKLOAD.replace("N=20000", f"N={N}").replace("d=5", f"d={d}"), "unit": "cells/s",
+           "value": N / (ms / 1000.0), "ms": ms, "vertices": vd.vd_mesh_count(mesh), "interfaces": nnz,
+           "mc_integrals_ms": ms_mc}
+    vd.vd_mc_free(m)
+    vd.vd_mesh_free(mesh)
+    vd.vd_destroy(ctx)
+    return out
 
 
 def run_highd(args, vd, stream):
@@ -613,6 +669,8 @@ def main():
     ap.add_argument("--only-batch", action="store_true")
     ap.add_argument("--no-highd", action="store_true")
     ap.add_argument("--only-highd", action="store_true")
+    ap.add_argument("--no-hmc", action="store_true")
+    ap.add_argument("--only-hmc", action="store_true")
     ap.add_argument("--highd-fp64", action="store_true", help="also time the binary64 path (about 25 s)")
     ap.add_argument("--highd-n", type=int, default=200000)
     ap.add_argument("--batch-sets", type=int, default=512)

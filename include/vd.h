@@ -201,6 +201,22 @@ typedef struct {
 } vd_func;
 
 vd_status vd_mc_integrals(const vd_mc* mc, const vd_func* f, int64_t m, double* FV, double* Fd, int32_t on_device);
+
+/* Heuristic Monte Carlo integration (Section 3.3) of the node set of `mc`,
+ * from its interface areas A_ij and the vertices of `mesh` (vd_vertices of
+ * the same node set):
+ *   VH_i = (1/d) sum_j h_ij A_ij  (h_ij = |x_j - x_i|/2, or the distance from
+ *          x_i to the box face j);
+ *   FH_ij = (d/(d+1)) (1/K_ij) sum_k f(nu_k) A_ij + (1/(d+1)) f(y_ij) A_ij,
+ *          nu_k the K_ij vertices whose tuple holds both i and j, y_ij their
+ *          mean (0 if the interface has no vertex);
+ *   IH_i = sum_j (h_ij/d) ((d/(d+1)) FH_ij + (1/(d+1)) A_ij f(x_i)), the cone
+ *          rule of Eq. (leibniz-int) with apex x_i.
+ * Binary64, fixed summation orders (k by ascending vertex index, j in CSR
+ * order).  VH, IH: N float64; FH: nnz float64 in vd_mc_get's col order; any
+ * may be NULL but not all three.  mesh must have the dimension of mc. */
+vd_status vd_hmc_integrals(const vd_mc* mc, const vd_mesh* mesh, const vd_func* f, double* VH, double* FH,
+                           double* IH, int32_t on_device);
 vd_status vd_mc_stats(const vd_mc* mc, vd_stats* out);
 int64_t vd_mc_count(const vd_mc* mc);
 void vd_mc_free(vd_mc* mc);

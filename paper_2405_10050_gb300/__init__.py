@@ -148,6 +148,26 @@ class Voronoi:
             if mc is not None:
                 vd.vd_mc_free(mc)
 
+    def hmc(self, rays_per_cell: int, seed: int, f):
+        """Heuristic MC (Section 3.3) of f (a vd.vd_func): the MC areas with
+        rays_per_cell rays, the vertices of the diagram, then the volumes VH,
+        interface integrals FH (CSR: rowptr, col) and cell integrals IH."""
+        import torch
+        mesh = vd.vd_vertices(self.ctx)
+        try:
+            res = self.mc_integrate(rays_per_cell, seed, keep_rays=False)
+            try:
+                N = self.N
+                VH = torch.empty(N, dtype=torch.float64, device="cuda")
+                IH = torch.empty(N, dtype=torch.float64, device="cuda")
+                FH = torch.empty(max(res.A.shape[0], 1), dtype=torch.float64, device="cuda")
+                vd.vd_hmc_integrals(res._mc, mesh, f, VH, FH, IH)
+                return VH, FH[:res.A.shape[0]], IH, res.rowptr, res.col
+            finally:
+                res.free()
+        finally:
+            vd.vd_mesh_free(mesh)
+
     def vertices(self):
         """All vertices of the clipped diagram: (tuples V x (d+1), coords V x d)."""
         import torch

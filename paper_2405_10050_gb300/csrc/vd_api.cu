@@ -27,6 +27,9 @@ cudaError_t mc_adjoint(const double* X, int64_t N, int d, int64_t R, uint64_t se
 cudaError_t mc_integrals(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set,
                          const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col,
                          const double* U, const vd_func& f, int64_t m, double* FV, double* Fd, cudaStream_t st);
+cudaError_t hmc_integrals(const double* X, int64_t N, int d, const int64_t* rowptr, const int32_t* col,
+                          const double* A, int64_t nnz, const int32_t* tuples, const double* coords, int64_t nv,
+                          const vd_func& f, double* VH, double* FH, double* IH, DevBufs& scratch, cudaStream_t st);
 cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, Workspace& ws,
                               DevBufs& out_bufs, int32_t** tuples, double** coords, int64_t* nv, vd_stats* stats,
                               Counters* ctr, cudaStream_t st, char* err, size_t errlen);
@@ -567,10 +570,14 @@ vd_status vd_mc_adjoint(const vd_mc* mc, const double* gV, const double* gA, dou
   return e == cudaSuccess ? VD_OK : (e == cudaErrorMemoryAllocation ? VD_ENOMEM : VD_ECUDA);
 }
 
+static bool func_ok(const vd_func* f, int d) {
+  if (f->kind != VD_F_ONE && f->kind != VD_F_POLY2 && f->kind != VD_F_SIN_SQ) return false;
+  return f->kind != VD_F_SIN_SQ || (f->axis >= 0 && f->axis < d);
+}
+
 vd_status vd_mc_integrals(const vd_mc* mc, const vd_func* f, int64_t m, double* FV, double* Fd, int32_t on_device) {
   if (!mc || !f || (!FV && !Fd)) return VD_EINVAL;
-  if (f->kind != VD_F_ONE && f->kind != VD_F_POLY2 && f->kind != VD_F_SIN_SQ) return VD_EINVAL;
-  if (f->kind == VD_F_SIN_SQ && (f->axis < 0 || f->axis >= mc->d)) return VD_EINVAL;
+  if (!func_ok(f, mc->d)) return VD_EINVAL;
   if (FV && (m < 1 || m > ((int64_t)1 << 32))) return VD_EINVAL;  // sample blocks s / 4 below 2^31
   if (!FV) m = 1;
   DevBufs tmp;
@@ -587,6 +594,31 @@ vd_status vd_mc_integrals(const vd_mc* mc, const vd_func* f, int64_t m, double* 
     e = cudaMemcpyAsync(FV, FVd, (size_t)mc->N * sizeof(double), cudaMemcpyDeviceToHost, mc->st);
   if (e == cudaSuccess && !on_device && Fd && mc->nnz > 0)
     e = cudaMemcpyAsync(Fd, Fdd, (size_t)mc->nnz * sizeof(double), cudaMemcpyDeviceToHost, mc->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(mc->st);
+  cudaStreamSynchronize(mc->st);
+  tmp.release();
+  return e == cudaSuccess ? VD_OK : (e == cudaErrorMemoryAllocation ? VD_ENOMEM : VD_ECUDA);
+}
+
+vd_status vd_hmc_integrals(const vd_mc* mc, const vd_mesh* mesh, const vd_func* f, double* VH, double* FH,
+                           double* IH, int32_t on_device) {
+  if (!mc || !mesh || !f || (!VH && !FH && !IH)) return VD_EINVAL;
+  if (mesh->d != mc->d || !func_ok(f, mc->d)) return VD_EINVAL;
+  DevBufs tmp;
+  double *VHd = VH, *FHd = FH, *IHd = IH;
+  cudaError_t e = cudaSuccess;
+  if (VH && !on_device) e = tmp.alloc_n(&VHd, (size_t)mc->N);
+  if (e == cudaSuccess && IH && !on_device) e = tmp.alloc_n(&IHd, (size_t)mc->N);
+  if (e == cudaSuccess && (!FH || !on_device)) e = tmp.alloc_n(&FHd, (size_t)std::max<int64_t>(mc->nnz, 1));
+  if (e == cudaSuccess)
+    e = vd::hmc_integrals(mc->X, mc->N, mc->d, mc->rowptr, mc->col, mc->A, mc->nnz, mesh->tuples, mesh->coords,
+                          mesh->nv, *f, VHd, FHd, IHd, tmp, mc->st);
+  if (e == cudaSuccess && !on_device && VH)
+    e = cudaMemcpyAsync(VH, VHd, (size_t)mc->N * sizeof(double), cudaMemcpyDeviceToHost, mc->st);
+  if (e == cudaSuccess && !on_device && IH)
+    e = cudaMemcpyAsync(IH, IHd, (size_t)mc->N * sizeof(double), cudaMemcpyDeviceToHost, mc->st);
+  if (e == cudaSuccess && !on_device && FH && mc->nnz > 0)
+    e = cudaMemcpyAsync(FH, FHd, (size_t)mc->nnz * sizeof(double), cudaMemcpyDeviceToHost, mc->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(mc->st);
   cudaStreamSynchronize(mc->st);
   tmp.release();

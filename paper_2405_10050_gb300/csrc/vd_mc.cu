@@ -735,6 +735,13 @@ cudaError_t mc_batch_reduce(const SetDesc* sets_dev, int nsets, int64_t nitems, 
   return cudaGetLastError();
 }
 
+// out[0..n] = exclusive scan of in[0..n) (out[n] = total), one block.
+cudaError_t mc_scan64(const int64_t* in, int64_t n, int64_t* out, cudaStream_t st) {
+  k_scan64<<<1, 1024, 0, st>>>(in, n, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // Counts the distinct hits per cell and writes rowptr (N+1); returns nnz.
 cudaError_t mc_rowptr(const int32_t* hit, int64_t N, int64_t R, int64_t* cnt_scratch, int64_t* rowptr,
                       int64_t* nnz_host, cudaStream_t st) {

@@ -74,7 +74,7 @@ class vd_stats(ctypes.Structure):
 EXPORTS = ["vd_kernel_launches", "vd_config_default", "vd_create", "vd_destroy", "vd_last_error", "vd_status_str", "vd_set_precision",
            "vd_last_stats", "vd_set_nodes", "vd_raycast", "vd_vertices", "vd_mesh_count", "vd_mesh_dim",
            "vd_mesh_copy", "vd_mesh_stats", "vd_mesh_free", "vd_mc_integrate", "vd_mc_get", "vd_mc_rays",
-           "vd_mc_adjoint", "vd_mc_integrals", "vd_mc_stats", "vd_mc_count", "vd_mc_free", "vd_mc_directions",
+           "vd_mc_adjoint", "vd_mc_integrals", "vd_hmc_integrals", "vd_mc_stats", "vd_mc_count", "vd_mc_free", "vd_mc_directions",
            "vd_mc_integrate_batch", "vd_raycast_noalloc"]
 
 _lib = None
@@ -118,6 +118,7 @@ def load(build_if_missing: bool = True):
         "vd_mc_rays": (i32, [P, P, P, i32]),
         "vd_mc_adjoint": (i32, [P, P, P, P, i32]),
         "vd_mc_integrals": (i32, [P, P, i64, P, P, i32]),
+        "vd_hmc_integrals": (i32, [P, P, P, P, P, P, i32]),
         "vd_mc_stats": (i32, [P, P]),
         "vd_mc_count": (i64, [P]),
         "vd_mc_free": (None, [P]),
@@ -301,6 +302,14 @@ def vd_mc_integrals(mc, f, m, FV=None, Fd=None):
     pd, dev2, k2 = _ptr(Fd, np.float64)
     dev = dev if dev is not None else (dev2 or 0)
     _check(None, load().vd_mc_integrals(mc, ctypes.byref(f), int(m), pv, pd, dev))
+
+
+def vd_hmc_integrals(mc, mesh, f, VH=None, FH=None, IH=None):
+    """Section 3.3's heuristic MC: VH (N), FH (nnz, vd_mc_get's col order),
+    IH (N) from the areas of mc and the vertices of mesh."""
+    ptrs = [_ptr(VH, np.float64), _ptr(FH, np.float64), _ptr(IH, np.float64)]
+    dev = next((p[1] for p in ptrs if p[1] is not None), 0)
+    _check(None, load().vd_hmc_integrals(mc, mesh, ctypes.byref(f), ptrs[0][0], ptrs[1][0], ptrs[2][0], dev))
 
 
 def vd_mc_stats(mc):

@@ -14,7 +14,7 @@ namespace vd {
 namespace {
 
 constexpr int kRsThreads = 256;
-constexpr int kRsSub = 64;                       // sub-chunks of 256 keys per block
+constexpr int kRsSub = 16;                       // sub-chunks of 256 keys per block
 constexpr int kRsChunk = kRsThreads * kRsSub;    // keys per block
 
 __global__ void k_bounds_partial(const double* X, int64_t N, int d, double* part) {
@@ -94,26 +94,62 @@ __global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, uint32_t* 
   counts[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of `total` counts in one block of 1024 threads.
-__global__ void k_rs_scan(uint32_t* counts, int64_t total) {
-  __shared__ uint32_t part[1024];
-  const int64_t seg = (total + 1023) / 1024;
-  const int64_t b = threadIdx.x * seg, e = min(total, b + seg);
+// Exclusive scan of `total` counts in place, in two launches of P <= 256
+// blocks of 1024 threads: block b owns the tile [b tile, (b+1) tile); the
+// first launch writes each tile's sum to part[b], the second scans its tile
+// (1024 values at a time, coalesced) from the sum of the tiles before it.
+constexpr int kScanThreads = 1024;
+
+__global__ void k_rs_scan_reduce(const uint32_t* counts, int64_t total, int64_t tile, uint32_t* part) {
+  __shared__ uint32_t ws[kScanThreads / 32];
+  const int64_t b0 = blockIdx.x * tile, b1 = min(total, b0 + tile);
   uint32_t s = 0;
-  for (int64_t i = b; i < e; ++i) s += counts[i];
-  part[threadIdx.x] = s;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += kScanThreads) s += counts[i];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const uint32_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  if (threadIdx.x < 32) {
+    s = ws[threadIdx.x];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
   }
-  uint32_t run = part[threadIdx.x] - s;
-  for (int64_t i = b; i < e; ++i) {
-    const uint32_t c = counts[i];
-    counts[i] = run;
-    run += c;
+}
+
+__global__ void k_rs_scan_tiles(uint32_t* counts, int64_t total, int64_t tile, const uint32_t* part) {
+  __shared__ uint32_t ws[kScanThreads / 32];
+  __shared__ uint32_t carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    uint32_t c = 0;
+    for (unsigned b = 0; b < blockIdx.x; ++b) c += part[b];
+    carry = c;
+  }
+  __syncthreads();
+  const int64_t b0 = blockIdx.x * tile, b1 = min(total, b0 + tile);
+  for (int64_t base = b0; base < b1; base += kScanThreads) {
+    const int64_t i = base + threadIdx.x;
+    const uint32_t x = i < b1 ? counts[i] : 0u;
+    uint32_t v = x;  // inclusive scan within the warp
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane == 31) ws[warp] = v;
+    __syncthreads();
+    if (warp == 0) {  // scan of the warp totals
+      uint32_t t = ws[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, t, o);
+        if (lane >= o) t += y;
+      }
+      ws[lane] = t;
+    }
+    __syncthreads();
+    const uint32_t before = carry + (warp > 0 ? ws[warp - 1] : 0u) + v - x;
+    if (i < b1) counts[i] = before;
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) carry = before + x;
+    __syncthreads();
   }
 }
 
@@ -284,11 +320,18 @@ inline int nblocks(int64_t n, int t) { return (int)std::max<int64_t>(1, (n + t -
 
 }  // namespace
 
-// Sorts (keys, vals) in place by key, stably; tmp buffers of the same sizes.
+// Sorts (keys, vals) in place by key, stably; tmp buffers of the same sizes;
+// counts holds 256 (ceil(n / 4096) + 1) values (the digit counts of every
+// 4096-key block, then the scan's tile sums).
 cudaError_t radix_sort_u64(uint64_t* keys, int32_t* vals, uint64_t* ktmp, int32_t* vtmp, int64_t n,
                            uint32_t* counts, unsigned long long* orand, cudaStream_t st) {
+  static_assert(kRsChunk == 4096, "callers size counts for 4096-key blocks");
   if (n <= 1) return cudaSuccess;
   const int nblk = nblocks(n, kRsChunk);
+  const int64_t total = (int64_t)256 * nblk;
+  const int nscan = (int)std::min<int64_t>(256, (total + kScanThreads - 1) / kScanThreads);
+  const int64_t tile = (total + nscan - 1) / nscan;
+  uint32_t* part = counts + total;
   unsigned long long init[2] = {0ull, ~0ull};
   cudaMemcpyAsync(orand, init, sizeof(init), cudaMemcpyHostToDevice, st);
   k_key_span<<<std::min(nblocks(n, 256), 1024), 256, 0, st>>>(keys, n, orand); count_launch();
@@ -304,7 +347,8 @@ cudaError_t radix_sort_u64(uint64_t* keys, int32_t* vals, uint64_t* ktmp, int32_
   for (int shift = 0; shift < 64; shift += 8) {
     if (((varying >> shift) & 255ull) == 0) continue;
     k_rs_hist<<<nblk, kRsThreads, 0, st>>>(ka, n, shift, counts, nblk); count_launch();
-    k_rs_scan<<<1, 1024, 0, st>>>(counts, (int64_t)256 * nblk); count_launch();
+    k_rs_scan_reduce<<<nscan, kScanThreads, 0, st>>>(counts, total, tile, part); count_launch();
+    k_rs_scan_tiles<<<nscan, kScanThreads, 0, st>>>(counts, total, tile, part); count_launch();
     k_rs_scatter<<<nblk, kRsThreads, 0, st>>>(ka, va, kb, vb, n, shift, counts, nblk); count_launch();
     std::swap(ka, kb);
     std::swap(va, vb);
@@ -354,7 +398,7 @@ cudaError_t build_tree(const double* X, int64_t N, int d, cudaStream_t st, DevBu
       (e = scratch.alloc_n(&bounds, 2 * d)) != cudaSuccess || (e = scratch.alloc_n(&keys, N)) != cudaSuccess ||
       (e = scratch.alloc_n(&ktmp, N)) != cudaSuccess || (e = scratch.alloc_n(&vals, N)) != cudaSuccess ||
       (e = scratch.alloc_n(&vtmp, N)) != cudaSuccess ||
-      (e = scratch.alloc_n(&counts, (size_t)256 * nblk)) != cudaSuccess ||
+      (e = scratch.alloc_n(&counts, (size_t)256 * (nblk + 1))) != cudaSuccess ||
       (e = scratch.alloc_n(&orand, 2)) != cudaSuccess) {
     scratch.release();
     return e;

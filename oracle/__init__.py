@@ -62,6 +62,8 @@ def lib():
         L.or_mc_tsamples.argtypes = [u64, u32, i64, i64, i64, P]
         L.or_mc_integrals.argtypes = [P, i64, i32, i64, u64, u32, i64, P, P, P, P, P, i32, i32, P, i64, P, P]
         L.or_hmc.argtypes = [P, i64, i32, P, P, P, P, P, i64, i32, i32, P, P, P, P, P]
+        L.or_leibniz.restype = i64
+        L.or_leibniz.argtypes = [P, i64, i32, P, P, i64, i32, i32, P, P, P, P, P, P, P, i64]
         L.or_vertex_coords.restype = ctypes.c_int
         L.or_vertex_coords.argtypes = [P, i32, P, P]
         L.or_search_direction.restype = ctypes.c_int
@@ -324,3 +326,27 @@ def hmc(X, rowptr, col, A, tuples, coords, f):
     lib().or_hmc(_p(X), N, d, _p(rowptr), _p(col), _p(A), _p(tuples), _p(coords), tuples.shape[0], kind, axis,
                  _p(coef), _p(VH), _p(FH), _p(IH), _p(K))
     return VH, FH[:nnz], IH, K[:nnz]
+
+
+def leibniz(X, tuples, coords, f=("one",)):
+    """Section 3.2's exact integration from the diagram's vertices: V (N), F
+    (N, the integral of f's piecewise linear interpolant), and the facets'
+    CSR (rowptr, col) with exact areas A and interpolant integrals Fd."""
+    X = _f64(X)
+    N, d = X.shape
+    tuples = np.ascontiguousarray(tuples, dtype=np.int32).reshape(-1, d + 1)
+    coords = _f64(coords).reshape(-1, d)
+    kind, axis, coef = func_code(f, d)
+    cap = 64 * N + 1024
+    while True:
+        V, F = np.empty(N), np.empty(N)
+        rowptr = np.empty(N + 1, np.int64)
+        col = np.empty(cap, np.int32)
+        A, Fd = np.empty(cap), np.empty(cap)
+        nnz = lib().or_leibniz(_p(X), N, d, _p(tuples), _p(coords), tuples.shape[0], kind, axis, _p(coef), _p(V),
+                               _p(F), _p(rowptr), _p(col), _p(A), _p(Fd), cap)
+        if nnz >= 0 or int(rowptr[-1]) <= cap:
+            break
+        cap = int(rowptr[-1]) + 1024
+    assert nnz >= 0, "degenerate input"
+    return V, F, rowptr, col[:nnz].copy(), A[:nnz].copy(), Fd[:nnz].copy()

@@ -647,6 +647,191 @@ void or_hmc(const double* X, int64_t N, int d, const int64_t* rowptr, const int3
 }
 
 /* ------------------------------------------------------------------------ */
+/* Exact volumes, interface areas and integrals of the piecewise linear      */
+/* interpolant of f (Section 3.2, Algorithms 4-5, IterativeVolume) from the  */
+/* vertices of the diagram.  For cell i the faces are walked depth first:    */
+/* level 1 is the cell (its vertices: tuples holding i), a face at level D   */
+/* keeps the vertices of its parent whose tuple also holds the generator j   */
+/* that defines it (candidates j in ascending id, not already in the face),  */
+/* down to the edges at level d (exactly two vertices nu, nu').  Each edge   */
+/* closes the simplex (x_i, m_2, ..., m_{d-1}, nu, nu') with m_D the mean of */
+/* the level-D face's vertices; its volume is |det(m_2 - x_i, ...,           */
+/* m_{d-1} - x_i, nu - x_i, nu' - x_i)| / d! (Gaussian elimination with      */
+/* partial pivoting, first maximal |entry|).  Integrals follow Algorithm 5:  */
+/* an edge returns F = (f(nu) + f(nu'))/2 V; a face at level 1 < D < d       */
+/* returns (sum V, ((d-D+1)/(d-D+2)) sum F + (1/(d-D+2)) f(m_D) sum V); the  */
+/* cell takes F_i = (d/(d+1)) sum F + (1/(d+1)) f(x_i) sum V.  A facet ij    */
+/* (level 2) gives A_ij = V_ij d / h_ij and Fd_ij = F_ij d / h_ij with       */
+/* h_ij = |x_j - x_i|/2 or the distance to the box face.  Row i of the CSR   */
+/* lists the facets in ascending j.  Returns -1 if an edge does not have     */
+/* two vertices (degenerate input) or cap is too small, else nnz.  d >= 2.   */
+/* ------------------------------------------------------------------------ */
+#define OR_LZ_MAXD 8
+
+static double lz_absdet(double* M, int d) { /* M row-major d x d, destroyed */
+  double det = 1.0;
+  for (int c = 0; c < d; ++c) {
+    int p = c;
+    for (int r = c + 1; r < d; ++r)
+      if (fabs(M[r * d + c]) > fabs(M[p * d + c])) p = r;
+    if (M[p * d + c] == 0.0) return 0.0;
+    if (p != c)
+      for (int k = 0; k < d; ++k) { double t = M[c * d + k]; M[c * d + k] = M[p * d + k]; M[p * d + k] = t; }
+    for (int r = c + 1; r < d; ++r) {
+      const double mlt = M[r * d + c] / M[c * d + c];
+      for (int k = c + 1; k < d; ++k) M[r * d + k] = M[r * d + k] - mlt * M[c * d + k];
+    }
+    det = det * M[c * d + c];
+  }
+  return fabs(det);
+}
+
+static int tuple_has(const int32_t* t, int L, int32_t g) {
+  for (int q = 0; q < L; ++q) if (t[q] == g) return 1;
+  return 0;
+}
+
+typedef struct {
+  const double* X; int d; int64_t i;
+  const int32_t* tuples; const double* coords;
+  int kind, axis; const double* coef;
+  double fact, mid[OR_LZ_MAXD + 1][OR_LZ_MAXD];
+  int32_t S[OR_LZ_MAXD + 2];
+  int bad;
+} lz_ctx;
+
+/* smallest generator > prev in the tuples of list[0..n) that is not in S[0..D) */
+static int64_t lz_next(const lz_ctx* c, const int64_t* list, int64_t n, int D, int64_t prev) {
+  int64_t best = INT64_MAX;
+  for (int64_t q = 0; q < n; ++q) {
+    const int32_t* t = c->tuples + list[q] * (c->d + 1);
+    for (int k = 0; k <= c->d; ++k) {
+      const int64_t g = t[k];
+      if (g <= prev || g >= best) continue;
+      int in = 0;
+      for (int s2 = 0; s2 < D; ++s2) in |= (c->S[s2] == g);
+      if (!in) best = g;
+    }
+  }
+  return best;
+}
+
+/* face at level D with vertex list (list, n); returns its V, F */
+static void lz_rec(lz_ctx* c, int D, const int64_t* list, int64_t n, double* Vout, double* Fout,
+                   double* Afac, double* Ffac, int64_t* nf, int64_t cap) {
+  const int d = c->d;
+  const double* xi = c->X + c->i * d;
+  if (D == d) { /* an edge */
+    if (n != 2) { c->bad = 1; *Vout = 0.0; *Fout = 0.0; return; }
+    double M[OR_LZ_MAXD * OR_LZ_MAXD];
+    for (int col = 0; col < d; ++col) {
+      const double* p = col < d - 2 ? c->mid[col + 2] : c->coords + list[col - (d - 2)] * d;
+      for (int r = 0; r < d; ++r) M[r * d + col] = p[r] - xi[r];
+    }
+    const double V = lz_absdet(M, d) / c->fact;
+    const double f0 = or_func_eval(c->kind, c->axis, c->coef, d, c->coords + list[0] * d);
+    const double f1 = or_func_eval(c->kind, c->axis, c->coef, d, c->coords + list[1] * d);
+    *Vout = V;
+    *Fout = (0.5 * (f0 + f1)) * V;
+    return;
+  }
+  double fm = 0.0;
+  if (D >= 2) { /* the face's vertex mean */
+    for (int a = 0; a < d; ++a) c->mid[D][a] = 0.0;
+    for (int64_t q = 0; q < n; ++q)
+      for (int a = 0; a < d; ++a) c->mid[D][a] = c->mid[D][a] + c->coords[list[q] * d + a];
+    for (int a = 0; a < d; ++a) c->mid[D][a] = c->mid[D][a] / (double)n;
+    fm = or_func_eval(c->kind, c->axis, c->coef, d, c->mid[D]);
+  }
+  int64_t* child = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  double sv = 0.0, sf = 0.0;
+  int64_t j = INT64_MIN;
+  while ((j = lz_next(c, list, n, D, j)) != INT64_MAX) {
+    int64_t m = 0;
+    for (int64_t q = 0; q < n; ++q)
+      if (tuple_has(c->tuples + list[q] * (d + 1), d + 1, (int32_t)j)) child[m++] = list[q];
+    c->S[D] = (int32_t)j;
+    double v = 0.0, f = 0.0;
+    lz_rec(c, D + 1, child, m, &v, &f, Afac, Ffac, nf, cap);
+    if (D == 1) { /* facet ij */
+      double h;
+      if (j >= 0) {
+        double ww = 0.0;
+        for (int a = 0; a < d; ++a) { double w = c->X[j * d + a] - xi[a]; ww = ww + w * w; }
+        h = 0.5 * sqrt(ww);
+      } else {
+        h = face_side((int32_t)j) ? 1.0 - xi[face_axis((int32_t)j)] : xi[face_axis((int32_t)j)];
+      }
+      if (*nf < cap) {
+        Afac[*nf] = (v * (double)d) / h;
+        Ffac[*nf] = (f * (double)d) / h;
+      } else {
+        c->bad = 1;
+      }
+      *nf += 1;
+    }
+    sv = sv + v;
+    sf = sf + f;
+  }
+  free(child);
+  *Vout = sv;
+  if (D == 1) {
+    const double fx = or_func_eval(c->kind, c->axis, c->coef, d, xi);
+    *Fout = ((double)d / (double)(d + 1)) * sf + (1.0 / (double)(d + 1)) * fx * sv;
+  } else {
+    const double w1 = (double)(d - D + 1) / (double)(d - D + 2), w0 = 1.0 / (double)(d - D + 2);
+    *Fout = w1 * sf + w0 * fm * sv;
+  }
+}
+
+int64_t or_leibniz(const double* X, int64_t N, int d, const int32_t* tuples, const double* coords, int64_t nv,
+                   int kind, int axis, const double* coef, double* V, double* F, int64_t* rowptr, int32_t* col,
+                   double* A, double* Fd, int64_t cap) {
+  if (d < 2 || d > OR_LZ_MAXD) return -1;
+  /* vertex lists of the cells, ascending vertex order */
+  int64_t* cnt = (int64_t*)calloc((size_t)N + 1, sizeof(int64_t));
+  for (int64_t v = 0; v < nv; ++v)
+    for (int k = 0; k <= d; ++k) {
+      const int32_t g = tuples[v * (d + 1) + k];
+      if (g >= 0 && g < N) cnt[g + 1] += 1;
+    }
+  for (int64_t i = 0; i < N; ++i) cnt[i + 1] += cnt[i];
+  int64_t* lists = (int64_t*)malloc(sizeof(int64_t) * (size_t)(cnt[N] > 0 ? cnt[N] : 1));
+  int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+  for (int64_t i = 0; i < N; ++i) cur[i] = cnt[i];
+  for (int64_t v = 0; v < nv; ++v)
+    for (int k = 0; k <= d; ++k) {
+      const int32_t g = tuples[v * (d + 1) + k];
+      if (g >= 0 && g < N) lists[cur[g]++] = v;
+    }
+  lz_ctx c;
+  memset(&c, 0, sizeof(c));
+  c.X = X; c.d = d; c.tuples = tuples; c.coords = coords; c.kind = kind; c.axis = axis; c.coef = coef;
+  c.fact = 1.0;
+  for (int k = 2; k <= d; ++k) c.fact = c.fact * (double)k;
+  int64_t nf = 0;
+  rowptr[0] = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    c.i = i;
+    c.S[0] = (int32_t)i;
+    const int64_t f0 = nf;
+    double v = 0.0, f = 0.0;
+    lz_rec(&c, 1, lists + cnt[i], cnt[i + 1] - cnt[i], &v, &f, A, Fd, &nf, cap);
+    /* the facet ids of row i, ascending (the order the walk visited them) */
+    int64_t j = INT64_MIN, q = f0;
+    while ((j = lz_next(&c, lists + cnt[i], cnt[i + 1] - cnt[i], 1, j)) != INT64_MAX) {
+      if (q < cap) col[q] = (int32_t)j;
+      ++q;
+    }
+    V[i] = v;
+    F[i] = f;
+    rowptr[i + 1] = nf;
+  }
+  free(cnt); free(lists); free(cur);
+  return c.bad ? -1 : nf;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Vertices: Algorithm 2 (VoronoiGraph) with the box faces as generators.   */
 /* ------------------------------------------------------------------------ */
 

@@ -512,7 +512,8 @@ HIGHD_WORKLOAD = ("MC volumes + interface areas + adjoint, d=16, N=200000 from a
 
 HMC_WORKLOAD = ("integrals of sin(x_1^2) over the cells and interfaces, d=5, N=20000 iid uniform in [0,1]^5 "
                 "(seed 0): heuristic MC (Section 3.3) from the areas of 1024 rays per cell and the diagram's "
-                "vertices, beside the MC integrals of Algorithm 3 (2 samples per ray) on the same rays")
+                "vertices, beside the MC integrals of Algorithm 3 (2 samples per ray) on the same rays and the "
+                "exact integration of Section 3.2 (Algorithms 4-5) on the same vertices")
 
 
 def run_hmc(args, vd, stream, reps=3):
@@ -536,7 +537,7 @@ def run_hmc(args, vd, stream, reps=3):
     FH = torch.empty(max(nnz, 1), dtype=torch.float64, device="cuda")
     f = vd.func_sin_sq(0)
 
-    def timed(fn):
+    def timed(fn, reps=reps):
         fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -548,10 +549,39 @@ def run_hmc(args, vd, stream, reps=3):
         return e0.elapsed_time(e1) / reps
 
     ms = timed(lambda: vd.vd_hmc_integrals(m, mesh, f, VH, FH[:nnz], IH))
-    ms_mc = timed(lambda: vd.vd_mc_integrals(m, f, 2, VH, FH[:nnz]))
+    FV = torch.empty(N, dtype=torch.float64, device="cuda")
+    ms_mc = timed(lambda: vd.vd_mc_integrals(m, f, 2, FV, FH[:nnz]))
+    # the exact integration of Section 3.2 on the same vertices, and the
+    # deviations of the MC volumes and of both integral estimates from it
+    # (the comparisons of the paper's Section 4, here at this size)
+    holder = []
+
+    def poly_once():
+        p = vd.vd_poly_integrate(ctx, mesh, f)
+        holder.append(p)
+
+    # one call, no warm-up: it takes seconds at this size (one thread per cell)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    poly_once()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1)
+    p = holder[-1]
+    VP = torch.empty(N, dtype=torch.float64, device="cuda")
+    FP = torch.empty(N, dtype=torch.float64, device="cuda")
+    vd.vd_poly_get(p, VP, FP)
+    vd.vd_poly_free(p)
+    VM = torch.empty(N, dtype=torch.float64, device="cuda")
+    vd.vd_mc_get(m, V=VM)
+    rel = lambda a, b: float(((a - b) / b).abs().mean())
     out = {"workload": HMC_WORKLOAD.replace("N=20000", f"N={N}").replace("d=5", f"d={d}"), "unit": "cells/s",
            "value": N / (ms / 1000.0), "ms": ms, "vertices": vd.vd_mesh_count(mesh), "interfaces": nnz,
-           "mc_integrals_ms": ms_mc}
+           "mc_integrals_ms": ms_mc, "exact_ms": ms_p, "exact_cells_per_s": N / (ms_p / 1000.0),
+           "exact_volume_sum": float(VP.sum()),
+           "mean_rel_dev_from_exact": {"mc_volume": rel(VM, VP), "mc_integral": rel(FV, FP),
+                                       "hmc_integral": rel(IH, FP)}}
     vd.vd_mc_free(m)
     vd.vd_mesh_free(mesh)
     vd.vd_destroy(ctx)

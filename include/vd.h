@@ -217,6 +217,25 @@ vd_status vd_mc_integrals(const vd_mc* mc, const vd_func* f, int64_t m, double* 
  * may be NULL but not all three.  mesh must have the dimension of mc. */
 vd_status vd_hmc_integrals(const vd_mc* mc, const vd_mesh* mesh, const vd_func* f, double* VH, double* FH,
                            double* IH, int32_t on_device);
+/* Exact cell volumes, interface areas and integrals of the piecewise linear
+ * interpolant of f (Section 3.2, Algorithms 4-5) of the context's node set
+ * from the vertices of `mesh` (vd_vertices of the same node set), 2 <= d <= 8.
+ * Each cell is split into simplices (x_i, m_2, ..., m_{d-1}, nu, nu'): m_D
+ * the vertex mean of a level-D face of the cell (level 2 = a facet), nu, nu'
+ * an edge of the last face; V_i sums their volumes |det| / d!; the integral
+ * is the one of the function that is linear on each simplex and equals f at
+ * its corners (Algorithm 5's weights); A_ij = (d / h_ij) times the volume of
+ * the pyramid over facet ij, Fd_ij the same for the integral.  Binary64,
+ * fixed order (faces by ascending generator, vertices ascending).  Returns
+ * VD_EDEGENERATE if an edge of the walk does not have two vertices. */
+typedef struct vd_poly vd_poly;
+vd_status vd_poly_integrate(vd_ctx* ctx, const vd_mesh* mesh, const vd_func* f, vd_poly** out);
+/* V, F: N float64; row i of the CSR (rowptr N+1 int64, col/A/Fd nnz) lists
+ * the facets of cell i by ascending generator id (faces first).  *nnz is
+ * always written; the arrays may be NULL. */
+vd_status vd_poly_get(const vd_poly* p, double* V, double* F, int64_t* nnz, int64_t* rowptr, int32_t* col,
+                      double* A, double* Fd, int32_t on_device);
+void vd_poly_free(vd_poly* p);
 vd_status vd_mc_stats(const vd_mc* mc, vd_stats* out);
 int64_t vd_mc_count(const vd_mc* mc);
 void vd_mc_free(vd_mc* mc);

@@ -168,6 +168,31 @@ class Voronoi:
         finally:
             vd.vd_mesh_free(mesh)
 
+    def poly(self, f=None):
+        """Exact integration from the vertices (Section 3.2): volumes V,
+        integrals F of f's piecewise linear interpolant, the facets' CSR
+        (rowptr, col) with exact areas A and interface integrals Fd."""
+        import torch
+        f = f if f is not None else vd.func_one()
+        mesh = vd.vd_vertices(self.ctx)
+        try:
+            p = vd.vd_poly_integrate(self.ctx, mesh, f)
+        finally:
+            vd.vd_mesh_free(mesh)
+        try:
+            N = self.N
+            nnz = vd.vd_poly_get(p)
+            dev = dict(device="cuda")
+            V, F = torch.empty(N, dtype=torch.float64, **dev), torch.empty(N, dtype=torch.float64, **dev)
+            rowptr = torch.empty(N + 1, dtype=torch.int64, **dev)
+            col = torch.empty(max(nnz, 1), dtype=torch.int32, **dev)
+            A = torch.empty(max(nnz, 1), dtype=torch.float64, **dev)
+            Fd = torch.empty(max(nnz, 1), dtype=torch.float64, **dev)
+            vd.vd_poly_get(p, V, F, rowptr, col, A, Fd)
+            return V, F, rowptr, col[:nnz], A[:nnz], Fd[:nnz]
+        finally:
+            vd.vd_poly_free(p)
+
     def vertices(self):
         """All vertices of the clipped diagram: (tuples V x (d+1), coords V x d)."""
         import torch

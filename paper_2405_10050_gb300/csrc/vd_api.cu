@@ -30,6 +30,10 @@ cudaError_t mc_integrals(const double* X, int64_t N, int d, int64_t R, uint64_t 
 cudaError_t hmc_integrals(const double* X, int64_t N, int d, const int64_t* rowptr, const int32_t* col,
                           const double* A, int64_t nnz, const int32_t* tuples, const double* coords, int64_t nv,
                           const vd_func& f, double* VH, double* FH, double* IH, DevBufs& scratch, cudaStream_t st);
+cudaError_t poly_integrate(const double* X, int64_t N, int d, const int32_t* tuples, const double* coords,
+                           int64_t nv, const vd_func& f, DevBufs& out, DevBufs& scratch, double** V, double** F,
+                           int64_t** rowptr, int32_t** col, double** A, double** Fd, int64_t* nnz, unsigned* flags_h,
+                           cudaStream_t st);
 cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, Workspace& ws,
                               DevBufs& out_bufs, int32_t** tuples, double** coords, int64_t* nv, vd_stats* stats,
                               Counters* ctr, cudaStream_t st, char* err, size_t errlen);
@@ -88,6 +92,15 @@ struct vd_mc {
   int32_t* col = nullptr;
   double* A = nullptr;
   vd_stats stats{};
+};
+
+struct vd_poly {
+  cudaStream_t st = nullptr;
+  int64_t N = 0, nnz = 0;
+  DevBufs bufs;
+  double *V = nullptr, *F = nullptr, *A = nullptr, *Fd = nullptr;
+  int64_t* rowptr = nullptr;
+  int32_t* col = nullptr;
 };
 
 namespace {
@@ -623,6 +636,65 @@ vd_status vd_hmc_integrals(const vd_mc* mc, const vd_mesh* mesh, const vd_func* 
   cudaStreamSynchronize(mc->st);
   tmp.release();
   return e == cudaSuccess ? VD_OK : (e == cudaErrorMemoryAllocation ? VD_ENOMEM : VD_ECUDA);
+}
+
+vd_status vd_poly_integrate(vd_ctx* ctx, const vd_mesh* mesh, const vd_func* f, vd_poly** out) {
+  if (!ctx || !mesh || !f || !out) return VD_EINVAL;
+  *out = nullptr;
+  if (!ctx->X) return set_err(ctx, VD_EINVAL, "vd_poly_integrate: no nodes set");
+  if (mesh->d != ctx->d || ctx->d < 2 || ctx->d > 8)
+    return set_err(ctx, VD_EINVAL, "vd_poly_integrate: needs the mesh of the context's nodes and 2 <= d <= 8");
+  if (!func_ok(f, ctx->d)) return set_err(ctx, VD_EINVAL, "vd_poly_integrate: bad function");
+  vd_poly* p = new (std::nothrow) vd_poly;
+  if (!p) return VD_ENOMEM;
+  p->st = ctx->st;
+  p->N = ctx->N;
+  DevBufs scratch;
+  unsigned flags = 0;
+  cudaError_t e = vd::poly_integrate(ctx->X, ctx->N, ctx->d, mesh->tuples, mesh->coords, mesh->nv, *f, p->bufs,
+                                     scratch, &p->V, &p->F, &p->rowptr, &p->col, &p->A, &p->Fd, &p->nnz, &flags,
+                                     ctx->st);
+  cudaStreamSynchronize(ctx->st);
+  scratch.release();
+  if (e != cudaSuccess) {
+    p->bufs.release();
+    delete p;
+    return set_err(ctx, e == cudaErrorMemoryAllocation ? VD_ENOMEM : VD_ECUDA, "vd_poly_integrate: %s",
+                   cudaGetErrorString(e));
+  }
+  if (flags) {
+    p->bufs.release();
+    delete p;
+    return set_err(ctx, VD_EDEGENERATE, "vd_poly_integrate: an edge without two vertices (flags %u)", flags);
+  }
+  *out = p;
+  return VD_OK;
+}
+
+vd_status vd_poly_get(const vd_poly* p, double* V, double* F, int64_t* nnz, int64_t* rowptr, int32_t* col,
+                      double* A, double* Fd, int32_t on_device) {
+  if (!p) return VD_EINVAL;
+  if (nnz) *nnz = p->nnz;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaSuccess;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    if (dst && bytes && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, k, p->st);
+  };
+  cp(V, p->V, (size_t)p->N * sizeof(double));
+  cp(F, p->F, (size_t)p->N * sizeof(double));
+  cp(rowptr, p->rowptr, (size_t)(p->N + 1) * sizeof(int64_t));
+  cp(col, p->col, (size_t)p->nnz * sizeof(int32_t));
+  cp(A, p->A, (size_t)p->nnz * sizeof(double));
+  cp(Fd, p->Fd, (size_t)p->nnz * sizeof(double));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->st);
+  return e == cudaSuccess ? VD_OK : VD_ECUDA;
+}
+
+void vd_poly_free(vd_poly* p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->st);
+  p->bufs.release();
+  delete p;
 }
 
 void vd_mc_free(vd_mc* mc) {

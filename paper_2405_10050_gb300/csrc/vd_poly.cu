@@ -1,0 +1,299 @@
+// vd_poly.cu -- exact cell volumes, interface areas and integrals of the
+// piecewise linear interpolant of f from the vertices of the diagram
+// (Section 3.2, Algorithms 4-5, IterativeVolume).
+//
+// For cell i the faces are walked depth first, one thread per cell: level 1
+// is the cell (the vertices whose tuple holds i, ascending), the face at
+// level D+1 keeps the vertices of its parent whose tuple holds the generator
+// j that defines it (candidates in ascending id, not yet in the face), down
+// to the edges at level d, which have exactly two vertices nu < nu'.  Every
+// edge closes the simplex (x_i, m_2, ..., m_{d-1}, nu, nu'), m_D the mean of
+// the level-D face's vertices, of volume |det(m_2 - x_i, ..., nu - x_i,
+// nu' - x_i)| / d! (Gaussian elimination, partial pivoting on the first
+// maximal |entry|).  Integrals take Algorithm 5's weights: an edge returns
+// F = (f(nu) + f(nu'))/2 V, a face at level D the sum of its children's V
+// and ((d-D+1)/(d-D+2)) sum F + (1/(d-D+2)) f(m_D) sum V, the cell
+// F_i = (d/(d+1)) sum F + (1/(d+1)) f(x_i) sum V; a facet ij gives
+// A_ij = V_ij d / h_ij and Fd_ij = F_ij d / h_ij.  Binary64 with the
+// operations in that order, so polynomial f reproduces the oracle bit for
+// bit.  The vertex lists of the deeper levels live in per-cell scratch
+// ((d-1) times the cell's vertex count).
+#include <algorithm>
+#include <cmath>
+
+#include "vd_dev.cuh"
+
+namespace vd {
+
+cudaError_t radix_sort_u64(uint64_t* keys, int32_t* vals, uint64_t* ktmp, int32_t* vtmp, int64_t n,
+                           uint32_t* counts, unsigned long long* orand, cudaStream_t st);
+cudaError_t mc_scan64(const int64_t* in, int64_t n, int64_t* out, cudaStream_t st);
+
+namespace {
+
+constexpr int kLzMaxD = 8;
+constexpr int64_t kLzNone = INT64_MAX;
+constexpr unsigned kLzFlagDegenerate = 1u, kLzFlagCap = 2u;
+
+__device__ double lz_f(const vd_func& f, int d, const double* y) {
+  if (f.kind == VD_F_POLY2) {
+    double s = f.c0;
+    for (int a = 0; a < d; ++a) s = __dadd_rn(s, __dmul_rn(f.b[a], y[a]));
+    for (int a = 0; a < d; ++a) s = __dadd_rn(s, __dmul_rn(f.q[a], __dmul_rn(y[a], y[a])));
+    return s;
+  }
+  if (f.kind == VD_F_SIN_SQ) return sin(__dmul_rn(y[f.axis], y[f.axis]));
+  return 1.0;
+}
+
+// smallest generator > prev in the tuples of list[0..n) outside S[0..ns)
+__device__ int64_t lz_next(const int32_t* tuples, int L, const int32_t* list, int n, const int32_t* S, int ns,
+                           int64_t prev) {
+  int64_t best = kLzNone;
+  for (int q = 0; q < n; ++q) {
+    const int32_t* t = tuples + (int64_t)list[q] * L;
+    for (int k = 0; k < L; ++k) {
+      const int64_t g = t[k];
+      if (g <= prev || g >= best) continue;
+      bool in = false;
+      for (int s = 0; s < ns; ++s) in |= (S[s] == g);
+      if (!in) best = g;
+    }
+  }
+  return best;
+}
+
+__device__ __forceinline__ bool lz_has(const int32_t* t, int L, int32_t g) {
+  bool in = false;
+  for (int k = 0; k < L; ++k) in |= (t[k] == g);
+  return in;
+}
+
+// |det| of the d x d row-major matrix M (destroyed)
+__device__ double lz_absdet(double* M, int d) {
+  double det = 1.0;
+  for (int c = 0; c < d; ++c) {
+    int p = c;
+    for (int r = c + 1; r < d; ++r)
+      if (fabs(M[r * d + c]) > fabs(M[p * d + c])) p = r;
+    if (M[p * d + c] == 0.0) return 0.0;
+    if (p != c)
+      for (int k = 0; k < d; ++k) {
+        const double t = M[c * d + k];
+        M[c * d + k] = M[p * d + k];
+        M[p * d + k] = t;
+      }
+    for (int r = c + 1; r < d; ++r) {
+      const double mlt = __ddiv_rn(M[r * d + c], M[c * d + c]);
+      for (int k = c + 1; k < d; ++k) M[r * d + k] = __dadd_rn(M[r * d + k], -__dmul_rn(mlt, M[c * d + k]));
+    }
+    det = __dmul_rn(det, M[c * d + c]);
+  }
+  return fabs(det);
+}
+
+// keys[v (d+1) + k] = the cell of node tuples[v][k] (N for a box face), vals = v
+__global__ void k_lz_pairs(const int32_t* tuples, int64_t nv, int d, int64_t N, uint64_t* keys, int32_t* vals,
+                           unsigned long long* cnt) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nv * (d + 1)) return;
+  const int32_t g = tuples[t];
+  const bool node = g >= 0 && g < N;
+  keys[t] = node ? (uint64_t)g : (uint64_t)N;
+  vals[t] = (int32_t)(t / (d + 1));
+  if (node) atomicAdd(&cnt[g], 1ull);
+}
+
+__global__ void k_lz_u64_to_i64(const unsigned long long* in, int64_t n, int64_t* out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (int64_t)in[i];
+}
+
+// number of facets of each cell: distinct generators other than i
+__global__ void k_lz_count(const int32_t* tuples, int d, int64_t N, const int64_t* voff, const int32_t* vlist,
+                           int64_t* fcnt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int32_t* L1 = vlist + voff[i];
+  const int n1 = (int)(voff[i + 1] - voff[i]);
+  const int32_t S0 = (int32_t)i;
+  int64_t c = 0, j = INT64_MIN;
+  while ((j = lz_next(tuples, d + 1, L1, n1, &S0, 1, j)) != kLzNone) ++c;
+  fcnt[i] = c;
+}
+
+// the walk of cell i (see the file comment)
+__global__ void k_lz_cells(const double* X, int64_t N, int d, const int32_t* tuples, const double* coords,
+                           const int64_t* voff, const int32_t* vlist, int32_t* scratch, const int64_t* rowptr,
+                           vd_func f, double fact, double* Vout, double* Fout, int32_t* col, double* A,
+                           double* Fd, unsigned* flags) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int L = d + 1;
+  const double* xi = X + i * d;
+  const double dd = (double)d;
+  const int n1 = (int)(voff[i + 1] - voff[i]);
+  const int32_t* lst[kLzMaxD + 1];
+  int cnt[kLzMaxD + 1];
+  int64_t prev[kLzMaxD + 1];
+  double sv[kLzMaxD + 1], sf[kLzMaxD + 1], fm[kLzMaxD + 1];
+  double mid[kLzMaxD + 1][kLzMaxD];
+  int32_t S[kLzMaxD + 1];
+  double M[kLzMaxD * kLzMaxD];
+  lst[1] = vlist + voff[i];
+  cnt[1] = n1;
+  prev[1] = INT64_MIN;
+  sv[1] = sf[1] = 0.0;
+  S[0] = (int32_t)i;
+  int64_t q = rowptr[i];
+  const int64_t qend = rowptr[i + 1];
+  int D = 1;
+  // a child of level D with generator j closed with (v, fv)
+  auto take = [&](int Dp, int32_t j, double v, double fv) {
+    if (Dp == 1) {  // facet ij
+      double h = 1.0;
+      if (j >= N || (j < 0 && face_axis(j) >= d)) {  // not a generator of this node set
+        atomicOr(flags, kLzFlagDegenerate);
+      } else if (j >= 0) {
+        double ww = 0.0;
+        for (int a = 0; a < d; ++a) {
+          const double w = __dadd_rn(X[(int64_t)j * d + a], -xi[a]);
+          ww = __dadd_rn(ww, __dmul_rn(w, w));
+        }
+        h = __dmul_rn(0.5, __dsqrt_rn(ww));
+      } else {
+        const double xa = xi[face_axis(j)];
+        h = face_side(j) ? __dadd_rn(1.0, -xa) : xa;
+      }
+      if (q < qend) {
+        col[q] = j;
+        A[q] = __ddiv_rn(__dmul_rn(v, dd), h);
+        Fd[q] = __ddiv_rn(__dmul_rn(fv, dd), h);
+      } else {
+        atomicOr(flags, kLzFlagCap);
+      }
+      ++q;
+    }
+    sv[Dp] = __dadd_rn(sv[Dp], v);
+    sf[Dp] = __dadd_rn(sf[Dp], fv);
+  };
+  while (true) {
+    const int64_t j = lz_next(tuples, L, lst[D], cnt[D], S, D, prev[D]);
+    if (j == kLzNone) {  // level D is complete
+      if (D == 1) {
+        const double cd = __ddiv_rn(dd, (double)(d + 1)), c1 = __ddiv_rn(1.0, (double)(d + 1));
+        Vout[i] = sv[1];
+        Fout[i] = __dadd_rn(__dmul_rn(cd, sf[1]), __dmul_rn(__dmul_rn(c1, lz_f(f, d, xi)), sv[1]));
+        break;
+      }
+      const double w1 = __ddiv_rn((double)(d - D + 1), (double)(d - D + 2)), w0 = __ddiv_rn(1.0, (double)(d - D + 2));
+      const double fv = __dadd_rn(__dmul_rn(w1, sf[D]), __dmul_rn(__dmul_rn(w0, fm[D]), sv[D]));
+      const double v = sv[D];
+      --D;
+      take(D, S[D], v, fv);
+      continue;
+    }
+    prev[D] = j;
+    S[D] = (int32_t)j;
+    // the child's vertex list: the parent's vertices whose tuple holds j
+    int32_t* child = scratch + (int64_t)(d - 1) * voff[i] + (int64_t)(D - 1) * n1;
+    int m = 0;
+    for (int p = 0; p < cnt[D]; ++p)
+      if (lz_has(tuples + (int64_t)lst[D][p] * L, L, (int32_t)j)) child[m++] = lst[D][p];
+    if (D + 1 == d) {  // an edge: the simplex it closes
+      if (m != 2) {
+        atomicOr(flags, kLzFlagDegenerate);
+        take(D, (int32_t)j, 0.0, 0.0);
+        continue;
+      }
+      for (int c = 0; c < d; ++c) {
+        const double* p = c < d - 2 ? mid[c + 2] : coords + (int64_t)child[c - (d - 2)] * d;
+        for (int r = 0; r < d; ++r) M[r * d + c] = __dadd_rn(p[r], -xi[r]);
+      }
+      const double v = __ddiv_rn(lz_absdet(M, d), fact);
+      const double f0 = lz_f(f, d, coords + (int64_t)child[0] * d), f1 = lz_f(f, d, coords + (int64_t)child[1] * d);
+      take(D, (int32_t)j, v, __dmul_rn(__dmul_rn(0.5, __dadd_rn(f0, f1)), v));
+      continue;
+    }
+    // descend into the child face: its vertex mean
+    ++D;
+    lst[D] = child;
+    cnt[D] = m;
+    prev[D] = INT64_MIN;
+    sv[D] = sf[D] = 0.0;
+    for (int a = 0; a < d; ++a) mid[D][a] = 0.0;
+    for (int p = 0; p < m; ++p)
+      for (int a = 0; a < d; ++a) mid[D][a] = __dadd_rn(mid[D][a], coords[(int64_t)child[p] * d + a]);
+    for (int a = 0; a < d; ++a) mid[D][a] = __ddiv_rn(mid[D][a], (double)m);
+    fm[D] = lz_f(f, d, mid[D]);
+  }
+}
+
+inline unsigned nb(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+}  // namespace
+
+// Exact integration of the node set X (N x d, device) from the vertices
+// (tuples, coords: nv rows, device).  Allocates the outputs from `out`
+// (V, F: N; rowptr: N+1; col, A, Fd: *nnz) and its scratch from `scratch`.
+cudaError_t poly_integrate(const double* X, int64_t N, int d, const int32_t* tuples, const double* coords,
+                           int64_t nv, const vd_func& f, DevBufs& out, DevBufs& scratch, double** V, double** F,
+                           int64_t** rowptr, int32_t** col, double** A, double** Fd, int64_t* nnz, unsigned* flags_h,
+                           cudaStream_t st) {
+  if (d < 2 || d > kLzMaxD) return cudaErrorInvalidValue;
+  cudaError_t e;
+  const int64_t np = std::max<int64_t>(nv * (d + 1), 1);
+  uint64_t *keys = nullptr, *ktmp = nullptr;
+  int32_t *vals = nullptr, *vtmp = nullptr, *lzs = nullptr;
+  uint32_t* counts = nullptr;
+  unsigned long long *orand = nullptr, *ccnt = nullptr;
+  int64_t *c64 = nullptr, *voff = nullptr, *fcnt = nullptr;
+  unsigned* flags = nullptr;
+  if ((e = scratch.alloc_n(&keys, np)) || (e = scratch.alloc_n(&ktmp, np)) || (e = scratch.alloc_n(&vals, np)) ||
+      (e = scratch.alloc_n(&vtmp, np)) || (e = scratch.alloc_n(&counts, (size_t)256 * (np / 4096 + 2))) ||
+      (e = scratch.alloc_n(&orand, 2)) || (e = scratch.alloc_n(&ccnt, N)) || (e = scratch.alloc_n(&c64, N)) ||
+      (e = scratch.alloc_n(&voff, N + 1)) || (e = scratch.alloc_n(&fcnt, N)) || (e = scratch.alloc_n(&flags, 1)) ||
+      (e = scratch.alloc_n(&lzs, (size_t)std::max<int64_t>((int64_t)(d - 1) * nv * (d + 1), 1))))
+    return e;
+  if ((e = cudaMemsetAsync(ccnt, 0, sizeof(unsigned long long) * N, st)) ||
+      (e = cudaMemsetAsync(flags, 0, sizeof(unsigned), st)))
+    return e;
+  // the cells' vertex lists in ascending vertex order: a stable sort of
+  // (cell, vertex) pairs written in vertex order
+  if (nv > 0) {
+    k_lz_pairs<<<nb(nv * (d + 1), 256), 256, 0, st>>>(tuples, nv, d, N, keys, vals, ccnt);
+    count_launch();
+    if ((e = radix_sort_u64(keys, vals, ktmp, vtmp, nv * (d + 1), counts, orand, st))) return e;
+  }
+  k_lz_u64_to_i64<<<nb(N, 256), 256, 0, st>>>(ccnt, N, c64);
+  count_launch();
+  if ((e = mc_scan64(c64, N, voff, st))) return e;
+  k_lz_count<<<nb(N, 128), 128, 0, st>>>(tuples, d, N, voff, vals, fcnt);
+  count_launch();
+  if ((e = out.alloc_n(rowptr, N + 1))) return e;
+  if ((e = mc_scan64(fcnt, N, *rowptr, st))) return e;
+  if ((e = cudaMemcpyAsync(nnz, *rowptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaStreamSynchronize(st))) return e;
+  const int64_t nn = std::max<int64_t>(*nnz, 1);
+  if ((e = out.alloc_n(V, N)) || (e = out.alloc_n(F, N)) || (e = out.alloc_n(col, nn)) || (e = out.alloc_n(A, nn)) ||
+      (e = out.alloc_n(Fd, nn)))
+    return e;
+  double fact = 1.0;
+  for (int k = 2; k <= d; ++k) fact *= (double)k;
+  {  // the walk keeps its per-level state in local memory: make sure the
+     // context's per-thread stack holds that frame
+    cudaFuncAttributes fa;
+    size_t cur = 0;
+    if ((e = cudaFuncGetAttributes(&fa, k_lz_cells)) || (e = cudaDeviceGetLimit(&cur, cudaLimitStackSize))) return e;
+    const size_t need = (fa.localSizeBytes + 1023) / 1024 * 1024 + 1024;
+    if (cur < need && (e = cudaDeviceSetLimit(cudaLimitStackSize, need))) return e;
+  }
+  k_lz_cells<<<nb(N, 64), 64, 0, st>>>(X, N, d, tuples, coords, voff, vals, lzs, *rowptr, f, fact, *V, *F, *col, *A,
+                                       *Fd, flags);
+  count_launch();
+  if ((e = cudaMemcpyAsync(flags_h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st))) return e;
+  if ((e = cudaStreamSynchronize(st))) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace vd

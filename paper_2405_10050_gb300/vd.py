@@ -75,7 +75,7 @@ EXPORTS = ["vd_kernel_launches", "vd_config_default", "vd_create", "vd_destroy",
            "vd_last_stats", "vd_set_nodes", "vd_raycast", "vd_vertices", "vd_mesh_count", "vd_mesh_dim",
            "vd_mesh_copy", "vd_mesh_stats", "vd_mesh_free", "vd_mc_integrate", "vd_mc_get", "vd_mc_rays",
            "vd_mc_adjoint", "vd_mc_integrals", "vd_hmc_integrals", "vd_mc_stats", "vd_mc_count", "vd_mc_free", "vd_mc_directions",
-           "vd_mc_integrate_batch", "vd_raycast_noalloc"]
+           "vd_mc_integrate_batch", "vd_raycast_noalloc", "vd_poly_integrate", "vd_poly_get", "vd_poly_free"]
 
 _lib = None
 
@@ -119,6 +119,9 @@ def load(build_if_missing: bool = True):
         "vd_mc_adjoint": (i32, [P, P, P, P, i32]),
         "vd_mc_integrals": (i32, [P, P, i64, P, P, i32]),
         "vd_hmc_integrals": (i32, [P, P, P, P, P, P, i32]),
+        "vd_poly_integrate": (i32, [P, P, P, P]),
+        "vd_poly_get": (i32, [P, P, P, P, P, P, P, P, i32]),
+        "vd_poly_free": (None, [P]),
         "vd_mc_stats": (i32, [P, P]),
         "vd_mc_count": (i64, [P]),
         "vd_mc_free": (None, [P]),
@@ -310,6 +313,27 @@ def vd_hmc_integrals(mc, mesh, f, VH=None, FH=None, IH=None):
     ptrs = [_ptr(VH, np.float64), _ptr(FH, np.float64), _ptr(IH, np.float64)]
     dev = next((p[1] for p in ptrs if p[1] is not None), 0)
     _check(None, load().vd_hmc_integrals(mc, mesh, ctypes.byref(f), ptrs[0][0], ptrs[1][0], ptrs[2][0], dev))
+
+
+def vd_poly_integrate(ctx, mesh, f):
+    """Section 3.2's exact integration of the context's nodes from mesh."""
+    p = ctypes.c_void_p()
+    _check(ctx, load().vd_poly_integrate(ctx, mesh, ctypes.byref(f), ctypes.byref(p)))
+    return p
+
+
+def vd_poly_get(p, V=None, F=None, rowptr=None, col=None, A=None, Fd=None):
+    nnz = ctypes.c_int64()
+    args = [_ptr(V, np.float64), _ptr(F, np.float64), _ptr(rowptr, np.int64), _ptr(col, np.int32),
+            _ptr(A, np.float64), _ptr(Fd, np.float64)]
+    dev = next((a[1] for a in args if a[1] is not None), 0)
+    _check(None, load().vd_poly_get(p, args[0][0], args[1][0], ctypes.byref(nnz), args[2][0], args[3][0], args[4][0],
+                                    args[5][0], dev))
+    return nnz.value
+
+
+def vd_poly_free(p):
+    load().vd_poly_free(p)
 
 
 def vd_mc_stats(mc):

@@ -1243,6 +1243,75 @@ int64_t or_vertices(const double* X, int64_t N, int d, int32_t seed_node, int64_
 }
 
 /* --- batch helpers for the tests ---------------------------------------- */
+/* ------------------------------------------------------------------------ */
+/* Random walks on the vertex graph (Section 2.3: the random walk that       */
+/* approximates the Voronoi graph, with the incircle RayCast).  Walker w    */
+/* starts at the vertex with sorted tuple start[w]; at step s it takes one   */
+/* of the edges of its vertex that hold a node: with the valid drop indices */
+/* a_0 < ... < a_{n-1} it takes a_k, k = (w0 n) >> 32, w0 = word 0 of       */
+/* Philox4x32-10 at counter (s, w, 0x57414C4B, 0), key (seed low, seed      */
+/* high); it casts the ray along that edge (SearchDirection, RayCast from   */
+/* the vertex, reference node first as in Algorithm 2) and moves to the     */
+/* far vertex sort(edge + hit), coordinates re-solved.  path_t: W x S x     */
+/* (d+1), path_x: W x S x d.  Returns 0, or -1 after a degenerate step      */
+/* (the walker then stays where it was).                                     */
+/* ------------------------------------------------------------------------ */
+int or_random_walk(const double* X, int64_t N, int d, const int32_t* start, int64_t W, int64_t S, uint64_t seed,
+                   int32_t* path_t, double* path_x) {
+  const int L = d + 1;
+  int rc = 0;
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int64_t w = 0; w < W; ++w) {
+    int32_t sig[OR_MAXD + 1];
+    double r[OR_MAXD];
+    for (int q = 0; q < L; ++q) sig[q] = start[w * L + q];
+    if (!or_vertex_coords(X, d, sig, r)) rc = -1;
+    for (int64_t s = 0; s < S; ++s) {
+      int valid[OR_MAXD + 1], n = 0;
+      for (int q = 0; q < L; ++q)
+        if (edge_has_node(sig, d, q)) valid[n++] = q;
+      int ok = n > 0;
+      if (ok) {
+        uint32_t ctr[4] = {(uint32_t)s, (uint32_t)w, 0x57414C4Bu, 0u}, o[4];
+        or_philox4x32_10(ctr, key, o);
+        const int drop = valid[(int)(((uint64_t)o[0] * (uint64_t)n) >> 32)];
+        int32_t eta[OR_MAXD + 1], er[OR_MAXD + 1];
+        edge_of(sig, d, drop, eta);
+        double u[OR_MAXD];
+        ok = or_search_direction(X, d, sig, drop, u);
+        if (ok) {
+          int gpos = 0;
+          while (eta[gpos] < 0) ++gpos;
+          er[0] = eta[gpos];
+          int me = 1;
+          for (int q2 = 0; q2 < d; ++q2)
+            if (q2 != gpos) er[me++] = eta[q2];
+          int32_t hit;
+          double t;
+          raycast1(X, N, d, 1, r, u, er, me, &hit, &t, NULL);
+          ok = hit != OR_NO_ID;
+          if (ok) {
+            int32_t ns[OR_MAXD + 1];
+            double x[OR_MAXD];
+            for (int q2 = 0; q2 < d; ++q2) ns[q2] = eta[q2];
+            ns[d] = hit;
+            sort_small(ns, L);
+            ok = or_vertex_coords(X, d, ns, x);
+            if (ok) {
+              for (int q2 = 0; q2 < L; ++q2) sig[q2] = ns[q2];
+              for (int a = 0; a < d; ++a) r[a] = x[a];
+            }
+          }
+        }
+      }
+      if (!ok) rc = -1;
+      for (int q = 0; q < L; ++q) path_t[(w * S + s) * L + q] = sig[q];
+      for (int a = 0; a < d; ++a) path_x[(w * S + s) * d + a] = r[a];
+    }
+  }
+  return rc;
+}
+
 void or_log32_batch(const float* x, float* y, int64_t n) {
   for (int64_t q = 0; q < n; ++q) y[q] = or_log32(x[q]);
 }

@@ -269,6 +269,9 @@ def run_ours(args):
     if args.only_hmc:
         print(json.dumps({"hmc": run_hmc(args, vd, torch.cuda.current_stream())}), flush=True)
         return
+    if args.only_walk:
+        print(json.dumps({"walk": run_walk(args, vd, torch.cuda.current_stream())}), flush=True)
+        return
     if args.only_batch:
         print(json.dumps({"batch": run_batch(args, vd, torch.cuda.current_stream())}), flush=True)
         return
@@ -393,6 +396,9 @@ def run_ours(args):
     hmc = None
     if not args.no_hmc:
         hmc = run_hmc(args, vd, stream)
+    walk = None
+    if not args.no_walk:
+        walk = run_walk(args, vd, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -420,7 +426,7 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": "raycasts/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "mc": mc, "highd": highd, "hmc": hmc}
+                "mc": mc, "highd": highd, "hmc": hmc, "walk": walk}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -588,6 +594,47 @@ def run_hmc(args, vd, stream, reps=3):
     return out
 
 
+WALK_WORKLOAD = ("random walks on the vertex graph (Section 2.3), d=5, N=20000 iid uniform in [0,1]^5 (seed 0): "
+                 "1,000,000 walkers from distinct vertices of the diagram, 8 steps each")
+
+
+def run_walk(args, vd, stream, W=1_000_000, S=8):
+    """Random walks: CUDA-event time of one vd_random_walk call (device
+    buffers), after one warm-up call; one RayCast per walker and step."""
+    import torch
+    from paper_2405_10050_gb300 import VD_FP32, synth
+    N, d = args.N, args.d
+    X = torch.tensor(synth.uniform(N, d, seed=0), device="cuda")
+    cfg = vd.vd_config_default()
+    cfg.precision = VD_FP32
+    ctx = vd.vd_create(cfg, stream.cuda_stream)
+    vd.vd_set_nodes(ctx, X)
+    mesh = vd.vd_vertices(ctx)
+    nv = vd.vd_mesh_count(mesh)
+    T = torch.empty((nv, d + 1), dtype=torch.int32, device="cuda")
+    vd.vd_mesh_copy(mesh, T, None)
+    vd.vd_mesh_free(mesh)
+    W = min(W, nv)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    start = T[torch.randperm(nv, generator=g)[:W].sort().values.to("cuda")].contiguous()
+    PT = torch.empty((W, S, d + 1), dtype=torch.int32, device="cuda")
+    PC = torch.empty((W, S, d), dtype=torch.float64, device="cuda")
+    vd.vd_random_walk(ctx, start, S, 1, PT, PC)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    vd.vd_random_walk(ctx, start, S, 2, PT, PC)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = vd.vd_last_stats(ctx)
+    distinct = int(torch.unique(PT.view(-1, d + 1), dim=0).shape[0])
+    vd.vd_destroy(ctx)
+    return {"workload": WALK_WORKLOAD.replace("N=20000", f"N={N}").replace("d=5", f"d={d}"), "unit": "raycasts/s",
+            "value": W * S / (ms / 1000.0), "ms": ms, "raycast_ms": st["raycast_ms"], "walkers": W, "steps": S,
+            "distinct_vertices_visited": distinct, "vertices": nv}
+
+
 def run_highd(args, vd, stream):
     """MC vol+grad cells/s on the high-dimensional workload: tensor-core walk
     (tcgen05 ball tests and leaf screening) vs the binary32 tree walk, same
@@ -700,6 +747,8 @@ def main():
     ap.add_argument("--no-highd", action="store_true")
     ap.add_argument("--only-highd", action="store_true")
     ap.add_argument("--no-hmc", action="store_true")
+    ap.add_argument("--no-walk", action="store_true")
+    ap.add_argument("--only-walk", action="store_true")
     ap.add_argument("--only-hmc", action="store_true")
     ap.add_argument("--highd-fp64", action="store_true", help="also time the binary64 path (about 25 s)")
     ap.add_argument("--highd-n", type=int, default=200000)

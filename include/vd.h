@@ -156,6 +156,21 @@ vd_status vd_mesh_copy(const vd_mesh* mesh, int32_t* tuples, double* coords, int
 vd_status vd_mesh_stats(const vd_mesh* mesh, vd_stats* out);
 void vd_mesh_free(vd_mesh* mesh);
 
+/* Random walks on the vertex graph (Section 2.3: the random walk that
+ * approximates the Voronoi graph, here with the incircle RayCast), 2 <= d
+ * <= 6, box on.  Walker w starts at the vertex with sorted tuple
+ * start[w] (W x (d+1) int32, a vertex of the context's diagram); at each
+ * step it takes one of its vertex's edges that hold a node, drawn by
+ * Philox4x32-10 at counter (step, w, 0x57414C4B, 0), key (seed): with the
+ * valid drop indices a_0 < ... < a_{n-1} of the tuple it takes a_k,
+ * k = (word0 n) >> 32; it casts the ray along that edge (SearchDirection,
+ * reference node first) and moves to the far vertex.  path_tuples: W x steps
+ * x (d+1) sorted tuples; path_coords: W x steps x d float64 (may be NULL).
+ * VD_EDEGENERATE if a step met a degenerate solve (that walker stays put).
+ * vd_last_stats: rays = W * steps, ms, raycast_ms. */
+vd_status vd_random_walk(vd_ctx* ctx, const int32_t* start, int64_t W, int64_t steps, uint64_t seed,
+                         int32_t* path_tuples, double* path_coords, int32_t on_device);
+
 /* Monte Carlo volumes and interface areas (Section 3.1, Algorithm 3) of all
  * N cells with R rays per cell.  Ray k of cell i has the direction drawn by
  * vd_mc_directions (Philox4x32-10 keyed by seed) and is cast from x_i with

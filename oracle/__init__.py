@@ -65,7 +65,7 @@ def lib():
         L.or_leibniz.restype = i64
         L.or_leibniz.argtypes = [P, i64, i32, P, P, i64, i32, i32, P, P, P, P, P, P, P, i64]
         L.or_random_walk.restype = ctypes.c_int
-        L.or_random_walk.argtypes = [P, i64, i32, P, i64, i64, u64, P, P]
+        L.or_random_walk.argtypes = [P, i64, i32, P, i64, i64, u64, P, P, P]
         L.or_vertex_coords.restype = ctypes.c_int
         L.or_vertex_coords.argtypes = [P, i32, P, P]
         L.or_search_direction.restype = ctypes.c_int
@@ -354,15 +354,20 @@ def leibniz(X, tuples, coords, f=("one",)):
     return V, F, rowptr, col[:nnz].copy(), A[:nnz].copy(), Fd[:nnz].copy()
 
 
-def random_walk(X, start, steps: int, seed: int):
+def random_walk(X, start, steps: int, seed: int, wid=None):
     """Walkers from the vertices start (W x (d+1) sorted tuples), steps moves
-    each along random edges: tuples (W x steps x (d+1)) and coordinates."""
+    each along random edges: tuples (W x steps x (d+1)) and coordinates;
+    wid: the walkers' indices in the draw (default 0..W-1)."""
     X = _f64(X)
     N, d = X.shape
     start = np.ascontiguousarray(start, dtype=np.int32).reshape(-1, d + 1)
     W = start.shape[0]
     T = np.empty((W, steps, d + 1), np.int32)
     C = np.empty((W, steps, d))
-    rc = lib().or_random_walk(_p(X), N, d, _p(start), W, steps, seed, _p(T), _p(C))
+    wp = None
+    if wid is not None:
+        wid = np.ascontiguousarray(wid, dtype=np.int64)
+        wp = _p(wid)
+    rc = lib().or_random_walk(_p(X), N, d, _p(start), W, steps, seed, wp, _p(T), _p(C))
     assert rc == 0, "degenerate step"
     return T, C

@@ -1252,12 +1252,13 @@ int64_t or_vertices(const double* X, int64_t N, int d, int32_t seed_node, int64_
 /* Philox4x32-10 at counter (s, w, 0x57414C4B, 0), key (seed low, seed      */
 /* high); it casts the ray along that edge (SearchDirection, RayCast from   */
 /* the vertex, reference node first as in Algorithm 2) and moves to the     */
-/* far vertex sort(edge + hit), coordinates re-solved.  path_t: W x S x     */
-/* (d+1), path_x: W x S x d.  Returns 0, or -1 after a degenerate step      */
-/* (the walker then stays where it was).                                     */
+/* far vertex sort(edge + hit), coordinates re-solved.  wid (nullable) gives */
+/* each walker's index w in the draw.  path_t: W x S x (d+1), path_x:       */
+/* W x S x d.  Returns 0, or -1 after a degenerate step (the walker then    */
+/* stays where it was).                                                      */
 /* ------------------------------------------------------------------------ */
 int or_random_walk(const double* X, int64_t N, int d, const int32_t* start, int64_t W, int64_t S, uint64_t seed,
-                   int32_t* path_t, double* path_x) {
+                   const int64_t* wid, int32_t* path_t, double* path_x) {
   const int L = d + 1;
   int rc = 0;
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -1272,7 +1273,7 @@ int or_random_walk(const double* X, int64_t N, int d, const int32_t* start, int6
         if (edge_has_node(sig, d, q)) valid[n++] = q;
       int ok = n > 0;
       if (ok) {
-        uint32_t ctr[4] = {(uint32_t)s, (uint32_t)w, 0x57414C4Bu, 0u}, o[4];
+        uint32_t ctr[4] = {(uint32_t)s, (uint32_t)(wid ? wid[w] : w), 0x57414C4Bu, 0u}, o[4];
         or_philox4x32_10(ctr, key, o);
         const int drop = valid[(int)(((uint64_t)o[0] * (uint64_t)n) >> 32)];
         int32_t eta[OR_MAXD + 1], er[OR_MAXD + 1];

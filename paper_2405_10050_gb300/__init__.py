@@ -193,6 +193,18 @@ class Voronoi:
         finally:
             vd.vd_poly_free(p)
 
+    def random_walk(self, start, steps: int, seed: int):
+        """Walkers from the vertices start (W x (d+1) sorted tuples, e.g. rows
+        of vertices()), steps random edges each (Section 2.3): the visited
+        tuples (W x steps x (d+1)) and coordinates."""
+        import torch
+        start = torch.as_tensor(start, dtype=torch.int32, device="cuda").contiguous()
+        W = start.shape[0]
+        T = torch.empty((W, steps, self.d + 1), dtype=torch.int32, device="cuda")
+        C = torch.empty((W, steps, self.d), dtype=torch.float64, device="cuda")
+        vd.vd_random_walk(self.ctx, start, steps, seed, T, C)
+        return T, C
+
     def vertices(self):
         """All vertices of the clipped diagram: (tuples V x (d+1), coords V x d)."""
         import torch

@@ -34,6 +34,9 @@ cudaError_t poly_integrate(const double* X, int64_t N, int d, const int32_t* tup
                            int64_t nv, const vd_func& f, DevBufs& out, DevBufs& scratch, double** V, double** F,
                            int64_t** rowptr, int32_t** col, double** A, double** Fd, int64_t* nnz, unsigned* flags_h,
                            cudaStream_t st);
+cudaError_t random_walk(const TreeView& tv, int precision, const int32_t* start, int64_t W, int64_t S, uint64_t seed,
+                        int32_t* path_t, double* path_x, Counters* ctr, DevBufs& scratch, cudaStream_t st,
+                        double* raycast_ms);
 cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, Workspace& ws,
                               DevBufs& out_bufs, int32_t** tuples, double** coords, int64_t* nv, vd_stats* stats,
                               Counters* ctr, cudaStream_t st, char* err, size_t errlen);
@@ -1009,6 +1012,58 @@ vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const*
 }
 
 // ------------------------------------------------------------- vertices --
+vd_status vd_random_walk(vd_ctx* ctx, const int32_t* start, int64_t W, int64_t steps, uint64_t seed,
+                         int32_t* path_tuples, double* path_coords, int32_t on_device) {
+  if (!ctx || (W > 0 && (!start || !path_tuples)) || W < 0 || steps < 0) return VD_EINVAL;
+  if (!ctx->X) return set_err(ctx, VD_EINVAL, "vd_random_walk: no node set");
+  if (!ctx->cfg.box) return set_err(ctx, VD_EINVAL, "vd_random_walk: needs box clipping");
+  if (ctx->d < 2 || ctx->d > 6) return set_err(ctx, VD_EINVAL, "vd_random_walk: needs 2 <= d <= 6");
+  if (W > ((int64_t)1 << 30) || steps > ((int64_t)1 << 31))
+    return set_err(ctx, VD_EINVAL, "vd_random_walk: too many walkers or steps");
+  const int d = ctx->d, L = d + 1;
+  DevBufs tmp;
+  const int32_t* st_d = start;
+  int32_t* pt = path_tuples;
+  double* px = path_coords;
+  cudaError_t e = cudaSuccess;
+  if (!on_device && W > 0) {
+    int32_t* s2 = nullptr;
+    e = tmp.alloc_n(&s2, (size_t)W * L);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s2, start, (size_t)W * L * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->st);
+    st_d = s2;
+    if (e == cudaSuccess) e = tmp.alloc_n(&pt, (size_t)std::max<int64_t>(W * steps, 1) * L);
+    if (e == cudaSuccess && path_coords) e = tmp.alloc_n(&px, (size_t)std::max<int64_t>(W * steps, 1) * d);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->st);
+  double rms = 0.0;
+  Timer tm(ctx->st);
+  if (e == cudaSuccess)
+    e = vd::random_walk(ctx->tree, effective_precision(ctx), st_d, W, steps, seed, pt, px, ctx->ctr, tmp, ctx->st, &rms);
+  const double ms = tm.stop();
+  if (e == cudaSuccess && !on_device && W > 0) {
+    e = cudaMemcpyAsync(path_tuples, pt, (size_t)W * steps * L * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->st);
+    if (e == cudaSuccess && path_coords)
+      e = cudaMemcpyAsync(path_coords, px, (size_t)W * steps * d * sizeof(double), cudaMemcpyDeviceToHost, ctx->st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  cudaStreamSynchronize(ctx->st);
+  tmp.release();
+  if (e != cudaSuccess) return cuda_err(ctx, e, "vd_random_walk");
+  Counters hc;
+  vd_status s = read_counters(ctx, &hc);
+  if (s == VD_OK) s = check_flags(ctx, hc);
+  if (s == VD_OK) {
+    vd_stats st{};
+    st.rays = W * steps;
+    st.ms = ms;
+    st.raycast_ms = rms;
+    st.rechecked = (int64_t)hc.rechecked;
+    st.pairs_screened = (int64_t)hc.pairs;
+    ctx->last = st;
+  }
+  return s;
+}
+
 vd_status vd_vertices(vd_ctx* ctx, vd_mesh** out) {
   if (!ctx || !out) return VD_EINVAL;
   *out = nullptr;

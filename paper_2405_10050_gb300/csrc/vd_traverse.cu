@@ -670,6 +670,128 @@ void launch_finish(Tables T, const double* X, const int32_t* cand, const int64_t
     else FN<16>(__VA_ARGS__);                 \
   } while (0)
 
+// ---- random walks on the vertex graph (Section 2.3) ----
+// Walker w at the vertex with sorted tuple sig[w] takes one of its edges that
+// hold a node: with the valid drop indices a_0 < ... < a_{n-1} it takes a_k,
+// k = (w0 n) >> 32, w0 = word 0 of Philox4x32-10 at counter (step, w,
+// 0x57414C4B, 0), key (seed); the ray along that edge (SearchDirection from
+// the vertex, reference node first) finds the far vertex sort(edge + hit).
+template <int D>
+__global__ void k_walk_init(const double* X, int d, int64_t W, const int32_t* sig, double* r, unsigned* flags) {
+  const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  int32_t s[D + 1];
+  for (int a = 0; a <= d; ++a) s[a] = sig[w * (d + 1) + a];
+  double x[D];
+  if (!vertex_coords<D>(X, d, s, x)) atomicOr(flags, kFlagDegenerate);
+  for (int a = 0; a < d; ++a) r[w * d + a] = x[a];
+}
+
+template <int D>
+__global__ void k_walk_dir(const double* X, int d, int64_t W, const int32_t* sig, const double* r, int64_t step,
+                           uint64_t seed, double* ro, double* rd, int32_t* reta, int32_t* drop_out, unsigned* flags) {
+  const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  const int L = d + 1;
+  int32_t s[D + 1];
+  for (int a = 0; a < L; ++a) s[a] = sig[w * L + a];
+  int valid[D + 1], n = 0;
+  for (int q = 0; q < L; ++q) {
+    bool node = false;
+    for (int k = 0; k < L; ++k) node |= (k != q && s[k] >= 0);
+    if (node) valid[n++] = q;
+  }
+  int drop = -1;
+  if (n > 0) {
+    uint32_t c[4] = {(uint32_t)step, (uint32_t)w, 0x57414C4Bu, 0u};
+    philox10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    drop = valid[(int)(((uint64_t)c[0] * (uint64_t)n) >> 32)];
+  }
+  double u[D];
+  for (int a = 0; a < D; ++a) u[a] = 0.0;
+  if (drop >= 0 && !search_direction<D>(X, d, s, drop, u)) {
+    atomicOr(flags, kFlagDegenerate);
+    for (int a = 0; a < D; ++a) u[a] = 0.0;
+    drop = -1;
+  }
+  // eta row: the edge, reference node first (a zero direction casts to nothing)
+  int32_t eta[D + 1];
+  int m = 0;
+  for (int a = 0; a < L; ++a)
+    if (a != (drop >= 0 ? drop : 0)) eta[m++] = s[a];
+  int gpos = 0;
+  while (gpos < d && eta[gpos] < 0) ++gpos;
+  if (gpos == d) {  // no node: not a vertex of this node set
+    atomicOr(flags, kFlagDegenerate);
+    drop = -1;
+    reta[w * d] = 0;
+    for (int a = 1; a < d; ++a) reta[w * d + a] = kNoId;
+  } else {
+    reta[w * d] = eta[gpos];
+    int k = 1;
+    for (int a = 0; a < d; ++a)
+      if (a != gpos) reta[w * d + k++] = eta[a];
+  }
+  for (int a = 0; a < d; ++a) {
+    ro[w * d + a] = r[w * d + a];
+    rd[w * d + a] = u[a];
+  }
+  drop_out[w] = drop;
+}
+
+template <int D>
+__global__ void k_walk_commit(const double* X, int d, int64_t W, int32_t* sig, double* r, const int32_t* drop,
+                              const int32_t* hit, int64_t step, int64_t S, int32_t* path_t, double* path_x,
+                              unsigned* flags) {
+  const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  const int L = d + 1;
+  int32_t s[D + 1];
+  for (int a = 0; a < L; ++a) s[a] = sig[w * L + a];
+  const int dr = drop[w];
+  const int32_t h = hit[w];
+  bool ok = dr >= 0 && h != kNoId;
+  if (ok) {
+    int32_t ns[D + 1];
+    int m = 0;
+    for (int a = 0; a < L; ++a)
+      if (a != dr) ns[m++] = s[a];
+    ns[d] = h;
+    sort_small(ns, L);
+    double x[D];
+    ok = vertex_coords<D>(X, d, ns, x);
+    if (ok) {
+      for (int a = 0; a < L; ++a) sig[w * L + a] = s[a] = ns[a];
+      for (int a = 0; a < d; ++a) r[w * d + a] = x[a];
+    }
+  }
+  if (!ok) atomicOr(flags, kFlagDegenerate);  // the walker stays where it was
+  for (int a = 0; a < L; ++a) path_t[(w * S + step) * L + a] = s[a];
+  if (path_x)
+    for (int a = 0; a < d; ++a) path_x[(w * S + step) * d + a] = r[w * d + a];
+}
+
+template <int D>
+void walk_init_d(const double* X, int d, int64_t W, const int32_t* sig, double* r, unsigned* flags, cudaStream_t st) {
+  k_walk_init<D><<<nb(W, 128), 128, 0, st>>>(X, d, W, sig, r, flags);
+  count_launch();
+}
+
+template <int D>
+void walk_dir_d(const double* X, int d, int64_t W, const int32_t* sig, const double* r, int64_t step, uint64_t seed,
+                double* ro, double* rd, int32_t* reta, int32_t* drop, unsigned* flags, cudaStream_t st) {
+  k_walk_dir<D><<<nb(W, 128), 128, 0, st>>>(X, d, W, sig, r, step, seed, ro, rd, reta, drop, flags);
+  count_launch();
+}
+
+template <int D>
+void walk_commit_d(const double* X, int d, int64_t W, int32_t* sig, double* r, const int32_t* drop,
+                   const int32_t* hit, int64_t step, int64_t S, int32_t* path_t, double* path_x, unsigned* flags,
+                   cudaStream_t st) {
+  k_walk_commit<D><<<nb(W, 128), 128, 0, st>>>(X, d, W, sig, r, drop, hit, step, S, path_t, path_x, flags);
+  count_launch();
+}
+
 int64_t pow2_at_least(int64_t x) {
   int64_t p = 1;
   while (p < x) p <<= 1;
@@ -948,6 +1070,68 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   stats->fallback_rays = nfallback;
   return cudaSuccess;
 #undef VD_TRY
+}
+
+// W walkers from the vertices start (device, W x (d+1) sorted tuples), S
+// steps each; path_t (W x S x (d+1)) and path_x (W x S x d, may be null) on
+// the device.  Flags (degenerate steps, bad input) go to ctr->flags.
+cudaError_t random_walk(const TreeView& tv, int precision, const int32_t* start, int64_t W, int64_t S, uint64_t seed,
+                        int32_t* path_t, double* path_x, Counters* ctr, DevBufs& scratch, cudaStream_t st,
+                        double* raycast_ms) {
+  const int d = tv.d, L = d + 1;
+  const int64_t w1 = std::max<int64_t>(W, 1);
+  int32_t *sig = nullptr, *reta = nullptr, *rhit = nullptr, *drop = nullptr, *ovl = nullptr, *fbl = nullptr;
+  double *r = nullptr, *ro = nullptr, *rd = nullptr, *rt = nullptr;
+  cudaError_t e;
+  if ((e = scratch.alloc_n(&sig, (size_t)w1 * L)) || (e = scratch.alloc_n(&r, (size_t)w1 * d)) ||
+      (e = scratch.alloc_n(&ro, (size_t)w1 * d)) || (e = scratch.alloc_n(&rd, (size_t)w1 * d)) ||
+      (e = scratch.alloc_n(&reta, (size_t)w1 * d)) || (e = scratch.alloc_n(&rhit, (size_t)w1)) ||
+      (e = scratch.alloc_n(&rt, (size_t)w1)) || (e = scratch.alloc_n(&drop, (size_t)w1)) ||
+      (e = scratch.alloc_n(&ovl, (size_t)w1)) || (e = scratch.alloc_n(&fbl, (size_t)w1)))
+    return e;
+  if (W == 0 || S == 0) return cudaSuccess;
+  if ((e = cudaMemcpyAsync(sig, start, (size_t)W * L * sizeof(int32_t), cudaMemcpyDeviceToDevice, st))) return e;
+  unsigned* flags = &ctr->flags;
+  VD_TRAV_D(d, walk_init_d, tv.X, d, W, sig, r, flags, st);
+  cudaEvent_t ev0, ev1;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  float total = 0.f;
+  for (int64_t step = 0; step < S && e == cudaSuccess; ++step) {
+    VD_TRAV_D(d, walk_dir_d, tv.X, d, W, sig, r, step, seed, ro, rd, reta, drop, flags, st);
+    RaySource rs;
+    rs.mode = 0;
+    rs.R = W;
+    rs.origins = ro;
+    rs.dirs = rd;
+    rs.eta = reta;
+    rs.eta_stride = d;
+    rs.box = 1;
+    RayOut rout;
+    rout.hit = rhit;
+    rout.t = rt;
+    rout.overflow_list = ovl;
+    rout.overflow_cap = W;
+    rout.fallback_list = fbl;
+    rout.fallback_cap = W;
+    if ((e = cudaMemsetAsync(&ctr->overflow, 0, sizeof(unsigned long long), st)) ||
+        (e = cudaMemsetAsync(&ctr->fallback, 0, sizeof(unsigned long long), st)))
+      break;
+    cudaEventRecord(ev0, st);
+    e = launch_raycast_async(tv, rs, rout, precision, ctr, st);
+    cudaEventRecord(ev1, st);
+    if (e != cudaSuccess) break;
+    VD_TRAV_D(d, walk_commit_d, tv.X, d, W, sig, r, drop, rhit, step, S, path_t, path_x, flags, st);
+    if ((e = cudaEventSynchronize(ev1)) == cudaSuccess) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) total += ms;
+    }
+  }
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (raycast_ms) *raycast_ms = total;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 }  // namespace vd

@@ -75,7 +75,7 @@ EXPORTS = ["vd_kernel_launches", "vd_config_default", "vd_create", "vd_destroy",
            "vd_last_stats", "vd_set_nodes", "vd_raycast", "vd_vertices", "vd_mesh_count", "vd_mesh_dim",
            "vd_mesh_copy", "vd_mesh_stats", "vd_mesh_free", "vd_mc_integrate", "vd_mc_get", "vd_mc_rays",
            "vd_mc_adjoint", "vd_mc_integrals", "vd_hmc_integrals", "vd_mc_stats", "vd_mc_count", "vd_mc_free", "vd_mc_directions",
-           "vd_mc_integrate_batch", "vd_raycast_noalloc", "vd_poly_integrate", "vd_poly_get", "vd_poly_free"]
+           "vd_mc_integrate_batch", "vd_raycast_noalloc", "vd_poly_integrate", "vd_poly_get", "vd_poly_free", "vd_random_walk"]
 
 _lib = None
 
@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True):
         "vd_poly_integrate": (i32, [P, P, P, P]),
         "vd_poly_get": (i32, [P, P, P, P, P, P, P, P, i32]),
         "vd_poly_free": (None, [P]),
+        "vd_random_walk": (i32, [P, P, i64, i64, u64, P, P, i32]),
         "vd_mc_stats": (i32, [P, P]),
         "vd_mc_count": (i64, [P]),
         "vd_mc_free": (None, [P]),
@@ -334,6 +335,15 @@ def vd_poly_get(p, V=None, F=None, rowptr=None, col=None, A=None, Fd=None):
 
 def vd_poly_free(p):
     load().vd_poly_free(p)
+
+
+def vd_random_walk(ctx, start, steps, seed, path_tuples, path_coords=None):
+    """W walkers from the vertices start (W x (d+1)), steps moves each."""
+    ps, dev, k1 = _ptr(start, np.int32)
+    pt, dev2, k2 = _ptr(path_tuples, np.int32)
+    pc, dev3, k3 = _ptr(path_coords, np.float64)
+    W = int(start.shape[0])
+    _check(ctx, load().vd_random_walk(ctx, ps, W, int(steps), int(seed), pt, pc, dev or 0))
 
 
 def vd_mc_stats(mc):

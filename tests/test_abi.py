@@ -38,3 +38,25 @@ def test_status_strings_and_defaults_without_gpu():
     cfg = vd.vd_config_default()
     assert cfg.box == 1 and cfg.precision == vd.VD_AUTO
 
+
+
+def _prototypes():
+    """name -> number of parameters of every function include/vd.h declares."""
+    src = open(os.path.join(ROOT, "include", "vd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(vd_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every function the ctypes binding declares takes as many arguments as
+    its prototype in include/vd.h (no GPU needed: the library only loads)."""
+    from paper_2405_10050_gb300 import vd
+    L = vd.load()
+    protos = _prototypes()
+    assert set(vd.EXPORTS) <= set(protos)
+    for name in vd.EXPORTS:
+        assert len(getattr(L, name).argtypes) == protos[name], name

@@ -335,7 +335,7 @@ vd_status vd_raycast(vd_ctx* ctx, const double* origins, const double* dirs, con
     if (screen_err) VD_CK(tmp.alloc_n(&se_d, R), "alloc");
   }
   int32_t *ovl = nullptr, *fbl = nullptr;
-  const int64_t ovcap = std::max<int64_t>(1024, R / 16);
+  const int64_t ovcap = R;  // every ray may overflow its binary32 candidate buffer (clustered nodes)
   VD_CK(tmp.alloc_n(&ovl, ovcap), "alloc");
   VD_CK(tmp.alloc_n(&fbl, R), "alloc");
   // eta rows must start with a node

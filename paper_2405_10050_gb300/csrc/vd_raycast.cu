@@ -665,12 +665,42 @@ __global__ void __launch_bounds__(kThrRays, (D <= 6 ? 6 : D <= 8 ? 4 : 3))
     // beyond which a list entry (and every later one) lies outside it
     float far2, wwx;
     bool stale = false;
+    // Ball test of a finite bound T (Section 2.2's incircle criterion): with
+    // w = x - g and q = p + T u, a node with den > 0 has t <= T exactly when
+    // f = |w|^2 - 2 w.q <= 0.  In binary32 (w32 within EW per component,
+    // q32 within EQ in norm, FMA chains within gam) f <= 0 implies
+    //   fl(fl(cb ww32) - 2 wq32) <= beta,
+    // cb = 1/(1+gam) - e1/(2 s0 (1-gam)) less two roundings, beta =
+    // e1 s0/2 + e0, where e1 s + e0 bounds every error term with s = |w32|
+    // (e1 = 2 gam Q + 2 sqrt(D) EW + 2 EQ + 4.03 u Q, e0 = D EW^2 +
+    // 2 sqrt(D) EW (Q + EQ), Q >= |q32|) and s <= (s^2/s0 + s0)/2 with
+    // s0 = Q.  A stale (larger) T gives a wider test, so it stays valid.
+    float q32[D];
+    float cb = 0.f, beta = 0.f;
+    bool fast = false;
     auto refresh = [&]() {
       Ball<D> ball;
       make_ball<D>(g32, p32, u32, T, B, ball);
       far2 = far_radius2<D>(tr, ball, g32);
       wwx = ww_exit(far2, gam, EW, D);
       stale = false;
+      fast = T < INFINITY;
+      if (fast) {
+        float Q2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          q32[k] = fmaf(T, u32[k], p32[k]);
+          Q2 = fmaf(q32[k], q32[k], Q2);
+        }
+        const float Q = fmaxf(sqrtf(Q2) * (1.f + 2.f * gam), 0x1p-60f);
+        const float EQ = 1.01f * kU32 * (Q + 1.0001f * T + P2) + 1e-37f;
+        const float sD = sqrtf((float)D) * 1.0001f;
+        const float e1 = 1.01f * (2.f * gam * Q + 2.f * sD * EW + 2.f * EQ + 4.03f * kU32 * Q);
+        const float e0 = 1.01f * ((float)D * EW * EW + 2.f * sD * EW * (Q + EQ));
+        const float c = (1.f - 1.01f * gam) - e1 / (2.f * Q * (1.f - gam)) * 1.0001f;
+        cb = c - 2.02f * kU32 * fabsf(c) - 1e-30f;
+        beta = (0.5f * e1 * Q + e0) * 1.001f + 1e-37f;
+      }
     };
     refresh();
     // ---- list scan ----
@@ -698,17 +728,28 @@ __global__ void __launch_bounds__(kThrRays, (D <= 6 ? 6 : D <= 8 ? 4 : 3))
       if (c + 2 < n) nnid = lst[c + 2];
       load_x32<D>(tr, nid, c + 1 < n, xn);
       float w[D];
-      float den = 0.f, ww = 0.f, pw = 0.f;
+      float ww = 0.f;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         w[k] = (k < d) ? xc[k] - g32[k] : 0.f;
-        den = fmaf(u32[k], w[k], den);
         ww = fmaf(w[k], w[k], ww);
       }
       if (ww >= wwx) {  // then true_d2_lower(ww) >= far2: this and every later node lie outside
         certified = true;
         break;
       }
+      if (fast) {  // outside the ball of T: t >= T (or den <= 0), not a candidate
+        float wq = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) wq = fmaf(w[k], q32[k], wq);
+        if (fmaf(-2.f, wq, cb * ww) > beta) continue;
+      }
+      bool ok = true;  // the generators of eta are excluded by id
+      for (int q = 0; q < m; ++q) ok &= (id != eta[q]);
+      if (!ok) continue;
+      float den = 0.f, pw = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) den = fmaf(u32[k], w[k], den);
       if (hasp) {
 #pragma unroll
         for (int k = 0; k < D; ++k) pw = fmaf(p32[k], w[k], pw);
@@ -721,9 +762,6 @@ __global__ void __launch_bounds__(kThrRays, (D <= 6 ? 6 : D <= 8 ? 4 : 3))
       const float Enum = fmaf(1.1f * kU32, fabsf(num), fmaf(1.1f * gam, ww, fmaf(b2, wn, b0c)));
       const float nlo = num - Enum;
       if (!(nlo <= 0.f || nlo <= 2.f * T * dh * (1.f + 8.f * kU32))) continue;
-      bool ok = true;  // the generators of eta are excluded by id
-      for (int q = 0; q < m; ++q) ok &= (id != eta[q]);
-      if (!ok) continue;
       const float dl = den - Eden;
       const float nhi = num + Enum;
       float thi = INFINITY, tlo = -INFINITY;
@@ -756,11 +794,11 @@ __global__ void __launch_bounds__(kThrRays, (D <= 6 ? 6 : D <= 8 ? 4 : 3))
       }
     }
     n_pairs += (unsigned)c;
+    const int64_t op = out_pos(rs, ro, r);
     if (!certified) {
       if (stale) refresh();
       certified = true_d2_lower(tr.kcert[g], gam, EW, D) >= far2;
     }
-    const int64_t op = out_pos(rs, ro, r);
     if (!certified) {  // finished by the tree walk, from the bound found so far
       const unsigned long long k = atomicAdd(&ctr->fallback, 1ull);
       if ((int64_t)k < ro.fallback_cap) ro.fallback_list[k] = (int32_t)r;

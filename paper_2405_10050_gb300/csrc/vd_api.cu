@@ -338,6 +338,9 @@ vd_status vd_raycast(vd_ctx* ctx, const double* origins, const double* dirs, con
   const int64_t ovcap = R;  // every ray may overflow its binary32 candidate buffer (clustered nodes)
   VD_CK(tmp.alloc_n(&ovl, ovcap), "alloc");
   VD_CK(tmp.alloc_n(&fbl, R), "alloc");
+  int32_t* grp = nullptr;
+  const int64_t grp_ints = effective_precision(ctx) == VD_TC16 ? vd::grp_ray_ints(ctx->N, R) : 0;
+  if (grp_ints > 0) VD_CK(tmp.alloc_n(&grp, (size_t)grp_ints), "alloc");
   // eta rows must start with a node
   vd::RaySource rs;
   rs.mode = 0;
@@ -355,6 +358,9 @@ vd_status vd_raycast(vd_ctx* ctx, const double* origins, const double* dirs, con
   ro.overflow_cap = ovcap;
   ro.fallback_list = fbl;
   ro.fallback_cap = R;
+  ro.grp_buf = grp;
+  ro.grp_ints = grp_ints;
+  rs.wait_limit = ctx->cfg.wait_limit;
   VD_CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->st), "memset");
   const long long l0 = vd::g_launches.load();
   Timer tm(ctx->st);

@@ -84,6 +84,8 @@ struct RaySource {
   // with R_dev set, the ray count is min(*R_dev, R), read on the device (the
   // launch needs no host round trip), and the batch size is chosen there
   const unsigned long long* R_dev = nullptr;
+  // bound on the polls of a device-side wait (tensor-core kernels); 0 = default
+  long long wait_limit = 0;
 };
 
 struct RayOut {
@@ -96,7 +98,14 @@ struct RayOut {
   int32_t* fallback_list = nullptr;  // rays the candidate lists could not certify
   int64_t fallback_cap = 0;
   double* u = nullptr;  // MC cell kernels: each ray's binary64 direction (row cell * mc_rpc + ray, d values)
+  // scratch of the tensor-core list RayCast, which groups the rays by their
+  // reference node (grp_ray_ints(N, R) int32 values; null: no grouping)
+  int32_t* grp_buf = nullptr;
+  int64_t grp_ints = 0;
 };
+
+// int32 values of RayOut::grp_buf for N nodes and at most R rays.
+int64_t grp_ray_ints(int64_t N, int64_t R);
 
 struct Counters {
   unsigned long long tiles;
@@ -194,6 +203,19 @@ cudaError_t launch_raycast(const TreeView& tv, const RaySource& rs, const RayOut
 // The caller zeroes ctr->fallback and ctr->overflow before the call.
 cudaError_t launch_raycast_async(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision,
                                  Counters* ctr, cudaStream_t st);
+// The list scan of explicit rays (rs.mode 0) on the tensor cores: rays
+// grouped by reference node, one MMA per chunk of 128 list entries against
+// the group's [u; p] rows.  Same contract as the list scan inside
+// launch_raycast_async (uncertified rays go to ro.fallback_list, rays whose
+// candidate buffer overflows to ro.overflow_list); needs tv.K > 0, d <= 8
+// and ro.grp_buf.
+cudaError_t launch_list_tc(const TreeView& tv, const RaySource& rs, const RayOut& ro, Counters* ctr,
+                           cudaStream_t st);
+// True when launch_list_tc serves these rays.
+inline bool list_tc_ok(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision) {
+  return precision == VD_TC16 && rs.mode == 0 && tv.K > 0 && tv.d <= 8 && ro.fallback_list != nullptr &&
+         ro.grp_buf != nullptr && ro.grp_ints >= grp_ray_ints(tv.N, rs.R);
+}
 // One point set of a batched MC launch (device array, one entry per set).
 struct SetDesc {
   TreeView tv;          // nodes, tiles, candidate lists of the set

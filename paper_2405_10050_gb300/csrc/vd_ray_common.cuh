@@ -3,6 +3,7 @@
 // distance and its lower bound, and the box-clipped reach of the ball.
 #pragma once
 #include "vd_dev.cuh"
+#include "vd_internal.h"
 
 namespace vd {
 
@@ -93,5 +94,81 @@ __device__ __forceinline__ float far_radius2(const TreeView& tr, const Ball<D>& 
   return fminf(s, 4.f * b.rho_hi * b.rho_hi * (1.f + 4.f * kU32));
 }
 
+
+// ---- ray and node loads shared by the RayCast kernels ----
+
+// Origin v and direction u of ray r of the source.
+template <int D>
+__device__ __forceinline__ void load_vu(const TreeView& tr, const RaySource& rs, int64_t r, double v[D], double u[D]) {
+  const int d = tr.d;
+  if (rs.mode == 0) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      v[k] = k < d ? rs.origins[r * d + k] : 0.0;
+      u[k] = k < d ? rs.dirs[r * d + k] : 0.0;
+    }
+  } else {
+    const int32_t cell = rs.mc_cell ? rs.mc_cell[r] : (int32_t)(r / rs.mc_rpc);
+    const int32_t k = rs.mc_cell ? rs.mc_ray[r] : (int32_t)(r % rs.mc_rpc);
+    mc_direction<D>(rs.seed, rs.set, (uint32_t)cell, (uint32_t)k, d, u);
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = k < d ? tr.X[(int64_t)cell * d + k] : 0.0;
+  }
+}
+
+// Loads ray r of the source: origin v, direction u, eta (m ids, eta[0] = g).
+template <int D>
+__device__ __forceinline__ void load_ray(const TreeView& tr, const RaySource& rs, int64_t r, double v[D], double u[D],
+                                         int32_t eta[D + 1], int& m) {
+  load_vu<D>(tr, rs, r, v, u);
+  if (rs.mode == 0) {
+    m = 0;
+    for (int q = 0; q < rs.eta_stride && q < D + 1; ++q) {
+      const int32_t e = rs.eta[r * rs.eta_stride + q];
+      if (e == kNoId) break;
+      eta[m++] = e;
+    }
+  } else {
+    eta[0] = rs.mc_cell ? rs.mc_cell[r] : (int32_t)(r / rs.mc_rpc);
+    m = 1;
+  }
+}
+
+__device__ __forceinline__ int64_t out_pos(const RaySource& rs, const RayOut& ro, int64_t r) {
+  if (rs.mode == 0 || rs.mc_cell == nullptr) return r;
+  return (int64_t)rs.mc_cell[r] * ro.mc_rpc + rs.mc_ray[r];
+}
+
+// Binary32 coordinates of node id (zeros when !valid): from the rows padded
+// to 16-byte vectors where they exist (d <= 8), else one by one.
+template <int D>
+__device__ __forceinline__ void load_x32(const TreeView& tr, int32_t id, bool valid, float (&x)[D]) {
+  if constexpr (D <= 8) {
+    if (tr.X32v != nullptr) {
+      constexpr int Q = (D + 3) / 4;
+      const float4* row = tr.X32v + (int64_t)id * tr.x32q;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        const float4 f = (valid && j < tr.x32q) ? row[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float e[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (4 * j + k < D) x[4 * j + k] = e[k];
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) x[k] = (valid && k < tr.d) ? tr.X32[(int64_t)id * tr.d + k] : 0.f;
+}
+
+// Upper bound of the norm from the binary32 sum of squares ww, with the same
+// margin (1 + gam) as sqrtf(ww) (1 + gam) plus 2^-20 for the reciprocal square
+// root (documented error 2 ulp) and the product; 0 for ww = 0, inf for
+// ww = inf.
+__device__ __forceinline__ float norm_up(float ww, float gam) {
+  const float s = ww < INFINITY ? fmaxf(ww * rsqrtf(ww), 0.f) : INFINITY;
+  return s * (1.f + gam + 0x1p-20f);
+}
 
 }  // namespace vd

@@ -826,7 +826,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   // workspace slots
   enum {
     kVt, kVx, kVslot, kEt, kEcnt, kEslot, kCnts, kRo, kRd, kRt, kReta, kRhit, kCand, kCslot, kOvl, kFbl, kSnode,
-    kSsig, kSm, kAlive, kSr, kPerm, kPtmp, kKeys, kKtmp, kCounts, kOrand, kItems, kWin, kVids
+    kSsig, kSm, kAlive, kSr, kPerm, kPtmp, kKeys, kKtmp, kCounts, kOrand, kItems, kWin, kVids, kGrp
   };
   int64_t vcap = cfg.hash_capacity > 0 ? cfg.hash_capacity
                                        : (int64_t)std::min(2.0e9, std::max(1.0e5, 2.0 * N * vertices_per_cell(d) / L +
@@ -865,7 +865,8 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   double *ro = nullptr, *rd = nullptr, *rt = nullptr;
   int32_t *reta = nullptr, *rhit = nullptr, *cand = nullptr;
   int64_t *cslot = nullptr, *items = nullptr;
-  int32_t *ovl = nullptr, *fbl = nullptr, *win = nullptr, *vids = nullptr;
+  int32_t *ovl = nullptr, *fbl = nullptr, *win = nullptr, *vids = nullptr, *grp = nullptr;
+  int64_t grp_ints = 0;
   auto grow = [&](int64_t need) -> cudaError_t {
     if (need <= rcap) return cudaSuccess;
     const int64_t c = std::max<int64_t>({need, rcap * 2, 4096});
@@ -877,6 +878,10 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
         (ee = ws.get_n(kFbl, (size_t)c, &fbl)) || (ee = ws.get_n(kItems, (size_t)c, &items)) ||
         (ee = ws.get_n(kWin, (size_t)c, &win)) || (ee = ws.get_n(kVids, (size_t)c, &vids)))
       return ee;
+    if (precision == VD_TC16) {  // grouping scratch of the tensor-core list RayCast
+      grp_ints = grp_ray_ints(N, c);
+      if ((ee = ws.get_n(kGrp, (size_t)grp_ints, &grp))) return ee;
+    }
     rcap = c;
     return cudaSuccess;
   };
@@ -905,6 +910,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     rs.eta = reta;
     rs.eta_stride = stride;
     rs.box = 1;
+    rs.wait_limit = cfg.wait_limit;
     RayOut rout;
     rout.hit = rhit;
     rout.t = rt;
@@ -912,6 +918,8 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     rout.overflow_cap = rcap;
     rout.fallback_list = fbl;
     rout.fallback_cap = rcap;
+    rout.grp_buf = grp;
+    rout.grp_ints = grp_ints;
     cudaError_t ee = cudaMemsetAsync(&ctr->overflow, 0, sizeof(unsigned long long), st);
     if (ee == cudaSuccess) ee = cudaMemsetAsync(&ctr->fallback, 0, sizeof(unsigned long long), st);
     if (ee != cudaSuccess) return ee;
@@ -1080,14 +1088,17 @@ cudaError_t random_walk(const TreeView& tv, int precision, const int32_t* start,
                         double* raycast_ms) {
   const int d = tv.d, L = d + 1;
   const int64_t w1 = std::max<int64_t>(W, 1);
-  int32_t *sig = nullptr, *reta = nullptr, *rhit = nullptr, *drop = nullptr, *ovl = nullptr, *fbl = nullptr;
+  int32_t *sig = nullptr, *reta = nullptr, *rhit = nullptr, *drop = nullptr, *ovl = nullptr, *fbl = nullptr,
+          *grp = nullptr;
+  const int64_t grp_ints = precision == VD_TC16 ? grp_ray_ints(tv.N, w1) : 0;
   double *r = nullptr, *ro = nullptr, *rd = nullptr, *rt = nullptr;
   cudaError_t e;
   if ((e = scratch.alloc_n(&sig, (size_t)w1 * L)) || (e = scratch.alloc_n(&r, (size_t)w1 * d)) ||
       (e = scratch.alloc_n(&ro, (size_t)w1 * d)) || (e = scratch.alloc_n(&rd, (size_t)w1 * d)) ||
       (e = scratch.alloc_n(&reta, (size_t)w1 * d)) || (e = scratch.alloc_n(&rhit, (size_t)w1)) ||
       (e = scratch.alloc_n(&rt, (size_t)w1)) || (e = scratch.alloc_n(&drop, (size_t)w1)) ||
-      (e = scratch.alloc_n(&ovl, (size_t)w1)) || (e = scratch.alloc_n(&fbl, (size_t)w1)))
+      (e = scratch.alloc_n(&ovl, (size_t)w1)) || (e = scratch.alloc_n(&fbl, (size_t)w1)) ||
+      (grp_ints > 0 && (e = scratch.alloc_n(&grp, (size_t)grp_ints))))
     return e;
   if (W == 0 || S == 0) return cudaSuccess;
   if ((e = cudaMemcpyAsync(sig, start, (size_t)W * L * sizeof(int32_t), cudaMemcpyDeviceToDevice, st))) return e;
@@ -1114,6 +1125,8 @@ cudaError_t random_walk(const TreeView& tv, int precision, const int32_t* start,
     rout.overflow_cap = W;
     rout.fallback_list = fbl;
     rout.fallback_cap = W;
+    rout.grp_buf = grp;
+    rout.grp_ints = grp_ints;
     if ((e = cudaMemsetAsync(&ctr->overflow, 0, sizeof(unsigned long long), st)) ||
         (e = cudaMemsetAsync(&ctr->fallback, 0, sizeof(unsigned long long), st)))
       break;

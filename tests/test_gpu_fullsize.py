@@ -68,13 +68,14 @@ def test_traversal_d5_n20000(orc):
     assert N < 2 ** 15
     X = synth.uniform(N, d, seed=0)
     out = {}
-    for prec in (VD_FP32, VD_FP64):
+    for prec in (VD_FP32, VD_FP64, VD_TC16):
         vor = Voronoi(X, precision=prec)
         t, c, st = vor.vertices()
         out[prec] = (t.cpu().numpy(), c.cpu().numpy(), st)
         vor.close()
     T, C, st = out[VD_FP32]
-    assert np.array_equal(T, out[VD_FP64][0]) and np.array_equal(C, out[VD_FP64][1])
+    for other in (VD_FP64, VD_TC16):
+        assert np.array_equal(T, out[other][0]) and np.array_equal(C, out[other][1])
     assert st["vertices"] == len(T) > 2_000_000
     assert np.all(np.diff(T, axis=1) > 0)  # each tuple sorted, no repeats
     assert int(np.sum(np.sum(T < 0, axis=1) == d)) == 2 ** d  # the cube corners

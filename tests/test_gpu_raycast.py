@@ -1,15 +1,17 @@
 """GPU parity of the RayCast (Section 2.2, Eq. (t), Algorithm 1) against the
 FP64 oracle: hit ids bit-exact and t bit-identical (both evaluate Eq. (t) in
-binary64 in the same canonical order), for the plain FP64 path and the
-binary32-screened path, at sizes spanning many tiles with a ragged tail."""
+binary64 in the same canonical order), for the plain FP64 path, the
+binary32-screened path and the tensor-core screened path (rays grouped by
+reference node, fp16 MMA over the candidate list), at sizes spanning many
+tiles with a ragged tail."""
 import numpy as np
 import pytest
 
 from gpu_util import edge_rays, need_cuda, random_unit
-from paper_2405_10050_gb300 import NO_ID, VD_FP32, VD_FP64, Voronoi, synth
+from paper_2405_10050_gb300 import NO_ID, VD_FP32, VD_FP64, VD_TC16, Voronoi, synth
 
 pytestmark = pytest.mark.gpu
-PRECS = [VD_FP64, VD_FP32]
+PRECS = [VD_FP64, VD_FP32, VD_TC16]
 
 
 def _run(X, O, U, E, prec, box=True, knn_k=0):
@@ -34,7 +36,7 @@ def test_rays_from_nodes(orc, prec, d, N):
     h1, t1, se, st = _run(X, X[cells], U, cells[:, None], prec)
     assert np.array_equal(h0, h1)
     assert np.array_equal(t0, t1)
-    if prec == VD_FP32:
+    if prec in (VD_FP32, VD_TC16):
         # (T - t) / t: the binary32 upper bound never undercuts the exact t;
         # its width is set by the absolute binary32 error of the coordinates
         assert np.all(se >= 0) and np.median(se) < 1e-2

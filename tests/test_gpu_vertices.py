@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from gpu_util import need_cuda
-from paper_2405_10050_gb300 import VD_FP32, VD_FP64, Voronoi, synth
+from paper_2405_10050_gb300 import VD_FP32, VD_FP64, VD_TC16, Voronoi, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -21,7 +21,7 @@ def _gpu_vertices(X, prec):
     return t.cpu().numpy(), c.cpu().numpy(), st
 
 
-@pytest.mark.parametrize("prec", [VD_FP64, VD_FP32])
+@pytest.mark.parametrize("prec", [VD_FP64, VD_FP32, VD_TC16])
 @pytest.mark.parametrize("d,N", [(2, 500), (3, 2000), (4, 300), (5, 120), (6, 40)])
 def test_vertices_parity(orc, prec, d, N):
     X = synth.uniform(N, d, seed=0)
@@ -33,7 +33,7 @@ def test_vertices_parity(orc, prec, d, N):
     assert st["vertices"] == len(t0) and st["levels"] >= 1
 
 
-@pytest.mark.parametrize("prec", [VD_FP64, VD_FP32])
+@pytest.mark.parametrize("prec", [VD_FP64, VD_FP32, VD_TC16])
 def test_vertices_mixture_and_tiny(orc, prec):
     for X in [synth.gaussian_mixture(400, 3, 8, 0.05, seed=2), synth.uniform(1, 2, seed=1),
               synth.uniform(2, 3, seed=2), synth.uniform(33, 2, seed=3)]:

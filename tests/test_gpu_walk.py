@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from gpu_util import need_cuda
-from paper_2405_10050_gb300 import VD_FP32, VD_FP64, Voronoi, synth, vd
+from paper_2405_10050_gb300 import VD_FP32, VD_FP64, VD_TC16, Voronoi, synth, vd
 
 pytestmark = pytest.mark.gpu
 
@@ -17,7 +17,7 @@ def test_walk_parity(orc, d, N):
     need_cuda()
     X = synth.uniform(N, d, seed=120 + d)
     out = []
-    for prec in (VD_FP32, VD_FP64):
+    for prec in (VD_FP32, VD_FP64, VD_TC16):
         vor = Voronoi(X, precision=prec)
         T, C, _ = vor.vertices()
         T = T.cpu().numpy()

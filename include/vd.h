@@ -63,7 +63,9 @@ typedef struct {
                              and MC); 0: unbounded rays may miss           */
   int64_t hash_capacity;  /* traversal vertex table entries, 0 = automatic */
   int64_t max_levels;     /* traversal BFS level cap, 0 = automatic        */
-  int64_t wait_limit;     /* spin iterations before a device wait gives up */
+  int64_t wait_limit;     /* polls before a bounded device wait gives up
+                             (VD_ETIMEOUT); 0 = default, < 0 = give up
+                             before the first poll (tests that path)       */
   int32_t knn_k;          /* candidate list length per node: 0 = automatic
                              by dimension, -1 = no lists (tree walk only)  */
   int32_t rays_per_block; /* MC rays per thread block, 0 = autotune        */
@@ -135,10 +137,11 @@ vd_status vd_raycast(vd_ctx* ctx, const double* origins, const double* dirs, con
  * VD_EINVAL).  Its work lists and counters live in one fixed 2 MiB device
  * array inside libvd (resident on every GPU that loads the library until the
  * process exits), shared by all calls and contexts: calls that overlap on the
- * GPU race on it.  The first call on a device looks up that array's device
- * address (once per device, with the device current), so make it before any
- * stream capture.  The context must already hold a node set (vd_set_nodes,
- * which does allocate); this call itself allocates nothing. */
+ * GPU race on it.  Each call looks up that array's address on the current
+ * device, which must be the context's device (VD_EINVAL otherwise), and waits
+ * for the context's stream before it returns.  The context must already hold
+ * a node set (vd_set_nodes, which does allocate); this call itself allocates
+ * nothing. */
 vd_status vd_raycast_noalloc(vd_ctx* ctx, const double* origins, const double* dirs, const int32_t* eta,
                              int32_t eta_stride, int64_t R, int32_t* hit, double* t);
 

@@ -7,7 +7,6 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
-#include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
@@ -52,6 +51,7 @@ using vd::TreeView;
 
 struct vd_ctx {
   vd_config cfg;
+  int dev = -1;  // the CUDA device current at vd_create
   cudaStream_t st = nullptr;
   char err[512] = {0};
   vd_stats last{};
@@ -229,7 +229,8 @@ vd_status vd_create(vd_ctx** out, const vd_config* cfg, void* stream) {
     return VD_EINVAL;
   }
   ctx->st = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = ctx->own.alloc_n(&ctx->ctr, 1);
+  cudaError_t e = cudaGetDevice(&ctx->dev);
+  if (e == cudaSuccess) e = ctx->own.alloc_n(&ctx->ctr, 1);
   if (e != cudaSuccess) {
     delete ctx;
     return e == cudaErrorMemoryAllocation ? VD_ENOMEM : VD_ECUDA;
@@ -465,6 +466,14 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
     else
       VD_CK(vd::launch_raycast(tv, rs, ro, prec, ctx->ctr, ctx->st, &mc->stats.fallback_rays), "mc raycast");
     mc->stats.raycast_ms = tr.stop();
+  }
+  {
+    // a tensor-core kernel that gave up a bounded wait left rays without a
+    // hit: stop before the kernels that read the hits
+    Counters hc0;
+    vd_status s0 = read_counters(ctx, &hc0);
+    if (s0 != VD_OK) return s0;
+    if (hc0.flags & vd::kFlagTimeout) return check_flags(ctx, hc0);
   }
   int64_t nnz = 0;
   VD_CK(vd::mc_rowptr(mc->hit, N, R, cnt, mc->rowptr, &nnz, ctx->st), "mc rowptr");
@@ -1166,27 +1175,22 @@ struct NoAllocScratch {
 // 2 MiB (+ counters), resident on every device that loads the library.
 __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-NoAllocScratch* g_noalloc_addr[kNoAllocMaxDevices] = {};
-
-// Device address of the scratch array on the current device.  Host code only
-// sees a host-side stand-in under the array's name, so the address is looked
-// up once per device (with that device current) and cached.
+// Device address of the scratch array for this call.  Host code only sees a
+// host-side stand-in under the array's name, so the address is looked up on
+// every call, with the context's device current: a cached address would go
+// stale once the device's context is torn down and created again (for
+// example after cudaDeviceReset), and a kernel given it would fault.
 vd_status noalloc_scratch(vd_ctx* ctx, NoAllocScratch** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_err(ctx, e, "vd_raycast_noalloc: cudaGetDevice");
-  if (dev < 0 || dev >= kNoAllocMaxDevices)
-    return set_err(ctx, VD_EINVAL, "vd_raycast_noalloc: device index %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) return cuda_err(ctx, e, "vd_raycast_noalloc: cudaGetSymbolAddress");
-    g_noalloc_addr[dev] = static_cast<NoAllocScratch*>(p);
-  }
-  *out = g_noalloc_addr[dev];
+  if (dev != ctx->dev)
+    return set_err(ctx, VD_EINVAL, "vd_raycast_noalloc: the current device %d is not the context's device %d", dev,
+                   ctx->dev);
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) return cuda_err(ctx, e, "vd_raycast_noalloc: cudaGetSymbolAddress");
+  *out = static_cast<NoAllocScratch*>(p);
   return VD_OK;
 }
 

@@ -120,6 +120,11 @@ struct Counters {
   unsigned int pad;
 };
 
+// Polls of a bounded device-side wait for the configured wait_limit: 0 is
+// the default (2^22 polls), a negative value gives up before the first poll
+// (which tests the time-out path on purpose).
+inline long long wait_polls(long long cfg) { return cfg == 0 ? (1ll << 22) : (cfg < 0 ? 0 : cfg); }
+
 // Process-wide count of kernel launches issued by libvd (diagnostics).
 extern std::atomic<long long> g_launches;
 inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }

@@ -278,7 +278,7 @@ cudaError_t launch_tc_d(const TreeView& tv, int64_t R, uint64_t seed, uint32_t s
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * occ, tv.N));
   cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
   k_mc_cell_tc<D><<<(unsigned)grid, kTcThreads, sm, st>>>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap,
-                                                           wait_limit > 0 ? wait_limit : (1ll << 22));
+                                                           wait_polls(wait_limit));
   count_launch();
   return cudaGetLastError();
 }

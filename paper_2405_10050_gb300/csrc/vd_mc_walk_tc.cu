@@ -466,7 +466,7 @@ cudaError_t launch_mc_walk_tc(const TreeView& tv, int64_t R, uint64_t seed, uint
   int32_t* fb_ray = ro.fallback_list + ro.fallback_cap / 2;
   const int64_t fb_cap = ro.fallback_cap / 2;
   const int cpt = (R < kWt && R % 32 == 0) ? (int)(kWt / R) : 1;
-  const long long wl = wait_limit > 0 ? wait_limit : (1ll << 22);
+  const long long wl = wait_polls(wait_limit);
   cudaMemsetAsync(&ctr->fallback, 0, sizeof(unsigned long long), st);
   cudaError_t e;
 #define VD_WALK(DD) launch_walk_d<DD>(tv, R, cpt, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, wl, st)

@@ -427,7 +427,8 @@ __global__ void __launch_bounds__(kGrpM, 6) k_ray_list_tc(TreeView tr, RaySource
   bool timed_out = false;
   unsigned long long n_pairs = 0, n_rech = 0;
 
-  for (int it = 0; !timed_out; ++it) {
+  int it = 0;
+  for (; !timed_out; ++it) {
     const int4 item = s_item[it & 1];
     if (item.x < 0) break;
     if (tid == 0) {  // the next item is fetched while this one runs
@@ -608,6 +609,32 @@ __global__ void __launch_bounds__(kGrpM, 6) k_ray_list_tc(TreeView tr, RaySource
     // this wait has its own generous bound, whatever limit gave up above
     tc::mbar_wait(&mbar, phase ^ 1u, wait_limit > (1ll << 24) ? wait_limit : (1ll << 24));
     if (tid == 0) atomicOr(&ctr->flags, kFlagTimeout);
+    // every ray of this block's unfinished items, and of the items still
+    // queued, gets "no hit", so that no later kernel reads a stale hit id
+    __syncthreads();
+    for (int k = 0;; ++k) {
+      int4 itm;
+      if (k < 2) {
+        itm = s_item[(it + k) & 1];
+      } else {
+        __syncthreads();
+        if (tid == 0) {
+          const unsigned long long w = atomicAdd(work, 1ull);
+          s_item[0] = (int64_t)w < nitems ? L.items[w] : make_int4(-1, 0, 0, 0);
+        }
+        __syncthreads();
+        itm = s_item[0];
+      }
+      if (itm.x < 0) {
+        if (k == 0) continue;  // nothing was current: look at the prefetched item
+        if (k >= 1) break;
+      }
+      for (int q = tid; q < itm.z; q += kGrpM) {
+        const int64_t op = out_pos(rs, ro, (int64_t)L.perm[itm.y + q]);
+        ro.hit[op] = kNoId;
+        ro.t[op] = NAN;
+      }
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -654,7 +681,7 @@ cudaError_t launch_list_tc_d(const TreeView& tv, const RaySource& rs, const RayO
   const int by_regs = regs_sm / std::max(1, regs_blk);
   const int by_smem = (int)(smem_sm / (fa.sharedSizeBytes + 1024));
   const int occ = std::max(1, std::min(std::min(by_regs, by_smem), 512 / kGrpCols));
-  const long long wl = rs.wait_limit > 0 ? rs.wait_limit : (1ll << 22);
+  const long long wl = wait_polls(rs.wait_limit);
   k_ray_list_tc<D><<<(unsigned)((int64_t)nsm * occ), kGrpM, 0, st>>>(tv, rs, ro, ctr, L, work, wl);
   count_launch();
   return cudaGetLastError();

@@ -404,15 +404,18 @@ __global__ void k_expand_dir(Tables T, const double* X, int64_t f0, const int64_
 
 // Phase 1 of the commit: claim the tuple's slot for ray r (or find it);
 // true if this ray owns a new vertex.
+// A seed that reached no vertex (Descent gave up on it) arrives with hit =
+// kNoId and is skipped when no_hit_ok is set; on a traversal level a ray
+// without a hit is a degenerate input.
 __device__ bool claim_slot(const Tables& T, const int32_t* reta, const int32_t* hit, int64_t r, int32_t* cand,
-                           int64_t* cslot, unsigned* flags) {
+                           int64_t* cslot, unsigned* flags, bool no_hit_ok) {
   const int d = T.d, L = d + 1;
   int32_t sig[VD_MAX_D + 1];
   for (int a = 0; a < d; ++a) sig[a] = reta[r * d + a];
   sig[d] = hit[r];
   cslot[r] = -1;
   if (sig[d] == kNoId) {
-    atomicOr(flags, kFlagDegenerate);
+    if (!no_hit_ok) atomicOr(flags, kFlagDegenerate);
     return false;
   }
   sort_small(sig, L);
@@ -441,9 +444,10 @@ __device__ bool claim_slot(const Tables& T, const int32_t* reta, const int32_t* 
 // Rays that own a new vertex are appended to win[] (count *nwin).
 __global__ void k_commit_claim(Tables T, const int32_t* reta, const int32_t* hit, int64_t nr,
                                const unsigned long long* nr_dev, int32_t* cand, int64_t* cslot, int32_t* win,
-                               unsigned long long* nwin, unsigned* flags) {
+                               unsigned long long* nwin, unsigned* flags, int seeds) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const bool owns = r < (nr_dev ? min(nr, (int64_t)*nr_dev) : nr) && claim_slot(T, reta, hit, r, cand, cslot, flags);
+  const bool owns =
+      r < (nr_dev ? min(nr, (int64_t)*nr_dev) : nr) && claim_slot(T, reta, hit, r, cand, cslot, flags, seeds != 0);
   const long long p = warp_append(owns, nwin);
   if (p >= 0) win[p] = (int32_t)r;
 }
@@ -977,18 +981,9 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   unsigned long long* nrays = cnts + 2;
   unsigned long long* nwin = cnts + 4;
   VD_TRY(cudaMemsetAsync(nwin, 0, sizeof(unsigned long long), st));
-  k_commit_claim<<<nb(ns), 256, 0, st>>>(T, reta, rhit, ns, nullptr, cand, cslot, win, nwin, flags); count_launch();
-  // seeds that did not reach a vertex were marked with hit = kNoId: clear the
-  // degenerate flag they raised (a missing seed is not an error)
-  {
-    unsigned hf = 0;
-    VD_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    VD_TRY(cudaStreamSynchronize(st));
-    if (hf & kFlagDegenerate) {
-      unsigned clr = hf & ~kFlagDegenerate;
-      VD_TRY(cudaMemcpyAsync(flags, &clr, sizeof(unsigned), cudaMemcpyHostToDevice, st));
-    }
-  }
+  // seeds that did not reach a vertex carry hit = kNoId and are skipped (a
+  // missing seed is not an error); every other flag stays as raised
+  k_commit_claim<<<nb(ns), 256, 0, st>>>(T, reta, rhit, ns, nullptr, cand, cslot, win, nwin, flags, 1); count_launch();
   VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, ns, nwin, vids, flags, st);
   unsigned long long hn2[4];
   VD_TRY(cudaMemcpyAsync(hn2, cnts, sizeof(hn2), cudaMemcpyDeviceToHost, st));
@@ -1015,7 +1010,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     VD_TRY(cudaGetLastError());
     const int64_t rmax = std::min(ncap, rcap);
     VD_TRY(cast(rmax, nrays, d));
-    k_commit_claim<<<nb(rmax), 256, 0, st>>>(T, reta, rhit, rmax, nrays, cand, cslot, win, nwin, flags);
+    k_commit_claim<<<nb(rmax), 256, 0, st>>>(T, reta, rhit, rmax, nrays, cand, cslot, win, nwin, flags, 0);
     count_launch();
     VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, rmax, nwin, vids, flags, st);
     VD_TRY(cudaGetLastError());

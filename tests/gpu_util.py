@@ -33,3 +33,21 @@ def edge_rays(orc, X, tuples, coords, nmax, rng):
             if len(O) >= nmax:
                 return np.array(O), np.array(U), np.array(E, np.int32)
     return np.array(O), np.array(U), np.array(E, np.int32)
+
+
+def clustered_fan(R=256, n_cluster=40, seed=0):
+    """Node g at (0.2, 0.5), a cluster of n_cluster nodes within 1e-9 of
+    (0.62, 0.5) (one binary32 point, distinct binary64 points) and background
+    nodes none of whose bisectors with g the fan of R rays from g (within
+    3e-3 rad of +x) crosses before the cluster's: every ray keeps the whole
+    cluster as binary32 candidates."""
+    rng = np.random.default_rng(seed)
+    g = np.array([0.2, 0.5])
+    cl = np.array([0.62, 0.5]) + 1e-9 * rng.standard_normal((n_cluster, 2))
+    bg = rng.uniform(0.0, 1.0, (600, 2))
+    w = bg - g
+    keep = (w[:, 0] <= 0) | (np.sum(w * w, axis=1) / (2 * np.maximum(w[:, 0] - 0.01 * np.abs(w[:, 1]), 1e-12)) > 0.3)
+    X = np.vstack([g[None, :], cl, bg[keep]])
+    th = rng.uniform(-3e-3, 3e-3, R)
+    U = np.stack([np.cos(th), np.sin(th)], axis=1)
+    return X, np.repeat(X[:1], R, axis=0), U, np.zeros((R, 1), np.int32)

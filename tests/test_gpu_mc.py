@@ -116,24 +116,23 @@ def test_autograd_function(orc):
 
 @pytest.mark.parametrize("d,N,R", [(3, 400, 64), (10, 300, 64)])
 def test_tensor_wait_limit(orc, d, N, R):
-    """Bounded waits of the tensor-core kernels with a limit of one poll: each
-    poll (mbarrier try_wait) may suspend the thread until the MMA completes
-    or a hardware time limit passes, so the call either completes or gives
-    up; giving up, the kernel waits (with its own bound) for the MMA still in
-    flight, frees its tensor memory and reports VD_ETIMEOUT.  Either way the
-    device stays usable and a normal call afterwards is exact."""
+    """The time-out path of the tensor-core kernels' bounded waits, taken on
+    purpose: a negative wait limit makes every wait give up before its first
+    poll, so the kernel abandons its work, waits (with its own bound) for the
+    MMA still in flight, frees its tensor memory and the call reports
+    VD_ETIMEOUT.  The device stays usable: a normal call afterwards is
+    exact."""
     torch = need_cuda()
     X = synth.uniform(N, d, seed=d)
     cfg = vd.vd_config_default()
     cfg.precision = VD_TC16
-    cfg.wait_limit = 1
+    cfg.wait_limit = -1
     ctx = vd.vd_create(cfg, torch.cuda.current_stream().cuda_stream)
     try:
         vd.vd_set_nodes(ctx, torch.tensor(X, device="cuda"))
-        try:
+        with pytest.raises(vd.VDError) as e:
             vd.vd_mc_free(vd.vd_mc_integrate(ctx, R, 5))
-        except vd.VDError as e:
-            assert e.status == -7  # VD_ETIMEOUT
+        assert e.value.status == -7  # VD_ETIMEOUT
     finally:
         vd.vd_destroy(ctx)
     torch.cuda.synchronize()

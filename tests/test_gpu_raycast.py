@@ -7,7 +7,7 @@ tiles with a ragged tail."""
 import numpy as np
 import pytest
 
-from gpu_util import edge_rays, need_cuda, random_unit
+from gpu_util import clustered_fan, edge_rays, need_cuda, random_unit
 from paper_2405_10050_gb300 import NO_ID, VD_FP32, VD_FP64, VD_TC16, Voronoi, synth
 
 pytestmark = pytest.mark.gpu
@@ -148,3 +148,49 @@ def test_invalid_arguments_are_rejected():
                           np.empty(1, np.int32), np.empty(1))
     finally:
         vd.vd_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_candidate_overflow_all_rays(orc, prec):
+    """Every ray of the fan has more binary32 candidates than its buffer holds
+    (far more than R/16 rays): all are redone on the binary64 path and the
+    hits equal the oracle's."""
+    X, O, U, E = clustered_fan()
+    h0, t0 = orc.raycast(X, O, U, E[:, 0])
+    assert np.all((h0 >= 1) & (h0 <= 40))  # the cluster is hit
+    h1, t1, _, st = _run(X, O, U, E, prec)
+    assert np.array_equal(h0, h1) and np.array_equal(t0, t1)
+    if prec != VD_FP64:
+        assert st["overflow_rays"] > len(O) // 16
+
+
+def test_tensor_list_wait_limit(orc):
+    """The tensor-core list RayCast's time-out path, taken on purpose (a
+    negative wait limit gives up before the first poll): the call reports
+    VD_ETIMEOUT and every ray it could not finish reads "no hit"; a normal
+    call afterwards is exact."""
+    torch = need_cuda()
+    from paper_2405_10050_gb300 import vd
+    X = synth.uniform(2000, 4, seed=41)
+    rng = np.random.default_rng(41)
+    cells = rng.integers(0, 2000, 3000).astype(np.int32)
+    U = random_unit(rng, 3000, 4)
+    cfg = vd.vd_config_default()
+    cfg.precision = VD_TC16
+    cfg.wait_limit = -1
+    ctx = vd.vd_create(cfg, torch.cuda.current_stream().cuda_stream)
+    try:
+        vd.vd_set_nodes(ctx, torch.tensor(X, device="cuda"))
+        hit = torch.zeros(3000, dtype=torch.int32, device="cuda")
+        t = torch.zeros(3000, dtype=torch.float64, device="cuda")
+        with pytest.raises(vd.VDError) as e:
+            vd.vd_raycast(ctx, torch.tensor(X[cells], device="cuda"), torch.tensor(U, device="cuda"),
+                          torch.tensor(cells[:, None], device="cuda"), hit, t)
+        assert e.value.status == -7  # VD_ETIMEOUT
+        assert bool(torch.all(hit == NO_ID))
+    finally:
+        vd.vd_destroy(ctx)
+    torch.cuda.synchronize()
+    h0, t0 = orc.raycast(X, X[cells], U, cells)
+    h1, t1, _, _ = _run(X, X[cells], U, cells[:, None], VD_TC16)
+    assert np.array_equal(h0, h1) and np.array_equal(t0, t1)

@@ -42,7 +42,12 @@ sys.path.insert(0, ROOT)
 METRIC = "raycasts/s and MC vol+grad cells/s: mixed vs FP64 path, same GB300, exact hits"
 WORKLOAD = "exhaustive vertex traversal, d=5, N=20000 iid uniform in [0,1]^5 (seed 0), clipped to the cube"
 NEIGHBOURS_D5 = 95  # neighbours per cell in d = 5 (the paper's table of vertices and neighbours per cell)
-RAYCAST_DRAM_BYTES_PER_STEP = 645.2e6  # ncu dram__bytes_read + write of k_ray_list_thr<5>, one traversal
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, ncu, summed over every launch of k_ray_list_thr<5>
+# in one traversal) of the binary32 list RayCast with the ball-test screen: 1935.3 MB over the three traversals
+# of `python bench.py --steps 1 --warmup 1 --no-fp64 --no-cpu --no-mc --no-highd --no-hmc --no-walk --no-small
+# --no-batch`, captured with `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+# --clock-control none -k regex:k_ray_list_thr`
+RAYCAST_DRAM_BYTES_PER_STEP = 645.1e6
 
 
 def _peaks():
@@ -170,7 +175,8 @@ def edge_rays_from_mesh(orc, X, tuples, coords, n, seed=0):
 
 def cpu_oracle_rate(X, tuples, coords, target_s=15.0):
     """Oracle raycasts/s on the host cores over a bounded sample of the
-    traversal's edge rays (about target_s seconds of CPU work)."""
+    traversal's edge rays (about target_s seconds of CPU work), with every
+    core and with one core (a sample a sixteenth the size)."""
     import oracle
     oracle.build()
     O, U, E = edge_rays_from_mesh(oracle, X, tuples, coords, 256, seed=1)
@@ -179,10 +185,19 @@ def cpu_oracle_rate(X, tuples, coords, target_s=15.0):
     dt = max(time.perf_counter() - t0, 1e-6)
     n = int(min(200000, max(512, 256 * target_s / dt)))
     O, U, E = edge_rays_from_mesh(oracle, X, tuples, coords, n, seed=2)
+    cores = oracle.max_threads()
     t0 = time.perf_counter()
     oracle.raycast(X, O, U, E)
     dt = time.perf_counter() - t0
-    return n / dt, n, dt, oracle.max_threads()
+    n1 = max(64, n // 16)
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.raycast(X, O[:n1], U[:n1], E[:n1])
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(cores)
+    return n / dt, n, dt, cores, n1 / dt1, n1, dt1
 
 
 def run_reference(args):
@@ -388,8 +403,8 @@ def run_ours(args):
     pairs = NEIGHBOURS_D5 + 2 * args.d
     flops_per_ray = pairs * (2 * args.d + 6)
     achieved = rays * flops_per_ray / (rc_ms / 1000.0) / 1e12 if rc_ms > 0 else None
-    # DRAM bytes of the list RayCast per traversal of this workload, from one ncu capture of the current
-    # kernel (profiles/traversal_d5_n20000_launches.md); the ray I/O alone is ~573 MB
+    # DRAM bytes of the list RayCast per traversal of this workload (one ncu capture of the current kernel,
+    # above); the ray I/O alone is ~573 MB
     traffic = RAYCAST_DRAM_BYTES_PER_STEP if (args.N, args.d, args.knn_k) == (20000, 5, 0) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": (achieved / peak_tflops) if achieved else None, "traffic": traffic,
@@ -410,13 +425,17 @@ def run_ours(args):
     walk = None
     if not args.no_walk:
         walk = run_walk(args, vd, stream)
+    small = None if args.no_small else run_small(args, vd, stream)
+    batch = None if args.no_batch else run_batch(args, vd, stream)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        rate, n, dt, cores = cpu_oracle_rate(X, tup.cpu().numpy(), crd.cpu().numpy(), target_s=args.cpu_seconds)
+        rate, n, dt, cores, rate1, n1, dt1 = cpu_oracle_rate(X, tup.cpu().numpy(), crd.cpu().numpy(),
+                                                             target_s=args.cpu_seconds)
         cpu = {"value": rate, "unit": "raycasts/s", "cores": cores, "kind": "oracle",
                "sample": f"{n} random edge rays of the workload's diagram, FP64 brute force over all "
-                         f"{args.N} nodes ({dt:.1f} s)"}
+                         f"{args.N} nodes ({dt:.1f} s)",
+               "one_core": {"value": rate1, "cores": 1, "sample": f"the first {n1} of those rays ({dt1:.1f} s)"}}
     vd.vd_destroy(ctx)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "raycasts/s", "n_gpus": ws, "steps": args.steps,
@@ -439,7 +458,7 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": "raycasts/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "mc": mc, "highd": highd, "hmc": hmc, "walk": walk}
+                "mc": mc, "highd": highd, "hmc": hmc, "walk": walk, "plain_fp64_d3": small, "batch": batch}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -703,6 +722,71 @@ BATCH_WORKLOAD = ("batched MC volumes + areas + adjoint: 512 sets, N log-uniform
                   "{2..8}, half uniform, half 8-component Gaussian mixtures (sigma 0.05), 256 rays per cell")
 
 
+SMALL_WORKLOAD = ("plain method in binary64: exhaustive vertex traversal + MC volumes, areas and adjoint with 64 "
+                  "rays per cell, d=3, N=2000 iid uniform in [0,1]^3 (seed 0), clipped to the cube")
+
+
+def run_small(args, vd, stream, reps=5):
+    """The plain binary64 method on the small workload: node preparation,
+    the traversal, MC volumes + areas + adjoint (R = 64) per step, beside the
+    same step on the default (screened) path; hits and tuples identical."""
+    import torch
+    from paper_2405_10050_gb300 import VD_AUTO, VD_FP64, synth
+    X = synth.uniform(2000, 3, seed=0)
+    Xd = torch.tensor(X, device="cuda")
+    R = 64
+    out = {"workload": SMALL_WORKLOAD, "unit": "raycasts/s"}
+    ref = None
+    for name, prec in (("fp64", VD_FP64), ("auto", VD_AUTO)):
+        cfg = vd.vd_config_default()
+        cfg.precision = prec
+        ctx = vd.vd_create(cfg, stream.cuda_stream)
+
+        def step():
+            vd.vd_set_nodes(ctx, Xd)
+            m = vd.vd_vertices(ctx)
+            mst = vd.vd_mesh_stats(m)
+            mc = vd.vd_mc_integrate(ctx, R, 1)
+            N = X.shape[0]
+            nnz = vd.vd_mc_get(mc)
+            gX = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+            vd.vd_mc_adjoint(mc, torch.ones(N, dtype=torch.float64, device="cuda"),
+                             torch.ones(max(nnz, 1), dtype=torch.float64, device="cuda")[:nnz], gX)
+            return m, mc, mst
+
+        m, mc, _ = step()
+        vd.vd_mesh_free(m)
+        vd.vd_mc_free(mc)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(reps):
+            m, mc, mst = step()
+            if k < reps - 1:
+                vd.vd_mesh_free(m)
+                vd.vd_mc_free(mc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        nv = vd.vd_mesh_count(m)
+        tup = torch.empty((nv, 4), dtype=torch.int32, device="cuda")
+        vd.vd_mesh_copy(m, tup, None)
+        hit = torch.empty((2000, R), dtype=torch.int32, device="cuda")
+        vd.vd_mc_rays(mc, hit, None)
+        vd.vd_mesh_free(m)
+        vd.vd_mc_free(mc)
+        vd.vd_destroy(ctx)
+        rays = mst["rays"] + 2000 * R
+        out[name] = {"value": rays / (ms / 1000.0), "ms_per_step": ms, "vertices": nv, "traversal_rays": mst["rays"],
+                     "mc_rays": 2000 * R, "mc_cells_per_s": 2000 / (ms / 1000.0)}
+        if ref is None:
+            ref = (tup, hit)
+        else:
+            out[name]["identical_to_fp64"] = bool(torch.equal(tup, ref[0]) and torch.equal(hit, ref[1]))
+    out["value"] = out["fp64"]["value"]
+    return out
+
+
 def run_batch(args, vd, stream):
     """MC vol+grad cells/s on the batched workload (one persistent,
     graph-captured forward launch over all sets, then the adjoint of each)."""
@@ -757,6 +841,8 @@ def main():
     ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--only-mc", action="store_true")
     ap.add_argument("--only-batch", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-highd", action="store_true")
     ap.add_argument("--only-highd", action="store_true")
     ap.add_argument("--no-hmc", action="store_true")

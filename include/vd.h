@@ -51,10 +51,16 @@ typedef enum {
   VD_FP64 = 0,  /* every (ray, node) pair in binary64                      */
   VD_FP32 = 1,  /* binary32 screening with a proven error margin, binary64
                    recheck of the survivors                                */
-  VD_TC16 = 2,  /* MC rays: u.w on the tensor cores (tcgen05, fp16 in,
+  VD_TC16 = 2,  /* dot products on the tensor cores (tcgen05, fp16 in,
                    fp32 accumulate) with a proven error margin, binary64
-                   recheck; other calls treat it as VD_FP32              */
-  VD_AUTO = 3   /* the library's autotuner picks among the above           */
+                   recheck: MC rays (cell lists, or the block tree walk
+                   without lists) and explicit rays with candidate lists
+                   (vd_raycast, vd_vertices, vd_random_walk; rays grouped
+                   by reference node); other calls treat it as VD_FP32   */
+  VD_AUTO = 3   /* per call, the path measured fastest on GB300: VD_TC16
+                   for MC rays of node sets without candidate lists
+                   (d > 8), VD_FP32 otherwise; results are identical on
+                   every path                                           */
 } vd_precision;
 
 typedef struct {

@@ -40,6 +40,7 @@ def lib():
         P = ctypes.c_void_p
         i64, i32, u32, u64 = ctypes.c_int64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
         L.or_max_threads.restype = ctypes.c_int
+        L.or_set_threads.argtypes = [i32]
         L.or_sphere_area.restype = ctypes.c_double
         L.or_sphere_area.argtypes = [i32]
         L.or_log32.restype = ctypes.c_float
@@ -88,6 +89,11 @@ def _f64(a):
 
 def max_threads() -> int:
     return int(lib().or_max_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on."""
+    lib().or_set_threads(int(n))
 
 
 def sphere_area(d: int) -> float:

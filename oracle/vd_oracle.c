@@ -46,6 +46,15 @@ int or_max_threads(void) {
 #endif
 }
 
+/* Threads of the OpenMP loops from now on (timing at one core). */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Counter-based random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw,  */
 /* "Parallel random numbers: as easy as 1, 2, 3", SC'11).  Ten rounds; each  */

@@ -66,6 +66,9 @@ struct vd_ctx {
   vd::Workspace trav_ws;  // traversal tables and level buffers, reused across vd_vertices calls
   vd::Workspace mc_ws;    // MC work lists, reused across vd_mc_integrate calls
   vd::Workspace batch_ws; // batched MC: trees, candidate lists, work lists of all sets (one block)
+  // batched MC forward pass: the instantiated graph, updated in place by the
+  // next call's capture (instantiated again only when its shape changes)
+  cudaGraphExec_t batch_exec = nullptr;
 };
 
 struct vd_mesh {
@@ -182,11 +185,17 @@ vd_status check_flags(vd_ctx* ctx, const Counters& hc) {
   return VD_OK;
 }
 
-int effective_precision(const vd_ctx* ctx) {
+// The path of a call.  VD_AUTO takes the fastest path measured on GB300 for
+// the call's kind and node set: Monte Carlo rays of a node set without
+// candidate lists (d > 8) take the tensor-core block walk (d = 16,
+// N = 200,000: ten times the binary32 tree walk); every other call takes the
+// binary32 screening, whose list kernels beat their tensor-core variants at
+// d <= 8 (the traversal at d = 5 and the MC cells at d = 4).
+int effective_precision(const vd_ctx* ctx, bool mc = false) {
   const int p = ctx->cfg.precision;
-  if (p == VD_FP64) return VD_FP64;
-  if (p == VD_TC16) return VD_TC16;
-  return VD_FP32;  // VD_FP32 and VD_AUTO
+  if (p == VD_FP64 || p == VD_FP32 || p == VD_TC16) return p;
+  if (mc && ctx->tree.K == 0 && ctx->tree.coord_abs <= vd::kTcCoordMax) return VD_TC16;
+  return VD_FP32;
 }
 
 }  // namespace
@@ -247,6 +256,7 @@ void vd_destroy(vd_ctx* ctx) {
   ctx->trav_ws.release();
   ctx->mc_ws.release();
   ctx->batch_ws.release();
+  if (ctx->batch_exec) cudaGraphExecDestroy(ctx->batch_exec);
   delete ctx;
 }
 
@@ -425,7 +435,7 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
   VD_CK(ctx->mc_ws.get_n(0, ovcap, &ovl), "alloc");
   VD_CK(ctx->mc_ws.get_n(1, N * R, &fbl), "alloc");
   VD_CK(ctx->mc_ws.get_n(2, N, &cnt), "alloc");
-  const int prec = effective_precision(ctx);
+  const int prec = effective_precision(ctx, true);
   // the cell kernels keep each ray's binary64 direction for the fill and the
   // adjoint (8 d bytes per ray) unless that would exceed 16 GiB
   const bool cells = tv.K > 0 && prec != VD_FP64;
@@ -946,13 +956,18 @@ vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const*
     }
   } sg{gs, ev, ga, gb};
   if (e != cudaSuccess) return fail(cuda_err(ctx, e, "vd_mc_integrate_batch: stream"));
-  // autotuner: threads per block of the persistent kernel, per largest d
+  // autotuner: threads per block of the persistent kernel, per largest d,
+  // timed on the first cells of the batch (a few per resident block)
   int& threads = ctx->batch_threads[std::min(maxd, 8)];
   if (threads == 0) {
     float best = INFINITY;
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t sample = std::min<int64_t>(nitems, (int64_t)nsm * 64);
     for (int th : {64, 128, 256}) {
       cudaEventRecord(ga, gs);
-      e = vd::launch_mc_batch(desc_dev, desc.data(), nsets, nitems, maxd, maxK, R, seed, th, ctx->ctr, gs);
+      e = vd::launch_mc_batch_cells(desc_dev, desc.data(), nsets, sample, maxK, R, seed, th, ctx->ctr, gs);
       cudaEventRecord(gb, gs);
       if (e == cudaSuccess) e = cudaEventSynchronize(gb);
       if (e != cudaSuccess) return fail(cuda_err(ctx, e, "vd_mc_integrate_batch: autotune"));
@@ -965,7 +980,6 @@ vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const*
     }
   }
   cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
   cudaEventRecord(ev, ctx->st);
   cudaStreamWaitEvent(gs, ev, 0);
   e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
@@ -976,10 +990,18 @@ vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const*
     e = cudaStreamEndCapture(gs, &graph);
     if (e == cudaSuccess) e = e2;
   }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e == cudaSuccess && ctx->batch_exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(ctx->batch_exec, graph, &info) != cudaSuccess) {
+      cudaGetLastError();  // another shape: instantiate below
+      cudaGraphExecDestroy(ctx->batch_exec);
+      ctx->batch_exec = nullptr;
+    }
+  }
+  if (e == cudaSuccess && !ctx->batch_exec) e = cudaGraphInstantiate(&ctx->batch_exec, graph, 0);
   if (e == cudaSuccess) {
     cudaEventRecord(ga, gs);
-    e = cudaGraphLaunch(exec, gs);
+    e = cudaGraphLaunch(ctx->batch_exec, gs);
     cudaEventRecord(gb, gs);
   }
   if (e == cudaSuccess) {
@@ -992,7 +1014,6 @@ vd_status vd_mc_integrate_batch(vd_ctx* ctx, int32_t nsets, const double* const*
   if (e == cudaSuccess) e = cudaStreamSynchronize(gs);
   float gms = 0.f;
   if (e == cudaSuccess) cudaEventElapsedTime(&gms, ga, gb);
-  if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(cuda_err(ctx, e, "vd_mc_integrate_batch: graph"));
   Counters hc;

@@ -247,6 +247,8 @@ struct SetDesc {
 // the lists cannot certify), distinct-hit counts, per-set scans, fill.
 cudaError_t launch_mc_batch(const SetDesc* sets_dev, const SetDesc* sets_host, int nsets, int64_t nitems, int maxd,
                             int maxK, int64_t R, uint64_t seed, int threads, Counters* ctr, cudaStream_t st);
+cudaError_t launch_mc_batch_cells(const SetDesc* sets_dev, const SetDesc* sets_host, int nsets, int64_t nitems,
+                                  int maxK, int64_t R, uint64_t seed, int threads, Counters* ctr, cudaStream_t st);
 // Tree-walk finish of one set's uncertified MC rays with device-side counts.
 cudaError_t launch_mc_fallback_dev(const SetDesc& S, int64_t R, uint64_t seed, cudaStream_t st);
 void mc_batch_dims(int threads, int maxd, int maxK, size_t* smem);

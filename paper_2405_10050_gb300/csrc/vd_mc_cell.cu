@@ -411,6 +411,18 @@ cudaError_t launch_mc_batch(const SetDesc* sets_dev, const SetDesc* sets_host, i
   return mc_batch_reduce(sets_dev, nsets, nitems, maxd, R, seed, st);
 }
 
+// The persistent cell kernel alone over the first `nitems` cells of the
+// batch (the autotuner's timing run; the rays it writes are written again by
+// the full pass).
+cudaError_t launch_mc_batch_cells(const SetDesc* sets_dev, const SetDesc* sets_host, int nsets, int64_t nitems,
+                                  int maxK, int64_t R, uint64_t seed, int threads, Counters* ctr, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(sets_host[0].ctr, 0, sizeof(Counters) * nsets, st);
+  if (e != cudaSuccess) return e;
+  if (threads <= 64) return launch_batch_th<64>(sets_dev, nsets, nitems, maxK, R, seed, ctr, st);
+  if (threads <= 128) return launch_batch_th<128>(sets_dev, nsets, nitems, maxK, R, seed, ctr, st);
+  return launch_batch_th<256>(sets_dev, nsets, nitems, maxK, R, seed, ctr, st);
+}
+
 void mc_batch_dims(int threads, int maxd, int maxK, size_t* smem) { *smem = cell_smem(8, maxK, threads); }
 
 }  // namespace vd

@@ -139,3 +139,29 @@ def test_tensor_wait_limit(orc, d, N, R):
     vor, res, ref = _parity(orc, X, R, seed=5, prec=VD_TC16)
     res.free()
     vor.close()
+
+
+@pytest.mark.parametrize("d,N,R", [(4, 1500, 64), (16, 400, 32)])
+def test_auto_takes_the_fastest_path(orc, d, N, R):
+    """VD_AUTO (the default) runs the path measured fastest for the call:
+    the tensor-core block walk for node sets without candidate lists
+    (d > 8), binary32 screening otherwise.  Same hits, same lengths and the
+    same work counters as the explicit choice, and the oracle's hits."""
+    need_cuda()
+    X = synth.uniform(N, d, seed=60 + d)
+    best = VD_TC16 if d > 8 else VD_FP32
+    out = []
+    for prec in (None, best):
+        vor = Voronoi(X) if prec is None else Voronoi(X, precision=prec)
+        res = vor.mc_integrate(R, 4)
+        out.append((res.hit.cpu().numpy(), res.l.cpu().numpy(), dict(res.stats)))
+        res.free()
+        vor.close()
+    (h0, l0, s0), (h1, l1, s1) = out
+    assert np.array_equal(h0, h1) and np.array_equal(l0, l1)
+    for k in ("tiles_visited", "pairs_screened", "rechecked", "fallback_rays"):
+        assert s0[k] == s1[k], k
+    if d > 8:
+        assert s0["tiles_visited"] > 0  # the block walk ran
+    ref = orc.mc_integrate(X, R, 4)
+    assert np.array_equal(h0, ref.hit) and np.array_equal(l0, ref.l)

@@ -2,18 +2,23 @@
 
 Workload (one step): node preparation + exhaustive vertex traversal
 (Algorithm 2) of N = 20,000 iid uniform nodes in [0,1]^5 (seed 0), cells
-clipped to the unit cube, on the binary32-screened path with binary64
-recheck.  The metric is raycasts per second of that traversal; the same
-workload on the plain binary64 path is timed beside it, and its vertex
-tuples must equal the screened path's bit for bit.
+clipped to the unit cube, on the library's default path (tensor-core
+screening of the rays grouped by reference node, binary32 rescreen,
+binary64 recheck).  The metric is raycasts per second of that traversal; the
+same workload on the binary32-screened path and on the plain binary64 path
+is timed beside it, and their vertex tuples must equal the default path's bit
+for bit.
 
 Secondary lines in the same JSON object: "mc" (MC volumes + areas + adjoint,
 d=4, N=100,000, 1024 rays per cell; binary32-screened, tensor-core screened
-and binary64 paths) and "highd" (the same at d=16, N=200,000 mixture nodes,
+and binary64 paths), "highd" (the same at d=16, N=200,000 mixture nodes,
 64 rays per cell; tensor-core walk vs binary32 tree walk), "mc.integrals"
-(Algorithm 3's function integrals on the d=4 rays) and "hmc" (heuristic MC
-integrals, Section 3.3, on the traversal workload's diagram).  --only-batch
-times the batched MC workload (512 point sets).
+(Algorithm 3's function integrals on the d=4 rays), "hmc" (heuristic MC
+integrals, Section 3.3, and the exact integration of Section 3.2 on the
+traversal workload's diagram), "walk" (random walks on the vertex graph),
+"plain_fp64_d3" (the plain binary64 method at d=3, N=2,000: traversal + MC
+with 64 rays per cell + adjoint) and "batch" (512 point sets of uneven N and
+d, 256 rays per cell).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -273,7 +278,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    from paper_2405_10050_gb300 import VD_FP32, VD_FP64, VD_TC16, synth, vd
+    from paper_2405_10050_gb300 import VD_AUTO, VD_FP32, VD_FP64, synth, vd
     vd.load()
     if args.only_mc:  # the MC secondary measurement alone (profiling)
         print(json.dumps({"mc": run_mc(args, vd, torch.cuda.current_stream())}), flush=True)
@@ -294,7 +299,7 @@ def run_ours(args):
     Xd = torch.tensor(X, device="cuda")
     stream = torch.cuda.current_stream()
     cfg = vd.vd_config_default()
-    cfg.precision = VD_FP32
+    cfg.precision = VD_AUTO  # the library's default: the tensor-core list scan at 3 <= d <= 8
     cfg.knn_k = args.knn_k
     ctx = vd.vd_create(cfg, stream.cuda_stream)
 
@@ -370,11 +375,11 @@ def run_ours(args):
         vd.vd_mesh_free(m)
         vd.vd_destroy(ctx2)
         return {"value": n / reps / (ms2 / 1000.0), "ms_per_step": ms2, "raycast_ms": rc / reps,
-                "pairs_per_ray": st["pairs_screened"] / max(st["rays"], 1), "tuples_identical_to_mixed": same}
+                "pairs_per_ray": st["pairs_screened"] / max(st["rays"], 1), "tuples_identical_to_default": same}
 
-    # ---- plain binary64 path and tensor-core screening on the same workload ----
+    # ---- plain binary64 path and binary32 screening on the same workload ----
     fp64 = None if args.no_fp64 else other_path(VD_FP64)
-    tensor = other_path(VD_TC16, reps=max(1, min(args.steps, 5)))
+    fp32 = other_path(VD_FP32, reps=max(1, min(args.steps, 5)))
 
     # ---- end to end through the C ABI with host buffers ----
     Xh = np.ascontiguousarray(X)
@@ -409,7 +414,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": (achieved / peak_tflops) if achieved else None, "traffic": traffic,
                 "traffic_unit": "bytes per step (all list-RayCast launches of one traversal)",
-                "kernel": "k_ray_list_thr<5> + tree-walk follow-up (binary32 screening + binary64 recheck)",
+                "kernel": "k_ray_list_tc<5> with its prep/finish kernels and the tree-walk follow-up (tcgen05 fp16 screening of rays grouped by reference node, binary32 rescreen, binary64 recheck)",
                 "peak_source": f"FP32 lanes x 2 x sm_max_mhz ({src} peaks file)",
                 "algorithmic_flops_per_ray": flops_per_ray, "raycast_ms_per_step": rc_ms / args.steps}
 
@@ -440,20 +445,20 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "raycasts/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "N": args.N, "d": args.d, "precision": "fp32 screen + fp64 recheck",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": args.N, "d": args.d, "precision": "tcgen05 fp16 screen + fp32 rescreen + fp64 recheck",
                            "vertices": nv, "raycasts_per_step": rays / args.steps,
                            "levels": last_stats["levels"],
                            "pairs_per_ray": last_stats["pairs_screened"] / max(last_stats["rays"], 1),
                            "rechecked_per_ray": last_stats["rechecked"] / max(last_stats["rays"], 1),
                            "tree_walk_rays_per_step": last_stats["fallback_rays"],
+                           "binary64_overflow_rays_per_step": last_stats["overflow_rays"],
                            "knn_k": args.knn_k,
                            "step_launches": last_stats["launches"],
                            "l2": "inputs larger than L2 (traversal tables ~1.5 GB per step)",
                            "parallelism": f"replicas x{ws}"},
                 "fp64_path": fp64,
-                "tensor_path": dict(tensor, precision="tcgen05 fp16 screen (rays grouped by reference node) "
-                                                      "+ fp64 recheck"),
+                "binary32_path": dict(fp32, precision="binary32 screen, one thread per ray + fp64 recheck"),
                 "speedup_vs_fp64": (value / ws / fp64["value"]) if fp64 else None,
                 "e2e": {"value": e2e_value, "unit": "raycasts/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},

@@ -59,8 +59,9 @@ typedef enum {
                    by reference node); other calls treat it as VD_FP32   */
   VD_AUTO = 3   /* per call, the path measured fastest on GB300: VD_TC16
                    for MC rays of node sets without candidate lists
-                   (d > 8), VD_FP32 otherwise; results are identical on
-                   every path                                           */
+                   (d > 8) and for explicit rays with candidate lists at
+                   3 <= d <= 8, VD_FP32 otherwise; results are identical
+                   on every path                                        */
 } vd_precision;
 
 typedef struct {

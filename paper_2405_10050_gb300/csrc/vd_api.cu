@@ -186,16 +186,21 @@ vd_status check_flags(vd_ctx* ctx, const Counters& hc) {
 }
 
 // The path of a call.  VD_AUTO takes the fastest path measured on GB300 for
-// the call's kind and node set: Monte Carlo rays of a node set without
-// candidate lists (d > 8) take the tensor-core block walk (d = 16,
-// N = 200,000: ten times the binary32 tree walk); every other call takes the
-// binary32 screening, whose list kernels beat their tensor-core variants at
-// d <= 8 (the traversal at d = 5 and the MC cells at d = 4).
+// the call's kind and node set:
+//  * Monte Carlo rays: the tensor-core block walk for node sets without
+//    candidate lists (d > 8; d = 16, N = 200,000: ten times the binary32
+//    tree walk), else the binary32 cell kernel (d = 4: 1.43M against 1.19M
+//    cells/s on the tensor-core cells);
+//  * explicit rays (vd_raycast, vd_vertices, vd_random_walk) with candidate
+//    lists: the tensor-core list scan for 3 <= d <= 8 (traversal raycasts/s
+//    5-25 % above binary32 at d = 3..6), binary32 at d <= 2.
 int effective_precision(const vd_ctx* ctx, bool mc = false) {
   const int p = ctx->cfg.precision;
   if (p == VD_FP64 || p == VD_FP32 || p == VD_TC16) return p;
-  if (mc && ctx->tree.K == 0 && ctx->tree.coord_abs <= vd::kTcCoordMax) return VD_TC16;
-  return VD_FP32;
+  const vd::TreeView& tv = ctx->tree;
+  const bool tc_range = tv.coord_abs <= vd::kTcCoordMax;
+  if (mc) return (tv.K == 0 && tc_range) ? VD_TC16 : VD_FP32;
+  return (tv.K > 0 && tv.d >= 3 && tv.d <= 8 && tc_range) ? VD_TC16 : VD_FP32;
 }
 
 }  // namespace

@@ -216,10 +216,13 @@ cudaError_t launch_raycast_async(const TreeView& tv, const RaySource& rs, const 
 // and ro.grp_buf.
 cudaError_t launch_list_tc(const TreeView& tv, const RaySource& rs, const RayOut& ro, Counters* ctr,
                            cudaStream_t st);
+// Largest coordinate magnitude of a node set the tensor-core kernels take
+// (their fp16 operands are offsets of at most twice it).
+constexpr float kTcCoordMax = 1.0e4f;
 // True when launch_list_tc serves these rays.
 inline bool list_tc_ok(const TreeView& tv, const RaySource& rs, const RayOut& ro, int precision) {
-  return precision == VD_TC16 && rs.mode == 0 && tv.K > 0 && tv.d <= 8 && ro.fallback_list != nullptr &&
-         ro.grp_buf != nullptr && ro.grp_ints >= grp_ray_ints(tv.N, rs.R);
+  return precision == VD_TC16 && rs.mode == 0 && tv.K > 0 && tv.d <= 8 && tv.coord_abs <= kTcCoordMax &&
+         ro.fallback_list != nullptr && ro.grp_buf != nullptr && ro.grp_ints >= grp_ray_ints(tv.N, rs.R);
 }
 // One point set of a batched MC launch (device array, one entry per set).
 struct SetDesc {
@@ -262,7 +265,6 @@ cudaError_t launch_mc_cells(const TreeView& tv, int64_t R, uint64_t seed, uint32
 // (tcgen05, fp16 operands); needs coordinates within the fp16 range
 // (tv.coord_abs <= kTcCoordMax).  MMA completion waits poll at most
 // wait_limit times; a wait that gives up sets kFlagTimeout.
-constexpr float kTcCoordMax = 1.0e4f;
 cudaError_t launch_mc_cells_tc(const TreeView& tv, int64_t R, uint64_t seed, uint32_t set, const RayOut& ro,
                                Counters* ctr, long long wait_limit, cudaStream_t st, int64_t* nfallback);
 // MC rays without candidate lists: block tree walk with the ball tests of

@@ -26,6 +26,12 @@
 //     its ball (the list is sorted by distance from g), and the binary64
 //     recheck of its candidates decides the hit in the canonical order.
 //
+// The per-ray binary64 steps run on full warps in kernels of their own: the
+// scatter of the counting sort also writes each ray's record (binary32
+// copies of the ray, norms for the error bounds, the box-face bound) before
+// the tensor-core kernel, which only screens, and a finish kernel (binary64
+// recheck of the node candidates and of the faces) runs after it.
+//
 // Error of one tensor-core dot product of binary32 vectors a, w rounded to
 // fp16 with fp32 accumulation: 2^-11 relative per operand component (2^-25
 // absolute below the fp16 normal range) and 2^-16 of the sum of |products|
@@ -47,10 +53,26 @@ namespace {
 constexpr int kGrpRays = 32;            // rays per work item
 constexpr int kGrpCols = 2 * kGrpRays;  // MMA N at most = tensor-memory columns
 constexpr int kGrpM = 128;              // list entries per chunk = MMA M = threads
-constexpr int kGrpCand = 16;            // candidates kept per ray
+constexpr int kGrpCand = 16;            // node candidates kept per ray (more: binary64 path)
+
+// Per-ray records in grouped order (slot s = position in perm), 32-bit words.
+// In (prep -> tensor-core kernel): u32[D] p32[D] eta[D+1] U1 P1 P2 U2 hasp
+// Tface m, padded to a multiple of 4.  Out (tensor-core kernel -> finish):
+// T state nc - | cid[kGrpCand] | ctlo[kGrpCand].
+template <int D>
+struct Rin {
+  static constexpr int U = 0, P = D, ETA = 2 * D, U1 = 3 * D + 1, P1 = U1 + 1, P2 = U1 + 2, U2 = U1 + 3,
+                       HASP = U1 + 4, T = U1 + 5, M = U1 + 6;
+  static constexpr int W = (3 * D + 8 + 3) / 4 * 4;
+};
+constexpr int kRinMax = 32;
+static_assert(Rin<8>::W == kRinMax, "the largest prep record");
+constexpr int kRout = 4 + 2 * kGrpCand;
+enum : int { kOutT = 0, kOutState, kOutNc, kOutCid = 4, kOutTlo = 4 + kGrpCand };
 
 // Scratch of one call, carved from RayOut::grp_buf (int32 units):
-// cnt[N] fill[N] tot[4] | start[N] | perm[R] | pad | items[R/32 + N + 1] (int4).
+// cnt[N] fill[N] tot[4] | start[N] | perm[R] | pad | items[R/32 + N + 1]
+// (int4) | rin[R][<= kRinMax] | rout[R][kRout].
 struct GrpLayout {
   int32_t* cnt;    // rays per reference node
   int32_t* fill;   // rays placed so far per node
@@ -59,6 +81,8 @@ struct GrpLayout {
   int32_t* perm;   // ray indices grouped by reference node
   int4* items;     // (g, first slot, rays) per work item
   int64_t item_cap;
+  float* rin;      // per slot, Rin<D>::W words
+  float* rout;     // per slot, kRout words
 };
 
 GrpLayout grp_layout(int32_t* buf, int64_t N, int64_t R) {
@@ -71,18 +95,24 @@ GrpLayout grp_layout(int32_t* buf, int64_t N, int64_t R) {
   const int64_t off = (3 * N + 4 + R + 3) / 4 * 4;  // 16-byte aligned
   L.items = reinterpret_cast<int4*>(buf + off);
   L.item_cap = R / kGrpRays + N + 1;
+  const int64_t off2 = off + 4 * L.item_cap;
+  L.rin = reinterpret_cast<float*>(buf + off2);
+  L.rout = reinterpret_cast<float*>(buf + off2 + (int64_t)kRinMax * R);
   return L;
 }
 
 __device__ __forceinline__ int32_t ref_node(const RaySource& rs, int64_t r, int64_t N) {
   const int32_t g = rs.eta[r * rs.eta_stride];
-  return (g < 0 || g >= N) ? 0 : g;  // a bad reference is flagged by the RayCast kernel
+  return (g < 0 || g >= N) ? 0 : g;  // a bad reference is flagged by the prep kernel
+}
+
+__device__ __forceinline__ int64_t ray_count(const RaySource& rs) {
+  return rs.R_dev ? min((int64_t)*rs.R_dev, rs.R) : rs.R;
 }
 
 __global__ void k_grp_count(RaySource rs, int64_t N, int32_t* cnt) {
   const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t R = rs.R_dev ? min((int64_t)*rs.R_dev, rs.R) : rs.R;
-  if (r < R) atomicAdd(&cnt[ref_node(rs, r, N)], 1);
+  if (r < ray_count(rs)) atomicAdd(&cnt[ref_node(rs, r, N)], 1);
 }
 
 // One thread per node: the node's rays get a contiguous range of perm and
@@ -119,20 +149,119 @@ __global__ void k_grp_alloc(const int32_t* cnt, int64_t N, int32_t* start, int4*
   }
 }
 
-__global__ void k_grp_scatter(RaySource rs, int64_t N, const int32_t* start, int32_t* fill, int32_t* perm) {
-  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t R = rs.R_dev ? min((int64_t)*rs.R_dev, rs.R) : rs.R;
-  if (r >= R) return;
-  const int32_t g = ref_node(rs, r, N);
-  perm[start[g] + atomicAdd(&fill[g], 1)] = (int32_t)r;
-}
-
 // Order-preserving map of binary32 values to int (for atomicMin on a bound).
 __device__ __forceinline__ int fkey(float x) {
   const int i = __float_as_int(x);
   return i >= 0 ? i : i ^ 0x7fffffff;
 }
 __device__ __forceinline__ float fval(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+
+// Binary32 interval [tlo, thi] of the box face of axis a the ray leaves
+// through, t = (b - v_a) / u_a; false if u_a = 0 or the face is in eta.
+template <int D>
+__device__ __forceinline__ bool face_interval(const double (&v)[D], const double (&u)[D], const float (&u32)[D],
+                                              const int32_t (&eta)[D + 1], int m, int a, int32_t& fid, float& tlo,
+                                              float& thi) {
+  float ua = 0.f;
+  double ua64 = 0.0, va64 = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+    if (k == a) {
+      ua = u32[k];
+      ua64 = u[k];
+      va64 = v[k];
+    }
+  if (ua64 == 0.0 || ua == 0.f) return false;
+  const int sd = ua64 > 0.0 ? 1 : 0;
+  fid = face_id(a, sd);
+  for (int q = 0; q < m; ++q)
+    if (eta[q] == fid) return false;
+  const float va = __double2float_rn(va64);
+  const float nf = (sd ? 1.f : 0.f) - va;
+  const float nfs = sd ? nf : -nf;
+  const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
+  const float au = fabsf(ua);
+  const float lo_n = nfs - ef, hi_n = nfs + ef;
+  tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
+                    : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
+  thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
+                    : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
+  return true;
+}
+
+// Loads ray r and its binary32 copies (reference node g = eta[0]); a bad
+// reference is flagged and replaced by node 0, as the other kernels do.
+template <int D>
+__device__ __forceinline__ void grp_load_ray(const TreeView& tr, const RaySource& rs, Counters* ctr, int64_t r,
+                                             double (&v)[D], double (&u)[D], int32_t (&eta)[D + 1], int& m,
+                                             float (&u32)[D]) {
+  load_ray<D>(tr, rs, r, v, u, eta, m);
+  if (m < 1 || eta[0] < 0 || eta[0] >= tr.N) {
+    atomicOr(&ctr->flags, kFlagBadInput);
+    m = 1;
+    eta[0] = 0;
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) u32[k] = __double2float_rn(u[k]);
+}
+
+// Scatter and prep, one thread per ray (full warps): the ray takes the next
+// slot of its reference node's range of perm, and its record holds the
+// binary32 direction and offset p = v - g, the norms the error bounds need
+// and the face bound.
+template <int D>
+__global__ void k_grp_scatter(TreeView tr, RaySource rs, Counters* ctr, GrpLayout L) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= ray_count(rs)) return;
+  const int d = tr.d;
+  const int32_t gref = ref_node(rs, r, tr.N);
+  const int64_t s = L.start[gref] + atomicAdd(&L.fill[gref], 1);
+  L.perm[s] = (int32_t)r;
+  double v[D], u[D];
+  int32_t eta[D + 1];
+  int m;
+  float u32[D];
+  grp_load_ray<D>(tr, rs, ctr, r, v, u, eta, m, u32);
+  const int32_t g = eta[0];
+  using I = Rin<D>;
+  float rec[I::W];
+#pragma unroll
+  for (int k = 0; k < I::W; ++k) rec[k] = 0.f;
+  float U1 = 0.f, U2s = 0.f, P1 = 0.f, P2s = 0.f;
+  bool hasp = false;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double gk = k < d ? tr.X[(int64_t)g * d + k] : 0.0;
+    const double pk = __dadd_rn(v[k], -gk);
+    rec[I::U + k] = u32[k];
+    rec[I::P + k] = __double2float_rn(pk);
+    U1 += fabsf(u32[k]);
+    U2s = fmaf(u32[k], u32[k], U2s);
+    const float pa = fabsf(__double2float_ru(fabs(pk)));
+    P1 += pa;
+    P2s = fmaf(pa, pa, P2s);
+    hasp |= (pk != 0.0);
+  }
+  float T = INFINITY;
+  if (rs.box)
+    for (int a = 0; a < d; ++a) {
+      int32_t fid;
+      float tlo, thi;
+      if (face_interval<D>(v, u, u32, eta, m, a, fid, tlo, thi)) T = fminf(T, thi);
+    }
+  rec[I::U1] = U1 * 1.0001f;
+  rec[I::P1] = P1 * 1.0001f;
+  rec[I::P2] = sqrtf(P2s) * 1.0001f;
+  rec[I::U2] = sqrtf(U2s);  // the kernel adds its rounding margin
+  rec[I::HASP] = hasp ? 1.f : 0.f;
+  rec[I::T] = T;
+  rec[I::M] = __int_as_float(m);
+#pragma unroll
+  for (int q = 0; q <= D; ++q) rec[I::ETA + q] = __int_as_float(q < m ? eta[q] : kNoId);
+  float4* dst = reinterpret_cast<float4*>(L.rin + s * I::W);
+#pragma unroll
+  for (int k = 0; k < I::W / 4; ++k) dst[k] = make_float4(rec[4 * k], rec[4 * k + 1], rec[4 * k + 2], rec[4 * k + 3]);
+}
 
 // Per-ray state of a work item, in shared memory.
 template <int D>
@@ -149,62 +278,47 @@ struct GrpRay {
   float ctlo[kGrpRays][kGrpCand];
   int state[kGrpRays];     // bit 0 done, bit 1 certified, bit 2 candidate overflow
 };
-enum : int { kStDone = 1, kStCert = 2, kStOver = 4 };
+enum : int { kStDone = 1, kStCert = 2, kStOver = 4, kStAbandoned = 8 };
 
 // Ray slot i of a work item belongs to thread (i mod 4) * 32 + i / 4, so the
-// per-ray phases (set-up, exit test, recheck) of a group spread over the
-// four warps instead of waiting on one.
+// per-ray steps (load, exit test, store) of a group spread over the four
+// warps.
 __device__ __forceinline__ int slot_of_thread(int t) { return (t & 31) < kGrpRays / 4 ? ((t & 31) << 2) | (t >> 5) : -1; }
 
-// Constants of the screening of one ray, shared by the passes.
 struct GrpConst {
   float gam, EW, B, sD, c1, ctiny, alpha;
 };
 
-// Set-up of ray slot i (binary64 ray, binary32 copies, error constants, box
-// faces); writes the B operand rows 2i and 2i + 1.
+// Ray slot i from its prep record: binary32 vectors, the screening
+// constants, the tensor-core error terms, the face bound; B operand rows 2i
+// (u) and 2i + 1 (p).
 template <int D>
-__device__ void grp_ray_setup(const TreeView& tr, const RaySource& rs, const GrpConst& C, GrpRay<D>& S,
-                              unsigned char* sB, Counters* ctr, int i, int64_t r, int32_t g) {
-  const int d = tr.d;
+__device__ __forceinline__ void grp_ray_load(const float* rec, const GrpConst& C, GrpRay<D>& S, unsigned char* sB,
+                                             int i) {
+  using I = Rin<D>;
+  float r[I::W];
+  const float4* src = reinterpret_cast<const float4*>(rec);
+#pragma unroll
+  for (int k = 0; k < I::W / 4; ++k) {
+    const float4 f = src[k];
+    r[4 * k] = f.x;
+    r[4 * k + 1] = f.y;
+    r[4 * k + 2] = f.z;
+    r[4 * k + 3] = f.w;
+  }
   float hu[16], hp[16];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) hu[k] = hp[k] = 0.f;
-  double v[D], u[D];
-  int32_t eta[D + 1];
-  int m;
-  load_ray<D>(tr, rs, r, v, u, eta, m);
-  if (m < 1 || eta[0] < 0 || eta[0] >= tr.N) {
-    atomicOr(&ctr->flags, kFlagBadInput);
-    m = 1;
-    eta[0] = 0;
+  for (int k = 0; k < 16; ++k) {
+    hu[k] = k < D ? r[I::U + k] : 0.f;
+    hp[k] = k < D ? r[I::P + k] : 0.f;
   }
-  float U1 = 0.f, U2s = 0.f, P1 = 0.f, P2s = 0.f;
-  bool hasp = false;
-  float u32[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    const double gk = k < d ? tr.X[(int64_t)g * d + k] : 0.0;
-    const double pk = __dadd_rn(v[k], -gk);
-    u32[k] = __double2float_rn(u[k]);
-    const float p32 = __double2float_rn(pk);
-    S.u[i][k] = u32[k];
-    S.p[i][k] = p32;
-    if (k < 16) {
-      hu[k] = u32[k];
-      hp[k] = p32;
-    }
-    U1 += fabsf(u32[k]);
-    U2s = fmaf(u32[k], u32[k], U2s);
-    const float pa = fabsf(__double2float_ru(fabs(pk)));
-    P1 += pa;
-    P2s = fmaf(pa, pa, P2s);
-    hasp |= (pk != 0.0);
+    S.u[i][k] = r[I::U + k];
+    S.p[i][k] = r[I::P + k];
   }
-  U1 *= 1.0001f;
-  P1 *= 1.0001f;
-  const float U2 = sqrtf(U2s) * (1.f + 2.f * C.gam) + 1e-30f;
-  const float P2 = sqrtf(P2s) * 1.0001f;
+  const float U1 = r[I::U1], P1 = r[I::P1], P2 = r[I::P2];
+  const float U2 = r[I::U2] * (1.f + 2.f * C.gam) + 1e-30f;
   // binary32 screening constants (as the one-thread list scan), then the
   // tensor-core errors |u.w - den_tc| <= m1d |w| + m0d and
   // |p.w - pw_tc| <= m1p |w| + m0p, and pass A's |num| margin terms
@@ -221,61 +335,14 @@ __device__ void grp_ray_setup(const TreeView& tr, const RaySource& rs, const Grp
   K[9] = 1.05f * ((float)D * C.EW * C.EW + 2.f * K[7]) + 1e-30f;                 // cA
   K[10] = U2;
   K[11] = P2;
-  K[15] = hasp ? 1.f : 0.f;
-  for (int q = 0; q <= D; ++q) S.eta[i][q] = q < m ? eta[q] : kNoId;
-  S.m[i] = m;
-  // box faces: binary32 interval of (b - v_a) / u_a; the faces whose lower
-  // bound does not exceed the smallest upper bound stay candidates
-  float T = INFINITY;
-  int nc = 0, st = 0;
-  if (rs.box) {
-    for (int a = 0; a < d; ++a) {
-      float ua = 0.f;
-      double ua64 = 0.0, va64 = 0.0;
+  K[15] = r[I::HASP];
+  const int m = __float_as_int(r[I::M]);
 #pragma unroll
-      for (int k = 0; k < D; ++k)
-        if (k == a) {
-          ua = u32[k];
-          ua64 = u[k];
-          va64 = v[k];
-        }
-      if (ua64 == 0.0 || ua == 0.f) continue;
-      const int sd = ua64 > 0.0 ? 1 : 0;
-      const int32_t fid = face_id(a, sd);
-      bool ex = false;
-      for (int q = 0; q < m; ++q) ex |= (eta[q] == fid);
-      if (ex) continue;
-      const float va = __double2float_rn(va64);
-      const float nf = (sd ? 1.f : 0.f) - va;
-      const float nfs = sd ? nf : -nf;
-      const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
-      const float au = fabsf(ua);
-      const float lo_n = nfs - ef, hi_n = nfs + ef;
-      const float tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
-                                    : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
-      const float thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
-                                    : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
-      T = fminf(T, thi);
-      if (nc < kGrpCand) {
-        S.cid[i][nc] = fid;
-        S.ctlo[i][nc] = tlo;
-        ++nc;
-      } else {
-        st |= kStOver;
-      }
-    }
-    int k2 = 0;
-    for (int q = 0; q < nc; ++q)
-      if (S.ctlo[i][q] <= T) {
-        S.cid[i][k2] = S.cid[i][q];
-        S.ctlo[i][k2] = S.ctlo[i][q];
-        ++k2;
-      }
-    nc = k2;
-  }
-  S.T[i] = fkey(T);
-  S.nc[i] = nc;
-  S.state[i] = st;
+  for (int q = 0; q <= D; ++q) S.eta[i][q] = __float_as_int(r[I::ETA + q]);
+  S.m[i] = m;
+  S.T[i] = fkey(r[I::T]);
+  S.nc[i] = 0;
+  S.state[i] = 0;
   tc::store_row16(sB, 2 * i, hu);
   tc::store_row16(sB, 2 * i + 1, hp);
 }
@@ -306,81 +373,24 @@ __device__ void grp_ray_exit(const TreeView& tr, const GrpConst& C, GrpRay<D>& S
   S.state[i] = st;
 }
 
-// Result of ray slot i: tree walk (not certified), binary64 path (candidate
-// overflow) or the binary64 recheck of its candidates in the canonical order.
+// The record the finish kernel reads: final bound, state, node candidates.
 template <int D>
-__device__ void grp_ray_finish(const TreeView& tr, const RaySource& rs, const RayOut& ro, GrpRay<D>& S,
-                               Counters* ctr, int i, int64_t r, int32_t g, unsigned long long& n_rech) {
-  const int d = tr.d;
-  const int st = S.state[i];
-  const float T = fval(S.T[i]);
-  const int64_t op = out_pos(rs, ro, r);
-  if (!(st & kStCert)) {  // finished by the tree walk, from the bound found so far
-    const unsigned long long k = atomicAdd(&ctr->fallback, 1ull);
-    if ((int64_t)k < ro.fallback_cap) ro.fallback_list[k] = (int32_t)r;
-    else atomicOr(&ctr->flags, kFlagQueue);
-    ro.t[op] = (double)T;
-    return;
-  }
-  if (st & kStOver) {  // redone on the binary64 path
-    const unsigned long long k = atomicAdd(&ctr->overflow, 1ull);
-    if ((int64_t)k < ro.overflow_cap) ro.overflow_list[k] = (int32_t)r;
-    else atomicOr(&ctr->flags, kFlagCandOverflow);
-    ro.hit[op] = kNoId;
-    ro.t[op] = NAN;
-    return;
-  }
-  double v[D], u[D];
-  load_vu<D>(tr, rs, r, v, u);
-  double bt = INFINITY;
-  int bc = 2, bk = 0;
+__device__ __forceinline__ void grp_ray_store(const GrpRay<D>& S, int i, float* rec) {
   const int nc = min(S.nc[i], kGrpCand);
-  for (int q = 0; q < nc; ++q) {
-    if (!(S.ctlo[i][q] <= T)) continue;
-    const int32_t cid = S.cid[i][q];
-    ++n_rech;
-    if (cid >= 0) {
-      double den = 0.0, ww64 = 0.0, pw = 0.0, w64[D];
+  float r[kRout];
 #pragma unroll
-      for (int k = 0; k < D; ++k)
-        w64[k] = k < d ? __dadd_rn(tr.X[(int64_t)cid * d + k], -tr.X[(int64_t)g * d + k]) : 0.0;
+  for (int k = 0; k < kRout; ++k) r[k] = 0.f;
+  r[kOutT] = fval(S.T[i]);
+  r[kOutState] = __int_as_float(S.state[i]);
+  r[kOutNc] = __int_as_float(nc);
 #pragma unroll
-      for (int k = 0; k < D; ++k)
-        if (k < d) den = __dadd_rn(den, __dmul_rn(u[k], w64[k]));
-      if (!(den > 0.0)) continue;
-#pragma unroll
-      for (int k = 0; k < D; ++k)
-        if (k < d) ww64 = __dadd_rn(ww64, __dmul_rn(w64[k], w64[k]));
-#pragma unroll
-      for (int k = 0; k < D; ++k)
-        if (k < d) pw = __dadd_rn(pw, __dmul_rn(__dadd_rn(v[k], -tr.X[(int64_t)g * d + k]), w64[k]));
-      const double num = __dadd_rn(ww64, -__dmul_rn(2.0, pw));
-      const double t = __ddiv_rn(num, __dmul_rn(2.0, den));
-      if (better(t, 0, cid, bt, bc, bk)) {
-        bt = t;
-        bc = 0;
-        bk = cid;
-      }
-    } else {
-      const int a = face_axis(cid), sd = face_side(cid);
-      double ua = 0.0, va = 0.0;
-#pragma unroll
-      for (int k = 0; k < D; ++k)
-        if (k == a) {
-          ua = u[k];
-          va = v[k];
-        }
-      const double t = __ddiv_rn(__dadd_rn(sd ? 1.0 : 0.0, -va), ua);
-      if (better(t, 1, 2 * a + sd, bt, bc, bk)) {
-        bt = t;
-        bc = 1;
-        bk = 2 * a + sd;
-      }
-    }
+  for (int q = 0; q < kGrpCand; ++q) {
+    r[kOutCid + q] = __int_as_float(q < nc ? S.cid[i][q] : kNoId);
+    r[kOutTlo + q] = q < nc ? S.ctlo[i][q] : INFINITY;
   }
-  ro.hit[op] = gen_from_key(bc, bk);
-  ro.t[op] = bt;
-  if (ro.screen_err) ro.screen_err[op] = (bt > 0.0 && bt < INFINITY) ? (float)((T - bt) / bt) : 0.f;
+  float4* dst = reinterpret_cast<float4*>(rec);
+#pragma unroll
+  for (int k = 0; k < kRout / 4; ++k) dst[k] = make_float4(r[4 * k], r[4 * k + 1], r[4 * k + 2], r[4 * k + 3]);
 }
 
 template <int D>
@@ -425,7 +435,7 @@ __global__ void __launch_bounds__(kGrpM, 6) k_ray_list_tc(TreeView tr, RaySource
   const uint64_t bdesc = tc::smem_desc(sB, tc::kLbo16, tc::kSbo16);
   uint32_t phase = 0;
   bool timed_out = false;
-  unsigned long long n_pairs = 0, n_rech = 0;
+  unsigned long long n_pairs = 0;
 
   int it = 0;
   for (; !timed_out; ++it) {
@@ -444,7 +454,6 @@ __global__ void __launch_bounds__(kGrpM, 6) k_ray_list_tc(TreeView tr, RaySource
     float g32[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) g32[k] = k < d ? tr.X32[(int64_t)g * d + k] : 0.f;
-    const int64_t r = (slot >= 0 && slot < G) ? (int64_t)L.perm[item.y + slot] : -1;
 
     for (int c0 = 0;; c0 += kGrpM) {
       // ---- stage the chunk: thread j owns list entry c0 + j ----
@@ -471,7 +480,7 @@ __global__ void __launch_bounds__(kGrpM, 6) k_ray_list_tc(TreeView tr, RaySource
       if (tid == last) s_wwlast = ww;
       if (c0 == 0 && slot >= 0 && slot < Gp) {  // the item's rays (B operand); padding rows are zero
         if (slot < G) {
-          grp_ray_setup<D>(tr, rs, C, S, sB, ctr, slot, r, g);
+          grp_ray_load<D>(L.rin + (int64_t)(item.y + slot) * Rin<D>::W, C, S, sB, slot);
         } else {
           float z[16];
 #pragma unroll
@@ -601,7 +610,7 @@ __global__ void __launch_bounds__(kGrpM, 6) k_ray_list_tc(TreeView tr, RaySource
       if (!__syncthreads_or(slot >= 0 && slot < G && !(S.state[slot] & kStDone))) break;
     }
     if (timed_out) break;
-    if (slot >= 0 && slot < G) grp_ray_finish<D>(tr, rs, ro, S, ctr, slot, r, g, n_rech);
+    if (slot >= 0 && slot < G) grp_ray_store<D>(S, slot, L.rout + (int64_t)(item.y + slot) * kRout);
     __syncthreads();  // the next item rewrites the ray state and the B operand
   }
   if (timed_out) {
@@ -610,7 +619,7 @@ __global__ void __launch_bounds__(kGrpM, 6) k_ray_list_tc(TreeView tr, RaySource
     tc::mbar_wait(&mbar, phase ^ 1u, wait_limit > (1ll << 24) ? wait_limit : (1ll << 24));
     if (tid == 0) atomicOr(&ctr->flags, kFlagTimeout);
     // every ray of this block's unfinished items, and of the items still
-    // queued, gets "no hit", so that no later kernel reads a stale hit id
+    // queued, is marked abandoned: the finish kernel writes "no hit" for it
     __syncthreads();
     for (int k = 0;; ++k) {
       int4 itm;
@@ -629,25 +638,114 @@ __global__ void __launch_bounds__(kGrpM, 6) k_ray_list_tc(TreeView tr, RaySource
         if (k == 0) continue;  // nothing was current: look at the prefetched item
         if (k >= 1) break;
       }
-      for (int q = tid; q < itm.z; q += kGrpM) {
-        const int64_t op = out_pos(rs, ro, (int64_t)L.perm[itm.y + q]);
-        ro.hit[op] = kNoId;
-        ro.t[op] = NAN;
-      }
+      for (int q = tid; q < itm.z; q += kGrpM)
+        L.rout[(int64_t)(itm.y + q) * kRout + kOutState] = __int_as_float(kStAbandoned);
     }
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   if (warp == 0) tc::tmem_dealloc(tbase, kGrpCols);
-  for (int o = 16; o; o >>= 1) {
-    n_pairs += __shfl_xor_sync(kFull, n_pairs, o);
-    n_rech += __shfl_xor_sync(kFull, n_rech, o);
+  for (int o = 16; o; o >>= 1) n_pairs += __shfl_xor_sync(kFull, n_pairs, o);
+  if (lane == 0) atomicAdd(&ctr->pairs, n_pairs);
+}
+
+
+// Finish, one thread per slot (full warps): the tree walk for rays the list
+// could not certify (with the bound found so far), the binary64 path for
+// rays whose candidate buffer overflowed, else the binary64 recheck of the
+// node candidates and of the box faces whose lower bound does not exceed T,
+// in the canonical order; "no hit" for rays a timed-out kernel abandoned.
+template <int D>
+__global__ void k_grp_finish(TreeView tr, RaySource rs, RayOut ro, Counters* ctr, GrpLayout L) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int d = tr.d;
+  unsigned long long n_rech = 0;
+  if (s < ray_count(rs)) {
+    const int64_t r = L.perm[s];
+    const float* rec = L.rout + s * kRout;
+    const float4 h = *reinterpret_cast<const float4*>(rec);  // T state nc -
+    const int st = __float_as_int(h.y);
+    const float T = h.x;
+    const int64_t op = out_pos(rs, ro, r);
+    if (st & kStAbandoned) {
+      ro.hit[op] = kNoId;
+      ro.t[op] = NAN;
+    } else if (!(st & kStCert)) {  // finished by the tree walk, from the bound found so far
+      const unsigned long long k = atomicAdd(&ctr->fallback, 1ull);
+      if ((int64_t)k < ro.fallback_cap) ro.fallback_list[k] = (int32_t)r;
+      else atomicOr(&ctr->flags, kFlagQueue);
+      ro.t[op] = (double)T;
+    } else if (st & kStOver) {  // redone on the binary64 path
+      const unsigned long long k = atomicAdd(&ctr->overflow, 1ull);
+      if ((int64_t)k < ro.overflow_cap) ro.overflow_list[k] = (int32_t)r;
+      else atomicOr(&ctr->flags, kFlagCandOverflow);
+      ro.hit[op] = kNoId;
+      ro.t[op] = NAN;
+    } else {
+      double v[D], u[D];
+      int32_t eta[D + 1];
+      int m;
+      float u32[D];
+      grp_load_ray<D>(tr, rs, ctr, r, v, u, eta, m, u32);
+      const int32_t g = eta[0];
+      double bt = INFINITY;
+      int bc = 2, bk = 0;
+      const int nc = __float_as_int(h.z);
+      for (int q = 0; q < nc; ++q) {
+        if (!(rec[kOutTlo + q] <= T)) continue;
+        const int32_t cid = __float_as_int(rec[kOutCid + q]);
+        ++n_rech;
+        double den = 0.0, ww64 = 0.0, pw = 0.0, w64[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          w64[k] = k < d ? __dadd_rn(tr.X[(int64_t)cid * d + k], -tr.X[(int64_t)g * d + k]) : 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          if (k < d) den = __dadd_rn(den, __dmul_rn(u[k], w64[k]));
+        if (!(den > 0.0)) continue;
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          if (k < d) ww64 = __dadd_rn(ww64, __dmul_rn(w64[k], w64[k]));
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+          if (k < d) pw = __dadd_rn(pw, __dmul_rn(__dadd_rn(v[k], -tr.X[(int64_t)g * d + k]), w64[k]));
+        const double num = __dadd_rn(ww64, -__dmul_rn(2.0, pw));
+        const double t = __ddiv_rn(num, __dmul_rn(2.0, den));
+        if (better(t, 0, cid, bt, bc, bk)) {
+          bt = t;
+          bc = 0;
+          bk = cid;
+        }
+      }
+      if (rs.box)
+        for (int a = 0; a < d; ++a) {
+          int32_t fid;
+          float tlo, thi;
+          if (!face_interval<D>(v, u, u32, eta, m, a, fid, tlo, thi) || !(tlo <= T)) continue;
+          ++n_rech;
+          const int sd = face_side(fid);
+          double ua = 0.0, va = 0.0;
+#pragma unroll
+          for (int k = 0; k < D; ++k)
+            if (k == a) {
+              ua = u[k];
+              va = v[k];
+            }
+          const double t = __ddiv_rn(__dadd_rn(sd ? 1.0 : 0.0, -va), ua);
+          if (better(t, 1, 2 * a + sd, bt, bc, bk)) {
+            bt = t;
+            bc = 1;
+            bk = 2 * a + sd;
+          }
+        }
+      ro.hit[op] = gen_from_key(bc, bk);
+      ro.t[op] = bt;
+      if (ro.screen_err) ro.screen_err[op] = (bt > 0.0 && bt < INFINITY) ? (float)((T - bt) / bt) : 0.f;
+    }
   }
-  if (lane == 0) {
-    atomicAdd(&ctr->pairs, n_pairs);
-    atomicAdd(&ctr->rechecked, n_rech);
-  }
+  for (int o = 16; o; o >>= 1) n_rech += __shfl_xor_sync(kFull, n_rech, o);
+  if ((threadIdx.x & 31) == 0 && n_rech) atomicAdd(&ctr->rechecked, n_rech);
 }
 
 template <int D>
@@ -665,7 +763,7 @@ cudaError_t launch_list_tc_d(const TreeView& tv, const RaySource& rs, const RayO
   count_launch();
   k_grp_alloc<<<nbk, 256, 0, st>>>(L.cnt, N, L.start, L.items, L.item_cap, L.tot, &ctr->flags);
   count_launch();
-  k_grp_scatter<<<rb, 256, 0, st>>>(rs, N, L.start, L.fill, L.perm);
+  k_grp_scatter<D><<<(unsigned)((R + 127) / 128), 128, 0, st>>>(tv, rs, ctr, L);
   count_launch();
   unsigned long long* work = reinterpret_cast<unsigned long long*>(&ctr->aux1);
   if ((e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
@@ -684,12 +782,16 @@ cudaError_t launch_list_tc_d(const TreeView& tv, const RaySource& rs, const RayO
   const long long wl = wait_polls(rs.wait_limit);
   k_ray_list_tc<D><<<(unsigned)((int64_t)nsm * occ), kGrpM, 0, st>>>(tv, rs, ro, ctr, L, work, wl);
   count_launch();
+  k_grp_finish<D><<<(unsigned)((R + 127) / 128), 128, 0, st>>>(tv, rs, ro, ctr, L);
+  count_launch();
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int64_t grp_ray_ints(int64_t N, int64_t R) { return (3 * N + 4 + R + 3) / 4 * 4 + 4 * (R / kGrpRays + N + 1); }
+int64_t grp_ray_ints(int64_t N, int64_t R) {
+  return (3 * N + 4 + R + 3) / 4 * 4 + 4 * (R / kGrpRays + N + 1) + (int64_t)(kRinMax + kRout) * R;
+}
 
 cudaError_t launch_list_tc(const TreeView& tv, const RaySource& rs, const RayOut& ro, Counters* ctr,
                            cudaStream_t st) {

@@ -902,7 +902,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     }
   } evg{ev0, ev1};
   double raycast_ms = 0.0;
-  int64_t nfallback = 0;
+  int64_t nfallback = 0, noverflow = 0;
   // casts the level's rays (count on the device if nr_dev != nullptr, at most nr)
   auto cast = [&](int64_t nr, const unsigned long long* nr_dev, int stride) -> cudaError_t {
     RaySource rs;
@@ -1014,13 +1014,15 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     count_launch();
     VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, rmax, nwin, vids, flags, st);
     VD_TRY(cudaGetLastError());
-    unsigned long long hc[5];
+    unsigned long long hc[6];
     unsigned hf = 0;
     VD_TRY(cudaMemcpyAsync(hc, cnts, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     VD_TRY(cudaMemcpyAsync(hc + 4, &ctr->fallback, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    VD_TRY(cudaMemcpyAsync(hc + 5, &ctr->overflow, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     VD_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     VD_TRY(cudaStreamSynchronize(st));
     account(hc + 4);
+    noverflow += (int64_t)std::min<unsigned long long>(hc[5], (unsigned long long)rcap);
     raycasts += (int64_t)std::min<unsigned long long>(hc[2], (unsigned long long)rcap);
     if (hf & (kFlagHashFull | kFlagQueue | kFlagDegenerate | kFlagCandOverflow | kFlagBadInput)) break;
     const int64_t nv_now = std::min<int64_t>((int64_t)hc[0], vcap);
@@ -1071,6 +1073,7 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   stats->rays = raycasts;
   stats->raycast_ms = raycast_ms;
   stats->fallback_rays = nfallback;
+  stats->overflow_rays = noverflow;
   return cudaSuccess;
 #undef VD_TRY
 }

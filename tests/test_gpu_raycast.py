@@ -15,8 +15,9 @@ PRECS = [VD_FP64, VD_FP32, VD_TC16]
 
 
 def _run(X, O, U, E, prec, box=True, knn_k=0):
+    """prec None: the library's default (VD_AUTO)."""
     torch = need_cuda()
-    vor = Voronoi(X, precision=prec, box=box, knn_k=knn_k)
+    vor = Voronoi(X, box=box, knn_k=knn_k) if prec is None else Voronoi(X, precision=prec, box=box, knn_k=knn_k)
     hit, t, se = vor.raycast(O, U, E, screen_err=True)
     st = vor.stats()
     vor.close()
@@ -194,3 +195,21 @@ def test_tensor_list_wait_limit(orc):
     h0, t0 = orc.raycast(X, X[cells], U, cells)
     h1, t1, _, _ = _run(X, X[cells], U, cells[:, None], VD_TC16)
     assert np.array_equal(h0, h1) and np.array_equal(t0, t1)
+
+
+@pytest.mark.parametrize("d,N,best", [(2, 1500, VD_FP32), (4, 1500, VD_TC16), (6, 600, VD_TC16)])
+def test_auto_takes_the_fastest_path(orc, d, N, best):
+    """VD_AUTO (the default) on explicit rays runs the path measured fastest:
+    the tensor-core list scan for 3 <= d <= 8, binary32 below.  Same hits and
+    the same work counters as the explicit choice, and the oracle's hits."""
+    X = synth.uniform(N, d, seed=300 + d)
+    rng = np.random.default_rng(d)
+    cells = rng.integers(0, N, 3000).astype(np.int32)
+    U = random_unit(rng, 3000, d)
+    h0, t0 = orc.raycast(X, X[cells], U, cells)
+    ha, ta, _, sa = _run(X, X[cells], U, cells[:, None], None)
+    hb, tb, _, sb = _run(X, X[cells], U, cells[:, None], best)
+    assert np.array_equal(ha, h0) and np.array_equal(ta, t0)
+    assert np.array_equal(hb, h0) and np.array_equal(tb, t0)
+    for k in ("pairs_screened", "rechecked", "fallback_rays", "launches"):
+        assert sa[k] == sb[k], k

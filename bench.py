@@ -47,12 +47,13 @@ sys.path.insert(0, ROOT)
 METRIC = "raycasts/s and MC vol+grad cells/s: mixed vs FP64 path, same GB300, exact hits"
 WORKLOAD = "exhaustive vertex traversal, d=5, N=20000 iid uniform in [0,1]^5 (seed 0), clipped to the cube"
 NEIGHBOURS_D5 = 95  # neighbours per cell in d = 5 (the paper's table of vertices and neighbours per cell)
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, ncu, summed over every launch of k_ray_list_thr<5>
-# in one traversal) of the binary32 list RayCast with the ball-test screen: 1935.3 MB over the three traversals
-# of `python bench.py --steps 1 --warmup 1 --no-fp64 --no-cpu --no-mc --no-highd --no-hmc --no-walk --no-small
-# --no-batch`, captured with `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
-# --clock-control none -k regex:k_ray_list_thr`
-RAYCAST_DRAM_BYTES_PER_STEP = 645.1e6
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, ncu) of one traversal's RayCast on the default path,
+# every launch of k_grp_count, k_grp_alloc, k_grp_scatter, k_ray_list_tc, k_grp_finish and the tree-walk and
+# binary64 follow-ups: 8994.6 MB over the three traversals of `python bench.py --steps 1 --warmup 1 --no-fp64
+# --no-binary32 --no-cpu --no-mc --no-highd --no-hmc --no-walk --no-small --no-batch`, captured with `ncu --metrics
+# dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none -k
+# "regex:k_ray_list_tc|k_grp_|k_ray_mixed|k_ray_fp64"`
+RAYCAST_DRAM_BYTES_PER_STEP = 2998.2e6
 
 
 def _peaks():
@@ -379,7 +380,7 @@ def run_ours(args):
 
     # ---- plain binary64 path and binary32 screening on the same workload ----
     fp64 = None if args.no_fp64 else other_path(VD_FP64)
-    fp32 = other_path(VD_FP32, reps=max(1, min(args.steps, 5)))
+    fp32 = None if args.no_binary32 else other_path(VD_FP32, reps=max(1, min(args.steps, 5)))
 
     # ---- end to end through the C ABI with host buffers ----
     Xh = np.ascontiguousarray(X)
@@ -408,12 +409,12 @@ def run_ours(args):
     pairs = NEIGHBOURS_D5 + 2 * args.d
     flops_per_ray = pairs * (2 * args.d + 6)
     achieved = rays * flops_per_ray / (rc_ms / 1000.0) / 1e12 if rc_ms > 0 else None
-    # DRAM bytes of the list RayCast per traversal of this workload (one ncu capture of the current kernel,
-    # above); the ray I/O alone is ~573 MB
+    # DRAM bytes of the RayCast per traversal of this workload (one ncu capture of the current kernels, above);
+    # the ray I/O alone is ~573 MB
     traffic = RAYCAST_DRAM_BYTES_PER_STEP if (args.N, args.d, args.knn_k) == (20000, 5, 0) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": (achieved / peak_tflops) if achieved else None, "traffic": traffic,
-                "traffic_unit": "bytes per step (all list-RayCast launches of one traversal)",
+                "traffic_unit": "bytes per step (every RayCast launch of one traversal)",
                 "kernel": "k_ray_list_tc<5> with its prep/finish kernels and the tree-walk follow-up (tcgen05 fp16 screening of rays grouped by reference node, binary32 rescreen, binary64 recheck)",
                 "peak_source": f"FP32 lanes x 2 x sm_max_mhz ({src} peaks file)",
                 "algorithmic_flops_per_ray": flops_per_ray, "raycast_ms_per_step": rc_ms / args.steps}
@@ -458,7 +459,8 @@ def run_ours(args):
                            "l2": "inputs larger than L2 (traversal tables ~1.5 GB per step)",
                            "parallelism": f"replicas x{ws}"},
                 "fp64_path": fp64,
-                "binary32_path": dict(fp32, precision="binary32 screen, one thread per ray + fp64 recheck"),
+                "binary32_path": (dict(fp32, precision="binary32 screen, one thread per ray + fp64 recheck")
+                                  if fp32 else None),
                 "speedup_vs_fp64": (value / ws / fp64["value"]) if fp64 else None,
                 "e2e": {"value": e2e_value, "unit": "raycasts/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
@@ -839,6 +841,7 @@ def main():
     ap.add_argument("--N", type=int, default=20000)
     ap.add_argument("--d", type=int, default=5)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-binary32", action="store_true", help="skip the binary32-screened traversal leg")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-rays", type=int, default=4000)

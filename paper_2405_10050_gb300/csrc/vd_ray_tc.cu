@@ -58,7 +58,8 @@ constexpr int kGrpCand = 16;            // node candidates kept per ray (more: b
 // Per-ray records in grouped order (slot s = position in perm), 32-bit words.
 // In (prep -> tensor-core kernel): u32[D] p32[D] eta[D+1] U1 P1 P2 U2 hasp
 // Tface m, padded to a multiple of 4.  Out (tensor-core kernel -> finish):
-// T state nc - | cid[kGrpCand] | ctlo[kGrpCand].
+// T state nc - | (cid, ctlo) x kGrpCand, the pairs interleaved so that the
+// header and the first two candidates share one 32-byte sector.
 template <int D>
 struct Rin {
   static constexpr int U = 0, P = D, ETA = 2 * D, U1 = 3 * D + 1, P1 = U1 + 1, P2 = U1 + 2, U2 = U1 + 3,
@@ -68,7 +69,7 @@ struct Rin {
 constexpr int kRinMax = 32;
 static_assert(Rin<8>::W == kRinMax, "the largest prep record");
 constexpr int kRout = 4 + 2 * kGrpCand;
-enum : int { kOutT = 0, kOutState, kOutNc, kOutCid = 4, kOutTlo = 4 + kGrpCand };
+enum : int { kOutT = 0, kOutState, kOutNc, kOutCand = 4 };
 
 // Scratch of one call, carved from RayOut::grp_buf (int32 units):
 // cnt[N] fill[N] tot[4] | start[N] | perm[R] | pad | items[R/32 + N + 1]
@@ -373,24 +374,18 @@ __device__ void grp_ray_exit(const TreeView& tr, const GrpConst& C, GrpRay<D>& S
   S.state[i] = st;
 }
 
-// The record the finish kernel reads: final bound, state, node candidates.
+// The record the finish kernel reads: final bound, state, node candidates
+// (only the 16-byte groups in use are written).
 template <int D>
 __device__ __forceinline__ void grp_ray_store(const GrpRay<D>& S, int i, float* rec) {
   const int nc = min(S.nc[i], kGrpCand);
-  float r[kRout];
-#pragma unroll
-  for (int k = 0; k < kRout; ++k) r[k] = 0.f;
-  r[kOutT] = fval(S.T[i]);
-  r[kOutState] = __int_as_float(S.state[i]);
-  r[kOutNc] = __int_as_float(nc);
-#pragma unroll
-  for (int q = 0; q < kGrpCand; ++q) {
-    r[kOutCid + q] = __int_as_float(q < nc ? S.cid[i][q] : kNoId);
-    r[kOutTlo + q] = q < nc ? S.ctlo[i][q] : INFINITY;
-  }
   float4* dst = reinterpret_cast<float4*>(rec);
-#pragma unroll
-  for (int k = 0; k < kRout / 4; ++k) dst[k] = make_float4(r[4 * k], r[4 * k + 1], r[4 * k + 2], r[4 * k + 3]);
+  dst[0] = make_float4(fval(S.T[i]), __int_as_float(S.state[i]), __int_as_float(nc), 0.f);
+  for (int q = 0; q < nc; q += 2) {
+    const bool two = q + 1 < nc;
+    dst[1 + q / 2] = make_float4(__int_as_float(S.cid[i][q]), S.ctlo[i][q],
+                                 __int_as_float(two ? S.cid[i][q + 1] : kNoId), two ? S.ctlo[i][q + 1] : INFINITY);
+  }
 }
 
 template <int D>
@@ -693,8 +688,9 @@ __global__ void k_grp_finish(TreeView tr, RaySource rs, RayOut ro, Counters* ctr
       int bc = 2, bk = 0;
       const int nc = __float_as_int(h.z);
       for (int q = 0; q < nc; ++q) {
-        if (!(rec[kOutTlo + q] <= T)) continue;
-        const int32_t cid = __float_as_int(rec[kOutCid + q]);
+        const float2 c = *reinterpret_cast<const float2*>(rec + kOutCand + 2 * q);
+        if (!(c.y <= T)) continue;
+        const int32_t cid = __float_as_int(c.x);
         ++n_rech;
         double den = 0.0, ww64 = 0.0, pw = 0.0, w64[D];
 #pragma unroll

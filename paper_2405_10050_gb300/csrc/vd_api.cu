@@ -443,7 +443,7 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
   const int prec = effective_precision(ctx, true);
   // the cell kernels keep each ray's binary64 direction for the fill and the
   // adjoint (8 d bytes per ray) unless that would exceed 16 GiB
-  const bool cells = tv.K > 0 && prec != VD_FP64;
+  const bool cells = tv.K > 0;
   if (cells && (double)N * R * d * 8.0 <= 16.0 * (1ull << 30))
     VD_CK(mc->bufs.alloc_n(&mc->u, (size_t)N * R * d), "mc alloc");
   vd::RaySource rs;
@@ -475,7 +475,7 @@ static vd_status mc_run(vd_ctx* ctx, const TreeView& tv, double* Xd, int64_t N, 
       VD_CK(vd::launch_mc_walk_tc(tv, R, seed, set, ro, ctx->ctr, ctx->cfg.wait_limit, ctx->st,
                                   &mc->stats.fallback_rays),
             "mc walk tc");
-    else if (tv.K > 0 && prec != VD_FP64)
+    else if (tv.K > 0)  // binary32 screening, or every pair in binary64 (same list scan)
       VD_CK(vd::launch_mc_cells(tv, R, seed, set, ro, prec, ctx->ctr, ctx->st, &mc->stats.fallback_rays),
             "mc cells");
     else

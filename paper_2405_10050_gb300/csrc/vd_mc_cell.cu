@@ -230,6 +230,136 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
   __syncthreads();
 }
 
+// Shared memory of one cell on the binary64 path: offsets [D][K] and |w|^2
+// in binary64, distance bounds and ids.
+__host__ __device__ inline size_t cell_smem_f64(int D, int K) { return (size_t)K * (8 * D + 16); }
+
+// All R rays of cell i with every pair in binary64 (VD_FP64): the same list,
+// order and exit test as cell_item, each candidate's t_j = |w|^2 / (2 u.w)
+// in the canonical order (w, |w|^2 and u.w summed left to right), the box
+// faces in binary64.  The division is skipped when the binary64 product
+// shows t_j above the current best by more than the rounding of t_j.
+template <int D, int TH>
+__device__ void cell_item_f64(const TreeView& tr, int64_t i, int64_t R, uint64_t seed, uint32_t set,
+                              int32_t* hit_out, double* t_out, double* smem, Counters* ctr, int32_t* fb_cell,
+                              int32_t* fb_ray, int64_t fb_cap, unsigned long long& n_pairs,
+                              unsigned long long* fb_count, double* u_out) {
+  const int K = tr.K;
+  const int d = tr.d;
+  double* sw = smem;                                 // [D][K] w = x_j - x_i
+  double* sww = sw + D * K;                          // |w|^2
+  float* sflo = reinterpret_cast<float*>(sww + K);   // lower bound of |x_j - x_i|^2 in list order
+  int32_t* sid = reinterpret_cast<int32_t*>(sflo + K);
+  const int tid = threadIdx.x;
+  const float B = tr.coord_abs;
+  const float gam = (float)(D + 1) * kU32 * 1.01f;
+  const float EW = 4.01f * kU32 * B;
+  const int n = tr.kcnt[i];
+  double g64[D];
+  float g32[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    g64[k] = k < d ? tr.X[i * d + k] : 0.0;
+    g32[k] = k < d ? tr.X32[i * d + k] : 0.f;
+  }
+  for (int c = tid; c < n; c += TH) {
+    const int32_t id = tr.knn[i * K + c];
+    double ww = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double w = k < d ? __dadd_rn(tr.X[(int64_t)id * d + k], -g64[k]) : 0.0;
+      sw[k * K + c] = w;
+      if (k < d) ww = __dadd_rn(ww, __dmul_rn(w, w));
+    }
+    sww[c] = ww;
+    sflo[c] = true_d2_lower(ww32_of<D>(tr.X32 + (int64_t)id * d, 1, g32, d), gam, EW, D);
+    sid[c] = id;
+  }
+  const float cert_lo = true_d2_lower(tr.kcert[i], gam, EW, D);
+  __syncthreads();
+  for (int64_t k = tid; k < R; k += TH) {
+    double u64[D];
+    mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u64);
+    if (u_out) {
+#pragma unroll
+      for (int q = 0; q < D; ++q)
+        if (q < d) u_out[(i * R + k) * d + q] = u64[q];
+    }
+    float u32[D], p0[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      u32[q] = __double2float_rn(u64[q]);
+      p0[q] = 0.f;
+    }
+    double bt = INFINITY;
+    int bc = 2, bk = 0;
+    for (int a = 0; a < d; ++a) {  // box faces, t = (b - x_ia) / u_a
+      double ua = 0.0, va = 0.0;
+#pragma unroll
+      for (int q = 0; q < D; ++q)
+        if (q == a) {
+          ua = u64[q];
+          va = g64[q];
+        }
+      if (ua == 0.0) continue;
+      const int sd = ua > 0.0 ? 1 : 0;
+      const double t = __ddiv_rn(__dadd_rn(sd ? 1.0 : 0.0, -va), ua);
+      if (better(t, 1, 2 * a + sd, bt, bc, bk)) {
+        bt = t;
+        bc = 1;
+        bk = 2 * a + sd;
+      }
+    }
+    // reach of the ball of the current best (binary32, rounded up)
+    auto reach = [&]() {
+      Ball<D> ball;
+      make_ball<D>(g32, p0, u32, f32_up(bt), B, ball);
+      return far_radius2<D>(tr, ball, g32);
+    };
+    float far2 = reach();
+    bool certified = false;
+    int c = 0;
+    for (; c < n; ++c) {
+      if (sflo[c] >= far2) {  // this and every later candidate lie outside the ball
+        certified = true;
+        break;
+      }
+      double den = 0.0;
+#pragma unroll
+      for (int q = 0; q < D; ++q)
+        if (q < d) den = __dadd_rn(den, __dmul_rn(u64[q], sw[q * K + c]));
+      if (!(den > 0.0)) continue;
+      const double ww = sww[c];
+      // ww > 2 den bt (1 + 2^-50), evaluated with two roundings, implies
+      // ww / (2 den) > bt (1 + 2^-51): the rounded t_j exceeds bt
+      if (bt < INFINITY && ww > __dmul_rn(__dmul_rn(__dmul_rn(2.0, den), bt), 1.0 + 0x1p-50)) continue;
+      const double t = __ddiv_rn(ww, __dmul_rn(2.0, den));  // num = |w|^2 since v = g
+      if (better(t, 0, sid[c], bt, bc, bk)) {
+        bt = t;
+        bc = 0;
+        bk = sid[c];
+        far2 = reach();
+      }
+    }
+    n_pairs += (unsigned long long)c;
+    if (!certified) certified = cert_lo >= far2;
+    if (!certified) {  // the binary64 tree walk finishes the ray
+      const unsigned long long q = atomicAdd(fb_count, 1ull);
+      if ((int64_t)q < fb_cap) {
+        fb_cell[q] = (int32_t)i;
+        fb_ray[q] = (int32_t)k;
+      } else {
+        atomicOr(&ctr->flags, kFlagQueue);
+      }
+      t_out[i * R + k] = bt;
+      continue;
+    }
+    hit_out[i * R + k] = gen_from_key(bc, bk);
+    t_out[i * R + k] = bt;
+  }
+  __syncthreads();
+}
+
 template <int TH>
 __device__ __forceinline__ void flush_counters(Counters* ctr, unsigned long long n_pairs, unsigned long long n_rech,
                                                unsigned long long n_brute) {
@@ -245,7 +375,7 @@ __device__ __forceinline__ void flush_counters(Counters* ctr, unsigned long long
   }
 }
 
-template <int D>
+template <int D, bool F64>
 __global__ void __launch_bounds__(kCellThreads) k_mc_cell(TreeView tr, int64_t R, uint64_t seed, uint32_t set,
                                                           RayOut ro, Counters* ctr, unsigned long long* work,
                                                           int32_t* fb_cell, int32_t* fb_ray, int64_t fb_cap) {
@@ -258,8 +388,12 @@ __global__ void __launch_bounds__(kCellThreads) k_mc_cell(TreeView tr, int64_t R
     const int64_t i = s_cell;
     __syncthreads();
     if (i >= tr.N) break;
-    cell_item<D, kCellThreads>(tr, i, R, seed, set, ro.hit, ro.t, smem, ctr, fb_cell, fb_ray, fb_cap,
-                                      n_pairs, n_rech, n_brute, &ctr->fallback, ro.u);
+    if constexpr (F64)
+      cell_item_f64<D, kCellThreads>(tr, i, R, seed, set, ro.hit, ro.t, reinterpret_cast<double*>(smem), ctr,
+                                     fb_cell, fb_ray, fb_cap, n_pairs, &ctr->fallback, ro.u);
+    else
+      cell_item<D, kCellThreads>(tr, i, R, seed, set, ro.hit, ro.t, smem, ctr, fb_cell, fb_ray, fb_cap, n_pairs,
+                                 n_rech, n_brute, &ctr->fallback, ro.u);
   }
   flush_counters<kCellThreads>(ctr, n_pairs, n_rech, n_brute);
 }
@@ -309,20 +443,21 @@ __global__ void __launch_bounds__(TH) k_mc_cell_batch(const SetDesc* sets, int n
   flush_counters<TH>(ctr, n_pairs, n_rech, n_brute);
 }
 
-template <int D>
+template <int D, bool F64>
 cudaError_t launch_cell_d(const TreeView& tv, int64_t R, uint64_t seed, uint32_t set, const RayOut& ro,
                           Counters* ctr, unsigned long long* work, int32_t* fb_cell, int32_t* fb_ray,
                           int64_t fb_cap, cudaStream_t st) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const size_t sm = cell_smem(D, tv.K, kCellThreads);
-  cudaFuncSetAttribute(k_mc_cell<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = F64 ? cell_smem_f64(D, tv.K) : cell_smem(D, tv.K, kCellThreads);
+  cudaFuncSetAttribute(k_mc_cell<D, F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mc_cell<D>, kCellThreads, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mc_cell<D, F64>, kCellThreads, sm);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1), tv.N));
   cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
-  k_mc_cell<D><<<(unsigned)grid, kCellThreads, sm, st>>>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap);
+  k_mc_cell<D, F64><<<(unsigned)grid, kCellThreads, sm, st>>>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray,
+                                                              fb_cap);
   count_launch();
   return cudaGetLastError();
 }
@@ -347,8 +482,9 @@ cudaError_t launch_batch_th(const SetDesc* sets, int nsets, int64_t nitems, int 
 
 }  // namespace
 
-// Casts all N*R MC rays of the node set with the cell kernel (lists needed);
-// rays it cannot certify are finished by the generic kernels.
+// Casts all N*R MC rays of the node set with the cell kernel (lists needed;
+// binary32 screening, or every pair in binary64 for VD_FP64); rays it cannot
+// certify are finished by the generic kernels on the same precision.
 cudaError_t launch_mc_cells(const TreeView& tv, int64_t R, uint64_t seed, uint32_t set, const RayOut& ro,
                             int precision, Counters* ctr, cudaStream_t st, int64_t* nfallback) {
   unsigned long long* work = reinterpret_cast<unsigned long long*>(&ctr->aux1);
@@ -357,15 +493,20 @@ cudaError_t launch_mc_cells(const TreeView& tv, int64_t R, uint64_t seed, uint32
   const int64_t fb_cap = ro.fallback_cap / 2;
   cudaMemsetAsync(&ctr->fallback, 0, sizeof(unsigned long long), st);
   cudaError_t e;
+  const bool f64 = precision == VD_FP64;
+#define VD_CELL(DD)                                                                                  \
+  (f64 ? launch_cell_d<DD, true>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st)      \
+       : launch_cell_d<DD, false>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st))
   switch (tv.d) {
-    case 1: e = launch_cell_d<1>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
-    case 2: e = launch_cell_d<2>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
-    case 3: e = launch_cell_d<3>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
-    case 4: e = launch_cell_d<4>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
-    case 5: e = launch_cell_d<5>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
-    case 6: e = launch_cell_d<6>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
-    default: e = launch_cell_d<8>(tv, R, seed, set, ro, ctr, work, fb_cell, fb_ray, fb_cap, st); break;
+    case 1: e = VD_CELL(1); break;
+    case 2: e = VD_CELL(2); break;
+    case 3: e = VD_CELL(3); break;
+    case 4: e = VD_CELL(4); break;
+    case 5: e = VD_CELL(5); break;
+    case 6: e = VD_CELL(6); break;
+    default: e = VD_CELL(8); break;
   }
+#undef VD_CELL
   if (e != cudaSuccess) return e;
   unsigned long long nfb = 0;
   cudaMemcpyAsync(&nfb, &ctr->fallback, sizeof(nfb), cudaMemcpyDeviceToHost, st);

@@ -144,15 +144,28 @@ __global__ void k_lz_facet_list(const int32_t* tuples, int d, int64_t N, const i
   if (mode == 0 && lane == 0) fcnt[i] = c;
 }
 
-// One thread per facet (i, j): the pyramid over it with apex x_i, walked
-// from the facet (level 2) down to its edges; writes the pyramid's volume
-// and integral (Vp, Fp) and the facet's A_ij, Fd_ij.
-__global__ void k_lz_facets(const double* X, int64_t N, int d, const int32_t* tuples, const double* coords,
-                            const int64_t* voff, const int32_t* vlist, const int32_t* col, const int32_t* erow,
-                            const int64_t* m2off, int64_t nnz, int32_t* scratch, vd_func f, double fact, double* Vp,
-                            double* Fp, double* A, double* Fd, unsigned* flags) {
+// Sort keys of the facets by decreasing vertex count (the stable sort keeps
+// the CSR order among equal counts): a warp then walks pyramids of similar
+// size.
+__global__ void k_lz_order_keys(const int64_t* m2off, int64_t nnz, uint64_t* keys, int32_t* vals) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= nnz) return;
+  const int64_t n2 = m2off[e + 1] - m2off[e];
+  keys[e] = 0xFFFFFFFFull - (uint64_t)(n2 < 0xFFFFFFFFll ? n2 : 0xFFFFFFFFll);
+  vals[e] = (int32_t)e;
+}
+
+// One thread per facet (i, j), facet e = order[t] of thread t: the pyramid
+// over it with apex x_i, walked from the facet (level 2) down to its edges;
+// writes the pyramid's volume and integral (Vp, Fp) and the facet's A_ij,
+// Fd_ij.
+__global__ void k_lz_facets(const double* X, int64_t N, int d, const int32_t* tuples, const double* coords,
+                            const int64_t* voff, const int32_t* vlist, const int32_t* col, const int32_t* erow,
+                            const int64_t* m2off, int64_t nnz, const int32_t* order, int32_t* scratch, vd_func f,
+                            double fact, double* Vp, double* Fp, double* A, double* Fd, unsigned* flags) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nnz) return;
+  const int64_t e = order[t];
   const int L = d + 1;
   const int64_t i = erow[e];
   const int32_t jf = col[e];
@@ -361,8 +374,16 @@ cudaError_t poly_integrate(const double* X, int64_t N, int d, const int32_t* tup
     const size_t need = (fa.localSizeBytes + 1023) / 1024 * 1024 + 1024;
     if (cur < need && (e = cudaDeviceSetLimit(cudaLimitStackSize, need))) return e;
   }
-  k_lz_facets<<<nb(*nnz, 64), 64, 0, st>>>(X, N, d, tuples, coords, voff, vals, *col, erow, m2off, *nnz, lzs, f, fact,
-                                           Vp, Fp, *A, *Fd, flags);
+  // facets by decreasing vertex count (the first sort's key buffers are free again)
+  int32_t *order = nullptr, *otmp = nullptr;
+  if ((e = scratch.alloc_n(&order, nn)) || (e = scratch.alloc_n(&otmp, nn))) return e;
+  if (*nnz > 0) {
+    k_lz_order_keys<<<nb(*nnz, 256), 256, 0, st>>>(m2off, *nnz, keys, order);
+    count_launch();
+    if ((e = radix_sort_u64(keys, order, ktmp, otmp, *nnz, counts, orand, st))) return e;
+  }
+  k_lz_facets<<<nb(*nnz, 64), 64, 0, st>>>(X, N, d, tuples, coords, voff, vals, *col, erow, m2off, *nnz, order, lzs, f,
+                                           fact, Vp, Fp, *A, *Fd, flags);
   count_launch();
   k_lz_cellsum<<<nb(N, 128), 128, 0, st>>>(X, N, d, *rowptr, Vp, Fp, f, *V, *F);
   count_launch();

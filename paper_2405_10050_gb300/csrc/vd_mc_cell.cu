@@ -24,9 +24,12 @@ namespace {
 constexpr int kCellThreads = 128;
 constexpr int kCellBuf = 8;  // candidates kept per ray
 
-// Shared memory of one cell: offsets [D][K], bounds, ids; per-thread buffers.
+// Shared memory of one cell: offsets [D][K], bounds, ids; per-thread
+// candidate buffers; for the recheck each thread's binary64 direction, the
+// results of its candidates and each warp's list of (ray, candidate) pairs.
 __host__ __device__ inline size_t cell_smem(int D, int K, int threads) {
-  return (size_t)K * (D + 5) * 4 + (size_t)threads * kCellBuf * 8;
+  return (size_t)K * (D + 5) * 4 + (size_t)threads * kCellBuf * 8 + 8 + (size_t)threads * D * 8 +
+         (size_t)threads * kCellBuf * 12;
 }
 
 // All R rays of cell i (see the file comment).  Rays the list cannot
@@ -46,7 +49,13 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
   int32_t* sid = reinterpret_cast<int32_t*>(sflo + K);
   int32_t* bid = sid + K;                // [TH][kCellBuf]
   float* btl = reinterpret_cast<float*>(bid + TH * kCellBuf);
+  double* su64 = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(btl + TH * kCellBuf) + 7) & ~(uintptr_t)7);
+  double* bres = su64 + TH * D;          // [TH][kCellBuf] binary64 t of each candidate
+  int* wpairs = reinterpret_cast<int*>(bres + TH * kCellBuf);  // [TH / 32][32 * kCellBuf]
   const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  double* su = su64 + tid * D;
+  int* wpair = wpairs + (tid >> 5) * 32 * kCellBuf;
   const float B = tr.coord_abs;
   const float gam = (float)(D + 1) * kU32 * 1.01f;
   const float EW = 4.01f * kU32 * B;
@@ -79,14 +88,22 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
   }
   const float cert_lo = true_d2_lower(tr.kcert[i], gam, EW, D);
   __syncthreads();
-  for (int64_t k = tid; k < R; k += TH) {
+  // every thread runs the same rounds (one ray each, k = k0 + tid), so that
+  // the warps can recheck their rays' survivors together
+  for (int64_t k0 = 0; k0 < R; k0 += TH) {
+    const int64_t k = k0 + tid;
+    const bool valid = k < R;
     double u64[D];
-    mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u64);
-    if (u_out) {
+#pragma unroll
+    for (int q = 0; q < D; ++q) u64[q] = 0.0;
+    if (valid) mc_direction<D>(seed, set, (uint32_t)i, (uint32_t)k, d, u64);
+    if (u_out && valid) {
 #pragma unroll
       for (int q = 0; q < D; ++q)
         if (q < d) u_out[(i * R + k) * d + q] = u64[q];
     }
+#pragma unroll
+    for (int q = 0; q < D; ++q) su[q] = u64[q];
     float u32[D], p0[D];
 #pragma unroll
     for (int q = 0; q < D; ++q) {
@@ -96,7 +113,7 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
     // box faces: binary32 interval of (b - x_ia) / u_a
     float T = INFINITY;
     int nc = 0;
-    for (int a = 0; a < d; ++a) {
+    for (int a = 0; a < d && valid; ++a) {
       double ua64 = 0.0;
       float ua = 0.f, va = 0.f;
 #pragma unroll
@@ -127,9 +144,9 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
     Ball<D> ball;
     make_ball<D>(g32, p0, u32, T, B, ball);
     float far2 = far_radius2<D>(tr, ball, g32);
-    bool certified = false, overflow = false;
+    bool certified = !valid, overflow = false;
     int c = 0;
-    for (; c < n; ++c) {
+    for (; c < n && valid; ++c) {
       if (sflo[c] >= far2) {
         certified = true;
         break;
@@ -171,9 +188,8 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
     }
     n_pairs += (unsigned long long)c;
     if (!certified) certified = cert_lo >= far2;
-    double bt = INFINITY;
-    int bc = 2, bk = 0;
-    if (!certified || overflow) {
+    const bool recheck = valid && certified && !overflow;
+    if (valid && !recheck) {  // the tree walk finishes the ray, from the bound found so far
       const unsigned long long q = atomicAdd(fb_count, 1ull);
       if ((int64_t)q < fb_cap) {
         fb_cell[q] = (int32_t)i;
@@ -181,51 +197,77 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
       } else {
         atomicOr(&ctr->flags, kFlagQueue);
       }
-      t_out[i * R + k] = (double)T;  // the bound found so far seeds the tree walk
-      continue;
-    } else {
-      // binary64 recheck of the survivors, canonical order
-      for (int q = 0; q < nc; ++q) {
-        if (!(ct[q] <= T)) continue;
-        const int32_t id = cb[q];
-        ++n_rech;
-        if (id >= 0) {
-          double w[D], den = 0.0, ww = 0.0;
+      t_out[i * R + k] = (double)T;
+    }
+    // ---- binary64 recheck of the warp's survivors, one (ray, candidate)
+    // pair per lane, canonical order; each ray then takes the best of its own
+    int m = 0;
+    if (recheck)
+      for (int q = 0; q < nc; ++q)
+        if (ct[q] <= T) cb[m++] = cb[q];
+    int excl = m;
 #pragma unroll
-          for (int a = 0; a < D; ++a) w[a] = a < d ? __dadd_rn(tr.X[(int64_t)id * d + a], -g64[a]) : 0.0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, excl, o);
+      if (lane >= o) excl += y;
+    }
+    const int total = __shfl_sync(kFull, excl, 31);
+    excl -= m;
+    for (int q = 0; q < m; ++q) wpair[excl + q] = (lane << 8) | q;
+    __syncwarp();
+    for (int p = lane; p < total; p += 32) {
+      const int owner = wpair[p] >> 8, q = wpair[p] & 255;
+      const int ot = (tid & ~31) + owner;  // the owner's thread in the block
+      const int32_t id = bid[ot * kCellBuf + q];
+      const double* uo = su64 + (int64_t)ot * D;
+      double t = NAN;  // NaN: not a candidate (u.w <= 0)
+      if (id >= 0) {
+        double w[D], den = 0.0, ww = 0.0;
 #pragma unroll
-          for (int a = 0; a < D; ++a)
-            if (a < d) den = __dadd_rn(den, __dmul_rn(u64[a], w[a]));
-          if (!(den > 0.0)) continue;
+        for (int a = 0; a < D; ++a) w[a] = a < d ? __dadd_rn(tr.X[(int64_t)id * d + a], -g64[a]) : 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+          if (a < d) den = __dadd_rn(den, __dmul_rn(uo[a], w[a]));
+        if (den > 0.0) {
 #pragma unroll
           for (int a = 0; a < D; ++a)
             if (a < d) ww = __dadd_rn(ww, __dmul_rn(w[a], w[a]));
-          const double t = __ddiv_rn(ww, __dmul_rn(2.0, den));  // num = ww since v = g
-          if (better(t, 0, id, bt, bc, bk)) {
-            bt = t;
-            bc = 0;
-            bk = id;
-          }
-        } else {
-          const int a = face_axis(id), s = face_side(id);
-          double ua = 0.0, va = 0.0;
+          t = __ddiv_rn(ww, __dmul_rn(2.0, den));  // num = ww since v = g
+        }
+      } else {
+        const int a = face_axis(id), s = face_side(id);
+        double ua = 0.0, va = 0.0;
 #pragma unroll
-          for (int q2 = 0; q2 < D; ++q2)
-            if (q2 == a) {
-              ua = u64[q2];
-              va = g64[q2];
-            }
-          const double t = __ddiv_rn(__dadd_rn(s ? 1.0 : 0.0, -va), ua);
-          if (better(t, 1, 2 * a + s, bt, bc, bk)) {
-            bt = t;
-            bc = 1;
-            bk = 2 * a + s;
+        for (int q2 = 0; q2 < D; ++q2)
+          if (q2 == a) {
+            ua = uo[q2];
+            va = g64[q2];
           }
+        t = __ddiv_rn(__dadd_rn(s ? 1.0 : 0.0, -va), ua);
+      }
+      bres[ot * kCellBuf + q] = t;
+    }
+    n_rech += (lane == 0) ? (unsigned long long)total : 0ull;
+    __syncwarp();
+    if (recheck) {
+      double bt = INFINITY;
+      int bc = 2, bk = 0;
+      for (int q = 0; q < m; ++q) {
+        const double t = bres[tid * kCellBuf + q];
+        if (t != t) continue;  // u.w <= 0
+        const int32_t id = cb[q];
+        const int cls = id >= 0 ? 0 : 1;
+        const int key = id >= 0 ? id : 2 * face_axis(id) + face_side(id);
+        if (better(t, cls, key, bt, bc, bk)) {
+          bt = t;
+          bc = cls;
+          bk = key;
         }
       }
+      hit_out[i * R + k] = gen_from_key(bc, bk);
+      t_out[i * R + k] = bt;
     }
-    hit_out[i * R + k] = gen_from_key(bc, bk);
-    t_out[i * R + k] = bt;
+    __syncwarp();  // the next round rewrites the pair list and the results
   }
   __syncthreads();
 }

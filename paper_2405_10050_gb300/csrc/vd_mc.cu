@@ -163,6 +163,155 @@ __device__ __forceinline__ int gather_rays(const int32_t* h, int64_t R, int32_t 
   return m;
 }
 
+// ---- rows sorted by entry (rows with many rays per hit id) ----
+// The warp sorts each chunk of up to kMcList rays of its row by entry
+// (stable: ascending ray order within an entry).  Each lane then sums a
+// contiguous range of the sorted node rays, one run per entry; runs that
+// cross a lane boundary are joined by a segmented scan over the lanes.  The
+// binary64 work thus runs on full warps with one pass over the row, and the
+// order of every sum depends only on the row's hits.
+constexpr int kEnt = kMcList / kFewRays;  // entries of a row on this path
+
+template <int NV>
+struct RowScratch {
+  double acc[kEnt][NV];  // per-entry sums over the chunks so far
+  double cst[kEnt][2];   // per-entry factors
+  int32_t L[kMcList];    // ray offset (in the chunk) of each sorted position
+  int32_t Ej[kMcList];   // entry << 16 | rank within the entry, per ray of the chunk
+  int32_t col[kEnt];     // the row's hit ids, ascending
+  int32_t cnt[kEnt];     // rays of the chunk per entry
+  int32_t st[kEnt];      // first sorted position per entry
+  uint8_t Es[kMcList];   // entry of each sorted position
+};
+
+// Sorts rays k0 .. k0 + C - 1 of the row (hits h, nnz <= kEnt entries in
+// S.col) by entry: S.L, S.Es, S.cnt, S.st.
+template <int NV>
+__device__ void sort_chunk(const int32_t* h, int64_t k0, int C, int nnz, RowScratch<NV>& S, int lane) {
+  for (int e = lane; e < nnz; e += 32) S.cnt[e] = 0;
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int j0 = 0; j0 < C; j0 += 32) {
+    const int j = j0 + lane;
+    const bool valid = j < C;
+    int e = -1;
+    if (valid) {
+      const int32_t id = h[k0 + j];
+      int lo = 0, hi = nnz - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (S.col[mid] < id) lo = mid + 1;
+        else hi = mid;
+      }
+      e = lo;
+    }
+    const unsigned peers = __match_any_sync(kFull, e);
+    const int pre = valid ? S.cnt[e] : 0;
+    __syncwarp();
+    if (valid) {
+      if (lane == __ffs(peers) - 1) S.cnt[e] = pre + __popc(peers);
+      S.Ej[j] = (e << 16) | (pre + __popc(peers & lt));
+    }
+    __syncwarp();
+  }
+  // exclusive scan of the counts (kEnt = 4 x 32)
+  int loc[kEnt / 32], s = 0;
+#pragma unroll
+  for (int t = 0; t < kEnt / 32; ++t) {
+    const int e = lane * (kEnt / 32) + t;
+    loc[t] = e < nnz ? S.cnt[e] : 0;
+    s += loc[t];
+  }
+  int incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  int run = incl - s;
+#pragma unroll
+  for (int t = 0; t < kEnt / 32; ++t) {
+    const int e = lane * (kEnt / 32) + t;
+    if (e < nnz) S.st[e] = run;
+    run += loc[t];
+  }
+  __syncwarp();
+  for (int j = lane; j < C; j += 32) {
+    const int v = S.Ej[j];
+    const int e = v >> 16, p = S.st[e] + (v & 0xFFFF);
+    S.L[p] = j;
+    S.Es[p] = (uint8_t)e;
+  }
+  __syncwarp();
+}
+
+template <int NV, int NR>
+__device__ __forceinline__ void put_acc(double (&a)[NV], const double (&r)[NR], bool first) {
+#pragma unroll
+  for (int v = 0; v < NR; ++v) a[v] = first ? r[v] : __dadd_rn(a[v], r[v]);
+}
+
+// Sums the sorted positions F0 .. C - 1 (node rays) per entry into
+// S.acc[e][0 .. NR); step(run, reset, e, j) adds ray offset j of entry e to
+// run (restarting it when reset).  first: the chunk is the row's first.
+template <int NV, int NR, class Step>
+__device__ __forceinline__ void seg_sums(RowScratch<NV>& S, int F0, int C, bool first, int lane, Step step) {
+  const int M = C - F0;
+  if (M <= 0) return;
+  const int Sz = (M + 31) >> 5;
+  const int beg = F0 + lane * Sz, end = min(beg + Sz, C);
+  double run[NR], hv[NR];
+#pragma unroll
+  for (int v = 0; v < NR; ++v) run[v] = hv[v] = 0.0;
+  int cur = -1, he = -1;
+  bool open = false;
+  for (int jj = 0; jj < Sz; ++jj) {
+    const int p = beg + jj;
+    if (p < end) {
+      const int e = S.Es[p];
+      step(run, e != cur, e, S.L[p]);
+      cur = e;
+      const int s0 = S.st[e];
+      open = p != s0 + S.cnt[e] - 1;
+      if (!open) {
+        if (s0 >= beg) {  // the entry's rays of this chunk lie in this lane's range
+          put_acc<NV, NR>(S.acc[e], run, first);
+        } else {  // it began in an earlier lane: joined after the scan
+          he = e;
+#pragma unroll
+          for (int v = 0; v < NR; ++v) hv[v] = run[v];
+        }
+      }
+    }
+  }
+  // segmented inclusive scan of the open runs at the range ends
+  const int key = open ? cur : -2 - lane;
+  double tv[NR];
+#pragma unroll
+  for (int v = 0; v < NR; ++v) tv[v] = open ? run[v] : 0.0;
+  const int kp = __shfl_up_sync(kFull, key, 1);
+  int f = (lane == 0 || kp != key) ? 1 : 0;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int fu = __shfl_up_sync(kFull, f, o);
+#pragma unroll
+    for (int v = 0; v < NR; ++v) {
+      const double up = __shfl_up_sync(kFull, tv[v], o);
+      if (lane >= o && !f) tv[v] = __dadd_rn(up, tv[v]);
+    }
+    if (lane >= o) f |= fu;
+  }
+  // a run that ended in this lane after beginning in an earlier one: the
+  // previous lane's scan value holds the earlier part
+#pragma unroll
+  for (int v = 0; v < NR; ++v) {
+    const double c = __shfl_up_sync(kFull, tv[v], 1);
+    if (he >= 0) hv[v] = __dadd_rn(c, hv[v]);
+  }
+  if (he >= 0) put_acc<NV, NR>(S.acc[he], hv, first);
+  __syncwarp();
+}
+
 // Area term of ray k of cell i that hit id.
 template <int D>
 __device__ __forceinline__ double area_term(const double* X, int d, int64_t i, int64_t k, int32_t id, double lk,
@@ -181,19 +330,71 @@ __device__ __forceinline__ double area_term(const double* X, int d, int64_t i, i
 template <int D>
 __device__ void fill_item(const double* X, int d, int64_t i, int64_t R, uint64_t seed, uint32_t set,
                           const int32_t* hit, const double* l, const int64_t* rowptr, double cV, double cA, double* V,
-                          int32_t* col, double* A, int32_t* L, double* Ts, int32_t* Es, int lane,
-                          const double* U = nullptr) {
+                          int32_t* col, double* A, RowScratch<2>& S, int lane, const double* U = nullptr) {
   const int32_t* h = hit + i * R;
   const double* li = l + i * R;
-  double vs = 0.0;
-  for (int64_t k = lane; k < R; k += 32) vs = __dadd_rn(vs, ipow_d(li[k], d));
-  vs = warp_sum_d(vs);
-  if (lane == 0) V[i] = __dmul_rn(cV, vs);
   int64_t q = rowptr[i];
   int32_t prev = 0;
   bool first = true;
   const int64_t q0 = q, nnz = rowptr[i + 1] - q0;
+  if (nnz * kFewRays <= R && nnz <= kEnt) {
+    // rows sorted by entry: V and the node areas from the per-entry sums of l^d
+    for (int e = 0;; ++e) {
+      const int32_t id = next_id(h, R, prev, first, lane);
+      if (id == INT32_MAX) break;
+      if (lane == 0) S.col[e] = id;
+      prev = id;
+      first = false;
+    }
+    __syncwarp();
+    int nfe = 0;  // face entries (negative ids) come first
+    for (int e0 = 0; e0 < nnz; e0 += 32) nfe += __popc(__ballot_sync(kFull, e0 + lane < nnz && S.col[e0 + lane] < 0));
+    for (int e = lane; e < nnz; e += 32) col[q0 + e] = S.col[e];
+    for (int64_t k0 = 0; k0 < R; k0 += kMcList) {
+      const int C = R - k0 < kMcList ? (int)(R - k0) : kMcList;
+      const bool fst = k0 == 0;
+      sort_chunk<2>(h, k0, C, (int)nnz, S, lane);
+      if (fst)
+        for (int e = lane; e < nnz; e += 32) S.acc[e][0] = S.acc[e][1] = 0.0;
+      __syncwarp();
+      for (int e = 0; e < nfe; ++e) {  // face entries: l^d and the area terms, a warp per entry
+        const int s0 = S.st[e], n = S.cnt[e];
+        if (n == 0) continue;
+        double r[2] = {0.0, 0.0};
+        for (int p = s0 + lane; p < s0 + n; p += 32) {
+          const int64_t k = k0 + S.L[p];
+          r[0] = __dadd_rn(r[0], ipow_d(li[k], d));
+          r[1] = __dadd_rn(r[1], area_term<D>(X, d, i, k, S.col[e], li[k], seed, set, U, R));
+        }
+        r[0] = warp_sum_d(r[0]);
+        r[1] = warp_sum_d(r[1]);
+        if (lane == 0) put_acc<2, 2>(S.acc[e], r, fst);
+      }
+      __syncwarp();
+      const int F0 = nfe < nnz ? S.st[nfe] : C;
+      seg_sums<2, 1>(S, F0, C, fst, lane, [&](double (&run)[1], bool reset, int, int j) {
+        run[0] = __dadd_rn(reset ? 0.0 : run[0], ipow_d(li[k0 + j], d));
+      });
+    }
+    double vs = 0.0;
+    for (int e = lane; e < nnz; e += 32) {
+      const int32_t id = S.col[e];
+      const double s = S.acc[e][0];
+      vs = __dadd_rn(vs, s);
+      // node hit: the factor 2 / |x_j - x_i| is applied once per entry
+      A[q0 + e] = __dmul_rn(cA, id >= 0 ? node_area_term<D>(X, d, i, id, s) : S.acc[e][1]);
+    }
+    vs = warp_sum_d(vs);
+    if (lane == 0) V[i] = __dmul_rn(cV, vs);
+    return;
+  }
+  double vs = 0.0;
+  for (int64_t k = lane; k < R; k += 32) vs = __dadd_rn(vs, ipow_d(li[k], d));
+  vs = warp_sum_d(vs);
+  if (lane == 0) V[i] = __dmul_rn(cV, vs);
   if (nnz * kFewRays > R) {  // few rays per id: terms ray-parallel, sums in ascending ray order
+    double* Ts = &S.acc[0][0];
+    int32_t* Es = S.Ej;
     while (true) {
       const int32_t id = next_id(h, R, prev, first, lane);
       if (id == INT32_MAX) break;
@@ -221,6 +422,8 @@ __device__ void fill_item(const double* X, int d, int64_t i, int64_t R, uint64_t
     for (int64_t e = q0 + lane; e < q0 + nnz; e += 32) A[e] = __dmul_rn(cA, A[e]);
     return;
   }
+  // more entries than the sorted path holds: one pass over the row per id
+  int32_t* L = S.L;
   while (true) {
     const int32_t id = next_id(h, R, prev, first, lane);
     if (id == INT32_MAX) break;
@@ -253,14 +456,12 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill(const double* X, int6
                                                            const double* l, const int64_t* rowptr, double cV,
                                                            double cA, double* V, int32_t* col, double* A,
                                                            const double* U) {
-  __shared__ int32_t Ls[kMcWarps][kMcList];
-  __shared__ double Ts[kMcWarps][32];
-  __shared__ int32_t Es[kMcWarps][32];
+  extern __shared__ __align__(16) unsigned char row_smem[];
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= N) return;
-  const int w = threadIdx.x >> 5;
-  fill_item<D>(X, d, i, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, Ls[w], Ts[w], Es[w], lane, U);
+  RowScratch<2>& S = reinterpret_cast<RowScratch<2>*>(row_smem)[threadIdx.x >> 5];
+  fill_item<D>(X, d, i, R, seed, set, hit, l, rowptr, cV, cA, V, col, A, S, lane, U);
 }
 
 // ---- function integrals F_d, F_V (Algorithm 3's F and F_V) ----
@@ -316,12 +517,11 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_func(const double* X, int6
                                                            const double* l, const int64_t* rowptr,
                                                            const int32_t* col, const double* U, vd_func f,
                                                            int64_t m, double cV, double cA, double* FV, double* Fd) {
-  __shared__ int32_t Ls[kMcWarps][kMcList];
-  __shared__ double Ts[kMcWarps][32];
-  __shared__ int32_t Es[kMcWarps][32];
+  extern __shared__ __align__(16) unsigned char row_smem[];
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= N) return;
+  RowScratch<1>& S = reinterpret_cast<RowScratch<1>*>(row_smem)[threadIdx.x >> 5];
   const int32_t* h = hit + i * R;
   const double* li = l + i * R;
   if (FV) {
@@ -349,6 +549,8 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_func(const double* X, int6
   if (!Fd) return;
   const int64_t q0 = rowptr[i], nnz = rowptr[i + 1] - q0;
   if (nnz * kFewRays > R) {  // few rays per id: terms ray-parallel, sums in ascending ray order
+    double* Ts = &S.acc[0][0];
+    int32_t* Es = S.Ej;
     for (int64_t e = q0 + lane; e < q0 + nnz; e += 32) Fd[e] = 0.0;
     __syncwarp();
     for (int64_t k0 = 0; k0 < R; k0 += 32) {
@@ -359,15 +561,58 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_func(const double* X, int6
         ray_dir<D>(U, seed, set, i, k, R, d, u);
         ray_point<D>(X, d, i, li[k], u, r);
         const double a = id >= 0 ? node_area_term<D>(X, d, i, id, ipow_d(li[k], d)) : face_term<D>(li[k], d, id, u);
-        Es[w][lane] = (int32_t)(entry_of(col, q0, nnz, id) - q0);
-        Ts[w][lane] = __dmul_rn(func_at<D>(f, d, r), a);
+        Es[lane] = (int32_t)(entry_of(col, q0, nnz, id) - q0);
+        Ts[lane] = __dmul_rn(func_at<D>(f, d, r), a);
       }
       __syncwarp();
       if (lane == 0)
-        for (int r2 = 0; r2 < 32 && k0 + r2 < R; ++r2) Fd[q0 + Es[w][r2]] = __dadd_rn(Fd[q0 + Es[w][r2]], Ts[w][r2]);
+        for (int r2 = 0; r2 < 32 && k0 + r2 < R; ++r2) Fd[q0 + Es[r2]] = __dadd_rn(Fd[q0 + Es[r2]], Ts[r2]);
       __syncwarp();
     }
     for (int64_t e = q0 + lane; e < q0 + nnz; e += 32) Fd[e] = __dmul_rn(cA, Fd[e]);
+    return;
+  }
+  if (nnz <= kEnt) {  // rows sorted by entry, the sums of the fill with f's factor on every ray
+    for (int e = lane; e < nnz; e += 32) S.col[e] = col[q0 + e];
+    __syncwarp();
+    int nfe = 0;
+    for (int e0 = 0; e0 < nnz; e0 += 32) nfe += __popc(__ballot_sync(kFull, e0 + lane < nnz && S.col[e0 + lane] < 0));
+    for (int64_t k0 = 0; k0 < R; k0 += kMcList) {
+      const int C = R - k0 < kMcList ? (int)(R - k0) : kMcList;
+      const bool fst = k0 == 0;
+      sort_chunk<1>(h, k0, C, (int)nnz, S, lane);
+      if (fst)
+        for (int e = lane; e < nnz; e += 32) S.acc[e][0] = 0.0;
+      __syncwarp();
+      for (int e = 0; e < nfe; ++e) {
+        const int s0 = S.st[e], n = S.cnt[e];
+        if (n == 0) continue;
+        double r[1] = {0.0};
+        for (int p = s0 + lane; p < s0 + n; p += 32) {
+          const int64_t k = k0 + S.L[p];
+          double u[D], y[D];
+          ray_dir<D>(U, seed, set, i, k, R, d, u);
+          ray_point<D>(X, d, i, li[k], u, y);
+          r[0] = __dadd_rn(r[0], __dmul_rn(func_at<D>(f, d, y), face_term<D>(li[k], d, S.col[e], u)));
+        }
+        r[0] = warp_sum_d(r[0]);
+        if (lane == 0) put_acc<1, 1>(S.acc[e], r, fst);
+      }
+      __syncwarp();
+      const int F0 = nfe < nnz ? S.st[nfe] : C;
+      seg_sums<1, 1>(S, F0, C, fst, lane, [&](double (&run)[1], bool reset, int, int j) {
+        const int64_t k = k0 + j;
+        double u[D], y[D];
+        ray_dir<D>(U, seed, set, i, k, R, d, u);
+        ray_point<D>(X, d, i, li[k], u, y);
+        run[0] = __dadd_rn(reset ? 0.0 : run[0], __dmul_rn(func_at<D>(f, d, y), ipow_d(li[k], d)));
+      });
+    }
+    for (int e = lane; e < nnz; e += 32) {
+      const int32_t id = S.col[e];
+      const double s = S.acc[e][0];
+      Fd[q0 + e] = __dmul_rn(cA, id >= 0 ? node_area_term<D>(X, d, i, id, s) : s);
+    }
     return;
   }
   for (int64_t e = q0; e < q0 + nnz; ++e) {
@@ -375,9 +620,9 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_func(const double* X, int6
     double s = 0.0;
     int64_t k0 = 0;
     while (k0 < R) {
-      const int mm = gather_rays(h, R, id, &k0, Ls[w], lane);
+      const int mm = gather_rays(h, R, id, &k0, S.L, lane);
       for (int p = lane; p < mm; p += 32) {
-        const int32_t k = Ls[w][p];
+        const int32_t k = S.L[p];
         double u[D], r[D];
         ray_dir<D>(U, seed, set, i, k, R, d, u);
         ray_point<D>(X, d, i, li[k], u, r);
@@ -451,21 +696,17 @@ __global__ void k_scan_batch(const SetDesc* sets) {
 
 __global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill_batch(const SetDesc* sets, int nsets, int64_t nitems,
                                                                  int64_t R, uint64_t seed) {
-  __shared__ int32_t Ls[kMcWarps][kMcList];
-  __shared__ double Tss[kMcWarps][32];
-  __shared__ int32_t Ess[kMcWarps][32];
+  extern __shared__ __align__(16) unsigned char row_smem[];
   const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (item >= nitems) return;
-  const SetDesc& S = sets[find_set(sets, nsets, item)];
-  const int64_t i = item - S.item0;
-  int32_t* L = Ls[threadIdx.x >> 5];
-  double* Ts = Tss[threadIdx.x >> 5];
-  int32_t* Es = Ess[threadIdx.x >> 5];
-  switch (S.tv.d) {
+  const SetDesc& SD = sets[find_set(sets, nsets, item)];
+  const int64_t i = item - SD.item0;
+  RowScratch<2>& S = reinterpret_cast<RowScratch<2>*>(row_smem)[threadIdx.x >> 5];
+  switch (SD.tv.d) {
 #define VD_FILL(DD)                                                                                              \
   case DD:                                                                                                       \
-    fill_item<DD>(S.tv.X, S.tv.d, i, R, seed, S.set, S.hit, S.l, S.rowptr, S.cV, S.cA, S.V, S.col, S.A, L, Ts, Es, \
+    fill_item<DD>(SD.tv.X, SD.tv.d, i, R, seed, SD.set, SD.hit, SD.l, SD.rowptr, SD.cV, SD.cA, SD.V, SD.col, SD.A, S, \
                   lane);                                                                                        \
     break;
     VD_FILL(1)
@@ -475,7 +716,7 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill_batch(const SetDesc* 
     VD_FILL(5)
     VD_FILL(6)
     default:
-      fill_item<8>(S.tv.X, S.tv.d, i, R, seed, S.set, S.hit, S.l, S.rowptr, S.cV, S.cA, S.V, S.col, S.A, L, Ts, Es,
+      fill_item<8>(SD.tv.X, SD.tv.d, i, R, seed, SD.set, SD.hit, SD.l, SD.rowptr, SD.cV, SD.cA, SD.V, SD.col, SD.A, S,
                    lane);
       break;
 #undef VD_FILL
@@ -493,17 +734,16 @@ __device__ __forceinline__ void adj_contrib(const double* X, int d, int64_t i, i
   ray_dir<D>(U, seed, set, i, k, R, d, u);
   const double ld1 = ipow_d(lk, d - 1), ld = ipow_d(lk, d);
   if (id >= 0) {
-    double w[D], den = 0.0, ww = 0.0;
+    double w[D], ww = 0.0;
 #pragma unroll
     for (int c = 0; c < D; ++c) w[c] = c < d ? __dadd_rn(X[(int64_t)id * d + c], -X[i * d + c]) : 0.0;
 #pragma unroll
     for (int c = 0; c < D; ++c)
-      if (c < d) den = __dadd_rn(den, __dmul_rn(u[c], w[c]));
-#pragma unroll
-    for (int c = 0; c < D; ++c)
       if (c < d) ww = __dadd_rn(ww, __dmul_rn(w[c], w[c]));
     const double inw = rsqrt(ww);
-    const double iden = 1.0 / den;
+    // the saved length is l = |w|^2 / (2 u.w) (Eq. (t) with v = g), so
+    // 1 / (u.w) = 2 l / |w|^2 up to one rounding of l
+    const double iden = 2.0 * lk / ww;
     const double c1 = 2.0 * (double)d * ld1 * inw, c2 = 2.0 * ld * inw * inw * inw;
     const double kV = gVi * cV * (double)d * ld1, kA = gAij * cA;
 #pragma unroll
@@ -527,68 +767,13 @@ __device__ __forceinline__ void adj_contrib(const double* X, int d, int64_t i, i
   }
 }
 
-// Row pass of the adjoint: P[q][*] = sum over the rays of cell i that hit
-// col[q] of dLoss/dw (node) ; own[i][*] = face terms of x_i.  The rays of a
-// column are gathered first so the binary64 work runs on full warps; rows
-// with few rays per entry compute 32 rays at once and add them per entry in
-// ascending ray order, the lanes splitting the components.
+// Row pass for rows with more entries than the sorted path holds: the rays
+// of each entry gathered in one pass over the row per entry.
 template <int D>
-__global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, int64_t N, int d, int64_t R,
-                                                               uint64_t seed, uint32_t set, const int32_t* hit,
-                                                               const double* l, const int64_t* rowptr,
-                                                               const int32_t* col, double cV, double cA,
-                                                               const double* gV, const double* gA, double* P,
-                                                               double* own, const double* U) {
-  __shared__ int32_t Ls[kMcWarps][kMcList];
-  __shared__ double Cs[kMcWarps][32][D + 1];
-  __shared__ int32_t Es[kMcWarps][32];
-  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= N) return;
-  const int wb = threadIdx.x >> 5;
-  int32_t* L = Ls[wb];
-  const int32_t* h = hit + i * R;
-  const double* li = l + i * R;
-  const double gVi = gV[i];
-  const int64_t q0 = rowptr[i], nnz = rowptr[i + 1] - q0;
-  if (nnz * kFewRays > R) {
-    for (int64_t e = lane; e < nnz * d; e += 32) P[q0 * d + e] = 0.0;
-    __syncwarp();
-    for (int64_t k0 = 0; k0 < R; k0 += 32) {
-      const int64_t k = k0 + lane;
-      if (k < R) {
-        const int32_t id = h[k];
-        const int64_t q = entry_of(col, q0, nnz, id);
-        double v[D];
-#pragma unroll
-        for (int c = 0; c < D; ++c) v[c] = 0.0;
-        adj_contrib<D>(X, d, i, k, id, li[k], gVi, gA ? gA[q] : 0.0, cV, cA, seed, set, U, R, v);
-#pragma unroll
-        for (int c = 0; c < D; ++c) Cs[wb][lane][c] = v[c];
-        Es[wb][lane] = (int32_t)(q - q0);
-      }
-      __syncwarp();
-      if (lane < d)
-        for (int r = 0; r < 32 && k0 + r < R; ++r) {
-          double* pe = P + (q0 + Es[wb][r]) * d + lane;
-          *pe += Cs[wb][r][lane];
-        }
-      __syncwarp();
-    }
-    if (lane < d) {  // x_i's own term: minus its node entries, plus its face entries, in entry order
-      double o = 0.0;
-      for (int64_t e = 0; e < nnz; ++e) {
-        const double v = P[(q0 + e) * d + lane];
-        o = col[q0 + e] >= 0 ? o - v : o + v;
-      }
-      own[i * d + lane] = o;
-    }
-    __syncwarp();
-    for (int64_t e = lane; e < nnz; e += 32)
-      if (col[q0 + e] < 0)
-        for (int c = 0; c < d; ++c) P[(q0 + e) * d + c] = 0.0;
-    return;
-  }
+__device__ void adj_rows_by_id(const double* X, int d, int64_t i, int64_t R, uint64_t seed, uint32_t set,
+                               const int32_t* h, const double* li, int64_t q0, int64_t nnz, const int32_t* col,
+                               double cV, double cA, double gVi, const double* gA, double* P, double* own,
+                               const double* U, int32_t* L, int lane) {
   double faceacc[D];
 #pragma unroll
   for (int c = 0; c < D; ++c) faceacc[c] = 0.0;
@@ -610,6 +795,9 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
       const double inw = rsqrt(ww);
       const double kA = gAij * cA;
       const double cwa = 2.0 * (double)d * inw, cwb = 2.0 * inw * inw * inw;
+      // 1 / (u.w) = 2 l / |w|^2 for every ray of the entry (l = |w|^2 / (2 u.w))
+      const double c2w = 2.0 / ww;
+      const double cg = gVi * cV * (double)d + kA * cwa;
       double asum = 0.0, bu[D];
 #pragma unroll
       for (int c = 0; c < D; ++c) bu[c] = 0.0;
@@ -621,12 +809,8 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
           const double lk = li[k];
           double u[D];
           ray_dir<D>(U, seed, set, i, k, R, d, u);
-          double den = 0.0;
-#pragma unroll
-          for (int c = 0; c < D; ++c)
-            if (c < d) den = __dadd_rn(den, __dmul_rn(u[c], w[c]));
           const double ld1 = ipow_d(lk, d - 1), ld = ld1 * lk;
-          const double g = (gVi * cV * (double)d * ld1 + kA * cwa * ld1) / den;  // coefficient of dl
+          const double g = cg * ld * c2w;  // coefficient of dl: (gV cV d + kA cwa) l^(d-1) / (u.w)
           asum += g - kA * cwb * ld;
           const double b = g * lk;
 #pragma unroll
@@ -666,6 +850,178 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
     for (int c = 0; c < d; ++c) own[i * d + c] = faceacc[c];
 }
 
+// Row pass of the adjoint: P[q][*] = sum over the rays of cell i that hit
+// col[q] of dLoss/dw (node) ; own[i][*] = face terms of x_i minus the node
+// entries.  Rows with many rays per entry are sorted by entry: every lane
+// sums a range of the sorted node rays (the scalar a_k and the vector
+// b_k u_k of each entry, P = (sum a_k) w - sum b_k u_k), face entries take a
+// warp each.  Rows with few rays per entry compute 32 rays at once and add
+// them per entry in ascending ray order, the lanes splitting the components.
+template <int D>
+__global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, int64_t N, int d, int64_t R,
+                                                               uint64_t seed, uint32_t set, const int32_t* hit,
+                                                               const double* l, const int64_t* rowptr,
+                                                               const int32_t* col, double cV, double cA,
+                                                               const double* gV, const double* gA, double* P,
+                                                               double* own, const double* U) {
+  extern __shared__ __align__(16) unsigned char row_smem[];
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;
+  RowScratch<D + 1>& S = reinterpret_cast<RowScratch<D + 1>*>(row_smem)[threadIdx.x >> 5];
+  const int32_t* h = hit + i * R;
+  const double* li = l + i * R;
+  const double gVi = gV[i];
+  const int64_t q0 = rowptr[i], nnz = rowptr[i + 1] - q0;
+  if (nnz * kFewRays > R) {
+    double(*Cs)[D + 1] = S.acc;
+    int32_t* Es = S.Ej;
+    for (int64_t e = lane; e < nnz * d; e += 32) P[q0 * d + e] = 0.0;
+    __syncwarp();
+    for (int64_t k0 = 0; k0 < R; k0 += 32) {
+      const int64_t k = k0 + lane;
+      if (k < R) {
+        const int32_t id = h[k];
+        const int64_t q = entry_of(col, q0, nnz, id);
+        double v[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) v[c] = 0.0;
+        adj_contrib<D>(X, d, i, k, id, li[k], gVi, gA ? gA[q] : 0.0, cV, cA, seed, set, U, R, v);
+#pragma unroll
+        for (int c = 0; c < D; ++c) Cs[lane][c] = v[c];
+        Es[lane] = (int32_t)(q - q0);
+      }
+      __syncwarp();
+      if (lane < d)
+        for (int r = 0; r < 32 && k0 + r < R; ++r) {
+          double* pe = P + (q0 + Es[r]) * d + lane;
+          *pe += Cs[r][lane];
+        }
+      __syncwarp();
+    }
+    if (lane < d) {  // x_i's own term: minus its node entries, plus its face entries, in entry order
+      double o = 0.0;
+      for (int64_t e = 0; e < nnz; ++e) {
+        const double v = P[(q0 + e) * d + lane];
+        o = col[q0 + e] >= 0 ? o - v : o + v;
+      }
+      own[i * d + lane] = o;
+    }
+    __syncwarp();
+    for (int64_t e = lane; e < nnz; e += 32)
+      if (col[q0 + e] < 0)
+        for (int c = 0; c < d; ++c) P[(q0 + e) * d + c] = 0.0;
+    return;
+  }
+  if (nnz > kEnt) {  // more entries than the sorted path holds: one pass over the row per entry
+    adj_rows_by_id<D>(X, d, i, R, seed, set, h, li, q0, nnz, col, cV, cA, gVi, gA, P, own, U, S.L, lane);
+    return;
+  }
+  // per-entry factors: node entries a_k = c0 l^d - c1 l^d, b_k = c0 l^(d+1)
+  // (from 1 / (u.w) = 2 l / |w|^2), face entries keep gA
+  for (int e = lane; e < nnz; e += 32) {
+    const int32_t id = col[q0 + e];
+    S.col[e] = id;
+    const double gAij = gA ? gA[q0 + e] : 0.0;
+    if (id >= 0) {
+      double ww = 0.0;
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        if (c < d) {
+          const double w = __dadd_rn(X[(int64_t)id * d + c], -X[i * d + c]);
+          ww = __dadd_rn(ww, __dmul_rn(w, w));
+        }
+      const double inw = rsqrt(ww);
+      const double kA = gAij * cA;
+      const double cwa = 2.0 * (double)d * inw, cwb = 2.0 * inw * inw * inw;
+      const double cg = gVi * cV * (double)d + kA * cwa;
+      S.cst[e][0] = cg * (2.0 / ww);
+      S.cst[e][1] = kA * cwb;
+    } else {
+      S.cst[e][0] = gAij;
+      S.cst[e][1] = 0.0;
+    }
+  }
+  __syncwarp();
+  int nfe = 0;  // face entries (negative ids) come first
+  for (int e0 = 0; e0 < nnz; e0 += 32) nfe += __popc(__ballot_sync(kFull, e0 + lane < nnz && S.col[e0 + lane] < 0));
+  for (int64_t k0 = 0; k0 < R; k0 += kMcList) {
+    const int C = R - k0 < kMcList ? (int)(R - k0) : kMcList;
+    const bool fst = k0 == 0;
+    sort_chunk<D + 1>(h, k0, C, (int)nnz, S, lane);
+    if (fst)
+      for (int e = lane; e < nnz; e += 32)
+#pragma unroll
+        for (int v = 0; v <= D; ++v) S.acc[e][v] = 0.0;
+    __syncwarp();
+    for (int e = 0; e < nfe; ++e) {  // face entries: the term on the face's axis, a warp per entry
+      const int s0 = S.st[e], n = S.cnt[e];
+      if (n == 0) continue;
+      const int32_t id = S.col[e];
+      const int a = face_axis(id);
+      double r[1] = {0.0};
+      for (int p = s0 + lane; p < s0 + n; p += 32) {
+        const int64_t k = k0 + S.L[p];
+        double v[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) v[c] = 0.0;
+        adj_contrib<D>(X, d, i, k, id, li[k], gVi, S.cst[e][0], cV, cA, seed, set, U, R, v);
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          if (c == a) r[0] = __dadd_rn(r[0], v[c]);
+      }
+      r[0] = warp_sum_d(r[0]);
+      if (lane == 0) put_acc<D + 1, 1>(S.acc[e], r, fst);
+    }
+    __syncwarp();
+    const int F0 = nfe < nnz ? S.st[nfe] : C;
+    seg_sums<D + 1, D + 1>(S, F0, C, fst, lane, [&](double (&run)[D + 1], bool reset, int e, int j) {
+      const int64_t k = k0 + j;
+      const double lk = li[k];
+      double u[D];
+      ray_dir<D>(U, seed, set, i, k, R, d, u);
+      const double ld = __dmul_rn(ipow_d(lk, d - 1), lk);
+      const double g = __dmul_rn(S.cst[e][0], ld);
+      const double b = __dmul_rn(g, lk);
+      run[0] = __dadd_rn(reset ? 0.0 : run[0], __fma_rn(-S.cst[e][1], ld, g));
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        if (c < d) run[1 + c] = __fma_rn(b, u[c], reset ? 0.0 : run[1 + c]);
+    });
+  }
+  // P of the node entries; every entry's vector for x_i's own term
+  for (int e = lane; e < nnz; e += 32) {
+    const int64_t q = q0 + e;
+    const int32_t id = S.col[e];
+    if (id >= 0) {
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        if (c < d) {
+          const double w = __dadd_rn(X[(int64_t)id * d + c], -X[i * d + c]);
+          const double v = __fma_rn(S.acc[e][0], w, -S.acc[e][1 + c]);
+          P[q * d + c] = v;
+          S.acc[e][1 + c] = v;
+        }
+    } else {
+      const int a = face_axis(id);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        if (c < d) P[q * d + c] = 0.0;
+        S.acc[e][1 + c] = c == a ? S.acc[e][0] : 0.0;
+      }
+    }
+  }
+  __syncwarp();
+  if (lane < d) {  // minus the node entries, plus the face entries, in entry order
+    double o = 0.0;
+    for (int e = 0; e < nnz; ++e) {
+      const double v = S.acc[e][1 + lane];
+      o = S.col[e] >= 0 ? __dadd_rn(o, -v) : __dadd_rn(o, v);
+    }
+    own[i * d + lane] = o;
+  }
+}
+
 // keys: column (node id) of each node entry, vals: entry index
 __global__ void k_mc_col_keys(const int32_t* col, int64_t nnz, uint64_t* keys, int32_t* vals) {
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -702,8 +1058,11 @@ template <int D>
 cudaError_t fill_d(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set, const int32_t* hit,
                    const double* l, const int64_t* rowptr, double cV, double cA, double* V, int32_t* col, double* A,
                    const double* U, cudaStream_t st) {
-  k_mc_fill<D><<<nblk(N * 32, kMcWarps * 32), kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA, V,
-                                                                      col, A, U);
+  const size_t sm = kMcWarps * sizeof(RowScratch<2>);
+  cudaError_t e = cudaFuncSetAttribute(k_mc_fill<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_mc_fill<D><<<nblk(N * 32, kMcWarps * 32), kMcWarps * 32, sm, st>>>(X, N, d, R, seed, set, hit, l, rowptr, cV, cA,
+                                                                       V, col, A, U);
   count_launch();
   return cudaGetLastError();
 }
@@ -713,8 +1072,11 @@ cudaError_t adj_rows_d(const double* X, int64_t N, int d, int64_t R, uint64_t se
                        const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, double cV,
                        double cA, const double* gV, const double* gA, double* P, double* own, const double* U,
                        cudaStream_t st) {
-  k_mc_adj_rows<D><<<nblk(N * 32, kMcWarps * 32), kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col,
-                                                                          cV, cA, gV, gA, P, own, U);
+  const size_t sm = kMcWarps * sizeof(RowScratch<D + 1>);
+  cudaError_t e = cudaFuncSetAttribute(k_mc_adj_rows<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_mc_adj_rows<D><<<nblk(N * 32, kMcWarps * 32), kMcWarps * 32, sm, st>>>(X, N, d, R, seed, set, hit, l, rowptr,
+                                                                           col, cV, cA, gV, gA, P, own, U);
   count_launch();
   return cudaGetLastError();
 }
@@ -730,7 +1092,10 @@ cudaError_t mc_batch_reduce(const SetDesc* sets_dev, int nsets, int64_t nitems, 
   count_launch();
   k_scan_batch<<<nsets, 1024, 0, st>>>(sets_dev);
   count_launch();
-  k_mc_fill_batch<<<nblk(nitems * 32, kMcWarps * 32), kMcWarps * 32, 0, st>>>(sets_dev, nsets, nitems, R, seed);
+  const size_t sm = kMcWarps * sizeof(RowScratch<2>);
+  cudaError_t e = cudaFuncSetAttribute(k_mc_fill_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_mc_fill_batch<<<nblk(nitems * 32, kMcWarps * 32), kMcWarps * 32, sm, st>>>(sets_dev, nsets, nitems, R, seed);
   count_launch();
   return cudaGetLastError();
 }
@@ -769,12 +1134,19 @@ cudaError_t mc_integrals(const double* X, int64_t N, int d, int64_t R, uint64_t 
   const double S = sphere_area(d);
   const double cV = S / ((double)R * (double)m), cA = S / (double)R;
   const unsigned g = nblk(N * 32, kMcWarps * 32);
-  if (d <= 4)
-    k_mc_func<4><<<g, kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, U, f, m, cV, cA, FV, Fd);
-  else if (d <= 8)
-    k_mc_func<8><<<g, kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, U, f, m, cV, cA, FV, Fd);
-  else
-    k_mc_func<16><<<g, kMcWarps * 32, 0, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, U, f, m, cV, cA, FV, Fd);
+  const size_t sm = kMcWarps * sizeof(RowScratch<1>);
+  cudaError_t e = cudaSuccess;
+  if (d <= 4) {
+    if ((e = cudaFuncSetAttribute(k_mc_func<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) == cudaSuccess)
+      k_mc_func<4><<<g, kMcWarps * 32, sm, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, U, f, m, cV, cA, FV, Fd);
+  } else if (d <= 8) {
+    if ((e = cudaFuncSetAttribute(k_mc_func<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) == cudaSuccess)
+      k_mc_func<8><<<g, kMcWarps * 32, sm, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, U, f, m, cV, cA, FV, Fd);
+  } else {
+    if ((e = cudaFuncSetAttribute(k_mc_func<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) == cudaSuccess)
+      k_mc_func<16><<<g, kMcWarps * 32, sm, st>>>(X, N, d, R, seed, set, hit, l, rowptr, col, U, f, m, cV, cA, FV, Fd);
+  }
+  if (e != cudaSuccess) return e;
   count_launch();
   return cudaGetLastError();
 }

@@ -155,24 +155,49 @@ __global__ void k_lz_order_keys(const int64_t* m2off, int64_t nnz, uint64_t* key
   vals[e] = (int32_t)e;
 }
 
-// One thread per facet (i, j), facet e = order[t] of thread t: the pyramid
-// over it with apex x_i, walked from the facet (level 2) down to its edges;
-// writes the pyramid's volume and integral (Vp, Fp) and the facet's A_ij,
-// Fd_ij.
-__global__ void k_lz_facets(const double* X, int64_t N, int d, const int32_t* tuples, const double* coords,
-                            const int64_t* voff, const int32_t* vlist, const int32_t* col, const int32_t* erow,
-                            const int64_t* m2off, int64_t nnz, const int32_t* order, int32_t* scratch, vd_func f,
-                            double fact, double* Vp, double* Fp, double* A, double* Fd, unsigned* flags) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nnz) return;
-  const int64_t e = order[t];
+// A warp per cell: the vertices of each facet (i, j) (the cell's vertices
+// whose tuple holds j), in the cell's vertex order, at
+// scratch + (d - 1) m2off[e]; the warp reads the cell's list once per facet.
+__global__ void k_lz_facet_verts(const int32_t* tuples, int d, int64_t N, const int64_t* voff, const int32_t* vlist,
+                                 const int64_t* rowptr, const int32_t* col, const int64_t* m2off, int32_t* scratch) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= N) return;
+  const int L = d + 1;
+  const int32_t* L1 = vlist + voff[i];
+  const int n1 = (int)(voff[i + 1] - voff[i]);
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+    const int32_t j = col[e];
+    const int64_t n2 = m2off[e + 1] - m2off[e];
+    int32_t* base = scratch + (int64_t)(d - 1) * m2off[e];
+    int64_t m = 0;
+    for (int p0 = 0; p0 < n1; p0 += 32) {
+      const int p = p0 + lane;
+      const bool has = p < n1 && lz_has(tuples + (int64_t)L1[p] * L, L, j);
+      const unsigned b = __ballot_sync(kFull, has);
+      const int64_t q = m + __popc(b & lt);
+      if (has && q < n2) base[q] = L1[p];
+      m += __popc(b);
+    }
+  }
+}
+
+// Facet (i, j), facet e = order[t] of position t (e = t without an order):
+// the pyramid over it with apex x_i, walked from the facet (level 2) down to
+// its edges; writes the pyramid's volume and integral (Vp, Fp) and the
+// facet's A_ij, Fd_ij.
+__device__ __forceinline__ void lz_facet(int64_t t, const double* X, int64_t N, int d, const int32_t* tuples,
+                                         const double* coords, const int32_t* col, const int32_t* erow,
+                                         const int64_t* m2off, const int32_t* order, int32_t* scratch, vd_func f,
+                                         double fact, double* Vp, double* Fp, double* A, double* Fd,
+                                         unsigned* flags) {
+  const int64_t e = order ? order[t] : t;
   const int L = d + 1;
   const int64_t i = erow[e];
   const int32_t jf = col[e];
   const double* xi = X + i * d;
   const double dd = (double)d;
-  const int32_t* L1 = vlist + voff[i];
-  const int n1 = (int)(voff[i + 1] - voff[i]);
   const int n2 = (int)(m2off[e + 1] - m2off[e]);
   int32_t* base = scratch + (int64_t)(d - 1) * m2off[e];
   const int32_t* lst[kLzMaxD + 1];
@@ -184,10 +209,7 @@ __global__ void k_lz_facets(const double* X, int64_t N, int d, const int32_t* tu
   double M[kLzMaxD * kLzMaxD];
   S[0] = (int32_t)i;
   S[1] = jf;
-  // the facet's vertices: the cell's vertices whose tuple holds j
-  int m = 0;
-  for (int p = 0; p < n1; ++p)
-    if (lz_has(tuples + (int64_t)L1[p] * L, L, jf) && m < n2) base[m++] = L1[p];
+  const int m = n2;  // the facet's vertices, listed at base by k_lz_facet_verts
   // an edge closing a simplex with the current means: its (v, fv)
   auto edge = [&](const int32_t* child, int mm, double& v, double& fv) {
     v = fv = 0.0;
@@ -287,6 +309,25 @@ __global__ void k_lz_facets(const double* X, int64_t N, int d, const int32_t* tu
   Fd[e] = __ddiv_rn(__dmul_rn(Fpy, dd), h);
 }
 
+// One thread per facet: each warp claims the next 32 positions until none is
+// left, so the walk's long tail spreads over the SMs whatever the number of
+// waves a one-shot grid would take.
+__global__ void k_lz_facets(const double* X, int64_t N, int d, const int32_t* tuples, const double* coords,
+                            const int32_t* col, const int32_t* erow, const int64_t* m2off, int64_t nnz,
+                            const int32_t* order, int32_t* scratch, vd_func f, double fact, double* Vp, double* Fp,
+                            double* A, double* Fd, unsigned* flags, unsigned long long* work) {
+  const int lane = threadIdx.x & 31;
+  while (true) {
+    unsigned long long t0 = 0;
+    if (lane == 0) t0 = atomicAdd(work, 32ull);
+    t0 = __shfl_sync(kFull, t0, 0);
+    if (t0 >= (unsigned long long)nnz) return;
+    const int64_t t = (int64_t)t0 + lane;
+    if (t < nnz) lz_facet(t, X, N, d, tuples, coords, col, erow, m2off, order, scratch, f, fact, Vp, Fp, A, Fd, flags);
+    __syncwarp();
+  }
+}
+
 // one thread per cell: V_i and F_i from its pyramids in facet order
 __global__ void k_lz_cellsum(const double* X, int64_t N, int d, const int64_t* rowptr, const double* Vp,
                              const double* Fp, vd_func f, double* V, double* F) {
@@ -374,16 +415,30 @@ cudaError_t poly_integrate(const double* X, int64_t N, int d, const int32_t* tup
     const size_t need = (fa.localSizeBytes + 1023) / 1024 * 1024 + 1024;
     if (cur < need && (e = cudaDeviceSetLimit(cudaLimitStackSize, need))) return e;
   }
-  // facets by decreasing vertex count (the first sort's key buffers are free again)
-  int32_t *order = nullptr, *otmp = nullptr;
-  if ((e = scratch.alloc_n(&order, nn)) || (e = scratch.alloc_n(&otmp, nn))) return e;
-  if (*nnz > 0) {
+  // Facets by decreasing vertex count (the first sort's key buffers are
+  // free again) when they fill the GPU more than twice over: the walk's long
+  // tail then dominates.  Fewer facets keep the CSR order, in which a warp's
+  // threads walk one cell's vertices and share their loads in L1.
+  int dev = 0, nsm = 0, occ = 0;
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lz_facets, 64, 0)))
+    return e;
+  const int64_t resident = (int64_t)nsm * std::max(occ, 1) * 64;
+  int32_t* order = nullptr;
+  if (*nnz > 2 * resident) {
+    int32_t* otmp = nullptr;
+    if ((e = scratch.alloc_n(&order, nn)) || (e = scratch.alloc_n(&otmp, nn))) return e;
     k_lz_order_keys<<<nb(*nnz, 256), 256, 0, st>>>(m2off, *nnz, keys, order);
     count_launch();
     if ((e = radix_sort_u64(keys, order, ktmp, otmp, *nnz, counts, orand, st))) return e;
   }
-  k_lz_facets<<<nb(*nnz, 64), 64, 0, st>>>(X, N, d, tuples, coords, voff, vals, *col, erow, m2off, *nnz, order, lzs, f,
-                                           fact, Vp, Fp, *A, *Fd, flags);
+  k_lz_facet_verts<<<nb(N * 32, 128), 128, 0, st>>>(tuples, d, N, voff, vals, *rowptr, *col, m2off, lzs);
+  count_launch();
+  unsigned long long* work = nullptr;
+  if ((e = scratch.alloc_n(&work, 1)) || (e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), st))) return e;
+  const unsigned grid = (unsigned)std::min<int64_t>(nb(*nnz, 64), (int64_t)nsm * std::max(occ, 1));
+  k_lz_facets<<<grid, 64, 0, st>>>(X, N, d, tuples, coords, *col, erow, m2off, *nnz, order, lzs, f, fact, Vp, Fp, *A,
+                                   *Fd, flags, work);
   count_launch();
   k_lz_cellsum<<<nb(N, 128), 128, 0, st>>>(X, N, d, *rowptr, Vp, Fp, f, *V, *F);
   count_launch();

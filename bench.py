@@ -16,7 +16,8 @@ and binary64 paths), "highd" (the same at d=16, N=200,000 mixture nodes,
 (Algorithm 3's function integrals on the d=4 rays), "hmc" (heuristic MC
 integrals, Section 3.3, and the exact integration of Section 3.2 on the
 traversal workload's diagram), "walk" (random walks on the vertex graph),
-"plain_fp64_d3" (the plain binary64 method at d=3, N=2,000: traversal + MC
+"cells" (the per-cell sequential exploration of Section 2.3 beside the
+whole-diagram traversal: time and table memory), "plain_fp64_d3" (the plain binary64 method at d=3, N=2,000: traversal + MC
 with 64 rays per cell + adjoint) and "batch" (512 point sets of uneven N and
 d, 256 rays per cell).
 
@@ -293,6 +294,9 @@ def run_ours(args):
     if args.only_walk:
         print(json.dumps({"walk": run_walk(args, vd, torch.cuda.current_stream())}), flush=True)
         return
+    if args.only_cells:
+        print(json.dumps({"cells": run_cells(args, vd, torch.cuda.current_stream())}), flush=True)
+        return
     if args.only_batch:
         print(json.dumps({"batch": run_batch(args, vd, torch.cuda.current_stream())}), flush=True)
         return
@@ -431,6 +435,7 @@ def run_ours(args):
     walk = None
     if not args.no_walk:
         walk = run_walk(args, vd, stream)
+    cells = None if args.no_cells else run_cells(args, vd, stream)
     small = None if args.no_small else run_small(args, vd, stream)
     batch = None if args.no_batch else run_batch(args, vd, stream)
 
@@ -465,7 +470,8 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": "raycasts/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "mc": mc, "highd": highd, "hmc": hmc, "walk": walk, "plain_fp64_d3": small, "batch": batch}
+                "mc": mc, "highd": highd, "hmc": hmc, "walk": walk, "cells": cells, "plain_fp64_d3": small,
+                "batch": batch}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
@@ -674,6 +680,58 @@ def run_walk(args, vd, stream, W=1_000_000, S=8):
             "distinct_vertices_visited": distinct, "vertices": nv}
 
 
+CELLS_WORKLOAD = ("per-cell sequential exploration (Section 2.3: cells in index order, 1024 at a time, the edge "
+                  "counters rebuilt per batch) beside the whole-diagram traversal, d=5, N=20000 iid uniform in [0,1]^5 "
+                  "(seed 0)")
+
+
+def run_cells(args, vd, stream, batch=1024, reps=2):
+    """Per-cell exploration against the whole-diagram traversal: CUDA-event
+    time of one call each (mean of reps after one warm-up), raycasts/s, the
+    edge and vertex tables' sizes, and the device memory each context holds
+    after its calls (the high-water mark of its workspace)."""
+    import torch
+    from paper_2405_10050_gb300 import synth
+    N, d = args.N, args.d
+    X = torch.tensor(synth.uniform(N, d, seed=0), device="cuda")
+    out, tuples = {}, {}
+    for name, b in (("by_cells", batch), ("whole", None)):
+        torch.cuda.synchronize()
+        ctx = vd.vd_create(None, stream.cuda_stream)
+        vd.vd_set_nodes(ctx, X)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        ms, st = 0.0, None
+        for r in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mesh = vd.vd_vertices(ctx) if b is None else vd.vd_vertices_by_cells(ctx, b)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                ms += e0.elapsed_time(e1) / reps
+            st = vd.vd_mesh_stats(mesh)
+            if r == reps:
+                nv = vd.vd_mesh_count(mesh)
+                T = torch.empty((nv, d + 1), dtype=torch.int32, device="cuda")
+                vd.vd_mesh_copy(mesh, T, None)
+                tuples[name] = T
+            vd.vd_mesh_free(mesh)
+        torch.cuda.synchronize()
+        held = free0 - torch.cuda.mem_get_info()[0]
+        vd.vd_destroy(ctx)
+        out[name] = {"ms": ms, "raycasts_per_s": st["rays"] / (ms / 1000.0), "rays": st["rays"],
+                     "levels": st["levels"], "vertices": st["vertices"], "edge_table_bytes": st["edge_table_bytes"],
+                     "vertex_table_bytes": st["vertex_table_bytes"], "device_bytes_held": held}
+    same = bool(torch.equal(tuples["by_cells"], tuples["whole"]))
+    c, w = out["by_cells"], out["whole"]
+    return {"workload": CELLS_WORKLOAD.replace("N=20000", f"N={N}").replace("d=5", f"d={d}")
+            .replace("1024 at a time", f"{batch} at a time"), "unit": "raycasts/s", "value": c["raycasts_per_s"],
+            "cells_per_batch": batch, "by_cells": c, "whole_diagram": w,
+            "edge_table_ratio": w["edge_table_bytes"] / max(c["edge_table_bytes"], 1),
+            "tuples_identical": same}
+
+
 def run_highd(args, vd, stream):
     """MC vol+grad cells/s on the high-dimensional workload: tensor-core walk
     (tcgen05 ball tests and leaf screening) vs the binary32 tree walk, same
@@ -856,6 +914,8 @@ def main():
     ap.add_argument("--no-hmc", action="store_true")
     ap.add_argument("--no-walk", action="store_true")
     ap.add_argument("--only-walk", action="store_true")
+    ap.add_argument("--no-cells", action="store_true")
+    ap.add_argument("--only-cells", action="store_true")
     ap.add_argument("--only-hmc", action="store_true")
     ap.add_argument("--highd-fp64", action="store_true", help="also time the binary64 path (about 25 s)")
     ap.add_argument("--highd-n", type=int, default=200000)

@@ -91,6 +91,8 @@ typedef struct {
   int64_t launches;        /* kernels launched by the call                  */
   double ms;               /* device time of the last call, milliseconds   */
   double raycast_ms;       /* device time of its RayCast kernels, ms        */
+  int64_t edge_table_bytes;   /* traversal: edge-counter table size, bytes */
+  int64_t vertex_table_bytes; /* traversal: vertex table size, bytes       */
 } vd_stats;
 
 typedef struct vd_ctx vd_ctx;
@@ -158,6 +160,18 @@ vd_status vd_raycast_noalloc(vd_ctx* ctx, const double* origins, const double* d
  * (d+1)-generator tuple.  Box must be on.  EHASHFULL if the vertex table
  * capacity is reached. */
 vd_status vd_vertices(vd_ctx* ctx, vd_mesh** out);
+
+/* Per-cell sequential exploration (Section 2.3: the cells are explored in
+ * sequential order so that the edge counts are reconstructed for each cell
+ * and the edge table holds only the current cells' edges).  Cells are taken
+ * in index order, cells_per_batch at a time (1 = one cell at a time; 0 =
+ * automatic, N / 16).  For each batch the edge counters are rebuilt from the
+ * vertices found so far (edges that hold a batch node only), batch cells
+ * without a known vertex are seeded by Descent, and the traversal follows
+ * only edges that hold a batch node.  Same result as vd_vertices (the same
+ * vertex set, tuples and coordinates bit for bit); stats report both tables'
+ * sizes.  EDEGENERATE if a cell ends a batch without a vertex. */
+vd_status vd_vertices_by_cells(vd_ctx* ctx, int64_t cells_per_batch, vd_mesh** out);
 int64_t vd_mesh_count(const vd_mesh* mesh);
 int32_t vd_mesh_dim(const vd_mesh* mesh);
 /* tuples: V x (d+1) int32, each row ascending, rows in lexicographic order;

@@ -205,10 +205,12 @@ class Voronoi:
         vd.vd_random_walk(self.ctx, start, steps, seed, T, C)
         return T, C
 
-    def vertices(self):
-        """All vertices of the clipped diagram: (tuples V x (d+1), coords V x d)."""
+    def vertices(self, cells_per_batch=None):
+        """All vertices of the clipped diagram: (tuples V x (d+1), coords V x d,
+        stats).  cells_per_batch: None for the whole-diagram traversal, else the
+        per-cell exploration in batches of that many cells (0 = automatic)."""
         import torch
-        m = vd.vd_vertices(self.ctx)
+        m = vd.vd_vertices(self.ctx) if cells_per_batch is None else vd.vd_vertices_by_cells(self.ctx, cells_per_batch)
         try:
             nv = vd.vd_mesh_count(m)
             tuples = torch.empty((nv, self.d + 1), dtype=torch.int32, device="cuda")

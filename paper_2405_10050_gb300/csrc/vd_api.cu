@@ -36,9 +36,9 @@ cudaError_t poly_integrate(const double* X, int64_t N, int d, const int32_t* tup
 cudaError_t random_walk(const TreeView& tv, int precision, const int32_t* start, int64_t W, int64_t S, uint64_t seed,
                         int32_t* path_t, double* path_x, Counters* ctr, DevBufs& scratch, cudaStream_t st,
                         double* raycast_ms);
-cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, Workspace& ws,
-                              DevBufs& out_bufs, int32_t** tuples, double** coords, int64_t* nv, vd_stats* stats,
-                              Counters* ctr, cudaStream_t st, char* err, size_t errlen);
+cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, int64_t cells_per_batch,
+                              Workspace& ws, DevBufs& out_bufs, int32_t** tuples, double** coords, int64_t* nv,
+                              vd_stats* stats, Counters* ctr, cudaStream_t st, char* err, size_t errlen);
 }  // namespace vd
 
 namespace vd {
@@ -1105,7 +1105,9 @@ vd_status vd_random_walk(vd_ctx* ctx, const int32_t* start, int64_t W, int64_t s
   return s;
 }
 
-vd_status vd_vertices(vd_ctx* ctx, vd_mesh** out) {
+// The whole-diagram traversal (cells_per_batch = 0) or the per-cell
+// exploration in batches of cells_per_batch cells.
+static vd_status vertices_impl(vd_ctx* ctx, int64_t cells_per_batch, vd_mesh** out) {
   if (!ctx || !out) return VD_EINVAL;
   *out = nullptr;
   if (!ctx->X) return set_err(ctx, VD_EINVAL, "vd_vertices: no node set");
@@ -1119,8 +1121,9 @@ vd_status vd_vertices(vd_ctx* ctx, vd_mesh** out) {
   const long long l0 = vd::g_launches.load();
   Timer tm(ctx->st);
   char err[256] = {0};
-  cudaError_t e = vd::traverse_vertices(ctx->tree, effective_precision(ctx), ctx->cfg, ctx->trav_ws, m->bufs, &m->tuples,
-                                        &m->coords, &m->nv, &m->stats, ctx->ctr, ctx->st, err, sizeof(err));
+  cudaError_t e = vd::traverse_vertices(ctx->tree, effective_precision(ctx), ctx->cfg, cells_per_batch, ctx->trav_ws,
+                                        m->bufs, &m->tuples, &m->coords, &m->nv, &m->stats, ctx->ctr, ctx->st, err,
+                                        sizeof(err));
   m->stats.ms = tm.stop();
   m->stats.launches = vd::g_launches.load() - l0;
   Counters hc;
@@ -1145,6 +1148,15 @@ vd_status vd_vertices(vd_ctx* ctx, vd_mesh** out) {
   ctx->last = m->stats;
   *out = m;
   return VD_OK;
+}
+
+vd_status vd_vertices(vd_ctx* ctx, vd_mesh** out) { return vertices_impl(ctx, 0, out); }
+
+vd_status vd_vertices_by_cells(vd_ctx* ctx, int64_t cells_per_batch, vd_mesh** out) {
+  if (!ctx || !out) return VD_EINVAL;
+  if (cells_per_batch < 0) return set_err(ctx, VD_EINVAL, "vd_vertices_by_cells: negative batch size");
+  const int64_t b = cells_per_batch > 0 ? cells_per_batch : std::max<int64_t>(1, (ctx->N + 15) / 16);
+  return vertices_impl(ctx, b, out);
 }
 
 int64_t vd_mesh_count(const vd_mesh* m) { return m ? m->nv : 0; }

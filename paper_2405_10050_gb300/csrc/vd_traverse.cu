@@ -51,7 +51,13 @@ struct Tables {
   int64_t ehmask;
   unsigned long long* ne;
   int edet;          // edge entries indexed v (d+1) + q (ecap >= vcap (d+1))
+  // edges are counted and expanded only if they hold a node in [bc0, bc1)
+  // (every node for the whole-diagram traversal; the current batch of
+  // cells for the per-cell exploration)
+  int32_t bc0, bc1;
 };
+
+__device__ __forceinline__ bool in_batch(const Tables& T, int32_t g) { return g >= T.bc0 && g < T.bc1; }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t h) {
   h ^= h >> 33;
@@ -334,25 +340,26 @@ __device__ __forceinline__ long long warp_append(bool want, unsigned long long* 
 }
 
 // Expansion, pass 1: every (frontier vertex, dropped generator) whose edge
-// holds a node and has fewer than two known endpoints is appended to the
-// level's work list (cheap hash lookups; pass 2 then runs the binary64
-// SearchDirection on full warps).
-__global__ void k_expand_mark(Tables T, int64_t f0, int64_t nf, int64_t* items, unsigned long long* nitems,
-                              int64_t rcap, unsigned* flags) {
+// holds a node (of the batch) and has fewer than two known endpoints is
+// appended to the level's work list (cheap hash lookups; pass 2 then runs the
+// binary64 SearchDirection on full warps).  Frontier vertex f is f0 + f, or
+// flist[f] when a list is given.
+__global__ void k_expand_mark(Tables T, int64_t f0, const int32_t* flist, int64_t nf, int64_t* items,
+                              unsigned long long* nitems, int64_t rcap, unsigned* flags) {
   const int d = T.d;
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool want = false;
   if (q < nf * (d + 1)) {
     const int64_t f = q / (d + 1);
     const int drop = (int)(q % (d + 1));
-    const int64_t v = f0 + f;
+    const int64_t v = flist ? (int64_t)flist[f] : f0 + f;
     int32_t eta[VD_MAX_D];
     int m = 0, hasnode = 0;
     for (int a = 0; a <= d; ++a)
       if (a != drop) {
         const int32_t g = T.vt[(int64_t)v * (d + 1) + a];
         eta[m++] = g;
-        hasnode |= g >= 0;
+        hasnode |= in_batch(T, g);
       }
     want = hasnode && edge_count(T, eta) < 2;
   }
@@ -369,7 +376,7 @@ __global__ void k_expand_mark(Tables T, int64_t f0, int64_t nf, int64_t* items, 
 // the vertex, direction = SearchDirection, eta = the edge (reference node
 // first).
 template <int D>
-__global__ void k_expand_dir(Tables T, const double* X, int64_t f0, const int64_t* items,
+__global__ void k_expand_dir(Tables T, const double* X, int64_t f0, const int32_t* flist, const int64_t* items,
                              const unsigned long long* nitems, int64_t rcap, double* ro, double* rd, int32_t* reta,
                              unsigned* flags) {
   const int d = T.d;
@@ -378,7 +385,7 @@ __global__ void k_expand_dir(Tables T, const double* X, int64_t f0, const int64_
   const int64_t q = items[r];
   const int64_t f = q / (d + 1);
   const int drop = (int)(q % (d + 1));
-  const int64_t v = f0 + f;
+  const int64_t v = flist ? (int64_t)flist[f] : f0 + f;
   int32_t sig[D + 1], eta[D];
   for (int a = 0; a <= d; ++a) sig[a] = T.vt[(int64_t)v * (d + 1) + a];
   int m = 0;
@@ -497,9 +504,60 @@ __global__ void k_commit_edges(Tables T, const int32_t* vids, int64_t nwcap, con
     if (a != q) {
       const int32_t g = T.vt[(int64_t)v * L + a];
       eta[m++] = g;
-      hasnode |= g >= 0;
+      hasnode |= in_batch(T, g);
     }
   if (hasnode) edge_increment(T, eta, T.edet ? (int64_t)v * L + q : -1, flags);
+}
+
+// ---- per-cell exploration (Section 2.3: cells explored in sequential order,
+// the edge counts reconstructed for the current cells only) ----
+// Start of a batch of cells [bc0, bc1), one thread per (known vertex, edge):
+// the counters of the edges that hold a batch node, the known vertices with a
+// batch node (the batch's first frontier, in flist) and the batch cells that
+// already have a vertex (hasv).
+__global__ void k_cell_recount(Tables T, int64_t nv, int32_t* flist, unsigned long long* nfl, int32_t* hasv,
+                               unsigned* flags) {
+  const int d = T.d, L = d + 1;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nv * L) return;
+  const int64_t v = t / L;
+  const int q = (int)(t % L);
+  const int32_t* sig = T.vt + v * L;
+  int32_t eta[VD_MAX_D];
+  int m = 0;
+  bool eb = false, vb = false;
+  for (int a = 0; a <= d; ++a) {
+    const int32_t g = sig[a];
+    const bool b = in_batch(T, g);
+    vb |= b;
+    if (a != q) {
+      eta[m++] = g;
+      eb |= b;
+    }
+  }
+  if (eb) edge_increment(T, eta, -1, flags);
+  if (q == 0 && vb)
+    for (int a = 0; a <= d; ++a)
+      if (in_batch(T, sig[a])) hasv[sig[a] - T.bc0] = 1;
+  const long long p = warp_append(q == 0 && vb, nfl);
+  if (p >= 0) flist[p] = (int32_t)v;
+}
+
+// flist[base + k] = a + k for the vertex ids a .. b - 1 (a batch's seeds).
+__global__ void k_append_range(int32_t* flist, int64_t base, int64_t a, int64_t b) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a + k < b) flist[base + k] = (int32_t)(a + k);
+}
+
+// Marks the batch cells with a vertex among the ids a .. b - 1.
+__global__ void k_cell_mark(Tables T, int64_t a, int64_t b, int32_t* hasv) {
+  const int L = T.d + 1;
+  const int64_t v = a + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= b) return;
+  for (int q = 0; q < L; ++q) {
+    const int32_t g = T.vt[v * L + q];
+    if (in_batch(T, g)) hasv[g - T.bc0] = 1;
+  }
 }
 
 // ---- Descent seeding ----------------------------------------------------------
@@ -608,6 +666,18 @@ __global__ void k_descent_cand(int d, int64_t ns, const int32_t* ssig, const int
   hit[s] = ssig[s * (VD_MAX_D + 1) + d];
 }
 
+// Seed s at node snode[s]: sigma = {node}, one generator, alive, r = x_node.
+__global__ void k_seed_init(const double* X, int d, int64_t ns, const int32_t* snode, int32_t* ssig, int* sm,
+                            int* alive, double* sr) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  ssig[s * (VD_MAX_D + 1)] = snode[s];
+  for (int k = 1; k <= VD_MAX_D; ++k) ssig[s * (VD_MAX_D + 1) + k] = kNoId;
+  sm[s] = 1;
+  alive[s] = 1;
+  for (int a = 0; a < VD_MAX_D; ++a) sr[s * VD_MAX_D + a] = a < d ? X[(int64_t)snode[s] * d + a] : 0.0;
+}
+
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
@@ -645,12 +715,14 @@ inline unsigned nb(int64_t n, int t = 256) { return (unsigned)std::max<int64_t>(
 // The level's rays: nf frontier vertices -> work list -> ray arrays (count
 // *nrays on the device, at most min(nf (d+1), rcap)).
 template <int D>
-void launch_expand(Tables T, const double* X, int64_t f0, int64_t nf, int64_t* items, double* ro, double* rd,
-                   int32_t* reta, unsigned long long* nrays, int64_t rcap, unsigned* flags, cudaStream_t st) {
+void launch_expand(Tables T, const double* X, int64_t f0, const int32_t* flist, int64_t nf, int64_t* items,
+                   double* ro, double* rd, int32_t* reta, unsigned long long* nrays, int64_t rcap, unsigned* flags,
+                   cudaStream_t st) {
   const int64_t n = nf * (T.d + 1);
-  k_expand_mark<<<nb(n), 256, 0, st>>>(T, f0, nf, items, nrays, rcap, flags);
+  k_expand_mark<<<nb(n), 256, 0, st>>>(T, f0, flist, nf, items, nrays, rcap, flags);
   count_launch();
-  k_expand_dir<D><<<nb(std::min(n, rcap), 128), 128, 0, st>>>(T, X, f0, items, nrays, rcap, ro, rd, reta, flags);
+  k_expand_dir<D><<<nb(std::min(n, rcap), 128), 128, 0, st>>>(T, X, f0, flist, items, nrays, rcap, ro, rd, reta,
+                                                                flags);
   count_launch();
 }
 
@@ -815,9 +887,10 @@ static double vertices_per_cell(int d) {
   return v;
 }
 
-cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, Workspace& ws,
-                              DevBufs& out_bufs, int32_t** tuples_out, double** coords_out, int64_t* nv_out,
-                              vd_stats* stats, Counters* ctr, cudaStream_t st, char* err, size_t errlen) {
+cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config& cfg, int64_t cells_per_batch,
+                              Workspace& ws, DevBufs& out_bufs, int32_t** tuples_out, double** coords_out,
+                              int64_t* nv_out, vd_stats* stats, Counters* ctr, cudaStream_t st, char* err,
+                              size_t errlen) {
   const int d = tv.d;
   const int L = d + 1;
   const int64_t N = tv.N;
@@ -830,16 +903,21 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   // workspace slots
   enum {
     kVt, kVx, kVslot, kEt, kEcnt, kEslot, kCnts, kRo, kRd, kRt, kReta, kRhit, kCand, kCslot, kOvl, kFbl, kSnode,
-    kSsig, kSm, kAlive, kSr, kPerm, kPtmp, kKeys, kKtmp, kCounts, kOrand, kItems, kWin, kVids, kGrp
+    kSsig, kSm, kAlive, kSr, kPerm, kPtmp, kKeys, kKtmp, kCounts, kOrand, kItems, kWin, kVids, kGrp, kFlist, kHasv
   };
   int64_t vcap = cfg.hash_capacity > 0 ? cfg.hash_capacity
                                        : (int64_t)std::min(2.0e9, std::max(1.0e5, 2.0 * N * vertices_per_cell(d) / L +
                                                                                        64.0 * (1 << std::min(d, 16)) +
                                                                                        8.0 * N * d));
   vcap = std::min<int64_t>(vcap, (int64_t)1 << 30);
-  // expected edges ~ V (d+1) / 2; entries indexed v (d+1) + q while that fits
-  const int64_t ehint = std::min<int64_t>((int64_t)1 << 30, vcap * L / 2 + vcap / 4 + 1024);
-  const bool edet = vcap * L < ((int64_t)1 << 31);
+  // expected edges ~ V (d+1) / 2; entries indexed v (d+1) + q while that fits.
+  // The per-cell exploration holds only the edges of one batch of cells: each
+  // cell has ~d/2 edges per vertex (edges of cell i hold i)
+  const int64_t B = cells_per_batch > 0 ? std::min<int64_t>(cells_per_batch, N) : 0;
+  int64_t ehint = std::min<int64_t>((int64_t)1 << 30, vcap * L / 2 + vcap / 4 + 1024);
+  if (B > 0)
+    ehint = std::min<int64_t>(ehint, (int64_t)std::min(1.0e9, (double)B * vertices_per_cell(d) * d + 65536.0));
+  const bool edet = B == 0 && vcap * L < ((int64_t)1 << 31);
   const int64_t ecap = edet ? vcap * L : ehint;
   const int64_t vh = pow2_at_least(2 * vcap), eh = pow2_at_least(2 * ehint);
   Tables T;
@@ -847,6 +925,8 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   T.vcap = vcap;
   T.ecap = ecap;
   T.edet = edet ? 1 : 0;
+  T.bc0 = 0;
+  T.bc1 = INT32_MAX;
   T.vhmask = vh - 1;
   T.ehmask = eh - 1;
   VD_TRY(ws.get_n(kVt, (size_t)vcap * L, &T.vt));
@@ -855,12 +935,12 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   VD_TRY(ws.get_n(kEt, (size_t)ecap * d, &T.et));
   VD_TRY(ws.get_n(kEcnt, (size_t)ecap, &T.ecnt));
   VD_TRY(ws.get_n(kEslot, (size_t)eh, &T.eslot));
-  unsigned long long* cnts = nullptr;  // nv, ne, nrays, (unused), nwin
-  VD_TRY(ws.get_n(kCnts, 5, &cnts));
+  unsigned long long* cnts = nullptr;  // nv, ne, nrays, (unused), nwin, frontier list length
+  VD_TRY(ws.get_n(kCnts, 6, &cnts));
   T.nv = cnts + 0;
   T.ne = cnts + 1;
   unsigned* flags = &ctr->flags;
-  VD_TRY(cudaMemsetAsync(cnts, 0, 5 * sizeof(unsigned long long), st));
+  VD_TRY(cudaMemsetAsync(cnts, 0, 6 * sizeof(unsigned long long), st));
   k_fill_i32<<<nb(vh), 256, 0, st>>>(T.vslot, vh, kEmpty); count_launch();
   k_fill_i32<<<nb(eh), 256, 0, st>>>(T.eslot, eh, kEmpty); count_launch();
 
@@ -939,95 +1019,160 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
     nfallback += (int64_t)std::min<unsigned long long>(*fb_host, (unsigned long long)rcap);
   };
 
-  // ---- seeds by Descent ----
-  const int64_t ns = std::min<int64_t>(N, 64);
+  unsigned long long* nrays = cnts + 2;
+  unsigned long long* nwin = cnts + 4;
+  int64_t raycasts = 0, levels = 0;
+  int64_t nv_known = 0;  // vertices in the table (host copy)
+  bool stop = false;     // a flag that ends the call was raised
+  auto read_nv = [&]() -> cudaError_t {
+    unsigned long long h = 0;
+    cudaError_t ee = cudaMemcpyAsync(&h, cnts, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (ee == cudaSuccess) ee = cudaStreamSynchronize(st);
+    nv_known = std::min<int64_t>((int64_t)h, vcap);
+    return ee;
+  };
+
+  // ---- Descent (Algorithm 2): nodes -> seed vertices, committed like a level ----
   int32_t *snode = nullptr, *ssig = nullptr;
   int *sm = nullptr, *alive = nullptr;
   double* sr = nullptr;
-  VD_TRY(ws.get_n(kSnode, ns, &snode));
-  VD_TRY(ws.get_n(kSsig, (size_t)ns * (VD_MAX_D + 1), &ssig));
-  VD_TRY(ws.get_n(kSm, ns, &sm));
-  VD_TRY(ws.get_n(kAlive, ns, &alive));
-  VD_TRY(ws.get_n(kSr, (size_t)ns * VD_MAX_D, &sr));
-  {
-    std::vector<int32_t> hn(ns), hsig(ns * (VD_MAX_D + 1), kNoId);
-    std::vector<int> hm(ns, 1), ha(ns, 1);
-    for (int64_t s = 0; s < ns; ++s) {
-      hn[s] = (int32_t)((s * N) / ns);
-      hsig[s * (VD_MAX_D + 1)] = hn[s];
+  auto descent = [&](const std::vector<int32_t>& nodes) -> cudaError_t {
+    const int64_t ns = (int64_t)nodes.size();
+    if (ns == 0) return cudaSuccess;
+    cudaError_t ee;
+    if ((ee = grow(ns)) || (ee = ws.get_n(kSnode, ns, &snode)) ||
+        (ee = ws.get_n(kSsig, (size_t)ns * (VD_MAX_D + 1), &ssig)) || (ee = ws.get_n(kSm, ns, &sm)) ||
+        (ee = ws.get_n(kAlive, ns, &alive)) || (ee = ws.get_n(kSr, (size_t)ns * VD_MAX_D, &sr)) ||
+        (ee = cudaMemcpyAsync(snode, nodes.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, st)))
+      return ee;
+    k_seed_init<<<nb(ns, 64), 64, 0, st>>>(tv.X, d, ns, snode, ssig, sm, alive, sr); count_launch();
+    for (int step = 0; step < d; ++step) {
+      k_descent_dir<<<nb(ns, 64), 64, 0, st>>>(tv.X, d, ns, snode, ssig, sm, sr, step, ro, rd, reta, alive);
+      count_launch();
+      if ((ee = cudaGetLastError()) || (ee = cast(ns, nullptr, L))) return ee;
+      raycasts += ns;
+      k_descent_update<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, sr, rd, rhit, rt, alive); count_launch();
     }
-    VD_TRY(cudaMemcpyAsync(snode, hn.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    VD_TRY(cudaMemcpyAsync(ssig, hsig.data(), hsig.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    VD_TRY(cudaMemcpyAsync(sm, hm.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
-    VD_TRY(cudaMemcpyAsync(alive, ha.data(), ns * sizeof(int), cudaMemcpyHostToDevice, st));
-    std::vector<double> hr(ns * VD_MAX_D, 0.0);
-    for (int64_t s = 0; s < ns; ++s)
-      VD_TRY(cudaMemcpyAsync(hr.data() + s * VD_MAX_D, tv.X + (int64_t)hn[s] * d, d * sizeof(double),
-                             cudaMemcpyDeviceToHost, st));
-    VD_TRY(cudaStreamSynchronize(st));
-    VD_TRY(cudaMemcpyAsync(sr, hr.data(), hr.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-  }
-  int64_t raycasts = 0;
-  for (int step = 0; step < d; ++step) {
-    k_descent_dir<<<nb(ns, 64), 64, 0, st>>>(tv.X, d, ns, snode, ssig, sm, sr, step, ro, rd, reta, alive); count_launch();
-    VD_TRY(cudaGetLastError());
-    VD_TRY(cast(ns, nullptr, L));
-    raycasts += ns;
-    k_descent_update<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, sr, rd, rhit, rt, alive); count_launch();
-    VD_TRY(cudaGetLastError());
-  }
-  k_descent_cand<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, alive, reta, rhit); count_launch();
-  // a level's frontier is the id range of the vertices the previous level added
-  unsigned long long* nrays = cnts + 2;
-  unsigned long long* nwin = cnts + 4;
-  VD_TRY(cudaMemsetAsync(nwin, 0, sizeof(unsigned long long), st));
-  // seeds that did not reach a vertex carry hit = kNoId and are skipped (a
-  // missing seed is not an error); every other flag stays as raised
-  k_commit_claim<<<nb(ns), 256, 0, st>>>(T, reta, rhit, ns, nullptr, cand, cslot, win, nwin, flags, 1); count_launch();
-  VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, ns, nwin, vids, flags, st);
-  unsigned long long hn2[4];
-  VD_TRY(cudaMemcpyAsync(hn2, cnts, sizeof(hn2), cudaMemcpyDeviceToHost, st));
-  VD_TRY(cudaStreamSynchronize(st));
-  int64_t f0 = 0;
-  int64_t nf = std::min<int64_t>((int64_t)hn2[0], vcap);
-  if (nf == 0) {
-    snprintf(err, errlen, "Descent found no seed vertex");
-    return cudaErrorUnknown;
-  }
-  // ---- levels: one host synchronisation each (the next frontier's size) ----
-  int64_t levels = 0;
+    k_descent_cand<<<nb(ns, 64), 64, 0, st>>>(d, ns, ssig, sm, alive, reta, rhit); count_launch();
+    if ((ee = cudaMemsetAsync(nwin, 0, sizeof(unsigned long long), st))) return ee;
+    // seeds that did not reach a vertex carry hit = kNoId and are skipped (a
+    // missing seed is not an error); every other flag stays as raised
+    k_commit_claim<<<nb(ns), 256, 0, st>>>(T, reta, rhit, ns, nullptr, cand, cslot, win, nwin, flags, 1);
+    count_launch();
+    VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, ns, nwin, vids, flags, st);
+    if ((ee = cudaGetLastError())) return ee;
+    return read_nv();
+  };
+
+  // ---- BFS levels from a frontier (the id range f0 .. f0 + nf - 1, or the
+  // first nf ids of fl); one host synchronisation per expansion; a level's new
+  // vertices (consecutive ids) are the next frontier.  A frontier wider than
+  // `slice` vertices is expanded in slices. ----
   const int64_t max_levels = cfg.max_levels > 0 ? cfg.max_levels : (int64_t)1 << 20;
-  while (nf > 0) {
-    if (levels >= max_levels) {
-      snprintf(err, errlen, "traversal stopped at the level cap %lld", (long long)max_levels);
+  auto run_levels = [&](int64_t f0, int64_t nf, const int32_t* fl, int64_t slice) -> cudaError_t {
+    cudaError_t ee;
+    while (nf > 0 && !stop) {
+      if (levels >= max_levels) {
+        snprintf(err, errlen, "traversal stopped at the level cap %lld", (long long)max_levels);
+        return cudaErrorUnknown;
+      }
+      ++levels;
+      const int64_t level_start = nv_known;
+      for (int64_t s0 = 0; s0 < nf && !stop; s0 += slice) {
+        const int64_t nfs = std::min(slice, nf - s0);
+        const int64_t ncap = nfs * L;  // at most one ray per (frontier vertex, edge)
+        if ((ee = grow(ncap)) || (ee = cudaMemsetAsync(cnts + 2, 0, 3 * sizeof(unsigned long long), st))) return ee;
+        VD_TRAV_D(d, launch_expand, T, tv.X, fl ? 0 : f0 + s0, fl ? fl + s0 : nullptr, nfs, items, ro, rd, reta,
+                  nrays, rcap, flags, st);
+        if ((ee = cudaGetLastError())) return ee;
+        const int64_t rmax = std::min(ncap, rcap);
+        if ((ee = cast(rmax, nrays, d))) return ee;
+        k_commit_claim<<<nb(rmax), 256, 0, st>>>(T, reta, rhit, rmax, nrays, cand, cslot, win, nwin, flags, 0);
+        count_launch();
+        VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, rmax, nwin, vids, flags, st);
+        if ((ee = cudaGetLastError())) return ee;
+        unsigned long long hc[6];
+        unsigned hf = 0;
+        if ((ee = cudaMemcpyAsync(hc, cnts, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) ||
+            (ee = cudaMemcpyAsync(hc + 4, &ctr->fallback, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) ||
+            (ee = cudaMemcpyAsync(hc + 5, &ctr->overflow, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) ||
+            (ee = cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) ||
+            (ee = cudaStreamSynchronize(st)))
+          return ee;
+        account(hc + 4);
+        noverflow += (int64_t)std::min<unsigned long long>(hc[5], (unsigned long long)rcap);
+        raycasts += (int64_t)std::min<unsigned long long>(hc[2], (unsigned long long)rcap);
+        nv_known = std::min<int64_t>((int64_t)hc[0], vcap);
+        if (hf & (kFlagHashFull | kFlagQueue | kFlagDegenerate | kFlagCandOverflow | kFlagBadInput)) stop = true;
+      }
+      nf = nv_known - level_start;
+      f0 = level_start;
+      fl = nullptr;
+    }
+    return cudaSuccess;
+  };
+
+  if (B == 0) {
+    // whole diagram: seeds at 64 nodes spread over the index range
+    const int64_t ns = std::min<int64_t>(N, 64);
+    std::vector<int32_t> hn(ns);
+    for (int64_t s = 0; s < ns; ++s) hn[s] = (int32_t)((s * N) / ns);
+    VD_TRY(descent(hn));
+    if (nv_known == 0) {
+      snprintf(err, errlen, "Descent found no seed vertex");
       return cudaErrorUnknown;
     }
-    ++levels;
-    const int64_t ncap = nf * L;  // at most one ray per (frontier vertex, edge)
-    VD_TRY(grow(ncap));
-    VD_TRY(cudaMemsetAsync(cnts + 2, 0, 3 * sizeof(unsigned long long), st));
-    VD_TRAV_D(d, launch_expand, T, tv.X, f0, nf, items, ro, rd, reta, nrays, rcap, flags, st);
-    VD_TRY(cudaGetLastError());
-    const int64_t rmax = std::min(ncap, rcap);
-    VD_TRY(cast(rmax, nrays, d));
-    k_commit_claim<<<nb(rmax), 256, 0, st>>>(T, reta, rhit, rmax, nrays, cand, cslot, win, nwin, flags, 0);
-    count_launch();
-    VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, rmax, nwin, vids, flags, st);
-    VD_TRY(cudaGetLastError());
-    unsigned long long hc[6];
-    unsigned hf = 0;
-    VD_TRY(cudaMemcpyAsync(hc, cnts, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    VD_TRY(cudaMemcpyAsync(hc + 4, &ctr->fallback, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    VD_TRY(cudaMemcpyAsync(hc + 5, &ctr->overflow, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-    VD_TRY(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    VD_TRY(cudaStreamSynchronize(st));
-    account(hc + 4);
-    noverflow += (int64_t)std::min<unsigned long long>(hc[5], (unsigned long long)rcap);
-    raycasts += (int64_t)std::min<unsigned long long>(hc[2], (unsigned long long)rcap);
-    if (hf & (kFlagHashFull | kFlagQueue | kFlagDegenerate | kFlagCandOverflow | kFlagBadInput)) break;
-    const int64_t nv_now = std::min<int64_t>((int64_t)hc[0], vcap);
-    nf = nv_now - (f0 + nf);
-    f0 = nv_now - nf;
+    VD_TRY(run_levels(0, nv_known, nullptr, INT64_MAX));
+  } else {
+    // per cell, batches of B cells in index order: the edge table is rebuilt
+    // for each batch from the vertices known so far, batch cells without a
+    // known vertex are seeded by Descent, and the BFS follows only edges that
+    // hold a batch node (both ends of such an edge are vertices of that cell)
+    int32_t *flist = nullptr, *hasv = nullptr;
+    VD_TRY(ws.get_n(kFlist, (size_t)vcap, &flist));
+    VD_TRY(ws.get_n(kHasv, (size_t)B, &hasv));
+    unsigned long long* nfl = cnts + 5;
+    const int64_t slice = std::max<int64_t>(4096, rcap / L);
+    std::vector<int32_t> hv(B);
+    for (int64_t c0 = 0; c0 < N && !stop; c0 += B) {
+      const int64_t c1 = std::min<int64_t>(N, c0 + B), nb_cells = c1 - c0;
+      T.bc0 = (int32_t)c0;
+      T.bc1 = (int32_t)c1;
+      k_fill_i32<<<nb(eh), 256, 0, st>>>(T.eslot, eh, kEmpty); count_launch();
+      VD_TRY(cudaMemsetAsync(T.ne, 0, sizeof(unsigned long long), st));
+      VD_TRY(cudaMemsetAsync(nfl, 0, sizeof(unsigned long long), st));
+      VD_TRY(cudaMemsetAsync(hasv, 0, (size_t)nb_cells * sizeof(int32_t), st));
+      if (nv_known > 0) {
+        k_cell_recount<<<nb(nv_known * L), 256, 0, st>>>(T, nv_known, flist, nfl, hasv, flags); count_launch();
+      }
+      unsigned long long hn_fl = 0;
+      VD_TRY(cudaMemcpyAsync(hv.data(), hasv, (size_t)nb_cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      VD_TRY(cudaMemcpyAsync(&hn_fl, nfl, sizeof(hn_fl), cudaMemcpyDeviceToHost, st));
+      VD_TRY(cudaStreamSynchronize(st));
+      std::vector<int32_t> seeds;
+      for (int64_t k = 0; k < nb_cells; ++k)
+        if (!hv[k]) seeds.push_back((int32_t)(c0 + k));
+      const int64_t batch_start = nv_known;
+      VD_TRY(descent(seeds));
+      const int64_t nfirst = (int64_t)hn_fl + (nv_known - batch_start);
+      if (nv_known > batch_start) {
+        k_append_range<<<nb(nv_known - batch_start), 256, 0, st>>>(flist, (int64_t)hn_fl, batch_start, nv_known);
+        count_launch();
+      }
+      VD_TRY(run_levels(0, nfirst, flist, slice));
+      if (stop) break;
+      // every batch cell must have been reached
+      if (nv_known > batch_start) {
+        k_cell_mark<<<nb(nv_known - batch_start), 256, 0, st>>>(T, batch_start, nv_known, hasv); count_launch();
+      }
+      VD_TRY(cudaMemcpyAsync(hv.data(), hasv, (size_t)nb_cells * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      VD_TRY(cudaStreamSynchronize(st));
+      for (int64_t k = 0; k < nb_cells; ++k)
+        if (!hv[k]) {
+          snprintf(err, errlen, "per-cell exploration reached no vertex of cell %lld", (long long)(c0 + k));
+          return cudaErrorUnknown;
+        }
+    }
   }
   unsigned long long hc[4];
   VD_TRY(cudaMemcpyAsync(hc, cnts, sizeof(hc), cudaMemcpyDeviceToHost, st));
@@ -1074,6 +1219,9 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
   stats->raycast_ms = raycast_ms;
   stats->fallback_rays = nfallback;
   stats->overflow_rays = noverflow;
+  stats->edge_table_bytes = ecap * (int64_t)(d + 1) * (int64_t)sizeof(int32_t) + eh * (int64_t)sizeof(int32_t);
+  stats->vertex_table_bytes =
+      vcap * (int64_t)(L * sizeof(int32_t) + d * sizeof(double)) + vh * (int64_t)sizeof(int32_t);
   return cudaSuccess;
 #undef VD_TRY
 }

@@ -65,14 +65,15 @@ class vd_stats(ctypes.Structure):
     _fields_ = [("rays", ctypes.c_int64), ("tiles_visited", ctypes.c_int64), ("pairs_screened", ctypes.c_int64),
                 ("rechecked", ctypes.c_int64), ("fallback_rays", ctypes.c_int64), ("overflow_rays", ctypes.c_int64),
                 ("ties", ctypes.c_int64), ("levels", ctypes.c_int64), ("vertices", ctypes.c_int64),
-                ("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("raycast_ms", ctypes.c_double)]
+                ("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("raycast_ms", ctypes.c_double),
+                ("edge_table_bytes", ctypes.c_int64), ("vertex_table_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 EXPORTS = ["vd_kernel_launches", "vd_config_default", "vd_create", "vd_destroy", "vd_last_error", "vd_status_str", "vd_set_precision",
-           "vd_last_stats", "vd_set_nodes", "vd_raycast", "vd_vertices", "vd_mesh_count", "vd_mesh_dim",
+           "vd_last_stats", "vd_set_nodes", "vd_raycast", "vd_vertices", "vd_vertices_by_cells", "vd_mesh_count", "vd_mesh_dim",
            "vd_mesh_copy", "vd_mesh_stats", "vd_mesh_free", "vd_mc_integrate", "vd_mc_get", "vd_mc_rays",
            "vd_mc_adjoint", "vd_mc_integrals", "vd_hmc_integrals", "vd_mc_stats", "vd_mc_count", "vd_mc_free", "vd_mc_directions",
            "vd_mc_integrate_batch", "vd_raycast_noalloc", "vd_poly_integrate", "vd_poly_get", "vd_poly_free", "vd_random_walk"]
@@ -108,6 +109,7 @@ def load(build_if_missing: bool = True):
         "vd_raycast": (i32, [P, P, P, P, i32, i64, P, P, P, i32]),
         "vd_raycast_noalloc": (i32, [P, P, P, P, i32, i64, P, P]),
         "vd_vertices": (i32, [P, P]),
+        "vd_vertices_by_cells": (i32, [P, i64, P]),
         "vd_mesh_count": (i64, [P]),
         "vd_mesh_dim": (i32, [P]),
         "vd_mesh_copy": (i32, [P, P, P, i32]),
@@ -363,6 +365,12 @@ def vd_mc_free(mc):
 def vd_vertices(ctx):
     m = ctypes.c_void_p()
     _check(ctx, load().vd_vertices(ctx, ctypes.byref(m)))
+    return m
+
+
+def vd_vertices_by_cells(ctx, cells_per_batch: int = 0):
+    m = ctypes.c_void_p()
+    _check(ctx, load().vd_vertices_by_cells(ctx, int(cells_per_batch), ctypes.byref(m)))
     return m
 
 

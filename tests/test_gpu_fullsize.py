@@ -76,6 +76,13 @@ def test_traversal_d5_n20000(orc):
     T, C, st = out[VD_FP32]
     for other in (VD_FP64, VD_TC16):
         assert np.array_equal(T, out[other][0]) and np.array_equal(C, out[other][1])
+    # the per-cell exploration (cells in index order, 1024 at a time, the edge
+    # table rebuilt per batch) finds the same vertices with a smaller edge table
+    vor = Voronoi(X)
+    t, c, stc = vor.vertices(cells_per_batch=1024)
+    vor.close()
+    assert np.array_equal(T, t.cpu().numpy()) and np.array_equal(C, c.cpu().numpy())
+    assert stc["edge_table_bytes"] * 4 < st["edge_table_bytes"]
     assert st["vertices"] == len(T) > 2_000_000
     assert np.all(np.diff(T, axis=1) > 0)  # each tuple sorted, no repeats
     assert int(np.sum(np.sum(T < 0, axis=1) == d)) == 2 ** d  # the cube corners

@@ -42,6 +42,43 @@ def test_vertices_mixture_and_tiny(orc, prec):
         assert np.array_equal(t1, t0) and np.array_equal(c1, c0)
 
 
+@pytest.mark.parametrize("prec", [VD_FP64, VD_FP32, VD_TC16])
+@pytest.mark.parametrize("d,N,batch", [(2, 500, 1), (2, 500, 37), (3, 2000, 100), (4, 300, 7), (5, 120, 16),
+                                       (6, 40, 1), (6, 40, 0)])
+def test_cell_exploration_parity(orc, prec, d, N, batch):
+    """Per-cell sequential exploration (Section 2.3): cells in index order,
+    `batch` at a time (1: one cell at a time, 0: automatic), the edge counters
+    rebuilt for each batch from the vertices found so far: the same tuples
+    and coordinates as the oracle's traversal, bit for bit, with a smaller
+    edge table than the whole-diagram traversal's."""
+    need_cuda()
+    X = synth.uniform(N, d, seed=0)
+    t0, c0, _ = orc.vertices(X)
+    vor = Voronoi(X, precision=prec)
+    t1, c1, st = vor.vertices(cells_per_batch=batch)
+    _, _, st_all = vor.vertices()
+    vor.close()
+    assert np.array_equal(t1.cpu().numpy(), t0) and np.array_equal(c1.cpu().numpy(), c0)
+    assert st["vertices"] == len(t0)
+    assert 0 < st["edge_table_bytes"] < st_all["edge_table_bytes"]
+    assert st["vertex_table_bytes"] == st_all["vertex_table_bytes"]
+
+
+@pytest.mark.parametrize("prec", [VD_FP32, VD_TC16])
+def test_cell_exploration_mixture_and_tiny(orc, prec):
+    """Clustered nodes (cells of very different sizes; most batch cells are
+    reached from their neighbours' vertices, not seeded), one and two nodes,
+    33 nodes in batches of 5 (a ragged last batch)."""
+    need_cuda()
+    for X, b in [(synth.gaussian_mixture(400, 3, 8, 0.05, seed=2), 50), (synth.uniform(1, 2, seed=1), 1),
+                 (synth.uniform(2, 3, seed=2), 1), (synth.uniform(33, 2, seed=3), 5)]:
+        t0, c0, _ = orc.vertices(X)
+        vor = Voronoi(X, precision=prec)
+        t1, c1, _ = vor.vertices(cells_per_batch=b)
+        vor.close()
+        assert np.array_equal(t1.cpu().numpy(), t0) and np.array_equal(c1.cpu().numpy(), c0)
+
+
 def test_vertex_invariants_larger(orc):
     """d = 5, N = 3000: every edge has two endpoints and each of the 2^d
     corners appears once; a sample of vertices is checked by the oracle's

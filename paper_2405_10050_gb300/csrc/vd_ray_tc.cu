@@ -388,9 +388,12 @@ __device__ __forceinline__ void grp_ray_store(const GrpRay<D>& S, int i, float* 
   }
 }
 
+// Blocks per SM: 8 (the 512 tensor-memory columns hold 8 blocks of 64; 64
+// registers per thread) for d <= 5, 7 above, where 64 registers would spill.
 template <int D>
-__global__ void __launch_bounds__(kGrpM, 6) k_ray_list_tc(TreeView tr, RaySource rs, RayOut ro, Counters* ctr,
-                                                       GrpLayout L, unsigned long long* work, long long wait_limit) {
+__global__ void __launch_bounds__(kGrpM, D <= 5 ? 8 : 7)
+    k_ray_list_tc(TreeView tr, RaySource rs, RayOut ro, Counters* ctr, GrpLayout L, unsigned long long* work,
+                  long long wait_limit) {
   __shared__ __align__(1024) unsigned char sA[kGrpM * 32];     // [128 x 16] fp16 list entries w_j
   __shared__ __align__(1024) unsigned char sB[kGrpCols * 32];  // [64 x 16] fp16: row 2i = u_i, 2i + 1 = p_i
   __shared__ __align__(16) GrpRay<D> S;

@@ -22,7 +22,7 @@ namespace vd {
 namespace {
 
 constexpr int kCellThreads = 128;
-constexpr int kCellBuf = 8;  // candidates kept per ray
+constexpr int kCellBuf = 4;  // candidates kept per ray (more: the tree walk finishes the ray)
 
 // Shared memory of one cell: offsets [D][K], bounds, ids; per-thread
 // candidate buffers; for the recheck each thread's binary64 direction, the
@@ -110,10 +110,21 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
       u32[q] = __double2float_rn(u64[q]);
       p0[q] = 0.f;
     }
-    // box faces: binary32 interval of (b - x_ia) / u_a
+    // box faces: binary32 interval of (b - x_ia) / u_a; a face is kept only
+    // if its lower bound does not exceed the smallest upper bound of all
     float T = INFINITY;
     int nc = 0;
-    for (int a = 0; a < d && valid; ++a) {
+    bool overflow = false;
+    float ftlo[D];
+    int fside[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      ftlo[a] = INFINITY;
+      fside[a] = 0;
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      if (a >= d || !valid) continue;
       double ua64 = 0.0;
       float ua = 0.f, va = 0.f;
 #pragma unroll
@@ -135,16 +146,24 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
       const float thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
                                     : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
       T = fminf(T, thi);
-      if (nc < kCellBuf) {
-        cb[nc] = face_id(a, s);
-        ct[nc] = tlo;
-        ++nc;
-      }
+      ftlo[a] = tlo;
+      fside[a] = s;
     }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (ftlo[a] <= T) {
+        if (nc < kCellBuf) {
+          cb[nc] = face_id(a, fside[a]);
+          ct[nc] = ftlo[a];
+          ++nc;
+        } else {
+          overflow = true;  // the tree walk finishes the ray
+        }
+      }
     Ball<D> ball;
     make_ball<D>(g32, p0, u32, T, B, ball);
     float far2 = far_radius2<D>(tr, ball, g32);
-    bool certified = !valid, overflow = false;
+    bool certified = !valid;
     int c = 0;
     for (; c < n && valid; ++c) {
       if (sflo[c] >= far2) {
@@ -417,10 +436,11 @@ __device__ __forceinline__ void flush_counters(Counters* ctr, unsigned long long
   }
 }
 
+// 8 blocks per SM for d <= 5 (64 registers, no spills), no bound above.
 template <int D, bool F64>
-__global__ void __launch_bounds__(kCellThreads) k_mc_cell(TreeView tr, int64_t R, uint64_t seed, uint32_t set,
-                                                          RayOut ro, Counters* ctr, unsigned long long* work,
-                                                          int32_t* fb_cell, int32_t* fb_ray, int64_t fb_cap) {
+__global__ void __launch_bounds__(kCellThreads, D <= 5 ? 8 : 1)
+    k_mc_cell(TreeView tr, int64_t R, uint64_t seed, uint32_t set, RayOut ro, Counters* ctr, unsigned long long* work,
+              int32_t* fb_cell, int32_t* fb_ray, int64_t fb_cap) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int64_t s_cell;
   unsigned long long n_pairs = 0, n_rech = 0, n_brute = 0;

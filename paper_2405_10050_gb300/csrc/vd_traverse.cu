@@ -92,6 +92,25 @@ __device__ __forceinline__ void sort_small(int32_t* t, int L) {
   }
 }
 
+// |x| rounded to binary32 (to nearest, ties to even) as an order-preserving
+// integer, the bit pattern of that binary32 value, by integer operations (the
+// same order as comparing __double2float_rn(fabs(x)), without the FP64-pipe
+// conversion); kNanKey for NaN, which compares as no other key does.
+constexpr int32_t kNanKey = INT32_MIN;
+__device__ __forceinline__ int32_t f32key_abs(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+  const int e = (int)(b >> 52);
+  const uint64_t m = b & ((1ull << 52) - 1);
+  if (e == 0x7FF) return m ? kNanKey : 0x7F800000;
+  const int fe = e - 1023 + 127;
+  if (fe <= 0) return __float_as_int(__double2float_rn(__longlong_as_double((long long)b)));  // zero or tiny
+  if (fe >= 255) return 0x7F800000;
+  uint32_t r = ((uint32_t)fe << 23) | (uint32_t)(m >> 29);
+  const uint64_t rem = m & ((1ull << 29) - 1);
+  if (rem > (1ull << 28) || (rem == (1ull << 28) && (r & 1u))) r += 1u;  // a carry moves into the exponent
+  return (int32_t)r;
+}
+
 // Canonical vertex coordinates from the sorted tuple (same steps as the
 // definition: x0 = first node, y = r - x0, fixed axes from the faces,
 // rows 2 w_k . y = |w_k|^2 on the free axes, partial pivoting with the
@@ -134,10 +153,11 @@ __device__ bool vertex_coords(const double* X, int d, const int32_t* sig, double
   double inv[D];
   for (int c = 0; c < nf; ++c) {
     int piv = c;
-    float pbest = __double2float_rn(fabs(M[c][c]));
+    int32_t pbest = f32key_abs(M[c][c]);
+    const bool pnan = pbest == kNanKey;  // a NaN magnitude compares below nothing
     for (int rr = c + 1; rr < nf; ++rr) {
-      const float a = __double2float_rn(fabs(M[rr][c]));
-      if (a > pbest) {
+      const int32_t a = f32key_abs(M[rr][c]);
+      if (!pnan && a > pbest) {
         piv = rr;
         pbest = a;
       }
@@ -207,10 +227,10 @@ __device__ bool search_direction(const double* X, int d, const int32_t* sig, int
   double inv[D];
   for (int c = 0; c < nr; ++c) {
     int pr = c, pc = c;
-    float best = -1.0f;
+    int32_t best = -1;  // below every magnitude (NaN has the lowest key)
     for (int rr = c; rr < nr; ++rr)
       for (int cc = c; cc < nf; ++cc) {
-        const float a = __double2float_rn(fabs(M[rr][cc]));
+        const int32_t a = f32key_abs(M[rr][cc]);
         if (a > best) {
           best = a;
           pr = rr;

@@ -1419,7 +1419,7 @@ cudaError_t launch_mc_fallback_dev(const SetDesc& S, int64_t R, uint64_t seed, c
 }
 
 int default_knn_k(int d) {
-  static const int k[] = {0, 16, 32, 96, 256, 512, 1024, 1024, 1024};
+  static const int k[] = {0, 16, 32, 96, 256, 1024, 1024, 1024, 1024};
   return d <= 8 ? k[d] : 0;
 }
 

@@ -50,11 +50,11 @@ WORKLOAD = "exhaustive vertex traversal, d=5, N=20000 iid uniform in [0,1]^5 (se
 NEIGHBOURS_D5 = 95  # neighbours per cell in d = 5 (the paper's table of vertices and neighbours per cell)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, ncu) of one traversal's RayCast on the default path,
 # every launch of k_grp_count, k_grp_alloc, k_grp_scatter, k_ray_list_tc, k_grp_finish and the tree-walk and
-# binary64 follow-ups: 8998.9 MB over the three traversals of `python bench.py --steps 1 --warmup 1 --no-fp64
+# binary64 follow-ups: 8964.0 MB over the three traversals of `python bench.py --steps 1 --warmup 1 --no-fp64
 # --no-binary32 --no-cpu --no-mc --no-highd --no-hmc --no-walk --no-small --no-batch --no-cells`, captured with
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none -k
-# "regex:k_ray_list_tc|k_grp_|k_ray_mixed|k_ray_fp64"` (list scan at 8 blocks per SM)
-RAYCAST_DRAM_BYTES_PER_STEP = 2999.6e6
+# "regex:k_ray_list_tc|k_grp_|k_ray_mixed|k_ray_fp64"` (list scan at 8 blocks per SM, lists of 1024 nodes)
+RAYCAST_DRAM_BYTES_PER_STEP = 2988.0e6
 
 
 def _peaks():

@@ -1088,6 +1088,84 @@ __device__ __forceinline__ void knn_sort(WarpKnn& S, int P, int lane) {
   }
 }
 
+// Sort of S.key/S.id[0, n) by (key, id) with the buffer's second half
+// S.key/S.id[n, 2n) as scratch (n <= cap / 2): a stable LSD radix sort by the
+// key's bits (4 passes of 8 bits; non-negative floats order like their bit
+// patterns; ranks among equal digits by __match_any_sync), then each run of
+// equal keys ordered by id (ties are rare: lane 0 sorts them in place).
+__device__ void knn_radix_sort(WarpKnn& S, int n, int lane) {
+  const unsigned lt = (1u << lane) - 1u;
+  float* kin = S.key;
+  int32_t* iin = S.id;
+  float* kout = S.key + n;
+  int32_t* iout = S.id + n;
+  for (int shift = 0; shift < 32; shift += 8) {
+    for (int b = lane; b < 256; b += 32) S.hist[b] = 0;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) atomicAdd(&S.hist[(__float_as_uint(kin[i]) >> shift) & 255u], 1);
+    __syncwarp();
+    int c[8], tot = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      c[j] = S.hist[lane * 8 + j];
+      tot += c[j];
+    }
+    int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int run = incl - tot;
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      S.hist[lane * 8 + j] = run;
+      run += c[j];
+    }
+    __syncwarp();
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      const int i = c0 + lane;
+      const bool valid = i < n;
+      const float k = valid ? kin[i] : 0.f;
+      const int32_t id = valid ? iin[i] : 0;
+      const int dg = valid ? (int)((__float_as_uint(k) >> shift) & 255u) : 256 + lane;
+      const unsigned peers = __match_any_sync(kFull, dg);
+      const int base = valid ? S.hist[dg] : 0;
+      __syncwarp();
+      if (valid) {
+        const int pos = base + __popc(peers & lt);
+        kout[pos] = k;
+        iout[pos] = id;
+        if (lane == __ffs(peers) - 1) S.hist[dg] = base + __popc(peers);
+      }
+      __syncwarp();
+    }
+    float* tk = kin;
+    kin = kout;
+    kout = tk;
+    int32_t* ti = iin;
+    iin = iout;
+    iout = ti;
+  }
+  // four passes: the sorted keys are back in S.key/S.id[0, n)
+  bool tie = false;
+  for (int i = lane + 1; i < n; i += 32) tie |= S.key[i] == S.key[i - 1];
+  if (__any_sync(kFull, tie) && lane == 0) {
+    for (int i = 1; i < n; ++i) {
+      const float k = S.key[i];
+      const int32_t x = S.id[i];
+      int j = i - 1;
+      while (j >= 0 && S.key[j] == k && S.id[j] > x) {
+        S.id[j + 1] = S.id[j];
+        --j;
+      }
+      S.id[j + 1] = x;
+    }
+  }
+  __syncwarp();
+}
+
 // Key of rank k (0-based) among S.key[0, n) (non-negative floats, whose bit
 // patterns order like the values): most-significant-byte-first radix select.
 __device__ __forceinline__ float knn_select(WarpKnn& S, int n, int k, int lane) {
@@ -1259,14 +1337,18 @@ __global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, 
       __syncwarp();
       n_sort = K;
     }
-    int P = 1;
-    while (P < n_sort) P <<= 1;
-    for (int i = n_sort + lane; i < P; i += 32) {
-      S.key[i] = INFINITY;
-      S.id[i] = INT32_MAX;
+    if (2 * n_sort <= cap) {
+      knn_radix_sort(S, n_sort, lane);
+    } else {  // lists longer than half the gather buffer: bitonic sort in place
+      int P = 1;
+      while (P < n_sort) P <<= 1;
+      for (int i = n_sort + lane; i < P; i += 32) {
+        S.key[i] = INFINITY;
+        S.id[i] = INT32_MAX;
+      }
+      __syncwarp();
+      knn_sort(S, P, lane);
     }
-    __syncwarp();
-    knn_sort(S, P, lane);
     const int nk = min(count, K);
     for (int c = lane; c < nk; c += 32) knn[g * K + c] = S.id[c];
     if (lane == 0) {

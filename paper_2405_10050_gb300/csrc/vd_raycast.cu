@@ -1235,6 +1235,17 @@ __global__ void __launch_bounds__(kKnnWpb * 32) k_knn_build(TreeView tr, int K, 
 #pragma unroll
     for (int k = 0; k < D; ++k) g32[k] = k < d ? tr.X32[g * d + k] : 0.f;
     float r = r0;
+    {  // near the faces of the nodes' bounding box the ball holds fewer nodes:
+       // one correction by the fraction of its bounding cube inside the box
+      float f = 1.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+        if (k < d) {
+          const float len = fminf(g32[k] + r, tr.root_hi[k]) - fmaxf(g32[k] - r, tr.root_lo[k]);
+          f *= fmaxf(len, 1e-3f * r) / (2.f * r);
+        }
+      r = fminf(r * __powf(f, -1.f / (float)d), rmax);
+    }
     int count = 0;
     const float target = fminf(1.5f * (float)K + 32.f, 0.75f * (float)cap);
     for (int attempt = 0; attempt < 64; ++attempt) {
@@ -1527,8 +1538,9 @@ cudaError_t build_knn(TreeView* tv, int K, cudaStream_t st, DevBufs& bufs) {
     tv->X32v = X32v;
     tv->x32q = q;
   }
-  // initial radius: about 2K nodes expected in the ball for the node density
-  // of the bounding box of the root
+  // initial radius: about 1.3 K nodes expected in the ball for the node
+  // density of the bounding box of the root (the kernel corrects it per node
+  // for the part of the ball outside that box)
   double vol = 1.0, diag2 = 0.0;
   {
     std::vector<double> lo(d), hi(d);
@@ -1548,7 +1560,7 @@ cudaError_t build_knn(TreeView* tv, int K, cudaStream_t st, DevBufs& bufs) {
     }
   }
   const double vball = std::pow(M_PI, 0.5 * d) / std::tgamma(0.5 * d + 1.0);
-  const float r0 = (float)std::pow(std::min(1.5 * K + 32, 0.75 * knn_cap(K)) * vol / ((double)N * vball), 1.0 / d);
+  const float r0 = (float)std::pow(std::min(1.3 * K + 32, 0.75 * knn_cap(K)) * vol / ((double)N * vball), 1.0 / d);
   const float rmax = (float)std::sqrt(diag2) * 1.01f + 1e-6f;
   e = VD_DISPATCH_D(d, launch_knn_d, tv, K, std::min(r0, rmax), rmax, knn, kcnt, kcert, st);
   if (e != cudaSuccess) return e;

@@ -186,10 +186,28 @@ struct Workspace {
   cudaError_t get_n(int slot, size_t n, T** p) {
     return get(slot, n * sizeof(T), reinterpret_cast<void**>(p));
   }
+  // 16 words of pinned host memory mapped into the device address space: a
+  // kernel writes counters there and the host reads them after a stream
+  // synchronisation, with no copy launched
+  unsigned long long* host_words = nullptr;
+  cudaError_t host_words_get(unsigned long long** p) {
+    if (!host_words) {
+      cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&host_words), 16 * sizeof(unsigned long long),
+                                    cudaHostAllocMapped);
+      if (e != cudaSuccess) {
+        host_words = nullptr;
+        return e;
+      }
+    }
+    *p = host_words;
+    return cudaSuccess;
+  }
   void release() {
     for (auto& s : slots)
       if (s.first) cudaFree(s.first);
     slots.clear();
+    if (host_words) cudaFreeHost(host_words);
+    host_words = nullptr;
   }
 };
 

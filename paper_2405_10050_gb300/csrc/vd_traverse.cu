@@ -686,6 +686,16 @@ __global__ void k_descent_cand(int d, int64_t ns, const int32_t* ssig, const int
   hit[s] = ssig[s * (VD_MAX_D + 1) + d];
 }
 
+// The level's counters (nv, ne, rays, -, winners), the tree-walk and binary64
+// follow-up counts and the flags, written to mapped host memory.
+__global__ void k_read_level(const unsigned long long* cnts, const Counters* ctr, volatile unsigned long long* out) {
+  const int t = threadIdx.x;
+  if (t < 5) out[t] = cnts[t];
+  else if (t == 5) out[5] = ctr->fallback;
+  else if (t == 6) out[6] = ctr->overflow;
+  else if (t == 7) out[7] = ctr->flags;
+}
+
 // Seed s at node snode[s]: sigma = {node}, one generator, alive, r = x_node.
 __global__ void k_seed_init(const double* X, int d, int64_t ns, const int32_t* snode, int32_t* ssig, int* sm,
                             int* alive, double* sr) {
@@ -1111,14 +1121,17 @@ cudaError_t traverse_vertices(const TreeView& tv, int precision, const vd_config
         count_launch();
         VD_TRAV_D(d, launch_finish, T, tv.X, cand, cslot, win, rmax, nwin, vids, flags, st);
         if ((ee = cudaGetLastError())) return ee;
+        unsigned long long* hw = nullptr;
+        if ((ee = ws.host_words_get(&hw))) return ee;
+        k_read_level<<<1, 32, 0, st>>>(cnts, ctr, hw);
+        count_launch();
+        if ((ee = cudaGetLastError()) || (ee = cudaStreamSynchronize(st))) return ee;
+        const volatile unsigned long long* hv = hw;
         unsigned long long hc[6];
-        unsigned hf = 0;
-        if ((ee = cudaMemcpyAsync(hc, cnts, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) ||
-            (ee = cudaMemcpyAsync(hc + 4, &ctr->fallback, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) ||
-            (ee = cudaMemcpyAsync(hc + 5, &ctr->overflow, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) ||
-            (ee = cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st)) ||
-            (ee = cudaStreamSynchronize(st)))
-          return ee;
+        for (int k = 0; k < 4; ++k) hc[k] = hv[k];
+        hc[4] = hv[5];
+        hc[5] = hv[6];
+        const unsigned hf = (unsigned)hv[7];
         account(hc + 4);
         noverflow += (int64_t)std::min<unsigned long long>(hc[5], (unsigned long long)rcap);
         raycasts += (int64_t)std::min<unsigned long long>(hc[2], (unsigned long long)rcap);

@@ -56,6 +56,10 @@ struct vd_ctx {
   char err[512] = {0};
   vd_stats last{};
   DevBufs node_bufs;
+  // one device block that the node set's buffers are carved from (sized by
+  // the previous node set), so that setting nodes of an unchanged size makes
+  // no cudaMalloc or cudaFree (both synchronise the device)
+  vd::Arena node_arena;
   TreeView tree;
   double* X = nullptr;
   int64_t N = 0;
@@ -257,6 +261,7 @@ void vd_destroy(vd_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->st);
   ctx->node_bufs.release();
+  if (ctx->node_arena.base) cudaFree(ctx->node_arena.base);
   ctx->own.release();
   ctx->trav_ws.release();
   ctx->mc_ws.release();
@@ -285,7 +290,19 @@ vd_status vd_set_nodes(vd_ctx* ctx, const double* X, int64_t N, int32_t d, int32
     return set_err(ctx, VD_EINVAL, "vd_set_nodes: need X, 1 <= N <= 2^30, 1 <= d <= 16 (N=%lld d=%d)",
                    (long long)N, d);
   VD_CK(cudaStreamSynchronize(ctx->st), "sync");
+  // the previous set asked for `requested` bytes: keep a block that holds them
+  const size_t need = ctx->node_bufs.requested;
   ctx->node_bufs.release();
+  if (need > ctx->node_arena.cap) {
+    if (ctx->node_arena.base) cudaFree(ctx->node_arena.base);
+    ctx->node_arena.base = nullptr;
+    ctx->node_arena.cap = 0;
+    const size_t cap = need + need / 8;
+    if (cudaMalloc(reinterpret_cast<void**>(&ctx->node_arena.base), cap) == cudaSuccess) ctx->node_arena.cap = cap;
+    else cudaGetLastError();
+  }
+  ctx->node_arena.off = 0;
+  ctx->node_bufs.arena = &ctx->node_arena;
   ctx->X = nullptr;
   ctx->N = 0;
   ctx->d = 0;

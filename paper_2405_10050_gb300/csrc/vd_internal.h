@@ -147,9 +147,11 @@ struct Arena {
 struct DevBufs {
   std::vector<void*> ptrs;
   Arena* arena = nullptr;  // if set, buffers come from it while it has room
+  size_t requested = 0;    // bytes asked for since the last release (rounded as the arena rounds)
   cudaError_t alloc(void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    requested += (bytes + 255) / 256 * 256;
     if (arena && (*p = arena->take(bytes)) != nullptr) return cudaSuccess;
     cudaError_t e = cudaMalloc(p, bytes);
     if (e == cudaSuccess) ptrs.push_back(*p);
@@ -160,6 +162,7 @@ struct DevBufs {
   void release() {
     for (void* p : ptrs) cudaFree(p);
     ptrs.clear();
+    requested = 0;
   }
 };
 

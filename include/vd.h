@@ -17,6 +17,11 @@
  *    call returns (every call synchronises its stream before returning).
  *  - Ownership: the caller owns every array it passes; library objects
  *    (vd_ctx, vd_mesh, vd_mc) are owned by the library until their free call.
+ *  - Device memory: freeing a vd_mesh or (unbatched) vd_mc hands its device
+ *    blocks to its context, which reuses them for its next results (up to
+ *    16 GiB are kept); they are returned to CUDA when the context and the
+ *    last of its results are freed.  A context keeps one block for its node
+ *    set, sized by the largest node set so far.
  *  - Errors: every call returns a vd_status and throws nothing across the
  *    ABI; vd_last_error() gives a message for the last failure on a context.
  *  - Floating point: the exact path (VD_FP64) and the recheck of the mixed

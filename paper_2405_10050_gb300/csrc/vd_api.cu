@@ -60,6 +60,8 @@ struct vd_ctx {
   // the previous node set), so that setting nodes of an unchanged size makes
   // no cudaMalloc or cudaFree (both synchronise the device)
   vd::Arena node_arena;
+  // device blocks of freed MC results and meshes, for the next ones
+  std::shared_ptr<vd::BufCache> result_cache = std::make_shared<vd::BufCache>();
   TreeView tree;
   double* X = nullptr;
   int64_t N = 0;
@@ -537,6 +539,7 @@ vd_status vd_mc_integrate(vd_ctx* ctx, int64_t R, uint64_t seed, vd_mc** out) {
     return set_err(ctx, VD_EINVAL, "vd_mc_integrate: bad rays_per_cell %lld", (long long)R);
   vd_mc* mc = new (std::nothrow) vd_mc();
   if (!mc) return VD_ENOMEM;
+  mc->bufs.cache = ctx->result_cache;
   double* Xc = nullptr;
   cudaError_t e = mc->bufs.alloc_n(&Xc, (size_t)ctx->N * ctx->d);
   if (e == cudaSuccess)
@@ -1132,6 +1135,7 @@ static vd_status vertices_impl(vd_ctx* ctx, int64_t cells_per_batch, vd_mesh** o
   if (ctx->N < 1) return set_err(ctx, VD_EINVAL, "vd_vertices: empty node set");
   vd_mesh* m = new (std::nothrow) vd_mesh();
   if (!m) return VD_ENOMEM;
+  m->bufs.cache = ctx->result_cache;
   m->st = ctx->st;
   m->d = ctx->d;
   VD_CK(cudaMemsetAsync(ctx->ctr, 0, sizeof(Counters), ctx->st), "memset");

@@ -3,6 +3,9 @@
 #pragma once
 #include <atomic>
 #include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <utility>
 #include <vector>
 #include <cuda_runtime.h>
@@ -144,15 +147,65 @@ struct Arena {
   }
 };
 
+// Device blocks of freed results kept for the next results of the same
+// context (result objects share it with the context; the last owner frees
+// it): a result of an unchanged size then makes no cudaMalloc or cudaFree.
+// Sizes are rounded up to 2 MiB; a block serves a request of at least half
+// its size; at most 16 GiB are kept.
+struct BufCache {
+  std::mutex m;
+  std::multimap<size_t, void*> blocks;
+  size_t bytes = 0;
+  static size_t round(size_t b) { return (b + ((size_t)2 << 20) - 1) / ((size_t)2 << 20) * ((size_t)2 << 20); }
+  void* take(size_t b, size_t* got) {
+    std::lock_guard<std::mutex> lk(m);
+    auto it = blocks.lower_bound(b);
+    if (it == blocks.end() || it->first > 2 * b) return nullptr;
+    void* p = it->second;
+    *got = it->first;
+    bytes -= it->first;
+    blocks.erase(it);
+    return p;
+  }
+  void give(void* p, size_t b) {
+    {
+      std::lock_guard<std::mutex> lk(m);
+      if (bytes + b <= ((size_t)16 << 30)) {
+        blocks.emplace(b, p);
+        bytes += b;
+        return;
+      }
+    }
+    cudaFree(p);
+  }
+  ~BufCache() {
+    for (auto& kv : blocks) cudaFree(kv.second);
+  }
+};
+
 struct DevBufs {
   std::vector<void*> ptrs;
   Arena* arena = nullptr;  // if set, buffers come from it while it has room
   size_t requested = 0;    // bytes asked for since the last release (rounded as the arena rounds)
+  std::shared_ptr<BufCache> cache;  // if set, blocks come from it and return to it
+  std::vector<size_t> sizes;        // with a cache: the block size of each of ptrs
   cudaError_t alloc(void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
     requested += (bytes + 255) / 256 * 256;
     if (arena && (*p = arena->take(bytes)) != nullptr) return cudaSuccess;
+    if (cache) {
+      const size_t b = BufCache::round(bytes);
+      size_t got = 0;
+      if ((*p = cache->take(b, &got)) == nullptr) {
+        cudaError_t e = cudaMalloc(p, b);
+        if (e != cudaSuccess) return e;
+        got = b;
+      }
+      ptrs.push_back(*p);
+      sizes.push_back(got);
+      return cudaSuccess;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e == cudaSuccess) ptrs.push_back(*p);
     return e;
@@ -160,8 +213,12 @@ struct DevBufs {
   template <class T>
   cudaError_t alloc_n(T** p, size_t n) { return alloc(reinterpret_cast<void**>(p), n * sizeof(T)); }
   void release() {
-    for (void* p : ptrs) cudaFree(p);
+    for (size_t k = 0; k < ptrs.size(); ++k) {
+      if (cache && k < sizes.size()) cache->give(ptrs[k], sizes[k]);
+      else cudaFree(ptrs[k]);
+    }
     ptrs.clear();
+    sizes.clear();
     requested = 0;
   }
 };

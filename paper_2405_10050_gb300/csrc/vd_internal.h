@@ -59,6 +59,8 @@ struct TreeView {
   const float* X32 = nullptr;     // [N][d] nearest binary32 of X, id order
   const float4* X32v = nullptr;   // d <= 8: [N][x32q] the same, rows zero padded to 16-byte vectors
   int x32q = 0;
+  double box_lo[16] = {};         // bounding box of all nodes (host copy, binary64)
+  double box_hi[16] = {};
   float root_lo[16] = {};         // bounding box of all nodes (binary32, outward)
   float root_hi[16] = {};
 };

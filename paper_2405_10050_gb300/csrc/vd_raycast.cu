@@ -1543,14 +1543,9 @@ cudaError_t build_knn(TreeView* tv, int K, cudaStream_t st, DevBufs& bufs) {
   // for the part of the ball outside that box)
   double vol = 1.0, diag2 = 0.0;
   {
-    std::vector<double> lo(d), hi(d);
-    for (int k = 0; k < d; ++k) {
-      cudaMemcpyAsync(&lo[k], tv->blo64 + k * tv->total + tv->off[tv->nlev - 1], sizeof(double),
-                      cudaMemcpyDeviceToHost, st);
-      cudaMemcpyAsync(&hi[k], tv->bhi64 + k * tv->total + tv->off[tv->nlev - 1], sizeof(double),
-                      cudaMemcpyDeviceToHost, st);
-    }
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    // the root's box is the nodes' bounding box the tree build read back
+    const double* lo = tv->box_lo;
+    const double* hi = tv->box_hi;
     for (int k = 0; k < d; ++k) {
       const double w = std::max(hi[k] - lo[k], 1e-12);
       vol *= w;

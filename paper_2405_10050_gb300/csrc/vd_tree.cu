@@ -411,6 +411,10 @@ cudaError_t build_tree(const double* X, int64_t N, int d, cudaStream_t st, DevBu
   if (e != cudaSuccess) { scratch.release(); return e; }
   double ca = 1.0;
   for (int k = 0; k < 2 * d; ++k) ca = std::max(ca, std::fabs(hb[k]));
+  for (int k = 0; k < d; ++k) {
+    t.box_lo[k] = hb[k];
+    t.box_hi[k] = hb[d + k];
+  }
   if (!std::isfinite(ca)) { scratch.release(); return cudaErrorInvalidValue; }
   t.coord_abs = (float)ca * (1.0f + 1e-6f);
   k_morton<<<nblocks(N, 256), 256, 0, st>>>(X, N, d, bounds, keys, vals); count_launch();
@@ -444,6 +448,7 @@ cudaError_t build_tree(const double* X, int64_t N, int d, cudaStream_t st, DevBu
     count_launch();
   }
   e = cudaStreamSynchronize(st);
+  bufs.requested += scratch.requested;  // the scratch was carved from the same block: size it for both
   scratch.release();
   if (e != cudaSuccess) return e;
   VD_TRY(cudaGetLastError());

@@ -273,6 +273,23 @@ struct Workspace {
   }
 };
 
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in
+// maximum, the same value on every call, so that launches of the same kernel
+// with different sizes from several host threads cannot lower the limit
+// between another thread's setting and its launch.
+template <class Kernel>
+inline cudaError_t allow_max_dyn_smem(Kernel kernel) {
+  int dev = 0, mx = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+  if (e == cudaSuccess)  // the limit counts the dynamic part only; static shared memory takes the rest
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+  if (e != cudaSuccess) cudaGetLastError();  // a later launch check must not see this error
+  return e;
+}
+
 // ---- launchers (defined in the .cu files) --------------------------------
 // Builds the tree of X_dev (N x d, device) into buffers owned by `bufs`.
 cudaError_t build_tree(const double* X_dev, int64_t N, int d, cudaStream_t st, DevBufs& bufs, TreeView* tv);

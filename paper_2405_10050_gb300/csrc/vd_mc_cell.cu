@@ -513,7 +513,7 @@ cudaError_t launch_cell_d(const TreeView& tv, int64_t R, uint64_t seed, uint32_t
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const size_t sm = F64 ? cell_smem_f64(D, tv.K) : cell_smem(D, tv.K, kCellThreads);
-  cudaFuncSetAttribute(k_mc_cell<D, F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  allow_max_dyn_smem(k_mc_cell<D, F64>);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mc_cell<D, F64>, kCellThreads, sm);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1), tv.N));
@@ -531,7 +531,7 @@ cudaError_t launch_batch_th(const SetDesc* sets, int nsets, int64_t nitems, int 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const size_t sm = cell_smem(8, maxK, TH);
-  cudaFuncSetAttribute(k_mc_cell_batch<TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  allow_max_dyn_smem(k_mc_cell_batch<TH>);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mc_cell_batch<TH>, TH, sm);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1), nitems));

@@ -259,7 +259,7 @@ cudaError_t launch_tc_d(const TreeView& tv, int64_t R, uint64_t seed, uint32_t s
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const size_t sm = tc_smem(tv.K);
-  cudaFuncSetAttribute(k_mc_cell_tc<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  allow_max_dyn_smem(k_mc_cell_tc<D>);
   // The occupancy API reports one block per SM for any kernel that allocates
   // tensor memory; the resident count follows from registers, shared memory
   // and warps, and 16 blocks of 32 columns fill the 512 tensor-memory columns.

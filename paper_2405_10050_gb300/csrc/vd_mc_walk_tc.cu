@@ -428,7 +428,7 @@ cudaError_t launch_walk_d(const TreeView& tv, int64_t R, int cpt, uint64_t seed,
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const size_t sm = sizeof(WalkSmem);
-  cudaFuncSetAttribute(k_mc_walk_tc<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  allow_max_dyn_smem(k_mc_walk_tc<D>);
   // resident blocks from registers, shared memory and warps (the occupancy
   // API reports one block per SM for kernels that allocate tensor memory);
   // tensor memory holds 512 / (32 cpt) blocks

@@ -1008,7 +1008,7 @@ cudaError_t launch_ray_d(const TreeView& tv, const RaySource& rs, const RayOut& 
   const int64_t batches = rs.R_dev ? (int64_t)nsm * 64 : (nrays + r2.rpb - 1) / r2.rpb;
   cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
   auto go = [&](auto kern, size_t sm) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_max_dyn_smem(kern);
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWpb * 32, sm);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1),
@@ -1392,7 +1392,7 @@ cudaError_t launch_knn_d(TreeView* tv, int K, float r0, float rmax, int32_t* knn
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int cap = knn_cap(K);
   const size_t sm = knn_warp_bytes(cap) * kKnnWpb;
-  cudaFuncSetAttribute(k_knn_build<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  allow_max_dyn_smem(k_knn_build<D>);  // batch preparation calls this from several threads
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_knn_build<D>, kKnnWpb * 32, sm);
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)nsm * std::max(occ, 1) * 4,

@@ -175,12 +175,12 @@ constexpr int kEnt = kMcList / kFewRays;  // entries of a row on this path
 template <int NV>
 struct RowScratch {
   double acc[kEnt][NV];  // per-entry sums over the chunks so far
-  double cst[kEnt][2];   // per-entry factors
-  int32_t L[kMcList];    // ray offset (in the chunk) of each sorted position
   int32_t Ej[kMcList];   // entry << 16 | rank within the entry, per ray of the chunk
+                         // (the gathered ray indices on the one-pass-per-id path)
   int32_t col[kEnt];     // the row's hit ids, ascending
-  int32_t cnt[kEnt];     // rays of the chunk per entry
-  int32_t st[kEnt];      // first sorted position per entry
+  int16_t L[kMcList];    // ray offset (in the chunk) of each sorted position
+  int16_t cnt[kEnt];     // rays of the chunk per entry
+  int16_t st[kEnt];      // first sorted position per entry
   uint8_t Es[kMcList];   // entry of each sorted position
 };
 
@@ -209,7 +209,7 @@ __device__ void sort_chunk(const int32_t* h, int64_t k0, int C, int nnz, RowScra
     const int pre = valid ? S.cnt[e] : 0;
     __syncwarp();
     if (valid) {
-      if (lane == __ffs(peers) - 1) S.cnt[e] = pre + __popc(peers);
+      if (lane == __ffs(peers) - 1) S.cnt[e] = (int16_t)(pre + __popc(peers));
       S.Ej[j] = (e << 16) | (pre + __popc(peers & lt));
     }
     __syncwarp();
@@ -232,14 +232,14 @@ __device__ void sort_chunk(const int32_t* h, int64_t k0, int C, int nnz, RowScra
 #pragma unroll
   for (int t = 0; t < kEnt / 32; ++t) {
     const int e = lane * (kEnt / 32) + t;
-    if (e < nnz) S.st[e] = run;
+    if (e < nnz) S.st[e] = (int16_t)run;
     run += loc[t];
   }
   __syncwarp();
   for (int j = lane; j < C; j += 32) {
     const int v = S.Ej[j];
     const int e = v >> 16, p = S.st[e] + (v & 0xFFFF);
-    S.L[p] = j;
+    S.L[p] = (int16_t)j;
     S.Es[p] = (uint8_t)e;
   }
   __syncwarp();
@@ -423,7 +423,7 @@ __device__ void fill_item(const double* X, int d, int64_t i, int64_t R, uint64_t
     return;
   }
   // more entries than the sorted path holds: one pass over the row per id
-  int32_t* L = S.L;
+  int32_t* L = S.Ej;
   while (true) {
     const int32_t id = next_id(h, R, prev, first, lane);
     if (id == INT32_MAX) break;
@@ -451,11 +451,10 @@ __device__ void fill_item(const double* X, int d, int64_t i, int64_t R, uint64_t
 }
 
 template <int D>
-__global__ void __launch_bounds__(kMcWarps * 32) k_mc_fill(const double* X, int64_t N, int d, int64_t R,
-                                                           uint64_t seed, uint32_t set, const int32_t* hit,
-                                                           const double* l, const int64_t* rowptr, double cV,
-                                                           double cA, double* V, int32_t* col, double* A,
-                                                           const double* U) {
+__global__ void __launch_bounds__(kMcWarps * 32, D <= 8 ? 5 : 1)
+    k_mc_fill(const double* X, int64_t N, int d, int64_t R, uint64_t seed, uint32_t set, const int32_t* hit,
+              const double* l, const int64_t* rowptr, double cV, double cA, double* V, int32_t* col, double* A,
+              const double* U) {
   extern __shared__ __align__(16) unsigned char row_smem[];
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -620,9 +619,9 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_func(const double* X, int6
     double s = 0.0;
     int64_t k0 = 0;
     while (k0 < R) {
-      const int mm = gather_rays(h, R, id, &k0, S.L, lane);
+      const int mm = gather_rays(h, R, id, &k0, S.Ej, lane);
       for (int p = lane; p < mm; p += 32) {
-        const int32_t k = S.L[p];
+        const int32_t k = S.Ej[p];
         double u[D], r[D];
         ray_dir<D>(U, seed, set, i, k, R, d, u);
         ray_point<D>(X, d, i, li[k], u, r);
@@ -869,6 +868,9 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
   const int lane = threadIdx.x & 31;
   if (i >= N) return;
   RowScratch<D + 1>& S = reinterpret_cast<RowScratch<D + 1>*>(row_smem)[threadIdx.x >> 5];
+  // per-entry factors of the sorted path, after the block's scratch array
+  double(*cst)[2] =
+      reinterpret_cast<double(*)[2]>(row_smem + kMcWarps * sizeof(RowScratch<D + 1>)) + (threadIdx.x >> 5) * kEnt;
   const int32_t* h = hit + i * R;
   const double* li = l + i * R;
   const double gVi = gV[i];
@@ -914,7 +916,7 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
     return;
   }
   if (nnz > kEnt) {  // more entries than the sorted path holds: one pass over the row per entry
-    adj_rows_by_id<D>(X, d, i, R, seed, set, h, li, q0, nnz, col, cV, cA, gVi, gA, P, own, U, S.L, lane);
+    adj_rows_by_id<D>(X, d, i, R, seed, set, h, li, q0, nnz, col, cV, cA, gVi, gA, P, own, U, S.Ej, lane);
     return;
   }
   // per-entry factors: node entries a_k = c0 l^d - c1 l^d, b_k = c0 l^(d+1)
@@ -935,11 +937,11 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
       const double kA = gAij * cA;
       const double cwa = 2.0 * (double)d * inw, cwb = 2.0 * inw * inw * inw;
       const double cg = gVi * cV * (double)d + kA * cwa;
-      S.cst[e][0] = cg * (2.0 / ww);
-      S.cst[e][1] = kA * cwb;
+      cst[e][0] = cg * (2.0 / ww);
+      cst[e][1] = kA * cwb;
     } else {
-      S.cst[e][0] = gAij;
-      S.cst[e][1] = 0.0;
+      cst[e][0] = gAij;
+      cst[e][1] = 0.0;
     }
   }
   __syncwarp();
@@ -965,7 +967,7 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
         double v[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) v[c] = 0.0;
-        adj_contrib<D>(X, d, i, k, id, li[k], gVi, S.cst[e][0], cV, cA, seed, set, U, R, v);
+        adj_contrib<D>(X, d, i, k, id, li[k], gVi, cst[e][0], cV, cA, seed, set, U, R, v);
 #pragma unroll
         for (int c = 0; c < D; ++c)
           if (c == a) r[0] = __dadd_rn(r[0], v[c]);
@@ -981,9 +983,9 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
       double u[D];
       ray_dir<D>(U, seed, set, i, k, R, d, u);
       const double ld = __dmul_rn(ipow_d(lk, d - 1), lk);
-      const double g = __dmul_rn(S.cst[e][0], ld);
+      const double g = __dmul_rn(cst[e][0], ld);
       const double b = __dmul_rn(g, lk);
-      run[0] = __dadd_rn(reset ? 0.0 : run[0], __fma_rn(-S.cst[e][1], ld, g));
+      run[0] = __dadd_rn(reset ? 0.0 : run[0], __fma_rn(-cst[e][1], ld, g));
 #pragma unroll
       for (int c = 0; c < D; ++c)
         if (c < d) run[1 + c] = __fma_rn(b, u[c], reset ? 0.0 : run[1 + c]);
@@ -1072,7 +1074,7 @@ cudaError_t adj_rows_d(const double* X, int64_t N, int d, int64_t R, uint64_t se
                        const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, double cV,
                        double cA, const double* gV, const double* gA, double* P, double* own, const double* U,
                        cudaStream_t st) {
-  const size_t sm = kMcWarps * sizeof(RowScratch<D + 1>);
+  const size_t sm = kMcWarps * (sizeof(RowScratch<D + 1>) + kEnt * 2 * sizeof(double));
   cudaError_t e = cudaFuncSetAttribute(k_mc_adj_rows<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_mc_adj_rows<D><<<nblk(N * 32, kMcWarps * 32), kMcWarps * 32, sm, st>>>(X, N, d, R, seed, set, hit, l, rowptr,

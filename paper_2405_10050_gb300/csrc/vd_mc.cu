@@ -142,15 +142,16 @@ __global__ void k_scan64(const int64_t* in, int64_t n, int64_t* out) {
 constexpr int kMcWarps = 4;      // warps (cells in flight) per block
 constexpr int kMcList = 1024;    // matching-ray indices gathered per pass
 
-// Gathers, in ascending ray order from *k0, up to kMcList indices k with
+// Gathers, in ascending ray order from *k0, up to CAP indices k with
 // h[k] == id into L; returns their number and advances *k0.  All lanes take
 // part, so the binary64 work on the gathered rays runs on full warps.
+template <int CAP = kMcList>
 __device__ __forceinline__ int gather_rays(const int32_t* h, int64_t R, int32_t id, int64_t* k0, int32_t* L,
                                            int lane) {
   const unsigned lt = (1u << lane) - 1u;
   int m = 0;
   int64_t k = *k0;
-  while (k < R && m + 32 <= kMcList) {
+  while (k < R && m + 32 <= CAP) {
     const int64_t kk = k + lane;
     const bool match = kk < R && h[kk] == id;
     const unsigned mask = __ballot_sync(kFull, match);
@@ -164,30 +165,35 @@ __device__ __forceinline__ int gather_rays(const int32_t* h, int64_t R, int32_t 
 }
 
 // ---- rows sorted by entry (rows with many rays per hit id) ----
-// The warp sorts each chunk of up to kMcList rays of its row by entry
+// The warp sorts each chunk of up to CH rays of its row by entry
 // (stable: ascending ray order within an entry).  Each lane then sums a
 // contiguous range of the sorted node rays, one run per entry; runs that
 // cross a lane boundary are joined by a segmented scan over the lanes.  The
 // binary64 work thus runs on full warps with one pass over the row, and the
 // order of every sum depends only on the row's hits.
 constexpr int kEnt = kMcList / kFewRays;  // entries of a row on this path
+// The adjoint rows sort chunks of half the size: their per-entry sums are
+// D + 1 wide, and the smaller sort arrays let 4 blocks share an SM at d <= 4
+// (3 with chunks of kMcList).
+constexpr int kAdjList = kMcList / 2;
 
-template <int NV>
+template <int NV, int CH = kMcList>
 struct RowScratch {
+  static constexpr int kCh = CH;
   double acc[kEnt][NV];  // per-entry sums over the chunks so far
-  int32_t Ej[kMcList];   // entry << 16 | rank within the entry, per ray of the chunk
+  int32_t Ej[CH];        // entry << 16 | rank within the entry, per ray of the chunk
                          // (the gathered ray indices on the one-pass-per-id path)
   int32_t col[kEnt];     // the row's hit ids, ascending
-  int16_t L[kMcList];    // ray offset (in the chunk) of each sorted position
+  int16_t L[CH];         // ray offset (in the chunk) of each sorted position
   int16_t cnt[kEnt];     // rays of the chunk per entry
   int16_t st[kEnt];      // first sorted position per entry
-  uint8_t Es[kMcList];   // entry of each sorted position
+  uint8_t Es[CH];        // entry of each sorted position
 };
 
 // Sorts rays k0 .. k0 + C - 1 of the row (hits h, nnz <= kEnt entries in
 // S.col) by entry: S.L, S.Es, S.cnt, S.st.
-template <int NV>
-__device__ void sort_chunk(const int32_t* h, int64_t k0, int C, int nnz, RowScratch<NV>& S, int lane) {
+template <int NV, int CH>
+__device__ void sort_chunk(const int32_t* h, int64_t k0, int C, int nnz, RowScratch<NV, CH>& S, int lane) {
   for (int e = lane; e < nnz; e += 32) S.cnt[e] = 0;
   __syncwarp();
   const unsigned lt = (1u << lane) - 1u;
@@ -254,8 +260,8 @@ __device__ __forceinline__ void put_acc(double (&a)[NV], const double (&r)[NR], 
 // Sums the sorted positions F0 .. C - 1 (node rays) per entry into
 // S.acc[e][0 .. NR); step(run, reset, e, j) adds ray offset j of entry e to
 // run (restarting it when reset).  first: the chunk is the row's first.
-template <int NV, int NR, class Step>
-__device__ __forceinline__ void seg_sums(RowScratch<NV>& S, int F0, int C, bool first, int lane, Step step) {
+template <int NV, int NR, int CH, class Step>
+__device__ __forceinline__ void seg_sums(RowScratch<NV, CH>& S, int F0, int C, bool first, int lane, Step step) {
   const int M = C - F0;
   if (M <= 0) return;
   const int Sz = (M + 31) >> 5;
@@ -767,7 +773,8 @@ __device__ __forceinline__ void adj_contrib(const double* X, int d, int64_t i, i
 }
 
 // Row pass for rows with more entries than the sorted path holds: the rays
-// of each entry gathered in one pass over the row per entry.
+// of each entry gathered in one pass over the row per entry (L: room for
+// kAdjList ray indices).
 template <int D>
 __device__ void adj_rows_by_id(const double* X, int d, int64_t i, int64_t R, uint64_t seed, uint32_t set,
                                const int32_t* h, const double* li, int64_t q0, int64_t nnz, const int32_t* col,
@@ -802,7 +809,7 @@ __device__ void adj_rows_by_id(const double* X, int d, int64_t i, int64_t R, uin
       for (int c = 0; c < D; ++c) bu[c] = 0.0;
       int64_t k0 = 0;
       while (k0 < R) {
-        const int m = gather_rays(h, R, id, &k0, L, lane);
+        const int m = gather_rays<kAdjList>(h, R, id, &k0, L, lane);
         for (int p = lane; p < m; p += 32) {
           const int32_t k = L[p];
           const double lk = li[k];
@@ -823,7 +830,7 @@ __device__ void adj_rows_by_id(const double* X, int d, int64_t i, int64_t R, uin
     } else {
       int64_t k0 = 0;
       while (k0 < R) {
-        const int m = gather_rays(h, R, id, &k0, L, lane);
+        const int m = gather_rays<kAdjList>(h, R, id, &k0, L, lane);
         for (int p = lane; p < m; p += 32) {
           const int32_t k = L[p];
           adj_contrib<D>(X, d, i, k, id, li[k], gVi, gAij, cV, cA, seed, set, U, R, acc);
@@ -867,10 +874,10 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
   const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= N) return;
-  RowScratch<D + 1>& S = reinterpret_cast<RowScratch<D + 1>*>(row_smem)[threadIdx.x >> 5];
+  using Scratch = RowScratch<D + 1, kAdjList>;
+  Scratch& S = reinterpret_cast<Scratch*>(row_smem)[threadIdx.x >> 5];
   // per-entry factors of the sorted path, after the block's scratch array
-  double(*cst)[2] =
-      reinterpret_cast<double(*)[2]>(row_smem + kMcWarps * sizeof(RowScratch<D + 1>)) + (threadIdx.x >> 5) * kEnt;
+  double(*cst)[2] = reinterpret_cast<double(*)[2]>(row_smem + kMcWarps * sizeof(Scratch)) + (threadIdx.x >> 5) * kEnt;
   const int32_t* h = hit + i * R;
   const double* li = l + i * R;
   const double gVi = gV[i];
@@ -947,8 +954,8 @@ __global__ void __launch_bounds__(kMcWarps * 32) k_mc_adj_rows(const double* X, 
   __syncwarp();
   int nfe = 0;  // face entries (negative ids) come first
   for (int e0 = 0; e0 < nnz; e0 += 32) nfe += __popc(__ballot_sync(kFull, e0 + lane < nnz && S.col[e0 + lane] < 0));
-  for (int64_t k0 = 0; k0 < R; k0 += kMcList) {
-    const int C = R - k0 < kMcList ? (int)(R - k0) : kMcList;
+  for (int64_t k0 = 0; k0 < R; k0 += kAdjList) {
+    const int C = R - k0 < kAdjList ? (int)(R - k0) : kAdjList;
     const bool fst = k0 == 0;
     sort_chunk<D + 1>(h, k0, C, (int)nnz, S, lane);
     if (fst)
@@ -1074,7 +1081,7 @@ cudaError_t adj_rows_d(const double* X, int64_t N, int d, int64_t R, uint64_t se
                        const int32_t* hit, const double* l, const int64_t* rowptr, const int32_t* col, double cV,
                        double cA, const double* gV, const double* gA, double* P, double* own, const double* U,
                        cudaStream_t st) {
-  const size_t sm = kMcWarps * (sizeof(RowScratch<D + 1>) + kEnt * 2 * sizeof(double));
+  const size_t sm = kMcWarps * (sizeof(RowScratch<D + 1, kAdjList>) + kEnt * 2 * sizeof(double));
   cudaError_t e = cudaFuncSetAttribute(k_mc_adj_rows<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_mc_adj_rows<D><<<nblk(N * 32, kMcWarps * 32), kMcWarps * 32, sm, st>>>(X, N, d, R, seed, set, hit, l, rowptr,

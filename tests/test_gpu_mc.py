@@ -78,10 +78,11 @@ def test_mc_parity_tensor_walk(orc, d, N, R, mix):
 
 
 @pytest.mark.parametrize("d,N,R", [(2, 300, 32), (3, 300, 32), (4, 300, 32), (2, 200, 512), (3, 150, 256),
-                                   (9, 120, 16)])
+                                   (9, 120, 16), (4, 120, 1100)])
 def test_adjoint_parity(orc, d, N, R):
-    """Rows with many rays per hit id (R = 256, 512: rays gathered per id) and
-    rows with few (R = 16, 32: 32 rays at a time, summed per entry)."""
+    """Rows with many rays per hit id (R = 256, 512, 1100: rays sorted by entry,
+    R = 1100 in several chunks with a ragged last one) and rows with few
+    (R = 16, 32: 32 rays at a time, summed per entry)."""
     torch = need_cuda()
     X = synth.uniform(N, d, seed=50 + d)
     vor, res, ref = _parity(orc, X, R, seed=3, prec=VD_FP32)

@@ -118,9 +118,12 @@ __device__ __forceinline__ void mc_direction(uint64_t seed, uint32_t set, uint32
     box_muller32(c[0], c[1], z[4 * blk + 0], z[4 * blk + 1]);
     box_muller32(c[2], c[3], z[4 * blk + 2], z[4 * blk + 3]);
   }
-  double ss = 0.0;
+  // sum of the squares from the left (d >= 1); the first term is taken as
+  // it is, since 0 + z_0^2 = z_0^2 exactly (z_0^2 >= +0)
+  const double z0 = (double)z[0];
+  double ss = __dmul_rn(z0, z0);
 #pragma unroll
-  for (int k = 0; k < D; ++k)
+  for (int k = 1; k < D; ++k)
     if (k < d) {
       const double zk = (double)z[k];
       ss = __dadd_rn(ss, __dmul_rn(zk, zk));

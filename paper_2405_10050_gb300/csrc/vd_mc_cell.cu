@@ -125,17 +125,19 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       if (a >= d || !valid) continue;
-      double ua64 = 0.0;
       float ua = 0.f, va = 0.f;
 #pragma unroll
       for (int q = 0; q < D; ++q)
         if (q == a) {
-          ua64 = u64[q];
           ua = u32[q];
           va = g32[q];
         }
-      if (ua64 == 0.0 || ua == 0.f) continue;
-      const int s = ua64 > 0.0 ? 1 : 0;
+      // u32 is u64 rounded to nearest: it has u64's sign and is zero whenever
+      // u64 is, so both tests run in binary32 (a face with 0 < |u64| <
+      // 2^-150, so u32 == 0, lies beyond t = 2^149, far past the face of the
+      // largest |u_a|, hit at t <= sqrt(d))
+      if (ua == 0.f) continue;
+      const int s = ua > 0.f ? 1 : 0;
       const float nf = (s ? 1.f : 0.f) - va;
       const float nfs = s ? nf : -nf;
       const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;

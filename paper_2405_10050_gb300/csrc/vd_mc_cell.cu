@@ -132,10 +132,10 @@ __device__ void cell_item(const TreeView& tr, int64_t i, int64_t R, uint64_t see
           ua = u32[q];
           va = g32[q];
         }
-      // u32 is u64 rounded to nearest: it has u64's sign and is zero whenever
-      // u64 is, so both tests run in binary32 (a face with 0 < |u64| <
-      // 2^-150, so u32 == 0, lies beyond t = 2^149, far past the face of the
-      // largest |u_a|, hit at t <= sqrt(d))
+      // u32 is u64 rounded to nearest, so it has u64's sign; and a component
+      // of an MC direction is either 0 or above 5e-12 in magnitude (Box-Muller
+      // radius >= 3.4e-4, sine and cosine 0 or >= 3.7e-7, |z| <= 24), so u32
+      // is zero exactly when u64 is: both tests run in binary32
       if (ua == 0.f) continue;
       const int s = ua > 0.f ? 1 : 0;
       const float nf = (s ? 1.f : 0.f) - va;

@@ -8,7 +8,7 @@
 namespace vd {
 
 // Binary32 interval [tlo, thi] of the face t = (b - g_a) / u_a met along
-// axis a (b = 1 if u_a > 0 else 0); false if u_a == 0.
+// axis a (b = 1 if u_a > 0 else 0; face_bounds32); false if u_a == 0.
 template <int D>
 __device__ __forceinline__ bool mc_face(int a, const double (&u64)[D], const float (&u32)[D], const float (&g32)[D],
                                         int& s, float& tlo, float& thi) {
@@ -21,18 +21,8 @@ __device__ __forceinline__ bool mc_face(int a, const double (&u64)[D], const flo
       ua = u32[q];
       va = g32[q];
     }
-  if (ua64 == 0.0 || ua == 0.f) return false;
-  s = ua64 > 0.0 ? 1 : 0;
-  const float nf = (s ? 1.f : 0.f) - va;
-  const float nfs = s ? nf : -nf;
-  const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
-  const float au = fabsf(ua);
-  const float lo_n = nfs - ef, hi_n = nfs + ef;
-  tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
-                    : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
-  thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
-                    : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
-  return true;
+  s = face_bounds32(ua, ua64, va, tlo, thi);
+  return s >= 0;
 }
 
 // Box faces of a ray from g as candidates: returns an upper bound T of the

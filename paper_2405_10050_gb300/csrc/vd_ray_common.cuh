@@ -7,6 +7,33 @@
 
 namespace vd {
 
+// Binary32 bounds [tlo, thi] of t = (b - v_a) / u_a, where the ray meets the
+// box face of axis a on the side it moves to (b = 1 if u_a > 0, else 0), from
+// ua = u_a rounded to binary32 and va = v_a rounded to binary32.  Returns the
+// side (1: b = 1, 0: b = 0), or -1 if u_a = 0 (the ray never meets the face).
+// ua has u_a's sign; it is 0 for 0 < |u_a| < 2^-150 too, and there binary32
+// bounds nothing (the face may still be near if v_a is within ~|u_a| of b):
+// the face then gets (-inf, inf) and so is always rechecked in binary64.
+__device__ __forceinline__ int face_bounds32(float ua, double ua64, float va, float& tlo, float& thi) {
+  if (ua == 0.f) {
+    if (ua64 == 0.0) return -1;
+    tlo = -INFINITY;
+    thi = INFINITY;
+    return ua64 > 0.0 ? 1 : 0;
+  }
+  const int s = ua > 0.f ? 1 : 0;
+  const float nf = (s ? 1.f : 0.f) - va;
+  const float nfs = s ? nf : -nf;  // t = nfs / |u_a|
+  const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
+  const float au = fabsf(ua);
+  const float lo_n = nfs - ef, hi_n = nfs + ef;
+  tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
+                    : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
+  thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
+                    : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
+  return s;
+}
+
 // Conservative binary32 ball: every point within distance rho of the exact
 // centre c = v + T u satisfies |y - c32|^2 <= lim2.
 template <int D>

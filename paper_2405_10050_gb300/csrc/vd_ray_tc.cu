@@ -158,7 +158,8 @@ __device__ __forceinline__ int fkey(float x) {
 __device__ __forceinline__ float fval(int k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
 
 // Binary32 interval [tlo, thi] of the box face of axis a the ray leaves
-// through, t = (b - v_a) / u_a; false if u_a = 0 or the face is in eta.
+// through, t = (b - v_a) / u_a (face_bounds32); false if u_a = 0 or the face
+// is in eta.
 template <int D>
 __device__ __forceinline__ bool face_interval(const double (&v)[D], const double (&u)[D], const float (&u32)[D],
                                               const int32_t (&eta)[D + 1], int m, int a, int32_t& fid, float& tlo,
@@ -172,21 +173,11 @@ __device__ __forceinline__ bool face_interval(const double (&v)[D], const double
       ua64 = u[k];
       va64 = v[k];
     }
-  if (ua64 == 0.0 || ua == 0.f) return false;
-  const int sd = ua64 > 0.0 ? 1 : 0;
+  const int sd = face_bounds32(ua, ua64, __double2float_rn(va64), tlo, thi);
+  if (sd < 0) return false;
   fid = face_id(a, sd);
   for (int q = 0; q < m; ++q)
     if (eta[q] == fid) return false;
-  const float va = __double2float_rn(va64);
-  const float nf = (sd ? 1.f : 0.f) - va;
-  const float nfs = sd ? nf : -nf;
-  const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
-  const float au = fabsf(ua);
-  const float lo_n = nfs - ef, hi_n = nfs + ef;
-  tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
-                    : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
-  thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
-                    : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
   return true;
 }
 

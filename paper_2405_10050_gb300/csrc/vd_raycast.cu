@@ -237,24 +237,13 @@ __global__ void __launch_bounds__(kWpb * 32) k_ray_mixed(TreeView tr, RaySource 
       int nc = 0;
       if (rs.box) {
         for (int a = 0; a < d; ++a) {
-          const float ua = S.u[lane][a];
-          if (u[a] == 0.0 || ua == 0.f) continue;
-          const int s = u[a] > 0.0 ? 1 : 0;
+          float tlo, thi;
+          const int s = face_bounds32(S.u[lane][a], u[a], __double2float_rn(v[a]), tlo, thi);
+          if (s < 0) continue;
           const int32_t fid = face_id(a, s);
           bool ex = false;
           for (int q = 0; q < m; ++q) ex |= (eta[q] == fid);
           if (ex) continue;
-          // t = (b - v_a) / u_a = nfs / |u_a| with nfs = (b - v_a) sign(u_a)
-          const float va = __double2float_rn(v[a]);
-          const float nf = (s ? 1.f : 0.f) - va;
-          const float nfs = s ? nf : -nf;
-          const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
-          const float au = fabsf(ua);
-          const float lo_n = nfs - ef, hi_n = nfs + ef;
-          const float tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
-                                        : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
-          const float thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
-                                        : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
           T = fminf(T, thi);
           if (nc < kCmax) {
             S.cid[lane][nc] = fid;
@@ -561,22 +550,13 @@ __global__ void __launch_bounds__(kThrRays, (D <= 6 ? 6 : D <= 8 ? 4 : 3))
             ua64 = u[k];
             va64 = v[k];
           }
-        if (ua64 == 0.0 || ua == 0.f) continue;
-        const int sd = ua64 > 0.0 ? 1 : 0;
+        float tlo, thi;
+        const int sd = face_bounds32(ua, ua64, __double2float_rn(va64), tlo, thi);
+        if (sd < 0) continue;
         const int32_t fid = face_id(a, sd);
         bool ex = false;
         for (int q = 0; q < m; ++q) ex |= (eta[q] == fid);
         if (ex) continue;
-        const float va = __double2float_rn(va64);
-        const float nf = (sd ? 1.f : 0.f) - va;
-        const float nfs = sd ? nf : -nf;
-        const float ef = 1.01f * kU32 * (fabsf(va) + fabsf(nf)) + 1e-38f;
-        const float au = fabsf(ua);
-        const float lo_n = nfs - ef, hi_n = nfs + ef;
-        const float tlo = lo_n >= 0.f ? lo_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32)
-                                      : lo_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32);
-        const float thi = hi_n >= 0.f ? hi_n / (au * (1.f - 2.f * kU32)) * (1.f + 4.f * kU32)
-                                      : hi_n / (au * (1.f + 2.f * kU32)) * (1.f - 4.f * kU32);
         T = fminf(T, thi);
         if (nc < kCmax) {
           cid[nc] = fid;

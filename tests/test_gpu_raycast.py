@@ -109,6 +109,28 @@ def test_edge_cases(orc, prec):
     assert np.any(h1 == NO_ID) and np.all(np.isinf(t1[h1 == NO_ID]))
 
 
+@pytest.mark.parametrize("prec", [None, VD_FP64, VD_FP32, VD_TC16])
+def test_face_behind_a_tiny_direction_component(orc, prec):
+    """A node 1e-60 from the face x_1 = 0, rays from it with u_1 = -1e-50:
+    u_1 rounds to 0 in binary32, which then bounds nothing, yet the face is
+    hit first, at t = 1e-10 (the binary64 recheck has to see it); with
+    u_1 = +1e-50 the far face, at t ~ 1e50, must not win.  With candidate
+    lists, with the tree walk alone and with a short list."""
+    X = synth.uniform(200, 3, seed=11).copy()
+    X[0] = [0.5, 1e-60, 0.5]
+    th = np.linspace(0.1, 6.0, 8)
+    U = np.stack([np.cos(th), np.full(8, -1e-50), np.sin(th)], 1)
+    U = np.vstack([U, U * np.array([1.0, -1.0, 1.0])])
+    O = np.repeat(X[:1], 16, 0)
+    E = np.zeros((16, 1), np.int32)
+    h0, t0 = orc.raycast(X, O, U, E)
+    assert np.all(h0[:8] == -3) and np.allclose(t0[:8], 1e-10, rtol=1e-15, atol=0)  # face x_1 = 0
+    assert np.all(h0[8:] >= 0)
+    for knn in (0, -1, 4):
+        h1, t1, _, _ = _run(X, O, U, E, prec, knn_k=knn)
+        assert np.array_equal(h0, h1) and np.array_equal(t0, t1), f"knn_k={knn}"
+
+
 def test_host_pointer_path_matches_device(orc):
     """vd_raycast with host (numpy) buffers equals the device-pointer call."""
     need_cuda()

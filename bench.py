@@ -53,8 +53,12 @@ NEIGHBOURS_D5 = 95  # neighbours per cell in d = 5 (the paper's table of vertice
 # binary64 follow-ups: 8964.0 MB over the three traversals of `python bench.py --steps 1 --warmup 1 --no-fp64
 # --no-binary32 --no-cpu --no-mc --no-highd --no-hmc --no-walk --no-small --no-batch --no-cells`, captured with
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none -k
-# "regex:k_ray_list_tc|k_grp_|k_ray_mixed|k_ray_fp64"` (list scan at 8 blocks per SM, lists of 1024 nodes)
+# "regex:k_ray_list_tc|k_grp_|k_ray_mixed|k_ray_fp64"` (list scan at 8 blocks per SM, lists of 1024 nodes).
+# k_grp_scatter and k_grp_finish changed after that capture (the box-face zero and sign tests moved to the
+# binary32 copy of u_a: arithmetic only, no load or store added or removed), so the line reports it as
+# `traffic_last_capture` and `traffic` stays null until the counters are taken again.
 RAYCAST_DRAM_BYTES_PER_STEP = 2988.0e6
+RAYCAST_TRAFFIC_CURRENT = False
 
 
 def _peaks():
@@ -415,10 +419,14 @@ def run_ours(args):
     achieved = rays * flops_per_ray / (rc_ms / 1000.0) / 1e12 if rc_ms > 0 else None
     # DRAM bytes of the RayCast per traversal of this workload (one ncu capture of the current kernels, above);
     # the ray I/O alone is ~573 MB
-    traffic = RAYCAST_DRAM_BYTES_PER_STEP if (args.N, args.d, args.knn_k) == (20000, 5, 0) else None
+    captured = RAYCAST_DRAM_BYTES_PER_STEP if (args.N, args.d, args.knn_k) == (20000, 5, 0) else None
+    traffic = captured if RAYCAST_TRAFFIC_CURRENT else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": (achieved / peak_tflops) if achieved else None, "traffic": traffic,
                 "traffic_unit": "bytes per step (every RayCast launch of one traversal)",
+                "traffic_last_capture": captured,
+                "traffic_last_capture_note": None if RAYCAST_TRAFFIC_CURRENT else
+                "k_grp_scatter and k_grp_finish changed since (arithmetic of the face tests only)",
                 "kernel": "k_ray_list_tc<5> with its prep/finish kernels and the tree-walk follow-up (tcgen05 fp16 screening of rays grouped by reference node, binary32 rescreen, binary64 recheck)",
                 "peak_source": f"FP32 lanes x 2 x sm_max_mhz ({src} peaks file)",
                 "algorithmic_flops_per_ray": flops_per_ray, "raycast_ms_per_step": rc_ms / args.steps}

@@ -417,8 +417,8 @@ def run_ours(args):
     pairs = NEIGHBOURS_D5 + 2 * args.d
     flops_per_ray = pairs * (2 * args.d + 6)
     achieved = rays * flops_per_ray / (rc_ms / 1000.0) / 1e12 if rc_ms > 0 else None
-    # DRAM bytes of the RayCast per traversal of this workload (one ncu capture of the current kernels, above);
-    # the ray I/O alone is ~573 MB
+    # DRAM bytes of the RayCast per traversal of this workload (one ncu capture, above; `traffic` is null while a
+    # kernel of the path has changed since); the ray I/O alone is ~573 MB
     captured = RAYCAST_DRAM_BYTES_PER_STEP if (args.N, args.d, args.knn_k) == (20000, 5, 0) else None
     traffic = captured if RAYCAST_TRAFFIC_CURRENT else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",

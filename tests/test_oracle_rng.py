@@ -70,6 +70,28 @@ def test_sincos_all_24bit_angles(orc):
     assert s[1 << 22] == 1.0 and c[1 << 23] == -1.0 and s[3 << 22] == -1.0
 
 
+def test_direction_components_are_zero_or_above_5e_12(orc):
+    """Every component of an MC direction (d <= 16) is 0 or above 5e-12 in
+    magnitude, over every input the draw can take: the binary32 radius
+    sqrt(-2 ln U) lies in [3.4e-4, 5.77] over all 2^23 values of U, the
+    cosine and sine of all 2^24 angles are 0 or at least 3.7e-7 in
+    magnitude, and |z| <= 4 * 5.77 at d = 16.  So a component rounds to 0 in
+    binary32 only when it is 0 (the MC kernels' binary32 face tests rely on
+    this)."""
+    U = (np.arange(1 << 23, dtype=np.uint64) * 2 + 1).astype(np.float32) * np.float32(2.0**-24)
+    L = orc.log32(U)
+    assert np.all(L < 0)
+    r = np.sqrt(np.float32(-2.0) * L)  # binary32, as in the draw
+    assert r.min() >= 3.4e-4 and r.max() <= 5.77
+    c, s = orc.sincos2pi24(np.arange(1 << 24, dtype=np.uint32))
+    for v in (c, s):
+        assert np.abs(v[v != 0]).min() >= 3.7e-7
+    z_min = 3.4e-4 * 3.7e-7 * (1 - 2.0**-23)  # the product rounded in binary32
+    assert z_min / (4 * 5.77 * (1 + 2.0**-50)) > 5e-12
+    u = orc.mc_directions(seed=7, set_id=0, N=64, R=1024, d=16)
+    assert np.abs(u[u != 0]).min() > 5e-12
+
+
 def test_gaussian_draw_is_standard_normal(orc):
     z = orc.mc_gaussians32(seed=11, set_id=0, N=2000, R=64, d=4).reshape(-1).astype(np.float64)
     n = z.size

@@ -11,7 +11,7 @@ namespace vd {
 // box face of axis a on the side it moves to (b = 1 if u_a > 0, else 0), from
 // ua = u_a rounded to binary32 and va = v_a rounded to binary32.  Returns the
 // side (1: b = 1, 0: b = 0), or -1 if u_a = 0 (the ray never meets the face).
-// ua has u_a's sign; it is 0 for 0 < |u_a| < 2^-150 too, and there binary32
+// ua has u_a's sign; it is 0 for 0 < |u_a| <= 2^-150 too, and there binary32
 // bounds nothing (the face may still be near if v_a is within ~|u_a| of b):
 // the face then gets (-inf, inf) and so is always rechecked in binary64.
 __device__ __forceinline__ int face_bounds32(float ua, double ua64, float va, float& tlo, float& thi) {
